@@ -1,0 +1,370 @@
+"""Benchmark: space-time DoF/s of the space-time Petrov-Galerkin heat solve on GB300.
+
+One step = one rational Krylov Galerkin solve (st_solve: rank compression,
+shifted solves, block Gram-Schmidt, projection, projected Sylvester solve,
+residual check, low-rank output) of the named workload, with the load factors
+resident in HBM.  The default workload is the 2D heat problem on a 255 x 255
+Q1 grid with 256 time intervals and the manufactured load (plain FP64 solve),
+compared on the same GPU with the mixed-precision solve and with Crank-Nicolson
+time stepping.  Prints one JSON line (rank 0).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                       [--impl ours|reference]
+Under torchrun every rank solves its own copy of the workload (independent
+instances, no collective on the data path: weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "space-time DoF/s at rel-res 1e-8, mixed vs plain FP64 and CN; p50/p99 latency"
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (CUDA cores and DMMA alike)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return dict(hbm_gbs=float(d["hbm_gbs"]), src="measured")
+    return dict(hbm_gbs=6800.0, src="fallback")
+
+
+class ClockSampler:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(st, prob, wl, torch):
+    if wl["rhs"] == "manufactured":
+        return prob.rhs_manufactured()
+    import workloads
+    F1, F2 = workloads.gaussian_factors(prob.n_h, prob.n_t, wl["p"], wl["seed"])
+    f1 = st.empty_colmajor(prob.n_h, wl["p"])
+    f2 = st.empty_colmajor(prob.n_t, wl["p"])
+    f1.copy_(torch.from_numpy(F1))
+    f2.copy_(torch.from_numpy(F2))
+    return f1, f2
+
+
+def roofline_of(prof, hbm_gbs):
+    """Dominant kernel of a profiled region and its roofline position."""
+    if not prof:
+        return None
+    tag, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    secs = d["ms"] * 1e-3
+    alu = FP64_PEAK_TFLOPS if tag.endswith("64") else FP32_PEAK_TFLOPS
+    t_hbm = d["bytes"] / (hbm_gbs * 1e9)
+    t_alu = d["flops"] / (alu * 1e12)
+    if t_hbm >= t_alu:
+        ach = d["bytes"] / secs / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs}
+    else:
+        ach = d["flops"] / secs / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": alu, "unit": "TFLOP/s", "frac": ach / alu,
+               "alu": "fp64" if tag.endswith("64") else "fp32"}
+    out.update(kernel=tag, launches=d["launches"], ms_per_launch=d["ms"] / max(1, d["launches"]),
+               bytes_per_launch=d["bytes"] / max(1, d["launches"]),
+               flops_per_launch=d["flops"] / max(1, d["launches"]), share=None, traffic=None)
+    tot = sum(v["ms"] for v in prof.values())
+    out["share"] = d["ms"] / tot if tot else None
+    traffic_file = ROOT / "profiles" / "traffic.json"
+    if traffic_file.exists():
+        tr = json.loads(traffic_file.read_text()).get(tag)
+        if tr and tr.get("valid_for") == out["kernel"]:
+            out["traffic"] = tr.get("bytes_per_launch")
+    return out
+
+
+def run_reference(args, wl, world, rank):
+    """The oracle (CPU, FP64) as it stands on a bounded sample of the workload."""
+    if rank != 0:
+        return None
+    from oracle import fem, kron, rhs as orhs, rksm as orksm, timefe
+    import workloads
+    dim, n, nt = wl["dim"], wl["n"], wl["n_t"]
+    M, A = fem.tensor_operators(dim, n, kappa=wl.get("kappa", 1.0))
+    D, C = timefe.time_matrices(nt, wl["T"])
+    if wl["rhs"] == "manufactured":
+        F1, F2 = orhs.manufactured_loads(dim, n, nt, wl["T"])
+    else:
+        F1, F2 = workloads.gaussian_factors(M.shape[0], nt, wl["p"], wl["seed"])
+    times = []
+    sample = ""
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        if M.shape[0] <= 70000:
+            out = orksm.rksm(M, A, D, C, F1, F2, tol=1e-8, maxit=60)
+            sample = f"full oracle RKSM solve ({M.shape[0]} x {nt})"
+            units = M.shape[0] * nt
+        else:
+            cols = 2
+            kron.forward_substitution(M, A, D, C, (F1 @ F2[:cols].T))
+            sample = f"{cols} forward-substitution time steps of the {M.shape[0]} x {nt} system"
+            units = M.shape[0] * cols
+        el = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(el)
+    ms = 1e3 * statistics.mean(times)
+    value = units / (ms * 1e-3)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "n_h": int(M.shape[0]), "n_t": nt},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def cpu_baseline(wl):
+    """Time the oracle on a bounded sample (about 10-30 s of CPU work)."""
+    import argparse as _a
+    a = _a.Namespace(warmup=0, steps=1)
+    line = run_reference(a, wl, 1, 0)
+    return line["cpu_baseline"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="heat2d")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    import workloads
+    wl = dict(workloads.WORKLOADS[args.workload])
+    wl["name"] = args.workload
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        line = run_reference(args, wl, world, rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    import paper_1912_10082_gb300 as st
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    stream = torch.cuda.Stream()
+    prec = st.ST_MIXED if wl["dim"] == 3 else st.ST_FP64
+    pk = peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def solver(precision):
+        return st.Problem(wl["dim"], wl["n"], wl["n_t"], wl["T"], kappa=wl.get("kappa", 1.0),
+                          precision=precision, tol=1e-8, maxit=400, stream=stream)
+
+    prob = solver(prec)
+    with torch.cuda.stream(stream):
+        f1, f2 = make_inputs(st, prob, wl, torch)
+    stream.synchronize()
+    units = prob.n_h * prob.n_t
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        lc0 = st.launch_count()
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        launches = st.launch_count() - lc0
+        if pg:
+            pg.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, launches
+
+    last = {}
+
+    def step():
+        V, Y, stats, status = prob.solve(f1, f2)
+        last["stats"] = stats
+        last["status"] = status
+
+    with ClockSampler(local) as clk:
+        ms, launches = timed(step, args.steps, args.warmup)
+    tot_ms = sum(ms)
+    if pg:
+        t = torch.tensor([tot_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * units * args.steps / (tot_ms * 1e-3)
+
+    # certification of the last solution, outside the timed region (FP64, independent formula)
+    V, Y, stats, status = prob.solve(f1, f2)
+    relres_cert = prob.residual_lowrank(V, Y, f1, f2)
+
+    # per-kernel profile of the same steps (separate pass right after the timed region)
+    st.profile_begin()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = st.profile_end()
+    roof = roofline_of(prof, pk["hbm_gbs"])
+    if roof:
+        roof["peak_source"] = pk["src"] if roof["unit"] == "GB/s" else "derived"
+
+    # e2e through the public API with host buffers: inputs H2D inside, result (V, Y) D2H inside
+    h1p = torch.empty((f1.shape[1], f1.shape[0]), dtype=torch.float64).pin_memory().t()
+    h1p.copy_(f1)
+    h2p = torch.empty((f2.shape[1], f2.shape[0]), dtype=torch.float64).pin_memory().t()
+    h2p.copy_(f2)
+    e2e_t = []
+    d2h = 0
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        V, Y, stats_e, _ = prob.solve(h1p, h2p)
+        Vh = V.cpu()
+        Yh = Y.cpu()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if it >= args.warmup:
+            e2e_t.append(el)
+        d2h = Vh.numel() * 8 + Yh.numel() * 8
+    e2e = {"value": world * units / statistics.mean(e2e_t), "unit": "DoF/s",
+           "h2d_bytes_per_step": int(h1p.numel() + h2p.numel()) * 8, "d2h_bytes_per_step": int(d2h)}
+
+    # comparators on the same GPU: the other precision and Crank-Nicolson
+    comps = {}
+    other = st.ST_FP64 if prec == st.ST_MIXED else st.ST_MIXED
+    prob2 = solver(other)
+
+    def step2():
+        prob2.solve(f1, f2)
+    ms2, _ = timed(step2, max(3, args.steps // 2), 3)
+    comps["mixed_rksm" if other == st.ST_MIXED else "fp64_rksm"] = {
+        "value": units / (statistics.mean(ms2) * 1e-3), "ms_per_step": statistics.mean(ms2)}
+    comps["fp64_rksm" if prec == st.ST_FP64 else "mixed_rksm"] = {"value": value / world, "ms_per_step": ms_per_step}
+    U = st.empty_colmajor(prob.n_h, prob.n_t)
+
+    def step_cn():
+        prob.timestep_cn(f1, f2, U)
+    ms3, _ = timed(step_cn, 3, 3)
+    comps["cn_fp64"] = {"value": units / (statistics.mean(ms3) * 1e-3), "ms_per_step": statistics.mean(ms3)}
+    prob2.close()
+
+    if rank != 0:
+        return 0
+    cb = None
+    if not args.no_cpu_baseline and world >= 1:
+        cb = cpu_baseline(wl)
+    s = last["stats"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == st.ST_FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wl['dim']}D heat, Q1 {wl['n']}^{wl['dim']} interior grid, "
+                               f"n_t={wl['n_t']}, T={wl['T']}, {wl['rhs']} load",
+                   "n_h": prob.n_h, "n_t": prob.n_t, "precision": "fp64" if prec == st.ST_FP64 else "mixed",
+                   "tol": 1e-8, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas{world}"},
+        "solver": {"status": last["status"], "iterations": s["iterations"], "basis_cols": s["basis_cols"],
+                   "rank": s["rank"], "relres": s["relres"], "relres_certified": relres_cert,
+                   "mu_mem": s["mu_mem"]},
+        "roofline": roof, "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()},
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+        "comparators": comps,
+    }
+    print(json.dumps(line), flush=True)
+    prob.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * st.h -- C ABI of the GB300 space-time Petrov-Galerkin heat solver.
+ *
+ * The solver computes the discrete solution of the heat equation
+ * u_t + A u = f, u(0) = 0, discretised in space and time together with the
+ * Petrov-Galerkin pair "hat functions in time (x) X_h" (trial) and
+ * "piecewise constants in time (x) X_h" (test) of Henning, Palitta, Simoncini
+ * and Urban, "Matrix oriented reduction of space-time Petrov-Galerkin
+ * variational problems" (arXiv:1912.10082), Section 3.  The linear system
+ * B u = f with B = D_t (x) M + C_t (x) A (Section 3, eq. par1) is never
+ * assembled; it is handled in its matrix form (Section 4)
+ *
+ *     M U D_t^T + A U C_t^T = F,   F = F1 F2^T                      (1)
+ *
+ * U is N_h x N_t, column k holding the coefficients of the trial function
+ * sigma^k (nodal values at t^k = k dt).  D_t = bidiag(1 | -1) and
+ * C_t = (dt/2) bidiag(1 | 1) are lower bidiagonal (rows: test functions).
+ * M and A are the spatial mass and operator matrices on a shared CSR pattern.
+ *
+ * Conventions
+ *  - Every call returns an int status: ST_OK (0) or a negative ST_E* code.
+ *    No C++ exception crosses this boundary.
+ *  - Dense matrices are column-major with an explicit leading dimension.
+ *  - "device" pointers are CUDA global memory of the current device; a few
+ *    inputs also accept host memory, as documented per argument (the library
+ *    tells them apart with cudaPointerGetAttributes).
+ *  - A problem handle is not thread-safe; distinct handles are independent.
+ *    Work is issued on the handle's stream.  Calls that return results through
+ *    host memory synchronise that stream before returning.
+ *  - Spatial nodes are the interior nodes of a box, numbered lexicographically
+ *    with x fastest (homogeneous Dirichlet data, Section 2).
+ */
+#ifndef ST_H_
+#define ST_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ST_ABI_VERSION 1
+
+/* status codes */
+#define ST_OK          0
+#define ST_EINVAL     -1   /* invalid argument (sizes, pointers, descriptor) */
+#define ST_ENOMEM     -2   /* a device or host allocation failed */
+#define ST_ENOTCONV   -3   /* maxit or max_basis reached above tol; best iterate returned */
+#define ST_EBREAKDOWN -4   /* the Krylov block lost rank and nothing was left to add */
+#define ST_ECUDA      -5   /* a CUDA runtime call or kernel launch failed */
+#define ST_ETIMEOUT   -6   /* a bounded device-side wait gave up */
+#define ST_ENOTSUP    -7   /* the requested operation needs a feature this problem lacks */
+
+/* precision modes of st_solve */
+#define ST_FP64  0   /* every N_h-sized step in FP64 */
+#define ST_MIXED 1   /* FP32 fast-diagonalisation solves refined to FP64 accuracy (Section 4 solve, see st_solve) */
+
+/* element types of st_apply */
+#define ST_F64 0
+#define ST_F32 1
+
+/* spatial operators (Section 2: A elliptic, a coercive) */
+#define ST_HEAT     0   /* a(u,v) = kappa (grad u, grad v) */
+#define ST_CONVDIFF 1   /* a(u,v) = eps (grad u, grad v) + (beta . grad u, v) */
+
+typedef struct st_problem st_problem;
+
+/* Problem description, read by st_setup only.  Zero-initialise, then set. */
+typedef struct st_desc {
+    int dim;            /* 1, 2 or 3: uniform box grid, P1 (dim 1) / Q1 (dim 2, 3) elements;
+                           0: user-supplied CSR matrices (fields n_h ... a_vals) */
+    int n[3];           /* interior nodes per direction (x, y, z); n[d] >= 1 */
+    double length[3];   /* box edge lengths; <= 0 means 1.0 */
+    int op;             /* ST_HEAT or ST_CONVDIFF */
+    double kappa;       /* ST_HEAT diffusion coefficient (> 0; 0 means 1.0) */
+    double eps;         /* ST_CONVDIFF diffusion (> 0) */
+    double beta[3];     /* ST_CONVDIFF velocity */
+    int n_t;            /* number of uniform time intervals N_t (>= 1) */
+    double T;           /* final time (> 0); dt = T / N_t (Section 3) */
+    /* dim == 0 only: host arrays copied by st_setup; shared sorted CSR pattern */
+    int n_h;            /* number of spatial unknowns */
+    int nnz;
+    const int* row_ptr; /* n_h + 1 entries, row_ptr[0] == 0 */
+    const int* col_idx; /* nnz entries, ascending within each row */
+    const double* m_vals; /* mass matrix values M */
+    const double* a_vals; /* operator matrix values A */
+    /* solver controls */
+    int precision;      /* ST_FP64 or ST_MIXED */
+    double tol;         /* target relative residual ||F - op(U)||_F / ||F||_F; <= 0 means 1e-8 (Section 5) */
+    int maxit;          /* maximum rational Krylov iterations; <= 0 means 400 */
+    int max_basis;      /* maximum basis columns; <= 0 means 2048 */
+    void* stream;       /* cudaStream_t to issue work on; NULL = default stream */
+} st_desc;
+
+/* Low-rank solution U ~= V Y returned by st_solve. */
+typedef struct st_solution {
+    int n_h, n_t, k;      /* V is n_h x k, Y is k x n_t */
+    const double* V;      /* device, column-major, ld = n_h; owned by the handle,
+                             valid until the next st_solve or st_destroy */
+    const double* Y;      /* device, column-major, ld = k; owned by the handle */
+    double* U_dense;      /* in: optional caller-owned device buffer for U = V Y (NULL: skip) */
+    int ldu;              /* in: leading dimension of U_dense (>= n_h) */
+} st_solution;
+
+/* Statistics of one st_solve. */
+typedef struct st_stats {
+    int iterations;       /* rational Krylov iterations (shifted solves) */
+    int basis_cols;       /* k = columns of V; memory is k * (N_h + N_t) numbers (Section 5, Table 1 mu_mem) */
+    int rank;             /* numerical rank of U: #{singular values of Y > 1e-8 * largest} */
+    int p;                /* rank of F after compression */
+    int converged;        /* 1 if relres <= tol */
+    int residual_checks;  /* how many times the projected equation was solved */
+    int mu_mem;           /* basis columns allocated, including the block computed at the last
+                             iteration (Section 5, Table 1: mu_mem = Its + 1 for a rank-1 load) */
+    double relres;        /* final relative residual, FP64 */
+    double ms_total;      /* wall time of the call (host clock) */
+    double ms_phase[8];   /* 0 compress, 1 shifted solves, 2 orthogonalisation, 3 projection,
+                             4 projected solve, 5 residual, 6 output, 7 other */
+    double shift_min, shift_max;  /* extremes of the shifts s used, as (A + s M)^{-1} */
+} st_stats;
+
+/* st_setup -- build a problem handle (Section 3: spatial matrices M_h, A_h;
+ * time grid t^k = k dt).  For dim 1..3 the library assembles the P1/Q1 mass
+ * and operator matrices on the device (Kronecker products of 1D
+ * M = h/6 tridiag(1,4,1), K = 1/h tridiag(-1,2,-1), G = 1/2 tridiag(-1,0,1))
+ * and tables for the fast-diagonalisation shifted solve.  For dim == 0 the
+ * CSR arrays are copied from host memory (st_solve and st_timestep_cn then
+ * return ST_ENOTSUP: they need the tensor-grid solver).
+ * Ownership: the handle owns every device buffer it allocates until
+ * st_destroy.  Errors: ST_EINVAL (bad sizes or fields, nnz > INT_MAX),
+ * ST_ENOMEM, ST_ECUDA.  *out is NULL on error. */
+int st_setup(const st_desc* d, st_problem** out);
+
+/* st_destroy -- free the handle and everything it owns.  NULL is accepted. */
+int st_destroy(st_problem* p);
+
+/* st_problem_info -- sizes of a problem (host outputs, any may be NULL). */
+int st_problem_info(const st_problem* p, int* n_h, int* n_t, int* nnz, double* dt);
+
+/* st_get_csr -- copy the assembled matrices to host arrays (sizes from
+ * st_problem_info): row_ptr (n_h+1), col_idx (nnz), m_vals, a_vals (nnz).
+ * Any pointer may be NULL.  Synchronises the stream. */
+int st_get_csr(st_problem* p, int* row_ptr, int* col_idx, double* m_vals, double* a_vals);
+
+/* st_apply -- Y = M U D_t^T + A U C_t^T (Section 4, the vec identity
+ * (D (x) A) vec(X) = vec(A X D^T) applied to B = D_t (x) M + C_t (x) A).
+ * Column l of Y is P u_l - N u_{l-1} with P = M + dt/2 A, N = M - dt/2 A,
+ * u_0 = 0.  U and Y: device, n_h x n_t, dtype ST_F64 (double) or ST_F32
+ * (float), ldu, ldy >= n_h; U and Y must not overlap.  Asynchronous. */
+int st_apply(st_problem* p, int dtype, const void* U, int ldu, void* Y, int ldy);
+
+/* st_rhs_manufactured -- load factors of the manufactured solution
+ * u = sin(pi t) prod_d sin(pi x_d / L_d) with exact integrals (Section 3,
+ * eq. par2): F1 = [g, g] (n_h x 2), F2 = [h_a, h_b] (n_t x 2) with
+ * g_j = (prod_d sin(pi x_d/L_d), phi_j), h_a[l] = (pi cos(pi t), tau^l),
+ * h_b[l] = (kappa sum_d (pi/L_d)^2 sin(pi t), tau^l).  Heat problems on boxes
+ * only (ST_ENOTSUP otherwise).  Outputs: device arrays.  Asynchronous. */
+int st_rhs_manufactured(st_problem* p, double* F1, int ldf1, double* F2, int ldf2);
+
+/* st_shift_solve -- W = (A + s M)^{-1} M X for p columns (Section 4: the
+ * resolvent (A_h - sigma M_h)^{-1} M_h with sigma = -s < 0), by fast
+ * diagonalisation on the tensor grid.  precision ST_FP64 computes the
+ * transforms in FP64; ST_MIXED computes them in FP32 and refines once with an
+ * FP64 residual.  X, W: device double, n_h x p, ld >= n_h; may alias.
+ * s > -lambda_min.  Asynchronous. */
+int st_shift_solve(st_problem* p, double s, const double* X, int ldx, int ncols,
+                   double* W, int ldw, int precision);
+
+/* st_solve -- rational Krylov Galerkin projection (RKSM) for (1) (Section 4):
+ * compress F to a full-column-rank F1 (QR + SVD), grow an orthonormal basis
+ * V of the rational Krylov space of the pencil (A, M) started from M^{-1} F1
+ * with adaptive shifts, impose V^T R = 0, solve the projected equation
+ * (V^T M V) Y D_t^T + (V^T A V) Y C_t^T = (V^T F1) F2^T by the time
+ * recurrence of the triangular time pencil, and stop when the relative
+ * residual (Frobenius, FP64, evaluated from low-rank factors) is <= tol.
+ * F1: n_h x p (ld ldf1), F2: n_t x p (ld ldf2), double, host OR device.
+ * 1 <= p <= 16.  Output in *sol (V, Y owned by the handle; U_dense filled if
+ * given).  stats may be NULL.  Synchronises.  Returns ST_OK, ST_ENOTCONV
+ * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL. */
+int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
+             st_solution* sol, st_stats* stats);
+
+/* st_residual -- relres = ||F - M U D_t^T - A U C_t^T||_F / ||F1 F2^T||_F in
+ * FP64 for a dense U (device double, ld >= n_h) (Section 5 stopping
+ * quantity).  F1, F2 host or device.  relres: host.  Synchronises. */
+int st_residual(st_problem* p, const double* U, int ldu, const double* F1, int ldf1,
+                const double* F2, int ldf2, int ncols, double* relres);
+
+/* st_residual_lowrank -- the same for U = V Y (V device n_h x k, Y device
+ * k x n_t), from the factors [F1, M V, A V] and [F2, -D_t Y^T, -C_t Y^T]
+ * without forming U or the Kronecker product (Section 4).  Synchronises. */
+int st_residual_lowrank(st_problem* p, const double* V, int ldv, const double* Y, int ldy, int k,
+                        const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
+                        double* relres);
+
+/* st_timestep_cn -- Crank-Nicolson time stepping on the same load matrix
+ * (Section 3: the scheme equals CN; Section 5 comparison):
+ * (M + dt/2 A) u_l = F[:, l] + (M - dt/2 A) u_{l-1}, l = 1..N_t, one
+ * fast-diagonalisation spatial solve per step, FP64.  U: device double,
+ * n_h x n_t, ld >= n_h, caller-owned (the full N_h * N_t storage of
+ * Section 5).  F1, F2 host or device.  Asynchronous after the inputs are
+ * staged. */
+int st_timestep_cn(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
+                   double* U, int ldu);
+
+/* st_error_string -- static text for a status code. */
+const char* st_error_string(int status);
+
+/* st_last_error -- text of the last CUDA failure seen by this thread. */
+const char* st_last_error(void);
+
+/* ---- launch accounting and kernel timing (tracing; no counterpart in the paper) ---- */
+
+/* Per-kernel totals of a profiling region. */
+typedef struct st_kernel_time {
+    char name[24];        /* kernel tag, e.g. "apply", "fd_gemm", "ts_tn" */
+    int launches;         /* launches recorded in the region */
+    double ms;            /* summed durations between the event pair around each launch */
+    double bytes;         /* summed algorithmic bytes (each input read once, each output written once) */
+    double flops;         /* summed algorithmic floating-point operations */
+} st_kernel_time;
+
+/* st_launch_count -- number of kernels this library has launched in the
+ * process (graph replays count every kernel node). */
+unsigned long long st_launch_count(void);
+
+/* st_profile_begin -- start recording an event pair on the launching stream
+ * around every tagged kernel launch (not inside graph capture). */
+int st_profile_begin(void);
+
+/* st_profile_end -- stop recording, wait for the events and aggregate per tag
+ * into out[0 .. min(*count, max)).  *count receives the number of tags. */
+int st_profile_end(st_kernel_time* out, int max, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H_ */

@@ -1,0 +1,327 @@
+"""GB300 space-time Petrov-Galerkin heat solver: Python binding of libst.so.
+
+The binding only marshals arguments; every computation runs in the CUDA library
+(``csrc/``), whose C ABI is declared in ``include/st.h``.  Matrices cross the
+boundary in column-major layout: an ``(rows, cols)`` torch tensor or numpy array
+whose first index is the fastest (``X.stride(0) == 1``).  ``colmajor`` makes
+such a copy when needed.
+
+Importing this package never compiles anything; ``build()`` (or
+``python -m paper_1912_10082_gb300.build``) builds the library in-tree.  A
+missing library raises ``RuntimeError`` at first use: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "_lib" / "libst.so"
+
+ST_OK, ST_EINVAL, ST_ENOMEM, ST_ENOTCONV, ST_EBREAKDOWN, ST_ECUDA, ST_ETIMEOUT, ST_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+ST_FP64, ST_MIXED = 0, 1
+ST_F64, ST_F32 = 0, 1
+ST_HEAT, ST_CONVDIFF = 0, 1
+
+# every symbol include/st.h declares
+ABI_SYMBOLS = (
+    "st_setup", "st_destroy", "st_problem_info", "st_get_csr", "st_apply", "st_rhs_manufactured",
+    "st_shift_solve", "st_solve", "st_residual", "st_residual_lowrank", "st_timestep_cn",
+    "st_error_string", "st_last_error", "st_launch_count", "st_profile_begin", "st_profile_end",
+)
+
+
+class StDesc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("n", C.c_int * 3), ("length", C.c_double * 3), ("op", C.c_int),
+        ("kappa", C.c_double), ("eps", C.c_double), ("beta", C.c_double * 3), ("n_t", C.c_int),
+        ("T", C.c_double), ("n_h", C.c_int), ("nnz", C.c_int), ("row_ptr", C.c_void_p),
+        ("col_idx", C.c_void_p), ("m_vals", C.c_void_p), ("a_vals", C.c_void_p),
+        ("precision", C.c_int), ("tol", C.c_double), ("maxit", C.c_int), ("max_basis", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+class StSolution(C.Structure):
+    _fields_ = [("n_h", C.c_int), ("n_t", C.c_int), ("k", C.c_int), ("V", C.c_void_p), ("Y", C.c_void_p),
+                ("U_dense", C.c_void_p), ("ldu", C.c_int)]
+
+
+class StStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("basis_cols", C.c_int), ("rank", C.c_int), ("p", C.c_int),
+                ("converged", C.c_int), ("residual_checks", C.c_int), ("mu_mem", C.c_int),
+                ("relres", C.c_double), ("ms_total", C.c_double), ("ms_phase", C.c_double * 8),
+                ("shift_min", C.c_double), ("shift_max", C.c_double)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "ms_phase"}
+        d["ms_phase"] = list(self.ms_phase)
+        return d
+
+
+class StKernelTime(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libst.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() or "
+                           "python -m paper_1912_10082_gb300.build (no CPU fallback exists)")
+    L = C.CDLL(str(LIB_PATH))
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "st_setup": ([C.POINTER(StDesc), C.POINTER(vp)], i),
+        "st_destroy": ([vp], i),
+        "st_problem_info": ([vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)], i),
+        "st_get_csr": ([vp, vp, vp, vp, vp], i),
+        "st_apply": ([vp, i, vp, i, vp, i], i),
+        "st_rhs_manufactured": ([vp, vp, i, vp, i], i),
+        "st_shift_solve": ([vp, d, vp, i, i, vp, i, i], i),
+        "st_solve": ([vp, vp, i, vp, i, i, C.POINTER(StSolution), C.POINTER(StStats)], i),
+        "st_residual": ([vp, vp, i, vp, i, vp, i, i, C.POINTER(d)], i),
+        "st_residual_lowrank": ([vp, vp, i, vp, i, i, vp, i, vp, i, i, C.POINTER(d)], i),
+        "st_timestep_cn": ([vp, vp, i, vp, i, i, vp, i], i),
+        "st_error_string": ([i], C.c_char_p),
+        "st_last_error": ([], C.c_char_p),
+        "st_launch_count": ([], C.c_ulonglong),
+        "st_profile_begin": ([], i),
+        "st_profile_end": ([C.POINTER(StKernelTime), i, C.POINTER(i)], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+class StError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = L.st_error_string(status).decode()
+        last = L.st_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f" [{last}]" if last else ""))
+        self.status = status
+
+
+def _check(status: int, where: str, ok=(ST_OK,)):
+    if status not in ok:
+        raise StError(status, where)
+    return status
+
+
+def colmajor(x):
+    """Column-major copy (or the array itself) of a 2D torch tensor or numpy array."""
+    if isinstance(x, np.ndarray):
+        return np.asfortranarray(x, dtype=np.float64) if x.dtype != np.float32 else np.asfortranarray(x)
+    import torch
+    if x.dim() == 1:
+        x = x[:, None]
+    if x.stride(0) == 1 and (x.shape[1] == 1 or x.stride(1) >= x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def _ptr_ld(x):
+    """(pointer, leading dimension, rows, cols) of a column-major 2D array."""
+    if isinstance(x, np.ndarray):
+        if x.ndim == 1:
+            x = x[:, None]
+        if not x.flags["F_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be Fortran-ordered (use colmajor)")
+        return x.ctypes.data, max(1, x.shape[0]), x.shape[0], x.shape[1]
+    if x.dim() == 1:
+        return x.data_ptr(), max(1, x.shape[0]), x.shape[0], 1
+    if x.stride(0) != 1 and x.shape[0] > 1:
+        raise ValueError("tensors must be column-major (stride(0) == 1); use colmajor")
+    ld = x.stride(1) if x.shape[1] > 1 else max(1, x.shape[0])
+    return x.data_ptr(), max(ld, x.shape[0], 1), x.shape[0], x.shape[1]
+
+
+class _DevView:
+    """__cuda_array_interface__ over library-owned device memory (column-major)."""
+
+    def __init__(self, ptr: int, rows: int, cols: int, ld: int):
+        self.__cuda_array_interface__ = {
+            "shape": (rows, cols), "typestr": "<f8", "data": (int(ptr or 0), False),
+            "strides": (8, 8 * ld), "version": 3,
+        }
+
+
+def empty_colmajor(rows: int, cols: int, dtype=None, device="cuda"):
+    import torch
+    dtype = dtype or torch.float64
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+class Problem:
+    """Owns one st_problem handle (see include/st.h for every argument)."""
+
+    def __init__(self, dim: int, n, n_t: int, T: float = 1.0, kappa: float = 1.0, *, length=None,
+                 op: int = ST_HEAT, eps: float = 0.0, beta=(0.0, 0.0, 0.0), precision: int = ST_FP64,
+                 tol: float = 1e-8, maxit: int = 0, max_basis: int = 0, stream=None, csr=None):
+        L = lib()
+        d = StDesc()
+        d.dim = int(dim)
+        ns = [int(n)] * 3 if np.isscalar(n) else list(n) + [1] * (3 - len(n))
+        for i in range(3):
+            d.n[i] = int(ns[i]) if i < max(dim, 1) else 1
+            d.length[i] = float(length[i]) if length is not None and i < len(length) else 1.0
+            d.beta[i] = float(beta[i]) if i < len(beta) else 0.0
+        d.op, d.kappa, d.eps = int(op), float(kappa), float(eps)
+        d.n_t, d.T = int(n_t), float(T)
+        d.precision, d.tol, d.maxit, d.max_basis = int(precision), float(tol), int(maxit), int(max_basis)
+        self._keep = []
+        if csr is not None:
+            row_ptr, col, mv, av = (np.ascontiguousarray(csr[0], dtype=np.int32),
+                                    np.ascontiguousarray(csr[1], dtype=np.int32),
+                                    np.ascontiguousarray(csr[2], dtype=np.float64),
+                                    np.ascontiguousarray(csr[3], dtype=np.float64))
+            self._keep = [row_ptr, col, mv, av]
+            d.dim = 0
+            d.n_h, d.nnz = len(row_ptr) - 1, len(col)
+            d.row_ptr, d.col_idx = row_ptr.ctypes.data, col.ctypes.data
+            d.m_vals, d.a_vals = mv.ctypes.data, av.ctypes.data
+        if stream is not None:
+            d.stream = int(getattr(stream, "cuda_stream", stream))
+        self.desc = d
+        h = C.c_void_p()
+        _check(L.st_setup(C.byref(d), C.byref(h)), "st_setup")
+        self.h = h
+        nh, nt, nnz, dt = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(L.st_problem_info(h, C.byref(nh), C.byref(nt), C.byref(nnz), C.byref(dt)), "st_problem_info")
+        self.n_h, self.n_t, self.nnz, self.dt = nh.value, nt.value, nnz.value, dt.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().st_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- set-up data ---------------------------------------------------------
+    def get_csr(self):
+        rp = np.empty(self.n_h + 1, dtype=np.int32)
+        col = np.empty(self.nnz, dtype=np.int32)
+        mv = np.empty(self.nnz)
+        av = np.empty(self.nnz)
+        _check(lib().st_get_csr(self.h, rp.ctypes.data, col.ctypes.data, mv.ctypes.data, av.ctypes.data),
+               "st_get_csr")
+        return rp, col, mv, av
+
+    def rhs_manufactured(self, F1=None, F2=None):
+        F1 = empty_colmajor(self.n_h, 2) if F1 is None else F1
+        F2 = empty_colmajor(self.n_t, 2) if F2 is None else F2
+        p1, l1, _, _ = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        _check(lib().st_rhs_manufactured(self.h, p1, l1, p2, l2), "st_rhs_manufactured")
+        return F1, F2
+
+    # -- hot path ------------------------------------------------------------
+    def apply(self, U, Y=None):
+        import torch
+        dtype = ST_F32 if U.dtype == torch.float32 else ST_F64
+        Y = empty_colmajor(self.n_h, self.n_t, dtype=U.dtype, device=U.device) if Y is None else Y
+        pu, lu, _, _ = _ptr_ld(U)
+        py, ly, _, _ = _ptr_ld(Y)
+        _check(lib().st_apply(self.h, dtype, pu, lu, py, ly), "st_apply")
+        return Y
+
+    def shift_solve(self, s: float, X, W=None, precision: int = ST_FP64):
+        W = empty_colmajor(self.n_h, X.shape[1] if X.dim() > 1 else 1, device=X.device) if W is None else W
+        px, lx, _, m = _ptr_ld(X)
+        pw, lw, _, _ = _ptr_ld(W)
+        _check(lib().st_shift_solve(self.h, float(s), px, lx, m, pw, lw, int(precision)), "st_shift_solve")
+        return W
+
+    def solve(self, F1, F2, U_dense=None, ok=(ST_OK,)):
+        """Returns (V, Y, stats, status); V, Y are views of library-owned memory."""
+        import torch
+        p1, l1, _, m = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        sol = StSolution()
+        if U_dense is not None:
+            pu, lu, _, _ = _ptr_ld(U_dense)
+            sol.U_dense, sol.ldu = pu, lu
+        stats = StStats()
+        st = lib().st_solve(self.h, p1, l1, p2, l2, m, C.byref(sol), C.byref(stats))
+        _check(st, "st_solve", ok)
+        k = sol.k
+        if k > 0:
+            V = torch.as_tensor(_DevView(sol.V, self.n_h, k, self.n_h), device="cuda")
+            Y = torch.as_tensor(_DevView(sol.Y, k, self.n_t, k), device="cuda")
+        else:
+            V = torch.zeros((self.n_h, 0), dtype=torch.float64, device="cuda")
+            Y = torch.zeros((0, self.n_t), dtype=torch.float64, device="cuda")
+        return V, Y, stats.as_dict(), st
+
+    def residual(self, U, F1, F2) -> float:
+        pu, lu, _, _ = _ptr_ld(U)
+        p1, l1, _, m = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        out = C.c_double()
+        _check(lib().st_residual(self.h, pu, lu, p1, l1, p2, l2, m, C.byref(out)), "st_residual")
+        return out.value
+
+    def residual_lowrank(self, V, Y, F1, F2) -> float:
+        pv, lv, _, k = _ptr_ld(V)
+        py, ly, _, _ = _ptr_ld(Y)
+        p1, l1, _, m = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        out = C.c_double()
+        _check(lib().st_residual_lowrank(self.h, pv, lv, py, max(ly, 1), k, p1, l1, p2, l2, m, C.byref(out)),
+               "st_residual_lowrank")
+        return out.value
+
+    def timestep_cn(self, F1, F2, U=None):
+        U = empty_colmajor(self.n_h, self.n_t) if U is None else U
+        p1, l1, _, m = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        pu, lu, _, _ = _ptr_ld(U)
+        _check(lib().st_timestep_cn(self.h, p1, l1, p2, l2, m, pu, lu), "st_timestep_cn")
+        return U
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().st_launch_count())
+
+
+def profile_begin():
+    _check(lib().st_profile_begin(), "st_profile_begin")
+
+
+def profile_end():
+    """Per-kernel totals since profile_begin(): {tag: dict(launches, ms, bytes, flops)}."""
+    L = lib()
+    arr = (StKernelTime * 64)()
+    cnt = C.c_int()
+    _check(L.st_profile_end(arr, 64, C.byref(cnt)), "st_profile_end")
+    return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes,
+                                       flops=arr[i].flops) for i in range(min(cnt.value, 64))}
+
+
+def build(force: bool = False):
+    from .build import build as _b
+    return _b(force=force)

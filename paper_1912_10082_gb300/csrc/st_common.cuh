@@ -1,0 +1,150 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "st.h"
+
+#define ST_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) { st_note_cuda(e__, #expr, __FILE__, __LINE__); return ST_ECUDA; } \
+    } while (0)
+
+#define ST_LAUNCH_CHECK()                                   \
+    do {                                                    \
+        st_count_launch();                                  \
+        cudaError_t e__ = cudaGetLastError();               \
+        if (e__ != cudaSuccess) { st_note_cuda(e__, "launch", __FILE__, __LINE__); return ST_ECUDA; } \
+    } while (0)
+
+#define ST_TRY(expr)                                        \
+    do { int s__ = (expr); if (s__ != ST_OK) return s__; } while (0)
+
+void st_note_cuda(cudaError_t e, const char* what, const char* file, int line);
+
+// launch accounting and optional event timing (st_profile.cu)
+void st_count_launch();
+void st_count_launches(unsigned long long n);
+void st_capture_enter();
+void st_capture_leave();
+void st_prof_begin(cudaStream_t s, const char* tag, double bytes, double flops);
+void st_prof_end(cudaStream_t s);
+
+// One device allocation owned by a handle.
+struct DevArray {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// 1D factors of one box direction for the fast-diagonalisation solve.
+struct FdAxis {
+    int n = 0;
+    double h = 0.0;         // mesh width L/(n+1)
+    double* Q64 = nullptr;  // n x n, Q[j][i] = sin((j+1)(i+1) pi/(n+1)), symmetric
+    float* Q32 = nullptr;
+    double* lam = nullptr;  // eigenvalues of K phi = lam M phi, j = 1..n
+    double* c2 = nullptr;   // 2 / ((n+1) mu_j), mu_j the M eigenvalue of sine mode j
+};
+
+struct st_problem {
+    st_desc d{};
+    cudaStream_t stream = nullptr;
+    int dim = 0;            // 0 for user CSR
+    int n[3] = {1, 1, 1};
+    double len[3] = {1, 1, 1};
+    int n_h = 0, n_t = 0, nnz = 0, max_row_nnz = 0;
+    double dt = 0.0, kappa = 1.0;
+    bool tensor_heat = false;   // fast-diagonalisation solver applies
+    // CSR, shared pattern (device)
+    int* row_ptr = nullptr;
+    int* col = nullptr;
+    double *m64 = nullptr, *a64 = nullptr, *p64 = nullptr, *q64 = nullptr;   // M, A, P=M+dt/2A, N=M-dt/2A
+    float *m32 = nullptr, *a32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+    FdAxis ax[3];
+    double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M)
+    std::vector<void*> owned;              // every device allocation of the handle
+    // solution of the last st_solve (device, owned)
+    double* V = nullptr;
+    double* Y = nullptr;
+    int k = 0;
+    size_t V_cap_cols = 0, Y_cap = 0;
+    // persistent solver workspace (device, owned), grown on demand
+    double* work = nullptr;
+    size_t work_bytes = 0;
+    // CN graph cache
+    void* cn_graph = nullptr;   // cudaGraphExec_t
+    size_t cn_nodes = 0;        // kernel nodes in the CN graph
+    double* cn_buf = nullptr;
+    const void* cn_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    // grow-only device workspace slots
+    void* slot_ptr[24] = {};
+    size_t slot_bytes[24] = {};
+};
+
+// Returns a device buffer of at least `bytes` for slot `id` (contents not kept on growth).
+int st_slot(st_problem* p, int id, size_t bytes, void** out);
+
+// ---- allocation helpers (st_setup.cu) ----
+int st_alloc(st_problem* p, void** ptr, size_t bytes);
+int st_free_one(st_problem* p, void* ptr);
+bool st_is_device_ptr(const void* ptr);
+// Copies a possibly-host column-major matrix into a device buffer with ld = rows.
+int st_stage_matrix(st_problem* p, const double* src, int ld, int rows, int cols, double* dst);
+
+// ---- kernels launched from several files (st_kernels.cu) ----
+// Out1 = M X, Out2 = A X for ncols columns (either output may be NULL).
+template <typename T>
+int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OutM, int ldm, T* OutA, int lda, cudaStream_t s);
+// Out = alpha * (Mv * M + Av * A) X + beta * Out
+int st_spmm_comb64(st_problem* p, double cm, double ca, const double* X, int ldx, int ncols,
+                   double beta, double* Out, int ldo, cudaStream_t s);
+// Space-time apply Y[:,l] = P u_l - N u_{l-1}.
+template <typename T>
+int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, cudaStream_t s);
+// Right-hand side of CN step l: out = N u + F1 F2[l, :]^T; u may be NULL (u_0 = 0).
+int st_cn_rhs_step(st_problem* p, const double* u, const double* F1, int ldf1, const double* F2, int ldf2, int l,
+                   int ncols, double* out, cudaStream_t s);
+
+// Fast-diagonalisation transform: W = coef * Q (x) diag(omega) Q (x) X with
+// omega(j) = weight(j) / (kappa * sum lam + shift), weight = prod c2 (kind 1) or 1 (kind 0).
+enum FdKind { FD_MASS_RESOLVENT = 0, FD_RESOLVENT = 1, FD_MASS_INVERSE = 2 };
+int st_fd_apply64(st_problem* p, FdKind kind, double shift, double coef, const double* X, int ldx,
+                  int ncols, double* W, int ldw, double* tmp, cudaStream_t s);
+int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const float* X, int ldx,
+                  int ncols, float* W, int ldw, float* tmp, cudaStream_t s);
+
+// Tall-skinny products.  H (k x m, ld ldh, device) = V^T W for V n x k, W n x m.
+// partial must hold tsgemm_partial_elems(n, k, m) doubles.
+size_t st_tsgemm_partial_elems(int n, int k, int m);
+int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W, int ldw,
+                 double* H, int ldh, double* partial, cudaStream_t s);
+// W = beta * W + alpha * V H   (V n x k, H k x m device, W n x m)
+int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, const double* H, int ldh,
+                 double beta, double* W, int ldw, cudaStream_t s);
+// W = W * R^{-1} for upper triangular R (m x m, device), in place
+int st_trsm_right_upper(int n, int m, const double* R, int ldr, double* W, int ldw, cudaStream_t s);
+
+// small vector helpers
+int st_copy_cols64(int n, int m, const double* X, int ldx, double* Y, int ldy, cudaStream_t s);
+int st_convert_64_32(int n, int m, const double* X, int ldx, float* Y, int ldy, cudaStream_t s);
+int st_convert_32_64_add(int n, int m, const float* X, int ldx, double* Y, int ldy, double beta, cudaStream_t s);
+int st_axpby64(int n, int m, double a, const double* X, int ldx, double b, double* Y, int ldy, cudaStream_t s);
+int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const double* Y, int ldy,
+                     double* U, int ldu, cudaStream_t s);
+
+// ---- host dense algebra (st_dense.cpp), column-major, FP64 ----
+namespace dense {
+bool cholesky(int n, double* A, int lda);                 // lower, in place
+void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs);
+bool lu(int n, double* A, int lda, int* piv);
+void lu_solve(int n, const double* LU, int lda, const int* piv, double* B, int ldb, int nrhs);
+bool lu_solve_transpose(int n, const double* LU, int lda, const int* piv, double* B, int ldb, int nrhs);
+void sym_eigvals(int n, double* A, int lda, double* w);   // destroys A, ascending w
+void sym_eig(int n, double* A, int lda, double* w);       // A <- eigenvectors (columns), ascending w
+int  thin_qr(int m, int n, double* A, int lda, double* R, int ldr); // Householder, A <- Q
+void svd_small(int m, int n, const double* A, int lda, double* U, double* s, double* Vt); // m, n small
+}  // namespace dense

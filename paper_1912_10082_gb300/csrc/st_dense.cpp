@@ -1,0 +1,377 @@
+// Small dense FP64 algebra for the projected problems (k x k, k <= a few
+// thousand), run on the host cores next to the GPU.  Column-major storage.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "st_common.cuh"
+
+namespace dense {
+
+#define A_(i, j) A[(size_t)(j) * lda + (i)]
+
+bool cholesky(int n, double* A, int lda) {
+    for (int j = 0; j < n; ++j) {
+        double s = A_(j, j);
+        for (int k = 0; k < j; ++k) s -= A_(j, k) * A_(j, k);
+        if (!(s > 0.0)) return false;
+        double d = std::sqrt(s);
+        A_(j, j) = d;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A_(i, j);
+            for (int k = 0; k < j; ++k) t -= A_(i, k) * A_(j, k);
+            A_(i, j) = t / d;
+        }
+        for (int i = 0; i < j; ++i) A_(i, j) = 0.0;
+    }
+    return true;
+}
+
+void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
+    for (int c = 0; c < nrhs; ++c) {
+        double* b = B + (size_t)c * ldb;
+        for (int i = 0; i < n; ++i) {
+            double s = b[i];
+            for (int k = 0; k < i; ++k) s -= L[(size_t)k * ldl + i] * b[k];
+            b[i] = s / L[(size_t)i * ldl + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = b[i];
+            for (int k = i + 1; k < n; ++k) s -= L[(size_t)i * ldl + k] * b[k];
+            b[i] = s / L[(size_t)i * ldl + i];
+        }
+    }
+}
+
+bool lu(int n, double* A, int lda, int* piv) {
+    bool ok = true;
+    for (int j = 0; j < n; ++j) {
+        int pr = j;
+        double mx = std::fabs(A_(j, j));
+        for (int i = j + 1; i < n; ++i)
+            if (std::fabs(A_(i, j)) > mx) {
+                mx = std::fabs(A_(i, j));
+                pr = i;
+            }
+        piv[j] = pr;
+        if (pr != j)
+            for (int c = 0; c < n; ++c) std::swap(A_(j, c), A_(pr, c));
+        double d = A_(j, j);
+        if (d == 0.0) {
+            ok = false;
+            continue;
+        }
+        for (int i = j + 1; i < n; ++i) A_(i, j) /= d;
+        for (int c = j + 1; c < n; ++c) {
+            double t = A_(j, c);
+            if (t == 0.0) continue;
+            double* colc = A + (size_t)c * lda;
+            const double* colj = A + (size_t)j * lda;
+            for (int i = j + 1; i < n; ++i) colc[i] -= colj[i] * t;
+        }
+    }
+    return ok;
+}
+
+void lu_solve(int n, const double* A, int lda, const int* piv, double* B, int ldb, int nrhs) {
+    for (int c = 0; c < nrhs; ++c) {
+        double* b = B + (size_t)c * ldb;
+        for (int i = 0; i < n; ++i)
+            if (piv[i] != i) std::swap(b[i], b[piv[i]]);
+        for (int j = 0; j < n; ++j) {
+            double t = b[j];
+            if (t == 0.0) continue;
+            for (int i = j + 1; i < n; ++i) b[i] -= A_(i, j) * t;
+        }
+        for (int j = n - 1; j >= 0; --j) {
+            b[j] /= A_(j, j);
+            double t = b[j];
+            if (t == 0.0) continue;
+            for (int i = 0; i < j; ++i) b[i] -= A_(i, j) * t;
+        }
+    }
+}
+
+// Solve A^T x = b with A = P^T L U from lu(): U^T L^T P x = b.
+bool lu_solve_transpose(int n, const double* A, int lda, const int* piv, double* B, int ldb, int nrhs) {
+    for (int c = 0; c < nrhs; ++c) {
+        double* b = B + (size_t)c * ldb;
+        for (int j = 0; j < n; ++j) {   // U^T y = b (lower triangular)
+            double s = b[j];
+            for (int i = 0; i < j; ++i) s -= A_(i, j) * b[i];
+            if (A_(j, j) == 0.0) return false;
+            b[j] = s / A_(j, j);
+        }
+        for (int j = n - 1; j >= 0; --j) {   // L^T z = y (unit upper)
+            double s = b[j];
+            for (int i = j + 1; i < n; ++i) s -= A_(i, j) * b[i];
+            b[j] = s;
+        }
+        for (int i = n - 1; i >= 0; --i)
+            if (piv[i] != i) std::swap(b[i], b[piv[i]]);
+    }
+    return true;
+}
+
+// Householder reduction of a symmetric matrix to tridiagonal form T = Q^T A Q.
+// d: diagonal, e: sub-diagonal (e[i] couples i and i+1).  If want_q, A is
+// overwritten by Q; otherwise A is destroyed.
+static void tridiagonalize(int n, double* A, int lda, double* d, double* e, bool want_q) {
+    std::vector<double> v(n), p(n), w(n);
+    std::vector<double> taus(n, 0.0);
+    for (int j = 0; j + 2 < n; ++j) {
+        int m = n - j - 1;
+        double* x = &A_(j + 1, j);
+        double alpha = 0.0;
+        for (int i = 0; i < m; ++i) alpha += x[i] * x[i];
+        alpha = std::sqrt(alpha);
+        if (alpha == 0.0) {
+            taus[j] = 0.0;
+            continue;
+        }
+        if (x[0] > 0) alpha = -alpha;
+        // v = x - alpha e1, normalised so that v[0] = 1
+        double v0 = x[0] - alpha;
+        for (int i = 0; i < m; ++i) v[i] = x[i] / v0;
+        v[0] = 1.0;
+        double vv = 0.0;
+        for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+        double tau = 2.0 / vv;
+        taus[j] = tau;
+        // p = tau * A22 v (symmetric, full storage)
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < m; ++k) s += A_(j + 1 + i, j + 1 + k) * v[k];
+            p[i] = tau * s;
+        }
+        double pv = 0.0;
+        for (int i = 0; i < m; ++i) pv += p[i] * v[i];
+        double K = 0.5 * tau * pv;
+        for (int i = 0; i < m; ++i) w[i] = p[i] - K * v[i];
+        for (int c = 0; c < m; ++c) {
+            double* col = &A_(j + 1, j + 1 + c);
+            double vc = v[c], wc = w[c];
+            for (int i = 0; i < m; ++i) col[i] -= v[i] * wc + w[i] * vc;
+        }
+        // store v below the sub-diagonal for Q accumulation
+        x[0] = alpha;
+        for (int i = 1; i < m; ++i) x[i] = v[i];
+    }
+    for (int i = 0; i < n; ++i) d[i] = A_(i, i);
+    for (int i = 0; i + 1 < n; ++i) e[i] = A_(i + 1, i);
+    if (!want_q) return;
+    // Q = H_0 H_1 ... H_{n-3}; accumulate backwards into identity
+    std::vector<double> Q((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    for (int j = n - 3; j >= 0; --j) {
+        if (taus[j] == 0.0) continue;
+        int m = n - j - 1;
+        v[0] = 1.0;
+        for (int i = 1; i < m; ++i) v[i] = A_(j + 1 + i, j);
+        for (int c = j + 1; c < n; ++c) {
+            double* col = &Q[(size_t)c * n + j + 1];
+            double s = 0.0;
+            for (int i = 0; i < m; ++i) s += v[i] * col[i];
+            s *= taus[j];
+            for (int i = 0; i < m; ++i) col[i] -= s * v[i];
+        }
+    }
+    for (int c = 0; c < n; ++c) std::memcpy(&A_(0, c), &Q[(size_t)c * n], sizeof(double) * n);
+}
+
+// Implicit QL iterations with Wilkinson-type shifts on a symmetric
+// tridiagonal matrix; Z (n x n, ldz) receives the rotations when non-null.
+static void tridiag_ql(int n, double* d, double* e, double* Z, int ldz) {
+    if (n <= 1) return;
+    std::vector<double> ee(n, 0.0);
+    for (int i = 0; i + 1 < n; ++i) ee[i] = e[i];
+    const double eps = 2.220446049250313e-16;
+    for (int l = 0; l < n; ++l) {
+        int iter = 0;
+        while (true) {
+            int m;
+            for (m = l; m < n - 1; ++m) {
+                double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(ee[m]) <= eps * dd) break;
+            }
+            if (m == l) break;
+            if (++iter > 60) break;
+            double g = (d[l + 1] - d[l]) / (2.0 * ee[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[m] - d[l] + ee[l] / (g + std::copysign(r, g));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i;
+            bool early = false;
+            for (i = m - 1; i >= l; --i) {
+                double f = s * ee[i];
+                double b = c * ee[i];
+                r = std::hypot(f, g);
+                ee[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    ee[m] = 0.0;
+                    early = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - b;
+                if (Z) {
+                    double* zi = Z + (size_t)i * ldz;
+                    double* zi1 = Z + (size_t)(i + 1) * ldz;
+                    for (int k = 0; k < n; ++k) {
+                        double t = zi1[k];
+                        zi1[k] = s * zi[k] + c * t;
+                        zi[k] = c * zi[k] - s * t;
+                    }
+                }
+            }
+            if (early) continue;
+            d[l] -= p;
+            ee[l] = g;
+            ee[m] = 0.0;
+        }
+    }
+}
+
+static void sort_eig(int n, double* w, double* Z, int ldz) {
+    for (int i = 0; i < n; ++i) {
+        int k = i;
+        for (int j = i + 1; j < n; ++j)
+            if (w[j] < w[k]) k = j;
+        if (k != i) {
+            std::swap(w[i], w[k]);
+            if (Z)
+                for (int r = 0; r < n; ++r) std::swap(Z[(size_t)i * ldz + r], Z[(size_t)k * ldz + r]);
+        }
+    }
+}
+
+void sym_eigvals(int n, double* A, int lda, double* w) {
+    if (n == 0) return;
+    std::vector<double> e(n, 0.0);
+    tridiagonalize(n, A, lda, w, e.data(), false);
+    tridiag_ql(n, w, e.data(), nullptr, 0);
+    sort_eig(n, w, nullptr, 0);
+}
+
+void sym_eig(int n, double* A, int lda, double* w) {
+    if (n == 0) return;
+    std::vector<double> e(n, 0.0);
+    tridiagonalize(n, A, lda, w, e.data(), true);
+    tridiag_ql(n, w, e.data(), A, lda);
+    sort_eig(n, w, A, lda);
+}
+
+// Householder QR of an m x n matrix (m >= n): A <- Q (m x n), R (n x n).
+int thin_qr(int m, int n, double* A, int lda, double* R, int ldr) {
+    std::vector<double> taus(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double* x = &A_(j, j);
+        int len = m - j;
+        double alpha = 0.0;
+        for (int i = 0; i < len; ++i) alpha += x[i] * x[i];
+        alpha = std::sqrt(alpha);
+        if (alpha == 0.0) {
+            taus[j] = 0.0;
+            continue;
+        }
+        if (x[0] > 0) alpha = -alpha;
+        double v0 = x[0] - alpha;
+        for (int i = 1; i < len; ++i) x[i] /= v0;
+        double vv = 1.0;
+        for (int i = 1; i < len; ++i) vv += x[i] * x[i];
+        double tau = 2.0 / vv;
+        taus[j] = tau;
+        x[0] = alpha;
+        for (int c = j + 1; c < n; ++c) {
+            double* y = &A_(j, c);
+            double s = y[0];
+            for (int i = 1; i < len; ++i) s += x[i] * y[i];
+            s *= tau;
+            y[0] -= s;
+            for (int i = 1; i < len; ++i) y[i] -= s * x[i];
+        }
+    }
+    for (int c = 0; c < n; ++c)
+        for (int r = 0; r < n; ++r) R[(size_t)c * ldr + r] = r <= c ? A_(r, c) : 0.0;
+    // form Q in place, backwards
+    std::vector<double> Q((size_t)m * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * m + i] = 1.0;
+    for (int j = n - 1; j >= 0; --j) {
+        if (taus[j] == 0.0) continue;
+        int len = m - j;
+        for (int c = j; c < n; ++c) {
+            double* y = &Q[(size_t)c * m + j];
+            double s = y[0];
+            for (int i = 1; i < len; ++i) s += A_(j + i, j) * y[i];
+            s *= taus[j];
+            y[0] -= s;
+            for (int i = 1; i < len; ++i) y[i] -= s * A_(j + i, j);
+        }
+    }
+    for (int c = 0; c < n; ++c) std::memcpy(&A_(0, c), &Q[(size_t)c * m], sizeof(double) * m);
+    return 0;
+}
+
+// One-sided Jacobi SVD of a small m x n matrix: A = U diag(s) Vt, s descending.
+// U: m x n (ld m), s: n, Vt: n x n (ld n).
+void svd_small(int m, int n, const double* A, int lda, double* U, double* s, double* Vt) {
+    std::vector<double> W((size_t)m * n), V((size_t)n * n, 0.0);
+    for (int c = 0; c < n; ++c)
+        for (int r = 0; r < m; ++r) W[(size_t)c * m + r] = A_(r, c);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                double a = 0, b = 0, g = 0;
+                for (int r = 0; r < m; ++r) {
+                    double wi = W[(size_t)i * m + r], wj = W[(size_t)j * m + r];
+                    a += wi * wi;
+                    b += wj * wj;
+                    g += wi * wj;
+                }
+                if (std::fabs(g) <= 1e-300 || std::fabs(g) <= 1e-15 * std::sqrt(a * b)) continue;
+                off = std::max(off, std::fabs(g) / std::sqrt(a * b));
+                double zeta = (b - a) / (2.0 * g);
+                double t = std::copysign(1.0, zeta) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+                for (int r = 0; r < m; ++r) {
+                    double wi = W[(size_t)i * m + r], wj = W[(size_t)j * m + r];
+                    W[(size_t)i * m + r] = c * wi - sn * wj;
+                    W[(size_t)j * m + r] = sn * wi + c * wj;
+                }
+                for (int r = 0; r < n; ++r) {
+                    double vi = V[(size_t)i * n + r], vj = V[(size_t)j * n + r];
+                    V[(size_t)i * n + r] = c * vi - sn * vj;
+                    V[(size_t)j * n + r] = sn * vi + c * vj;
+                }
+            }
+        if (off < 1e-15) break;
+    }
+    std::vector<int> order(n);
+    std::vector<double> sv(n);
+    for (int i = 0; i < n; ++i) {
+        double a = 0;
+        for (int r = 0; r < m; ++r) a += W[(size_t)i * m + r] * W[(size_t)i * m + r];
+        sv[i] = std::sqrt(a);
+        order[i] = i;
+    }
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return sv[x] > sv[y]; });
+    for (int k = 0; k < n; ++k) {
+        int i = order[k];
+        s[k] = sv[i];
+        for (int r = 0; r < m; ++r) U[(size_t)k * m + r] = sv[i] > 0 ? W[(size_t)i * m + r] / sv[i] : 0.0;
+        for (int r = 0; r < n; ++r) Vt[(size_t)r * n + k] = V[(size_t)i * n + r];
+    }
+}
+
+#undef A_
+
+}  // namespace dense

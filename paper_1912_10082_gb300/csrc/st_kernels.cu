@@ -1,0 +1,734 @@
+// Device kernels of the hot path: fused space-time apply, block SpMM,
+// fast-diagonalisation mode products, tall-skinny block products.
+#include <algorithm>
+#include <cmath>
+
+#include "st_common.cuh"
+
+namespace {
+
+constexpr int kMaxCols = 16;   // widest block handled by the tall-skinny and SpMM kernels
+
+// ---------------------------------------------------------------------------
+// Fused space-time apply (Section 4, vec identity): column l of
+// Y = M U D_t^T + A U C_t^T equals P u_l - N u_{l-1} with P = M + dt/2 A and
+// N = M - dt/2 A on the shared CSR pattern.  One thread owns one row: its
+// column indices and P, N values stay in registers while the thread walks a
+// chunk of time columns, so the matrix is read once per chunk.  Lanes of a
+// warp own consecutive rows, so the gathers U[col, l] of a warp are
+// coalesced.  t_N of step l is carried to step l+1.
+// ---------------------------------------------------------------------------
+template <typename T, int MAXNNZ>
+__global__ void __launch_bounds__(128) k_apply_reg(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
+                                                   const int* __restrict__ col, const T* __restrict__ pv,
+                                                   const T* __restrict__ nv, const T* __restrict__ U, long long ldu,
+                                                   T* __restrict__ Y, long long ldy) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    int l0 = blockIdx.y * chunk;
+    int l1 = min(n_t, l0 + chunk);
+    int a = row_ptr[r];
+    int cnt = row_ptr[r + 1] - a;
+    int c[MAXNNZ];
+    T P[MAXNNZ], N[MAXNNZ];
+#pragma unroll
+    for (int e = 0; e < MAXNNZ; ++e) {
+        bool ok = e < cnt;
+        c[e] = ok ? col[a + e] : r;
+        P[e] = ok ? pv[a + e] : T(0);
+        N[e] = ok ? nv[a + e] : T(0);
+    }
+    T prevN = T(0);
+    if (l0 > 0) {
+        const T* u = U + (size_t)(l0 - 1) * ldu;
+#pragma unroll
+        for (int e = 0; e < MAXNNZ; ++e) prevN += N[e] * u[c[e]];
+    }
+    for (int l = l0; l < l1; ++l) {
+        const T* u = U + (size_t)l * ldu;
+        T tP = T(0), tN = T(0);
+#pragma unroll
+        for (int e = 0; e < MAXNNZ; ++e) {
+            T x = u[c[e]];
+            tP += P[e] * x;
+            tN += N[e] * x;
+        }
+        Y[(size_t)l * ldy + r] = tP - prevN;
+        prevN = tN;
+    }
+}
+
+// Generic CSR rows (any length): entries re-read from L1/L2 each step.
+template <typename T>
+__global__ void k_apply_generic(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
+                                const int* __restrict__ col, const T* __restrict__ pv, const T* __restrict__ nv,
+                                const T* __restrict__ U, long long ldu, T* __restrict__ Y, long long ldy) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    int l0 = blockIdx.y * chunk;
+    int l1 = min(n_t, l0 + chunk);
+    int a = row_ptr[r], b = row_ptr[r + 1];
+    T prevN = T(0);
+    if (l0 > 0) {
+        const T* u = U + (size_t)(l0 - 1) * ldu;
+        for (int e = a; e < b; ++e) prevN += nv[e] * u[col[e]];
+    }
+    for (int l = l0; l < l1; ++l) {
+        const T* u = U + (size_t)l * ldu;
+        T tP = T(0), tN = T(0);
+        for (int e = a; e < b; ++e) {
+            T x = u[col[e]];
+            tP += pv[e] * x;
+            tN += nv[e] * x;
+        }
+        Y[(size_t)l * ldy + r] = tP - prevN;
+        prevN = tN;
+    }
+}
+
+// Block SpMM: OutM = M X, OutA = A X for ncols columns (K1b).
+template <typename T, int MAXNNZ>
+__global__ void __launch_bounds__(128) k_spmm_ma_reg(int n_h, int ncols, const int* __restrict__ row_ptr,
+                                                     const int* __restrict__ col, const T* __restrict__ mv,
+                                                     const T* __restrict__ av, const T* __restrict__ X, long long ldx,
+                                                     T* __restrict__ OM, long long ldm, T* __restrict__ OA,
+                                                     long long lda) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    int a0 = row_ptr[r];
+    int cnt = row_ptr[r + 1] - a0;
+    int c[MAXNNZ];
+    T Mv[MAXNNZ], Av[MAXNNZ];
+#pragma unroll
+    for (int e = 0; e < MAXNNZ; ++e) {
+        bool ok = e < cnt;
+        c[e] = ok ? col[a0 + e] : r;
+        Mv[e] = ok ? mv[a0 + e] : T(0);
+        Av[e] = ok ? av[a0 + e] : T(0);
+    }
+    for (int j = 0; j < ncols; ++j) {
+        const T* x = X + (size_t)j * ldx;
+        T sm = T(0), sa = T(0);
+#pragma unroll
+        for (int e = 0; e < MAXNNZ; ++e) {
+            T v = x[c[e]];
+            sm += Mv[e] * v;
+            sa += Av[e] * v;
+        }
+        if (OM) OM[(size_t)j * ldm + r] = sm;
+        if (OA) OA[(size_t)j * lda + r] = sa;
+    }
+}
+
+template <typename T>
+__global__ void k_spmm_ma_generic(int n_h, int ncols, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                                  const T* __restrict__ mv, const T* __restrict__ av, const T* __restrict__ X,
+                                  long long ldx, T* __restrict__ OM, long long ldm, T* __restrict__ OA,
+                                  long long lda) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    int a0 = row_ptr[r], b0 = row_ptr[r + 1];
+    for (int j = 0; j < ncols; ++j) {
+        const T* x = X + (size_t)j * ldx;
+        T sm = T(0), sa = T(0);
+        for (int e = a0; e < b0; ++e) {
+            T v = x[col[e]];
+            sm += mv[e] * v;
+            sa += av[e] * v;
+        }
+        if (OM) OM[(size_t)j * ldm + r] = sm;
+        if (OA) OA[(size_t)j * lda + r] = sa;
+    }
+}
+
+// Out = cm (M X) + ca (A X) + beta Out, FP64.
+__global__ void k_spmm_comb64(int n_h, int ncols, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                              const double* __restrict__ mv, const double* __restrict__ av, double cm, double ca,
+                              const double* __restrict__ X, long long ldx, double beta, double* __restrict__ O,
+                              long long ldo) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    int a0 = row_ptr[r], b0 = row_ptr[r + 1];
+    for (int j = 0; j < ncols; ++j) {
+        const double* x = X + (size_t)j * ldx;
+        double sm = 0.0, sa = 0.0;
+        for (int e = a0; e < b0; ++e) {
+            double v = x[col[e]];
+            sm += mv[e] * v;
+            sa += av[e] * v;
+        }
+        double o = cm * sm + ca * sa;
+        double* po = O + (size_t)j * ldo + r;
+        *po = beta == 0.0 ? o : o + beta * (*po);
+    }
+}
+
+// CN right-hand side of step l: out = N u + sum_q F1[:,q] F2[l,q].
+__global__ void k_cn_rhs(int n_h, const int* __restrict__ row_ptr, const int* __restrict__ col,
+                         const double* __restrict__ nv, const double* __restrict__ u, const double* __restrict__ F1,
+                         long long ldf1, const double* __restrict__ F2, long long ldf2, int l, int ncols,
+                         double* __restrict__ out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    double s = 0.0;
+    if (u) {
+        int a0 = row_ptr[r], b0 = row_ptr[r + 1];
+        for (int e = a0; e < b0; ++e) s += nv[e] * u[col[e]];
+    }
+    for (int q = 0; q < ncols; ++q) s += F1[(size_t)q * ldf1 + r] * F2[(size_t)q * ldf2 + l];
+    out[r] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Batched GEMM with row-major operands for the fast-diagonalisation mode
+// products: C_b (M x N) = A_b (M x K) B_b (K x N), followed by an epilogue
+// that scales by a constant and optionally by the spectral weight of the
+// output entry.  64 x 64 tiles, 256 threads, 4 x 4 outputs per thread.
+// ---------------------------------------------------------------------------
+struct FdEpi {
+    int scale;          // 0: C = coef * acc; 1: C = coef * omega(e) * acc
+    int left;           // 1: linear index e = m * J + j (batch = one vector column); 0: e = m
+    long long J;
+    int dim, nx, ny, nz;
+    const double *l0, *l1, *l2;   // eigenvalues per direction
+    const double *c0, *c1, *c2;   // c2 factors per direction (resolvent of a general right-hand side)
+    int kind;           // FdKind
+    double kappa, shift, coef;
+};
+
+__device__ __forceinline__ double fd_omega(const FdEpi& ep, long long e) {
+    int x = (int)(e % ep.nx);
+    long long t = e / ep.nx;
+    int y = (int)(t % ep.ny);
+    int z = (int)(t / ep.ny);
+    double lam = ep.l0[x];
+    double w = ep.c0[x];
+    if (ep.dim > 1) {
+        lam += ep.l1[y];
+        w *= ep.c1[y];
+    }
+    if (ep.dim > 2) {
+        lam += ep.l2[z];
+        w *= ep.c2[z];
+    }
+    if (ep.kind == FD_MASS_INVERSE) return w;
+    if (ep.kind == FD_RESOLVENT) return w / (ep.kappa * lam + ep.shift);
+    return 1.0 / (ep.kappa * lam + ep.shift);
+}
+
+// Batch index z = blockIdx.z splits into (z2, z1) = (z / nb1, z % nb1); the
+// operand offsets are z1 * s*1 + z2 * s*2.
+struct Batch2 {
+    int nb1;
+    long long sA1, sA2, sB1, sB2, sC1, sC2;
+};
+
+template <typename T, int TM>
+__global__ void __launch_bounds__(256) k_gemm_rr(int M, int N, int K, const T* __restrict__ A, long long lda,
+                                                 const T* __restrict__ B, long long ldb, T* __restrict__ C,
+                                                 long long ldc, Batch2 bt, FdEpi ep) {
+    constexpr int BM = 16 * TM, BN = 16 * TM, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN];
+    int z = blockIdx.z;
+    int z1 = z % bt.nb1, z2 = z / bt.nb1;
+    A += (size_t)z1 * bt.sA1 + (size_t)z2 * bt.sA2;
+    B += (size_t)z1 * bt.sB1 + (size_t)z2 * bt.sB2;
+    C += (size_t)z1 * bt.sC1 + (size_t)z2 * bt.sC2;
+    int tid = threadIdx.x;
+    int tx = tid % 16, ty = tid / 16;
+    int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    T acc[TM][TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += 256) {
+            int mm = idx / BK, kk = idx % BK;
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : T(0);
+        }
+        for (int idx = tid; idx < BK * BN; idx += 256) {
+            int kk = idx / BN, nn = idx % BN;
+            int gk = k0 + kk, gn = n0 + nn;
+            Bs[kk][nn] = (gk < K && gn < N) ? B[(size_t)gk * ldb + gn] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], bb[TM];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TM; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TM; ++j) acc[i][j] += a[i] * bb[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            double f = ep.coef;
+            if (ep.scale) {
+                long long e = ep.left ? (long long)gm * ep.J + gn : (long long)gn;
+                f *= fd_omega(ep, e);
+            }
+            C[(size_t)gm * ldc + gn] = (T)(f * (double)acc[i][j]);
+        }
+    }
+}
+
+template <typename T>
+int launch_gemm_rr(int M, int N, int K, const T* A, long long lda, const T* B, long long ldb, T* C, long long ldc,
+                   int batch, const Batch2& bt, const FdEpi& ep, cudaStream_t s, const char* tag) {
+    if (M <= 0 || N <= 0 || batch <= 0) return ST_OK;
+    long long tiles64 = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
+    bool small = tiles64 < 2 * 152;
+    int bm = small ? 32 : 64;
+    dim3 grid((N + bm - 1) / bm, (M + bm - 1) / bm, batch);
+    if (grid.y > 65535 || grid.z > 65535) return ST_EINVAL;
+    double bytes = (double)sizeof(T) * ((double)M * K + ((double)K * N + (double)M * N) * batch);
+    st_prof_begin(s, tag, bytes, 2.0 * M * N * (double)K * batch);
+    if (small)
+        k_gemm_rr<T, 2><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bt, ep);
+    else
+        k_gemm_rr<T, 4><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bt, ep);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tall-skinny products over the long dimension n (N_h).
+// H = V^T W: each CTA reduces a chunk of rows into a k x m partial, a second
+// kernel sums the partials in chunk order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int TS_THREADS = 256;
+
+__host__ __device__ inline int ts_rows_per_cta(int n) {
+    // enough CTAs to fill the GPU: about 4 per SM of 152 SMs
+    int r = (n + 607) / 608;
+    r = ((r + 31) / 32) * 32;
+    return r < 64 ? 64 : (r > 512 ? 512 : r);
+}
+
+__global__ void __launch_bounds__(TS_THREADS) k_ts_tn_partial(int n, int k, int m, int rows,
+                                                              const double* __restrict__ V, long long ldv,
+                                                              const double* __restrict__ W, long long ldw,
+                                                              double* __restrict__ part) {
+    extern __shared__ double Ws[];   // [m][rows]
+    int chunk = blockIdx.x;
+    int r0 = chunk * rows;
+    int nr = min(rows, n - r0);
+    for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
+        int b = idx / rows, rr = idx % rows;
+        Ws[idx] = rr < nr ? W[(size_t)b * ldw + r0 + rr] : 0.0;
+    }
+    __syncthreads();
+    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double* out = part + (size_t)chunk * k * m;
+    for (int a = warp; a < k; a += TS_THREADS / 32) {
+        const double* v = V + (size_t)a * ldv + r0;
+        double acc[kMaxCols];
+#pragma unroll
+        for (int b = 0; b < kMaxCols; ++b) acc[b] = 0.0;
+        for (int rr = lane; rr < nr; rr += 32) {
+            double x = v[rr];
+#pragma unroll
+            for (int b = 0; b < kMaxCols; ++b)
+                if (b < m) acc[b] += x * Ws[b * rows + rr];
+        }
+#pragma unroll
+        for (int b = 0; b < kMaxCols; ++b) {
+            if (b >= m) break;
+            double t = acc[b];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            if (lane == 0) out[(size_t)a * m + b] = t;
+        }
+    }
+}
+
+__global__ void k_ts_reduce(int nchunks, int k, int m, const double* __restrict__ part, double* __restrict__ H,
+                            long long ldh) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= k * m) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * k * m + idx];
+    int a = idx / m, b = idx % m;
+    H[(size_t)b * ldh + a] = s;
+}
+
+// W = beta W + alpha V H, thread per row, H staged through shared memory.
+__global__ void __launch_bounds__(256) k_ts_nn(int n, int k, int m, double alpha, const double* __restrict__ V,
+                                               long long ldv, const double* __restrict__ H, long long ldh,
+                                               double beta, double* __restrict__ W, long long ldw) {
+    constexpr int KT = 128;
+    __shared__ double Hs[KT * kMaxCols];
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[kMaxCols];
+#pragma unroll
+    for (int b = 0; b < kMaxCols; ++b) acc[b] = 0.0;
+    for (int a0 = 0; a0 < k; a0 += KT) {
+        int kt = min(KT, k - a0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kt * m; idx += blockDim.x) {
+            int a = idx / m, b = idx % m;
+            Hs[idx] = H[(size_t)b * ldh + a0 + a];
+        }
+        __syncthreads();
+        if (r < n) {
+            for (int a = 0; a < kt; ++a) {
+                double x = V[(size_t)(a0 + a) * ldv + r];
+#pragma unroll
+                for (int b = 0; b < kMaxCols; ++b)
+                    if (b < m) acc[b] += x * Hs[a * m + b];
+            }
+        }
+    }
+    if (r >= n) return;
+#pragma unroll
+    for (int b = 0; b < kMaxCols; ++b) {
+        if (b >= m) break;
+        double* w = W + (size_t)b * ldw + r;
+        *w = beta == 0.0 ? alpha * acc[b] : beta * (*w) + alpha * acc[b];
+    }
+}
+
+__global__ void k_trsm_right_upper(int n, int m, const double* __restrict__ R, long long ldr, double* __restrict__ W,
+                                   long long ldw) {
+    __shared__ double Rs[kMaxCols * kMaxCols];
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Rs[idx] = R[(size_t)(idx / m) * ldr + idx % m];
+    __syncthreads();
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double x[kMaxCols];
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) x[j] = j < m ? W[(size_t)j * ldw + r] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) {
+        if (j >= m) break;
+        double s = x[j];
+#pragma unroll
+        for (int i = 0; i < kMaxCols; ++i)
+            if (i < j) s -= x[i] * Rs[j * m + i];   // R[i][j] stored column-major: Rs[j*m + i]
+        x[j] = s / Rs[j * m + j];
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j)
+        if (j < m) W[(size_t)j * ldw + r] = x[j];
+}
+
+template <typename S, typename D>
+__global__ void k_copy_cols(int n, int m, const S* __restrict__ X, long long ldx, D* __restrict__ Y, long long ldy,
+                            double beta) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long tot = (long long)n * m;
+    if (idx >= tot) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    D v = (D)X[(size_t)j * ldx + i];
+    D* y = Y + (size_t)j * ldy + i;
+    *y = beta == 0.0 ? v : (D)(beta * (double)(*y)) + v;
+}
+
+__global__ void k_axpby(int n, int m, double a, const double* __restrict__ X, long long ldx, double b,
+                        double* __restrict__ Y, long long ldy) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long tot = (long long)n * m;
+    if (idx >= tot) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    double* y = Y + (size_t)j * ldy + i;
+    *y = (b == 0.0 ? 0.0 : b * (*y)) + a * X[(size_t)j * ldx + i];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+template <typename T>
+int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, cudaStream_t s) {
+    const T* pv;
+    const T* nv;
+    if constexpr (sizeof(T) == 8) {
+        pv = (const T*)p->p64;
+        nv = (const T*)p->q64;
+    } else {
+        pv = (const T*)p->p32;
+        nv = (const T*)p->q32;
+    }
+    int rows_blocks = (p->n_h + 127) / 128;
+    // split time into chunks so that the grid holds about 300k threads
+    long long want = 300000;
+    int nchunk = (int)std::min<long long>(n_t, std::max<long long>(1, want / std::max(1, p->n_h)));
+    int chunk = (n_t + nchunk - 1) / nchunk;
+    nchunk = (n_t + chunk - 1) / chunk;
+    dim3 grid(rows_blocks, nchunk);
+    double ts = (double)sizeof(T);
+    st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32",
+                  ts * 2.0 * (double)p->n_h * n_t + (double)p->nnz * (4.0 + 2.0 * ts) + 4.0 * (p->n_h + 1),
+                  4.0 * (double)p->nnz * n_t);
+    if (p->max_row_nnz <= 3)
+        k_apply_reg<T, 3><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
+    else if (p->max_row_nnz <= 9)
+        k_apply_reg<T, 9><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
+    else if (p->max_row_nnz <= 27)
+        k_apply_reg<T, 27><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
+    else
+        k_apply_generic<T><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+template int st_apply_kernel<double>(st_problem*, const double*, int, double*, int, int, cudaStream_t);
+template int st_apply_kernel<float>(st_problem*, const float*, int, float*, int, int, cudaStream_t);
+
+template <typename T>
+int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OM, int ldm, T* OA, int lda, cudaStream_t s) {
+    if (ncols <= 0) return ST_OK;
+    const T *mv, *av;
+    if constexpr (sizeof(T) == 8) {
+        mv = (const T*)p->m64;
+        av = (const T*)p->a64;
+    } else {
+        mv = (const T*)p->m32;
+        av = (const T*)p->a32;
+    }
+    int blocks = (p->n_h + 127) / 128;
+    double ts = (double)sizeof(T);
+    int nout = (OM ? 1 : 0) + (OA ? 1 : 0);
+    st_prof_begin(s, sizeof(T) == 8 ? "spmm64" : "spmm32",
+                  (double)p->nnz * (4.0 + 2.0 * ts) + 4.0 * (p->n_h + 1) + ts * (double)p->n_h * ncols * (1 + nout),
+                  4.0 * (double)p->nnz * ncols);
+    if (p->max_row_nnz <= 3)
+        k_spmm_ma_reg<T, 3><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
+    else if (p->max_row_nnz <= 9)
+        k_spmm_ma_reg<T, 9><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
+    else if (p->max_row_nnz <= 27)
+        k_spmm_ma_reg<T, 27><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
+    else
+        k_spmm_ma_generic<T><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+template int st_spmm_ma<double>(st_problem*, const double*, int, int, double*, int, double*, int, cudaStream_t);
+template int st_spmm_ma<float>(st_problem*, const float*, int, int, float*, int, float*, int, cudaStream_t);
+
+int st_spmm_comb64(st_problem* p, double cm, double ca, const double* X, int ldx, int ncols, double beta, double* Out,
+                   int ldo, cudaStream_t s) {
+    if (ncols <= 0) return ST_OK;
+    int blocks = (p->n_h + 127) / 128;
+    st_prof_begin(s, "spmm_comb64", (double)p->nnz * 20.0 + 4.0 * (p->n_h + 1) + 8.0 * p->n_h * ncols * (beta == 0.0 ? 2 : 3),
+                  4.0 * (double)p->nnz * ncols);
+    k_spmm_comb64<<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->m64, p->a64, cm, ca, X, ldx, beta, Out, ldo);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_cn_rhs_step(st_problem* p, const double* u, const double* F1, int ldf1, const double* F2, int ldf2, int l,
+                   int ncols, double* out, cudaStream_t s) {
+    int blocks = (p->n_h + 127) / 128;
+    st_prof_begin(s, "cn_rhs", (double)p->nnz * 12.0 + 4.0 * (p->n_h + 1) + 8.0 * p->n_h * (2 + ncols),
+                  2.0 * (double)p->nnz + 2.0 * p->n_h * ncols);
+    k_cn_rhs<<<blocks, 128, 0, s>>>(p->n_h, p->row_ptr, p->col, p->q64, u, F1, ldf1, F2, ldf2, l, ncols, out);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+// Fast diagonalisation W = coef * Q(x) diag(omega) Q(x) X on the tensor grid.
+// The vector of one column is the tensor X[z][y][x] (x fastest).  Forward
+// products run over x, y, z; the spectral weights are applied in the epilogue
+// of the last forward product; the backward products reuse Q (symmetric).
+// Every product handles all columns in one launch.  Buffers alternate
+// X -> tmp -> W -> tmp -> ... so that the last product lands in W (2*dim
+// products); X is read only by the first, so X and W may alias.
+template <typename T>
+static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, const T* X, int ldx, int ncols, T* W,
+                         int ldw, T* tmp, cudaStream_t s, const T* const* Q, const char* tag) {
+    int dim = p->dim;
+    int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+    long long nh = p->n_h;
+    FdEpi plain{};
+    plain.scale = 0;
+    plain.coef = 1.0;
+    FdEpi sc{};
+    sc.scale = 1;
+    sc.dim = dim;
+    sc.nx = nx;
+    sc.ny = ny;
+    sc.nz = nz;
+    sc.l0 = p->ax[0].lam;
+    sc.l1 = dim > 1 ? p->ax[1].lam : p->ax[0].lam;
+    sc.l2 = dim > 2 ? p->ax[2].lam : p->ax[0].lam;
+    sc.c0 = p->ax[0].c2;
+    sc.c1 = dim > 1 ? p->ax[1].c2 : p->ax[0].c2;
+    sc.c2 = dim > 2 ? p->ax[2].c2 : p->ax[0].c2;
+    sc.kind = kind;
+    sc.kappa = p->kappa;
+    sc.shift = shift;
+    sc.coef = 1.0;
+    if (kind == FD_MASS_RESOLVENT)
+        for (int d = 0; d < dim; ++d) sc.coef *= 2.0 / (p->n[d] + 1);
+    FdEpi fin = plain;
+    fin.coef = coef;
+    const T* src = X;
+    long long lds = ldx;
+    T* bufs[2] = {tmp, W};
+    long long ldb[2] = {nh, ldw};
+    int step = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int d = 0; d < dim; ++d) {
+            T* dst = bufs[step % 2];
+            long long ldd = ldb[step % 2];
+            bool last_fwd = (pass == 0 && d == dim - 1);
+            bool last_all = (pass == 1 && d == dim - 1);
+            FdEpi ep = last_fwd ? sc : (last_all ? fin : plain);
+            if (d == 0) {
+                long long R = nh / nx;
+                ep.left = 0;
+                ep.J = 1;
+                Batch2 bt{1, 0, lds, 0, 0, 0, ldd};   // one batch per column: z2 = column
+                ST_TRY(launch_gemm_rr<T>((int)R, nx, nx, src, nx, Q[0], nx, dst, nx, ncols, bt, ep, s, tag));
+            } else {
+                long long J = (d == 1) ? nx : (long long)nx * ny;
+                int nd = p->n[d];
+                int outer = (int)(nh / (J * nd));
+                ep.left = 1;
+                ep.J = J;
+                Batch2 bt{outer, 0, 0, (long long)nd * J, lds, (long long)nd * J, ldd};
+                ST_TRY(launch_gemm_rr<T>(nd, (int)J, nd, Q[d], nd, src, J, dst, J, outer * ncols, bt, ep, s, tag));
+            }
+            src = dst;
+            lds = ldd;
+            ++step;
+        }
+    }
+    return ST_OK;
+}
+
+int st_fd_apply64(st_problem* p, FdKind kind, double shift, double coef, const double* X, int ldx, int ncols,
+                  double* W, int ldw, double* tmp, cudaStream_t s) {
+    if (!p->tensor_heat) return ST_ENOTSUP;
+    const double* Q[3] = {p->ax[0].Q64, p->ax[1].Q64, p->ax[2].Q64};
+    return fd_apply_impl<double>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, "fd_gemm64");
+}
+
+int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const float* X, int ldx, int ncols, float* W,
+                  int ldw, float* tmp, cudaStream_t s) {
+    if (!p->tensor_heat) return ST_ENOTSUP;
+    const float* Q[3] = {p->ax[0].Q32, p->ax[1].Q32, p->ax[2].Q32};
+    return fd_apply_impl<float>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, "fd_gemm32");
+}
+
+size_t st_tsgemm_partial_elems(int n, int k, int m) {
+    int rows = ts_rows_per_cta(n);
+    size_t nch = (size_t)((n + rows - 1) / rows);
+    return nch * (size_t)k * (size_t)m;
+}
+
+int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W, int ldw, double* H, int ldh,
+                 double* partial, cudaStream_t s) {
+    if (k <= 0 || m <= 0) return ST_OK;
+    if (m > kMaxCols) return ST_EINVAL;
+    if (n <= 0) {
+        // empty sum
+        for (int b = 0; b < m; ++b) ST_CUDA_TRY(cudaMemsetAsync(H + (size_t)b * ldh, 0, sizeof(double) * k, s));
+        return ST_OK;
+    }
+    int rows = ts_rows_per_cta(n);
+    int nch = (n + rows - 1) / rows;
+    size_t smem = sizeof(double) * (size_t)m * rows;
+    static bool smem_set = false;
+    if (!smem_set) {
+        cudaFuncSetAttribute(k_ts_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        smem_set = true;
+    }
+    st_prof_begin(s, "ts_tn", 8.0 * (double)n * (k + m) + 8.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
+    k_ts_tn_partial<<<nch, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, partial);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    int tot = k * m;
+    k_ts_reduce<<<(tot + 255) / 256, 256, 0, s>>>(nch, k, m, partial, H, ldh);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, const double* H, int ldh, double beta,
+                 double* W, int ldw, cudaStream_t s) {
+    if (n <= 0 || m <= 0) return ST_OK;
+    if (m > kMaxCols) return ST_EINVAL;
+    if (k <= 0) {
+        if (beta == 1.0) return ST_OK;
+        return st_axpby64(n, m, 0.0, W, ldw, beta, W, ldw, s);
+    }
+    st_prof_begin(s, "ts_nn", 8.0 * (double)n * (k + m * (beta == 0.0 ? 1 : 2)), 2.0 * (double)n * k * m);
+    k_ts_nn<<<(n + 255) / 256, 256, 0, s>>>(n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_trsm_right_upper(int n, int m, const double* R, int ldr, double* W, int ldw, cudaStream_t s) {
+    if (n <= 0 || m <= 0) return ST_OK;
+    if (m > kMaxCols) return ST_EINVAL;
+    k_trsm_right_upper<<<(n + 255) / 256, 256, 0, s>>>(n, m, R, ldr, W, ldw);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_copy_cols64(int n, int m, const double* X, int ldx, double* Y, int ldy, cudaStream_t s) {
+    long long tot = (long long)n * m;
+    if (tot <= 0) return ST_OK;
+    k_copy_cols<double, double><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, X, ldx, Y, ldy, 0.0);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_convert_64_32(int n, int m, const double* X, int ldx, float* Y, int ldy, cudaStream_t s) {
+    long long tot = (long long)n * m;
+    if (tot <= 0) return ST_OK;
+    k_copy_cols<double, float><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, X, ldx, Y, ldy, 0.0);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_convert_32_64_add(int n, int m, const float* X, int ldx, double* Y, int ldy, double beta, cudaStream_t s) {
+    long long tot = (long long)n * m;
+    if (tot <= 0) return ST_OK;
+    k_copy_cols<float, double><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, X, ldx, Y, ldy, beta);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_axpby64(int n, int m, double a, const double* X, int ldx, double b, double* Y, int ldy, cudaStream_t s) {
+    long long tot = (long long)n * m;
+    if (tot <= 0) return ST_OK;
+    k_axpby<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, a, X, ldx, b, Y, ldy);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+// U (n x n_t, col-major) = V (n x k) Y (k x n_t): as row-major U^T = Y^T V^T.
+int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const double* Y, int ldy, double* U, int ldu,
+                     cudaStream_t s) {
+    FdEpi plain{};
+    plain.coef = 1.0;
+    if (k == 0) {
+        for (int l = 0; l < n_t; ++l) ST_CUDA_TRY(cudaMemsetAsync(U + (size_t)l * ldu, 0, sizeof(double) * n, s));
+        return ST_OK;
+    }
+    Batch2 bt{1, 0, 0, 0, 0, 0, 0};
+    return launch_gemm_rr<double>(n_t, n, k, Y, ldy, V, ldv, U, ldu, 1, bt, plain, s, "lowrank_gemm");
+}

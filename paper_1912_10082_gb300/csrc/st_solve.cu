@@ -1,0 +1,920 @@
+// Rational Krylov Galerkin projection (RKSM) for M U D_t^T + A U C_t^T = F1 F2^T
+// (paper Section 4, heat part), residuals, and the shifted-solve entry point.
+//
+// Device work: everything of size N_h (shifted solves, Gram-Schmidt, SpMM,
+// projections).  Host work (Grace cores): the k x k projected problems, the
+// adaptive shifts and the time recurrence of the projected equation.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "st_common.cuh"
+
+int st_slot(st_problem* p, int id, size_t bytes, void** out) {
+    if (id < 0 || id >= 24) return ST_EINVAL;
+    if (p->slot_bytes[id] < bytes) {
+        if (p->slot_ptr[id]) {
+            cudaStreamSynchronize(p->stream);
+            st_free_one(p, p->slot_ptr[id]);
+        }
+        p->slot_ptr[id] = nullptr;
+        p->slot_bytes[id] = 0;
+        ST_TRY(st_alloc(p, &p->slot_ptr[id], bytes));
+        p->slot_bytes[id] = bytes;
+    }
+    *out = p->slot_ptr[id];
+    return ST_OK;
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+inline double ms_since(Clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+enum SlotId {
+    S_F1D = 0, S_F1C, S_MAQ, S_WH, S_WH2, S_TMP, S_X32, S_W32, S_T32, S_SMALL, S_PART, S_COPY, S_MV,
+    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP
+};
+
+struct Ctx {
+    st_problem* p;
+    cudaStream_t s;
+    int n;
+};
+
+int read_dev(Ctx& c, const double* d, int ld, int rows, int cols, double* h, int ldh) {
+    if (rows == 0 || cols == 0) return ST_OK;
+    ST_CUDA_TRY(cudaMemcpy2DAsync(h, sizeof(double) * ldh, d, sizeof(double) * ld, sizeof(double) * rows, cols,
+                                  cudaMemcpyDeviceToHost, c.s));
+    ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+    return ST_OK;
+}
+
+int write_dev(Ctx& c, const double* h, int ldh, int rows, int cols, double* d, int ld) {
+    if (rows == 0 || cols == 0) return ST_OK;
+    ST_CUDA_TRY(cudaMemcpy2DAsync(d, sizeof(double) * ld, h, sizeof(double) * ldh, sizeof(double) * rows, cols,
+                                  cudaMemcpyHostToDevice, c.s));
+    return ST_OK;
+}
+
+// H (host, k x m) = V^T W over the n rows.
+int ts_tn_host(Ctx& c, int k, int m, const double* V, int ldv, const double* W, int ldw, double* H) {
+    if (k == 0 || m == 0) return ST_OK;
+    double* dH;
+    double* part;
+    ST_TRY(st_slot(c.p, S_SMALL, sizeof(double) * (size_t)k * m, (void**)&dH));
+    ST_TRY(st_slot(c.p, S_PART, sizeof(double) * st_tsgemm_partial_elems(c.n, k, m), (void**)&part));
+    ST_TRY(st_tsgemm_tn(c.n, k, m, V, ldv, W, ldw, dH, k, part, c.s));
+    return read_dev(c, dH, k, k, m, H, k);
+}
+
+// W = beta W + alpha V H with H given on the host (k x m).
+int ts_nn_host(Ctx& c, int k, int m, double alpha, const double* V, int ldv, const double* H, double beta, double* W,
+               int ldw) {
+    if (m == 0) return ST_OK;
+    double* dH;
+    ST_TRY(st_slot(c.p, S_SMALL, sizeof(double) * (size_t)std::max(1, k) * m, (void**)&dH));
+    ST_TRY(write_dev(c, H, k, k, m, dH, k));
+    return st_tsgemm_nn(c.n, k, m, alpha, V, ldv, dH, k, beta, W, ldw, c.s);
+}
+
+// Orthonormalise the m columns of W (device) in place by CholQR2 with a
+// rank-revealing fallback.  On return the first r columns hold Q and
+// R (host, r x m, ld m) satisfies W_in = Q R up to directions whose norm is
+// below drop * max(|W_in|, ref).  ref2 = squared norm of reference.
+int block_qr(Ctx& c, double* W, int ldw, int m, double ref2, double drop, std::vector<double>& R, int* r_out) {
+    *r_out = 0;
+    R.assign((size_t)m * m, 0.0);
+    if (m == 0) return ST_OK;
+    std::vector<double> G((size_t)m * m), E((size_t)m * m), w(m);
+    ST_TRY(ts_tn_host(c, m, m, W, ldw, W, ldw, G.data()));
+    E = G;
+    dense::sym_eig(m, E.data(), m, w.data());
+    double lmax = std::max(w[m - 1], 0.0);
+    double thr = drop * drop * std::max(lmax, ref2);
+    int r = 0;
+    for (int i = 0; i < m; ++i) r += w[i] > thr;
+    if (r == 0) return ST_OK;
+    double* dR;
+    std::vector<double> L = G;
+    bool full = (r == m) && dense::cholesky(m, L.data(), m) && w[0] > 1e-24 * lmax;
+    if (full) {
+        // R1 = L^T; W <- W R1^{-1}; second pass
+        std::vector<double> R1((size_t)m * m, 0.0);
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i <= j; ++i) R1[(size_t)j * m + i] = L[(size_t)i * m + j];
+        ST_TRY(st_slot(c.p, S_SMALL, sizeof(double) * m * m, (void**)&dR));
+        ST_TRY(write_dev(c, R1.data(), m, m, m, dR, m));
+        ST_TRY(st_trsm_right_upper(c.n, m, dR, m, W, ldw, c.s));
+        std::vector<double> G2((size_t)m * m);
+        ST_TRY(ts_tn_host(c, m, m, W, ldw, W, ldw, G2.data()));
+        if (!dense::cholesky(m, G2.data(), m)) return ST_EBREAKDOWN;
+        std::vector<double> R2((size_t)m * m, 0.0);
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i <= j; ++i) R2[(size_t)j * m + i] = G2[(size_t)i * m + j];
+        ST_TRY(st_slot(c.p, S_SMALL, sizeof(double) * m * m, (void**)&dR));
+        ST_TRY(write_dev(c, R2.data(), m, m, m, dR, m));
+        ST_TRY(st_trsm_right_upper(c.n, m, dR, m, W, ldw, c.s));
+        // R = R2 R1 (upper)
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i <= j; ++i) {
+                double s = 0.0;
+                for (int q = i; q <= j; ++q) s += R2[(size_t)q * m + i] * R1[(size_t)j * m + q];
+                R[(size_t)j * m + i] = s;
+            }
+        *r_out = m;
+        return ST_OK;
+    }
+    // rank-deficient: Q0 = W U_r diag(1/sqrt(w_r)), re-orthonormalise, R = Q^T W_in
+    double* copy;
+    ST_TRY(st_slot(c.p, S_COPY, sizeof(double) * (size_t)c.n * m, (void**)&copy));
+    ST_TRY(st_copy_cols64(c.n, m, W, ldw, copy, c.n, c.s));
+    std::vector<double> T((size_t)m * r);
+    for (int j = 0; j < r; ++j) {
+        int src = m - r + j;   // largest eigenvalues are last
+        double sc = 1.0 / std::sqrt(w[src]);
+        for (int i = 0; i < m; ++i) T[(size_t)j * m + i] = E[(size_t)src * m + i] * sc;
+    }
+    ST_TRY(ts_nn_host(c, m, r, 1.0, copy, c.n, T.data(), 0.0, W, ldw));
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<double> G2((size_t)r * r);
+        ST_TRY(ts_tn_host(c, r, r, W, ldw, W, ldw, G2.data()));
+        if (!dense::cholesky(r, G2.data(), r)) return ST_EBREAKDOWN;
+        std::vector<double> R2((size_t)r * r, 0.0);
+        for (int j = 0; j < r; ++j)
+            for (int i = 0; i <= j; ++i) R2[(size_t)j * r + i] = G2[(size_t)i * r + j];
+        ST_TRY(st_slot(c.p, S_SMALL, sizeof(double) * r * r, (void**)&dR));
+        ST_TRY(write_dev(c, R2.data(), r, r, r, dR, r));
+        ST_TRY(st_trsm_right_upper(c.n, r, dR, r, W, ldw, c.s));
+    }
+    std::vector<double> Rq((size_t)r * m);
+    ST_TRY(ts_tn_host(c, r, m, W, ldw, copy, c.n, Rq.data()));
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < r; ++i) R[(size_t)j * m + i] = Rq[(size_t)j * r + i];
+    *r_out = r;
+    return ST_OK;
+}
+
+// Shifted solve W = (A + s M)^{-1} M X (ncols columns), FP64 or FP32 + one FP64 refinement.
+// MX, if given, holds M X already (used by the refinement residual).
+int shifted_solve(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx, int ncols,
+                  double* W, int ldw) {
+    st_problem* p = c.p;
+    size_t nm = (size_t)c.n * ncols;
+    if (prec == ST_FP64) {
+        double* tmp;
+        ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&tmp));
+        return st_fd_apply64(p, FD_MASS_RESOLVENT, shift, 1.0, X, ldx, ncols, W, ldw, tmp, c.s);
+    }
+    float *x32, *w32, *t32;
+    double* r64;
+    ST_TRY(st_slot(p, S_X32, sizeof(float) * nm, (void**)&x32));
+    ST_TRY(st_slot(p, S_W32, sizeof(float) * nm, (void**)&w32));
+    ST_TRY(st_slot(p, S_T32, sizeof(float) * nm, (void**)&t32));
+    ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&r64));
+    ST_TRY(st_convert_64_32(c.n, ncols, X, ldx, x32, c.n, c.s));
+    ST_TRY(st_fd_apply32(p, FD_MASS_RESOLVENT, shift, 1.0, x32, c.n, ncols, w32, c.n, t32, c.s));
+    ST_TRY(st_convert_32_64_add(c.n, ncols, w32, c.n, W, ldw, 0.0, c.s));
+    // r = M X - (A + s M) W, in FP64
+    ST_TRY(st_spmm_comb64(p, -shift, -1.0, W, ldw, ncols, 0.0, r64, c.n, c.s));
+    if (MX) {
+        ST_TRY(st_axpby64(c.n, ncols, 1.0, MX, ldmx, 1.0, r64, c.n, c.s));
+    } else {
+        ST_TRY(st_spmm_comb64(p, 1.0, 0.0, X, ldx, ncols, 1.0, r64, c.n, c.s));
+    }
+    // W += (A + s M)^{-1} r
+    ST_TRY(st_convert_64_32(c.n, ncols, r64, c.n, x32, c.n, c.s));
+    ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, c.n, ncols, w32, c.n, t32, c.s));
+    ST_TRY(st_convert_32_64_add(c.n, ncols, w32, c.n, W, ldw, 1.0, c.s));
+    return ST_OK;
+}
+
+// M^{-1} X for the start block, FP64 or FP32 + refinement.
+int mass_inverse(Ctx& c, int prec, const double* X, int ldx, int ncols, double* W, int ldw) {
+    st_problem* p = c.p;
+    size_t nm = (size_t)c.n * ncols;
+    if (prec == ST_FP64) {
+        double* tmp;
+        ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&tmp));
+        return st_fd_apply64(p, FD_MASS_INVERSE, 0.0, 1.0, X, ldx, ncols, W, ldw, tmp, c.s);
+    }
+    float *x32, *w32, *t32;
+    double* r64;
+    ST_TRY(st_slot(p, S_X32, sizeof(float) * nm, (void**)&x32));
+    ST_TRY(st_slot(p, S_W32, sizeof(float) * nm, (void**)&w32));
+    ST_TRY(st_slot(p, S_T32, sizeof(float) * nm, (void**)&t32));
+    ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&r64));
+    ST_TRY(st_convert_64_32(c.n, ncols, X, ldx, x32, c.n, c.s));
+    ST_TRY(st_fd_apply32(p, FD_MASS_INVERSE, 0.0, 1.0, x32, c.n, ncols, w32, c.n, t32, c.s));
+    ST_TRY(st_convert_32_64_add(c.n, ncols, w32, c.n, W, ldw, 0.0, c.s));
+    for (int it = 0; it < 2; ++it) {
+        ST_TRY(st_spmm_comb64(p, -1.0, 0.0, W, ldw, ncols, 0.0, r64, c.n, c.s));
+        ST_TRY(st_axpby64(c.n, ncols, 1.0, X, ldx, 1.0, r64, c.n, c.s));
+        ST_TRY(st_convert_64_32(c.n, ncols, r64, c.n, x32, c.n, c.s));
+        ST_TRY(st_fd_apply32(p, FD_MASS_INVERSE, 0.0, 1.0, x32, c.n, ncols, w32, c.n, t32, c.s));
+        ST_TRY(st_convert_32_64_add(c.n, ncols, w32, c.n, W, ldw, 1.0, c.s));
+    }
+    return ST_OK;
+}
+
+// Next shift by the adaptive rule: maximise prod_j |s - s_j| / prod_i |s + theta_i|
+// over a log-spaced grid of [a, b] (products renormalised to avoid overflow).
+double next_shift(double a, double b, const std::vector<double>& used, const std::vector<double>& ritz, int grid) {
+    double best = a, bestv = -1e300;
+    double la = std::log(a), lb = std::log(b);
+    for (int g = 0; g < grid; ++g) {
+        double s = std::exp(la + (lb - la) * g / (grid - 1));
+        double prod = 1.0;
+        long long ex = 0;
+        int cnt = 0;
+        for (double sj : used) {
+            prod *= std::fabs(s - sj) / b;
+            if (++cnt == 16) {
+                int e;
+                prod = std::frexp(prod, &e);
+                ex += e;
+                cnt = 0;
+            }
+        }
+        for (double th : ritz) {
+            prod /= std::fabs(s + th) / b;
+            if (++cnt == 16) {
+                int e;
+                prod = std::frexp(prod, &e);
+                ex += e;
+                cnt = 0;
+            }
+        }
+        if (prod <= 0.0) continue;
+        double v = std::log(prod) + ex * std::log(2.0);
+        if (v > bestv) {
+            bestv = v;
+            best = s;
+        }
+    }
+    return best;
+}
+
+// Ritz values of the pencil (Am, Mm): eigenvalues of L^{-1} Am L^{-T}, Mm = L L^T.
+bool ritz_values(int k, const double* Am, const double* Mm, int ld, std::vector<double>& out) {
+    std::vector<double> L((size_t)k * k), C((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            L[(size_t)j * k + i] = Mm[(size_t)j * ld + i];
+            C[(size_t)j * k + i] = Am[(size_t)j * ld + i];
+        }
+    if (!dense::cholesky(k, L.data(), k)) return false;
+    // X = L^{-1} C (column by column), then C = L^{-1} X^T
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int j = 0; j < k; ++j) {
+            double* b = &C[(size_t)j * k];
+            for (int i = 0; i < k; ++i) {
+                double s = b[i];
+                for (int q = 0; q < i; ++q) s -= L[(size_t)q * k + i] * b[q];
+                b[i] = s / L[(size_t)i * k + i];
+            }
+        }
+        for (int j = 0; j < k; ++j)
+            for (int i = j + 1; i < k; ++i) std::swap(C[(size_t)j * k + i], C[(size_t)i * k + j]);
+    }
+    for (int j = 0; j < k; ++j)
+        for (int i = j + 1; i < k; ++i) {
+            double v = 0.5 * (C[(size_t)j * k + i] + C[(size_t)i * k + j]);
+            C[(size_t)j * k + i] = v;
+            C[(size_t)i * k + j] = v;
+        }
+    out.resize(k);
+    dense::sym_eigvals(k, C.data(), k, out.data());
+    return true;
+}
+
+// Projected equation Mm Y D_t^T + Am Y C_t^T = GF (k x n_t), by the time
+// recurrence of the lower-bidiagonal time pencil:
+// (Mm + dt/2 Am) y_l = GF_l + (Mm - dt/2 Am) y_{l-1}.
+bool projected_solve(int k, int n_t, double dt, const double* Mm, const double* Am, int ld, const double* GF,
+                     std::vector<double>& Y) {
+    std::vector<double> P((size_t)k * k), N((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) {
+            double m = Mm[(size_t)j * ld + i], a = Am[(size_t)j * ld + i];
+            P[(size_t)j * k + i] = m + 0.5 * dt * a;
+            N[(size_t)j * k + i] = m - 0.5 * dt * a;
+        }
+    if (!dense::cholesky(k, P.data(), k)) return false;
+    Y.assign((size_t)k * n_t, 0.0);
+    std::vector<double> r(k);
+    for (int l = 0; l < n_t; ++l) {
+        const double* g = GF + (size_t)l * k;
+        for (int i = 0; i < k; ++i) r[i] = g[i];
+        if (l > 0) {
+            const double* yp = &Y[(size_t)(l - 1) * k];
+            for (int j = 0; j < k; ++j) {
+                double t = yp[j];
+                const double* nc = &N[(size_t)j * k];
+                for (int i = 0; i < k; ++i) r[i] += nc[i] * t;
+            }
+        }
+        dense::chol_solve(k, P.data(), k, r.data(), k, 1);
+        std::memcpy(&Y[(size_t)l * k], r.data(), sizeof(double) * k);
+    }
+    return true;
+}
+
+int ensure_basis(st_problem* p, Ctx& c, int need_cols, int keep_cols, double** MV) {
+    if ((size_t)need_cols <= p->V_cap_cols && p->slot_bytes[S_MV] >= sizeof(double) * (size_t)c.n * need_cols) {
+        *MV = (double*)p->slot_ptr[S_MV];
+        return ST_OK;
+    }
+    size_t cap = std::max<size_t>({(size_t)need_cols, 2 * p->V_cap_cols, 32});
+    cap = std::min<size_t>(cap, (size_t)p->d.max_basis + 16);
+    if (cap < (size_t)need_cols) cap = need_cols;
+    double *nv, *nmv;
+    ST_TRY(st_alloc(p, (void**)&nv, sizeof(double) * (size_t)c.n * cap));
+    ST_TRY(st_alloc(p, (void**)&nmv, sizeof(double) * (size_t)c.n * cap));
+    if (keep_cols > 0) {
+        ST_CUDA_TRY(cudaMemcpyAsync(nv, p->V, sizeof(double) * (size_t)c.n * keep_cols, cudaMemcpyDeviceToDevice, c.s));
+        ST_CUDA_TRY(cudaMemcpyAsync(nmv, p->slot_ptr[S_MV], sizeof(double) * (size_t)c.n * keep_cols,
+                                    cudaMemcpyDeviceToDevice, c.s));
+    }
+    ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+    if (p->V) st_free_one(p, p->V);
+    if (p->slot_ptr[S_MV]) st_free_one(p, p->slot_ptr[S_MV]);
+    p->V = nv;
+    p->V_cap_cols = cap;
+    p->slot_ptr[S_MV] = nmv;
+    p->slot_bytes[S_MV] = sizeof(double) * (size_t)c.n * cap;
+    *MV = nmv;
+    return ST_OK;
+}
+
+struct HostSym {
+    std::vector<double> a;
+    int ld = 0;
+    void grow(int need) {
+        if (need <= ld) return;
+        int nl = std::max(need, 2 * ld + 16);
+        std::vector<double> b((size_t)nl * nl, 0.0);
+        for (int j = 0; j < ld; ++j)
+            for (int i = 0; i < ld; ++i) b[(size_t)j * nl + i] = a[(size_t)j * ld + i];
+        a.swap(b);
+        ld = nl;
+    }
+    double& operator()(int i, int j) { return a[(size_t)j * ld + i]; }
+};
+
+int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int p0, st_solution* sol,
+               st_stats* st) {
+    auto t_start = Clock::now();
+    Ctx c{p, p->stream, p->n_h};
+    const int n = p->n_h, nt = p->n_t;
+    const double dt = p->dt;
+    const int prec = p->d.precision;
+    const double tol = p->d.tol;
+    st_stats S{};
+    auto tp = Clock::now();
+
+    // ---- A1: rank compression of F = F1 F2^T ----
+    double* F1d;
+    ST_TRY(st_slot(p, S_F1D, sizeof(double) * (size_t)n * p0, (void**)&F1d));
+    ST_TRY(st_stage_matrix(p, F1, ldf1, n, p0, F1d));
+    std::vector<double> F2h((size_t)nt * p0);
+    if (st_is_device_ptr(F2)) {
+        ST_CUDA_TRY(cudaMemcpy2DAsync(F2h.data(), sizeof(double) * nt, F2, sizeof(double) * ldf2, sizeof(double) * nt,
+                                      p0, cudaMemcpyDeviceToHost, c.s));
+        ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+    } else {
+        for (int j = 0; j < p0; ++j) std::memcpy(&F2h[(size_t)j * nt], F2 + (size_t)j * ldf2, sizeof(double) * nt);
+    }
+    std::vector<double> R1;
+    int r1 = 0;
+    ST_TRY(block_qr(c, F1d, n, p0, 0.0, 1e-14, R1, &r1));   // F1d <- Q1 (n x r1), F1 = Q1 R1
+    // F2 = Q2 R2 (host Householder)
+    std::vector<double> Q2 = F2h, R2((size_t)p0 * p0);
+    dense::thin_qr(nt, p0, Q2.data(), nt, R2.data(), p0);
+    // B = R1 R2^T (r1 x p0)
+    std::vector<double> B((size_t)r1 * p0, 0.0);
+    for (int j = 0; j < p0; ++j)
+        for (int i = 0; i < r1; ++i) {
+            double s = 0.0;
+            for (int q = 0; q < p0; ++q) s += R1[(size_t)q * p0 + i] * R2[(size_t)q * p0 + j];
+            B[(size_t)j * r1 + i] = s;
+        }
+    int r = 0;
+    std::vector<double> Ub, sb, Vbt;
+    if (r1 > 0) {
+        Ub.resize((size_t)r1 * p0);
+        sb.resize(p0);
+        Vbt.resize((size_t)p0 * p0);
+        // SVD of B^T (p0 x r1) is easier to pass as m >= n: use B^T when p0 >= r1
+        std::vector<double> Bt((size_t)p0 * r1);
+        for (int j = 0; j < p0; ++j)
+            for (int i = 0; i < r1; ++i) Bt[(size_t)i * p0 + j] = B[(size_t)j * r1 + i];
+        std::vector<double> U2((size_t)p0 * r1), s2(r1), V2t((size_t)r1 * r1);
+        dense::svd_small(p0, r1, Bt.data(), p0, U2.data(), s2.data(), V2t.data());
+        // B = V2 diag(s2) U2^T
+        for (int i = 0; i < r1; ++i)
+            if (s2[i] > 1e-14 * s2[0]) ++r;
+        // F1c = Q1 V2[:, :r], F2c = Q2 U2[:, :r] diag(s)
+        Ub.assign((size_t)r1 * r, 0.0);
+        for (int j = 0; j < r; ++j)
+            for (int i = 0; i < r1; ++i) Ub[(size_t)j * r1 + i] = V2t[(size_t)i * r1 + j];
+        sb.assign(s2.begin(), s2.begin() + r);
+        Vbt.assign((size_t)p0 * r, 0.0);
+        for (int j = 0; j < r; ++j)
+            for (int i = 0; i < p0; ++i) Vbt[(size_t)j * p0 + i] = U2[(size_t)j * p0 + i];
+    }
+    double normF = 0.0;
+    for (double v : sb) normF += v * v;
+    normF = std::sqrt(normF);
+    S.p = r;
+    if (r == 0) {
+        // F = 0: U = 0
+        p->k = 0;
+        if (sol) {
+            sol->n_h = n;
+            sol->n_t = nt;
+            sol->k = 0;
+            sol->V = p->V;
+            sol->Y = p->Y;
+            if (sol->U_dense)
+                for (int l = 0; l < nt; ++l)
+                    ST_CUDA_TRY(cudaMemsetAsync(sol->U_dense + (size_t)l * sol->ldu, 0, sizeof(double) * n, c.s));
+        }
+        ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+        S.converged = 1;
+        S.ms_total = ms_since(t_start);
+        if (st) *st = S;
+        return ST_OK;
+    }
+    double* F1c;
+    ST_TRY(st_slot(p, S_F1C, sizeof(double) * (size_t)n * r, (void**)&F1c));
+    ST_TRY(ts_nn_host(c, r1, r, 1.0, F1d, n, Ub.data(), 0.0, F1c, n));
+    std::vector<double> F2c((size_t)nt * r, 0.0);   // Q2 U2 diag(s)
+    for (int j = 0; j < r; ++j)
+        for (int i = 0; i < nt; ++i) {
+            double s = 0.0;
+            for (int q = 0; q < p0; ++q) s += Q2[(size_t)q * nt + i] * Vbt[(size_t)j * p0 + q];
+            F2c[(size_t)j * nt + i] = s * sb[j];
+        }
+    S.ms_phase[0] += ms_since(tp);
+
+    // ---- start block v_1 = orth(M^{-1} F1c) ----
+    const int pmax = r;
+    double* MV = nullptr;
+    ST_TRY(ensure_basis(p, c, std::min(2 * pmax + 8, p->d.max_basis + 16), 0, &MV));
+    tp = Clock::now();
+    ST_TRY(mass_inverse(c, prec, F1c, n, r, p->V, n));
+    S.ms_phase[1] += ms_since(tp);
+    std::vector<double> Rx;
+    int k = 0;
+    ST_TRY(block_qr(c, p->V, n, r, 0.0, 1e-12, Rx, &k));
+    if (k == 0) return ST_EBREAKDOWN;
+    double* MAq;   // [M q, A q] staging, n x 2 pmax
+    ST_TRY(st_slot(p, S_MAQ, sizeof(double) * (size_t)n * 2 * pmax, (void**)&MAq));
+    ST_TRY(st_spmm_ma<double>(p, p->V, n, k, MAq, n, MAq + (size_t)n * k, n, c.s));
+    ST_CUDA_TRY(cudaMemcpyAsync(MV, MAq, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, c.s));
+    HostSym Mm, Am, Hb;
+    std::vector<double> Gm;   // k x r, ld = kcap_h
+    int ldg = 0;
+    {
+        std::vector<double> X((size_t)k * 2 * k), G((size_t)k * r);
+        ST_TRY(ts_tn_host(c, k, 2 * k, p->V, n, MAq, n, X.data()));
+        ST_TRY(ts_tn_host(c, k, r, p->V, n, F1c, n, G.data()));
+        Mm.grow(k);
+        Am.grow(k);
+        for (int j = 0; j < k; ++j)
+            for (int i = 0; i < k; ++i) {
+                Mm(i, j) = 0.5 * (X[(size_t)j * k + i] + X[(size_t)i * k + j]);
+                Am(i, j) = 0.5 * (X[(size_t)(k + j) * k + i] + X[(size_t)(k + i) * k + j]);
+            }
+        ldg = std::max(64, 2 * k);
+        Gm.assign((size_t)ldg * r, 0.0);
+        for (int j = 0; j < r; ++j)
+            for (int i = 0; i < k; ++i) Gm[(size_t)j * ldg + i] = G[(size_t)j * k + i];
+    }
+    std::vector<int> boff{0}, bsz{k};
+    std::vector<double> shifts, ritz, Y;
+    int last_ritz_k = -1;
+    double res = 1.0;
+    int status = ST_ENOTCONV;
+    int it = 0;
+    int next_check = 1;
+    int mu_extra = 0;
+    const double a_int = p->lam_min, b_int = p->lam_max;
+    std::vector<double> hist;
+
+    while (true) {
+        if (it >= p->d.maxit) break;
+        int pl = bsz.back();
+        int lo = boff.back();
+        if (k + pl > p->d.max_basis) break;
+        ST_TRY(ensure_basis(p, c, k + pl, k, &MV));
+        // ---- shift ----
+        tp = Clock::now();
+        int ritz_every = k <= 96 ? 1 : (k + 47) / 48;
+        if (last_ritz_k < 0 || it % ritz_every == 0) {
+            if (!ritz_values(k, Am.a.data(), Mm.a.data(), Mm.ld, ritz)) ritz.clear();
+            last_ritz_k = k;
+        }
+        double s = next_shift(a_int, b_int, shifts, ritz, 600);
+        shifts.push_back(s);
+        S.ms_phase[7] += ms_since(tp);
+        ++it;
+        // ---- A3 shifted solve into the next basis slot ----
+        tp = Clock::now();
+        double* W = p->V + (size_t)k * n;
+        ST_TRY(shifted_solve(c, prec, s, p->V + (size_t)lo * n, n, MV + (size_t)lo * n, n, pl, W, n));
+        ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+        S.ms_phase[1] += ms_since(tp);
+        // ---- A4 block CGS2 + QR ----
+        tp = Clock::now();
+        std::vector<double> G0((size_t)pl * pl);
+        ST_TRY(ts_tn_host(c, pl, pl, W, n, W, n, G0.data()));
+        double ref2 = 0.0;
+        for (int i = 0; i < pl; ++i) ref2 = std::max(ref2, G0[(size_t)i * pl + i]);
+        std::vector<double> Hcol((size_t)k * pl, 0.0), h((size_t)k * pl);
+        for (int pass = 0; pass < 2; ++pass) {
+            ST_TRY(ts_tn_host(c, k, pl, p->V, n, W, n, h.data()));
+            ST_TRY(ts_nn_host(c, k, pl, -1.0, p->V, n, h.data(), 1.0, W, n));
+            for (size_t i = 0; i < h.size(); ++i) Hcol[i] += h[i];
+        }
+        std::vector<double> Rq;
+        int pn = 0;
+        ST_TRY(block_qr(c, W, n, pl, ref2, 1e-10, Rq, &pn));
+        S.ms_phase[2] += ms_since(tp);
+        // ---- A5 products of the new block ----
+        tp = Clock::now();
+        std::vector<double> X1((size_t)k * 2 * pn), X2((size_t)pn * 2 * pn), X3((size_t)pn * r);
+        if (pn > 0) {
+            ST_TRY(st_spmm_ma<double>(p, W, n, pn, MAq, n, MAq + (size_t)n * pn, n, c.s));
+            ST_TRY(ts_tn_host(c, k, 2 * pn, p->V, n, MAq, n, X1.data()));
+            ST_TRY(ts_tn_host(c, pn, 2 * pn, W, n, MAq, n, X2.data()));
+            ST_TRY(ts_tn_host(c, pn, r, W, n, F1c, n, X3.data()));
+        }
+        S.ms_phase[3] += ms_since(tp);
+        mu_extra = pn;
+        // Hbar column block: rows 0..k-1 = Hcol, rows k..k+pn-1 = Rq
+        Hb.grow(k + pn);
+        for (int j = 0; j < pl; ++j) {
+            for (int i = 0; i < k; ++i) Hb(i, lo + j) = Hcol[(size_t)j * k + i];
+            for (int i = 0; i < pn; ++i) Hb(k + i, lo + j) = Rq[(size_t)j * pl + i];
+        }
+        // ---- A6/A7 residual check of the current basis V (k columns) ----
+        bool check = (pn == 0) || (it >= next_check) || (it >= p->d.maxit) || (k + pn + pn > p->d.max_basis);
+        if (check) {
+            tp = Clock::now();
+            std::vector<double> GF((size_t)k * nt, 0.0);
+            for (int l = 0; l < nt; ++l)
+                for (int q = 0; q < r; ++q) {
+                    double f = F2c[(size_t)q * nt + l];
+                    if (f == 0.0) continue;
+                    for (int i = 0; i < k; ++i) GF[(size_t)l * k + i] += Gm[(size_t)q * ldg + i] * f;
+                }
+            if (!projected_solve(k, nt, dt, Mm.a.data(), Am.a.data(), Mm.ld, GF.data(), Y)) return ST_EBREAKDOWN;
+            S.ms_phase[4] += ms_since(tp);
+            S.residual_checks++;
+            tp = Clock::now();
+            double rr = 0.0;
+            if (pn > 0) {
+                // w_hat = -(s M q + A q) R_q  (n x pl); V^T w_hat from X1
+                double* Wh;
+                double* Wh2;
+                ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n * pl, (void**)&Wh));
+                ST_TRY(st_slot(p, S_WH2, sizeof(double) * (size_t)n * pl, (void**)&Wh2));
+                // -R_q as pn x pl col-major: element (i, j) = -Rq[j*pl + i]
+                std::vector<double> negR((size_t)pn * pl);
+                for (int j = 0; j < pl; ++j)
+                    for (int i = 0; i < pn; ++i) negR[(size_t)j * pn + i] = -Rq[(size_t)j * pl + i];
+                ST_TRY(st_copy_cols64(n, pn, MAq + (size_t)n * pn, n, Wh, n, c.s));
+                ST_TRY(st_axpby64(n, pn, s, MAq, n, 1.0, Wh, n, c.s));   // Wh = s Mq + Aq
+                ST_TRY(ts_nn_host(c, pn, pl, 1.0, Wh, n, negR.data(), 0.0, Wh2, n));
+                // Vt w_hat = -(s X1_M + X1_A) R_q   (k x pl)
+                std::vector<double> Vw((size_t)k * pl, 0.0);
+                for (int j = 0; j < pl; ++j)
+                    for (int q = 0; q < pn; ++q) {
+                        double rq = -Rq[(size_t)j * pl + q];
+                        for (int i = 0; i < k; ++i)
+                            Vw[(size_t)j * k + i] += (s * X1[(size_t)q * k + i] + X1[(size_t)(pn + q) * k + i]) * rq;
+                    }
+                // c = Mm^{-1} Vw ; b = w_hat - M V c
+                std::vector<double> L((size_t)k * k);
+                for (int j = 0; j < k; ++j)
+                    for (int i = 0; i < k; ++i) L[(size_t)j * k + i] = Mm(i, j);
+                if (!dense::cholesky(k, L.data(), k)) return ST_EBREAKDOWN;
+                dense::chol_solve(k, L.data(), k, Vw.data(), k, pl);
+                ST_TRY(ts_nn_host(c, k, pl, -1.0, MV, n, Vw.data(), 1.0, Wh2, n));
+                std::vector<double> Gb((size_t)pl * pl);
+                ST_TRY(ts_tn_host(c, pl, pl, Wh2, n, Wh2, n, Gb.data()));
+                // f = H^{-T} E_last  (k x pl)
+                std::vector<double> H((size_t)k * k), f((size_t)k * pl, 0.0);
+                for (int j = 0; j < k; ++j)
+                    for (int i = 0; i < k; ++i) H[(size_t)j * k + i] = Hb(i, j);
+                std::vector<int> piv(k);
+                dense::lu(k, H.data(), k, piv.data());
+                for (int j = 0; j < pl; ++j) f[(size_t)j * k + lo + j] = 1.0;
+                if (!dense::lu_solve_transpose(k, H.data(), k, piv.data(), f.data(), k, pl)) return ST_EBREAKDOWN;
+                // g_l = f^T (dt/2)(y_l + y_{l-1});  ||R||^2 = sum_l g_l^T Gb g_l
+                std::vector<double> gl(pl);
+                for (int l = 0; l < nt; ++l) {
+                    const double* y = &Y[(size_t)l * k];
+                    const double* yp = l > 0 ? &Y[(size_t)(l - 1) * k] : nullptr;
+                    for (int j = 0; j < pl; ++j) {
+                        double sacc = 0.0;
+                        const double* fj = &f[(size_t)j * k];
+                        for (int i = 0; i < k; ++i) sacc += fj[i] * (y[i] + (yp ? yp[i] : 0.0));
+                        gl[j] = 0.5 * dt * sacc;
+                    }
+                    for (int a = 0; a < pl; ++a)
+                        for (int b2 = 0; b2 < pl; ++b2) rr += gl[a] * Gb[(size_t)b2 * pl + a] * gl[b2];
+                }
+            }
+            res = std::sqrt(std::max(rr, 0.0)) / normF;
+            hist.push_back(res);
+            S.ms_phase[5] += ms_since(tp);
+            if (res <= tol || pn == 0) {
+                status = res <= tol ? ST_OK : ST_ENOTCONV;
+                if (pn == 0 && res > tol) status = ST_EBREAKDOWN;
+                break;
+            }
+            // schedule the next check: every iteration while the projected solve is cheap
+            double cost = (double)k * k * nt;
+            int gap = (int)std::max(1.0, std::min(16.0, cost / 4e6));
+            // when far from tol and converging geometrically, skip ahead
+            next_check = it + gap;
+        }
+        if (pn == 0) {
+            status = ST_EBREAKDOWN;
+            break;
+        }
+        // ---- append the new block ----
+        tp = Clock::now();
+        ST_CUDA_TRY(cudaMemcpyAsync(MV + (size_t)k * n, MAq, sizeof(double) * (size_t)n * pn, cudaMemcpyDeviceToDevice,
+                                    c.s));
+        int kn = k + pn;
+        Mm.grow(kn);
+        Am.grow(kn);
+        for (int j = 0; j < pn; ++j) {
+            for (int i = 0; i < k; ++i) {
+                Mm(i, k + j) = Mm(k + j, i) = X1[(size_t)j * k + i];
+                Am(i, k + j) = Am(k + j, i) = X1[(size_t)(pn + j) * k + i];
+            }
+            for (int i = 0; i < pn; ++i) {
+                Mm(k + i, k + j) = 0.5 * (X2[(size_t)j * pn + i] + X2[(size_t)i * pn + j]);
+                Am(k + i, k + j) = 0.5 * (X2[(size_t)(pn + j) * pn + i] + X2[(size_t)(pn + i) * pn + j]);
+            }
+        }
+        if (kn > ldg) {
+            int nl = std::max(2 * ldg, kn);
+            std::vector<double> g2((size_t)nl * r, 0.0);
+            for (int j = 0; j < r; ++j)
+                for (int i = 0; i < k; ++i) g2[(size_t)j * nl + i] = Gm[(size_t)j * ldg + i];
+            Gm.swap(g2);
+            ldg = nl;
+        }
+        for (int j = 0; j < r; ++j)
+            for (int i = 0; i < pn; ++i) Gm[(size_t)j * ldg + k + i] = X3[(size_t)j * pn + i];
+        boff.push_back(k);
+        bsz.push_back(pn);
+        k = kn;
+        S.ms_phase[3] += ms_since(tp);
+    }
+    if (Y.empty() || (int)(Y.size() / std::max(1, nt)) != k) {
+        // iterations ended without a check of the final basis
+        std::vector<double> GF((size_t)k * nt, 0.0);
+        for (int l = 0; l < nt; ++l)
+            for (int q = 0; q < r; ++q)
+                for (int i = 0; i < k; ++i) GF[(size_t)l * k + i] += Gm[(size_t)q * ldg + i] * F2c[(size_t)q * nt + l];
+        if (!projected_solve(k, nt, dt, Mm.a.data(), Am.a.data(), Mm.ld, GF.data(), Y)) return ST_EBREAKDOWN;
+        mu_extra = 0;
+    }
+    // ---- A9 output ----
+    tp = Clock::now();
+    if (p->Y_cap < (size_t)k * nt) {
+        if (p->Y) st_free_one(p, p->Y);
+        p->Y = nullptr;
+        p->Y_cap = 0;
+        ST_TRY(st_alloc(p, (void**)&p->Y, sizeof(double) * (size_t)k * nt));
+        p->Y_cap = (size_t)k * nt;
+    }
+    ST_TRY(write_dev(c, Y.data(), k, k, nt, p->Y, k));
+    p->k = k;
+    if (sol) {
+        sol->n_h = n;
+        sol->n_t = nt;
+        sol->k = k;
+        sol->V = p->V;
+        sol->Y = p->Y;
+        if (sol->U_dense) {
+            if (sol->ldu < n) return ST_EINVAL;
+            ST_TRY(st_lowrank_dense(n, k, nt, p->V, n, p->Y, k, sol->U_dense, sol->ldu, c.s));
+        }
+    }
+    ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+    S.ms_phase[6] += ms_since(tp);
+    // numerical rank of Y (V orthonormal): eigenvalues of Y Y^T
+    if (st) {
+        std::vector<double> G((size_t)k * k, 0.0), w(k);
+        for (int l = 0; l < nt; ++l) {
+            const double* y = &Y[(size_t)l * k];
+            for (int j = 0; j < k; ++j)
+                for (int i = 0; i <= j; ++i) G[(size_t)j * k + i] += y[i] * y[j];
+        }
+        for (int j = 0; j < k; ++j)
+            for (int i = j + 1; i < k; ++i) G[(size_t)j * k + i] = G[(size_t)i * k + j];
+        dense::sym_eigvals(k, G.data(), k, w.data());
+        double smax = k ? std::sqrt(std::max(w[k - 1], 0.0)) : 0.0;
+        int rank = 0;
+        for (int i = 0; i < k; ++i) rank += std::sqrt(std::max(w[i], 0.0)) > 1e-8 * smax;
+        S.rank = rank;
+    }
+    S.iterations = it;
+    S.basis_cols = k;
+    S.mu_mem = k + mu_extra;
+    S.relres = res;
+    S.converged = res <= tol;
+    if (!shifts.empty()) {
+        S.shift_min = *std::min_element(shifts.begin(), shifts.end());
+        S.shift_max = *std::max_element(shifts.begin(), shifts.end());
+    }
+    S.ms_total = ms_since(t_start);
+    if (st) *st = S;
+    if (status == ST_EBREAKDOWN && res <= tol) status = ST_OK;
+    return status;
+}
+
+// ||L Z^T||_F for L (device n x m) and Z (host nt x m): block CGS2 QR of L
+// into R (m x m), then the small product on the host.
+int lowrank_fro(Ctx& c, double* L, int m, const std::vector<double>& Z, int nt, double* out) {
+    std::vector<double> R((size_t)m * m, 0.0);
+    const int bs = 8;
+    for (int j0 = 0; j0 < m; j0 += bs) {
+        int mb = std::min(bs, m - j0);
+        double* Wb = L + (size_t)j0 * c.n;
+        std::vector<double> Hc((size_t)j0 * mb, 0.0), hh((size_t)j0 * mb);
+        for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
+            ST_TRY(ts_tn_host(c, j0, mb, L, c.n, Wb, c.n, hh.data()));
+            ST_TRY(ts_nn_host(c, j0, mb, -1.0, L, c.n, hh.data(), 1.0, Wb, c.n));
+            for (size_t i = 0; i < hh.size(); ++i) Hc[i] += hh[i];
+        }
+        std::vector<double> Rb;
+        int rb = 0;
+        ST_TRY(block_qr(c, Wb, c.n, mb, 0.0, 1e-15, Rb, &rb));
+        if (rb < mb) {
+            // zero the dropped directions so later blocks ignore them
+            for (int j = rb; j < mb; ++j)
+                ST_CUDA_TRY(cudaMemsetAsync(Wb + (size_t)j * c.n, 0, sizeof(double) * c.n, c.s));
+        }
+        for (int j = 0; j < mb; ++j) {
+            for (int i = 0; i < j0; ++i) R[(size_t)(j0 + j) * m + i] = Hc[(size_t)j * j0 + i];
+            for (int i = 0; i < rb; ++i) R[(size_t)(j0 + j) * m + j0 + i] = Rb[(size_t)j * mb + i];
+        }
+    }
+    // R is block upper triangular with dense diagonal blocks (rank-deficient blocks
+    // give a dense r x m factor), so the product runs over every column.
+    double s = 0.0;
+    for (int l = 0; l < nt; ++l)
+        for (int i = 0; i < m; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < m; ++j) v += R[(size_t)j * m + i] * Z[(size_t)j * nt + l];
+            s += v * v;
+        }
+    *out = std::sqrt(s);
+    return ST_OK;
+}
+
+__global__ void k_dense_resid(int n, int nt, const double* __restrict__ F1, long long ldf1,
+                              const double* __restrict__ F2, long long ldf2, int p, const double* __restrict__ Yop,
+                              long long ldy, double* __restrict__ part) {
+    __shared__ double sr[256], sf[256];
+    double ar = 0.0, af = 0.0;
+    long long tot = (long long)n * nt;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int l = (int)(idx / n), i = (int)(idx % n);
+        double f = 0.0;
+        for (int q = 0; q < p; ++q) f += F1[(size_t)q * ldf1 + i] * F2[(size_t)q * ldf2 + l];
+        double rres = f - Yop[(size_t)l * ldy + i];
+        ar += rres * rres;
+        af += f * f;
+    }
+    sr[threadIdx.x] = ar;
+    sf[threadIdx.x] = af;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sr[threadIdx.x] += sr[threadIdx.x + w];
+            sf[threadIdx.x] += sf[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sr[0];
+        part[2 * blockIdx.x + 1] = sf[0];
+    }
+}
+
+}  // namespace
+
+extern "C" int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
+                        st_solution* sol, st_stats* stats) {
+    if (!p || !F1 || !F2) return ST_EINVAL;
+    if (ncols < 1 || ncols > 16 || ldf1 < p->n_h || ldf2 < p->n_t) return ST_EINVAL;
+    if (!p->tensor_heat) return ST_ENOTSUP;
+    return solve_impl(p, F1, ldf1, F2, ldf2, ncols, sol, stats);
+}
+
+extern "C" int st_apply(st_problem* p, int dtype, const void* U, int ldu, void* Y, int ldy) {
+    if (!p || !U || !Y || ldu < p->n_h || ldy < p->n_h) return ST_EINVAL;
+    if (dtype == ST_F64) return st_apply_kernel<double>(p, (const double*)U, ldu, (double*)Y, ldy, p->n_t, p->stream);
+    if (dtype == ST_F32) return st_apply_kernel<float>(p, (const float*)U, ldu, (float*)Y, ldy, p->n_t, p->stream);
+    return ST_EINVAL;
+}
+
+extern "C" int st_shift_solve(st_problem* p, double s, const double* X, int ldx, int ncols, double* W, int ldw,
+                              int precision) {
+    if (!p || !X || !W || ncols < 1 || ldx < p->n_h || ldw < p->n_h) return ST_EINVAL;
+    if (precision != ST_FP64 && precision != ST_MIXED) return ST_EINVAL;
+    if (!p->tensor_heat) return ST_ENOTSUP;
+    if (!(s > -p->lam_min)) return ST_EINVAL;
+    Ctx c{p, p->stream, p->n_h};
+    // process in column groups of at most 16 through a private buffer (X and W may alias)
+    for (int j0 = 0; j0 < ncols; j0 += 16) {
+        int m = std::min(16, ncols - j0);
+        double* buf;
+        ST_TRY(st_slot(p, S_COPY, sizeof(double) * (size_t)p->n_h * m, (void**)&buf));
+        ST_TRY(shifted_solve(c, precision, s, X + (size_t)j0 * ldx, ldx, nullptr, 0, m, buf, p->n_h));
+        ST_TRY(st_copy_cols64(p->n_h, m, buf, p->n_h, W + (size_t)j0 * ldw, ldw, p->stream));
+    }
+    return ST_OK;
+}
+
+extern "C" int st_residual(st_problem* p, const double* U, int ldu, const double* F1, int ldf1, const double* F2,
+                           int ldf2, int ncols, double* relres) {
+    if (!p || !U || !F1 || !F2 || !relres || ncols < 1 || ldu < p->n_h || ldf1 < p->n_h || ldf2 < p->n_t)
+        return ST_EINVAL;
+    int n = p->n_h, nt = p->n_t;
+    double *f1, *f2, *Yop, *part;
+    ST_TRY(st_slot(p, S_LRQ, sizeof(double) * (size_t)n * ncols, (void**)&f1));
+    ST_TRY(st_slot(p, S_LRZ, sizeof(double) * (size_t)nt * ncols, (void**)&f2));
+    ST_TRY(st_slot(p, S_RES, sizeof(double) * (size_t)n * nt, (void**)&Yop));
+    const int blocks = 1216;
+    ST_TRY(st_slot(p, S_RESP, sizeof(double) * 2 * blocks, (void**)&part));
+    ST_TRY(st_stage_matrix(p, F1, ldf1, n, ncols, f1));
+    ST_TRY(st_stage_matrix(p, F2, ldf2, nt, ncols, f2));
+    ST_TRY(st_apply_kernel<double>(p, U, ldu, Yop, n, nt, p->stream));
+    k_dense_resid<<<blocks, 256, 0, p->stream>>>(n, nt, f1, n, f2, nt, ncols, Yop, n, part);
+    ST_LAUNCH_CHECK();
+    std::vector<double> h(2 * blocks);
+    ST_CUDA_TRY(cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, p->stream));
+    ST_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    double rr = 0.0, ff = 0.0;
+    for (int b = 0; b < blocks; ++b) {
+        rr += h[2 * b];
+        ff += h[2 * b + 1];
+    }
+    *relres = ff > 0 ? std::sqrt(rr / ff) : std::sqrt(rr);
+    return ST_OK;
+}
+
+extern "C" int st_residual_lowrank(st_problem* p, const double* V, int ldv, const double* Y, int ldy, int k,
+                                   const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
+                                   double* relres) {
+    if (!p || !V || !Y || !F1 || !F2 || !relres || k < 0 || ncols < 1 || ldv < p->n_h || ldy < std::max(1, k) ||
+        ldf1 < p->n_h || ldf2 < p->n_t)
+        return ST_EINVAL;
+    Ctx c{p, p->stream, p->n_h};
+    int n = p->n_h, nt = p->n_t;
+    int m = ncols + 2 * k;
+    double* L;
+    ST_TRY(st_slot(p, S_LRQ, sizeof(double) * (size_t)n * m, (void**)&L));
+    ST_TRY(st_stage_matrix(p, F1, ldf1, n, ncols, L));
+    if (k > 0) ST_TRY(st_spmm_ma<double>(p, V, ldv, k, L + (size_t)n * ncols, n, L + (size_t)n * (ncols + k), n, c.s));
+    // Z = [F2, -D_t Y^T, -C_t Y^T] on the host
+    std::vector<double> Yh((size_t)std::max(1, k) * nt), F2h((size_t)nt * ncols);
+    if (k > 0) ST_TRY(read_dev(c, Y, ldy, k, nt, Yh.data(), k));
+    if (st_is_device_ptr(F2)) {
+        ST_TRY(read_dev(c, F2, ldf2, nt, ncols, F2h.data(), nt));
+    } else {
+        for (int j = 0; j < ncols; ++j) std::memcpy(&F2h[(size_t)j * nt], F2 + (size_t)j * ldf2, sizeof(double) * nt);
+    }
+    std::vector<double> Z((size_t)nt * m, 0.0);
+    for (int j = 0; j < ncols; ++j) std::memcpy(&Z[(size_t)j * nt], &F2h[(size_t)j * nt], sizeof(double) * nt);
+    for (int a = 0; a < k; ++a)
+        for (int l = 0; l < nt; ++l) {
+            double y = Yh[(size_t)l * k + a], yp = l > 0 ? Yh[(size_t)(l - 1) * k + a] : 0.0;
+            Z[(size_t)(ncols + a) * nt + l] = -(y - yp);
+            Z[(size_t)(ncols + k + a) * nt + l] = -0.5 * p->dt * (y + yp);
+        }
+    double num = 0.0, den = 0.0;
+    ST_TRY(lowrank_fro(c, L, m, Z, nt, &num));
+    // ||F||: QR of F1 alone
+    ST_TRY(st_stage_matrix(p, F1, ldf1, n, ncols, L));
+    std::vector<double> Zf(F2h);
+    ST_TRY(lowrank_fro(c, L, ncols, Zf, nt, &den));
+    *relres = den > 0 ? num / den : num;
+    return ST_OK;
+}

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+
+import ctypes
+import re
+import subprocess
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1912_10082_gb300.build import build
+
+    path = build()
+    return ctypes.CDLL(str(path))
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(st_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("st_setup", "st_apply", "st_solve", "st_residual", "st_timestep_cn", "st_destroy",
+                     "st_error_string"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_declared_symbol():
+    import paper_1912_10082_gb300 as st
+
+    assert set(declared_functions()) <= set(st.ABI_SYMBOLS)
+
+
+def test_error_strings_without_gpu(lib):
+    lib.st_error_string.restype = ctypes.c_char_p
+    assert lib.st_error_string(0) == b"ok"
+    assert lib.st_error_string(-3).startswith(b"not converged")
+    lib.st_setup.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.st_setup(None, None) == -1          # host-side argument check, no GPU call
+
+
+def test_struct_layouts_match_c(tmp_path):
+    """sizeof/offsetof of the ABI structs seen by gcc equal the ctypes mirrors."""
+    import paper_1912_10082_gb300 as st
+
+    fields = {"st_desc": st.StDesc, "st_solution": st.StSolution, "st_stats": st.StStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "st.h"', "int main(void){"]
+    for cname, cls in fields.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.splitlines())
+    for cname, cls in fields.items():
+        assert int(out[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
