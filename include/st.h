@@ -164,6 +164,27 @@ int st_rhs_manufactured(st_problem* p, double* F1, int ldf1, double* F2, int ldf
 int st_shift_solve(st_problem* p, double s, const double* X, int ldx, int ncols,
                    double* W, int ldw, int precision);
 
+/* st_shift_solve_noalloc -- the FP64 shifted solve of st_shift_solve,
+ * W = (A + s M)^{-1} M X, for callers that cannot allocate device memory
+ * while they run: code recording its own stream capture, or a real-time
+ * loop whose memory is fixed after start-up, where a cudaMalloc (which can
+ * synchronise the device or fail) is not allowed.  st_shift_solve may grow a
+ * workspace owned by the handle; this call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  The paper has no counterpart.
+ * Scratch: a file-scope device array of 4,194,304 doubles (32 MiB), present
+ * on every GPU that loads the library until the process exits; calls with
+ * n_h * ncols above that return ST_EINVAL (text in st_last_error).  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array (each call overwrites it completely before reading it),
+ * so calls that overlap on the GPU, on any stream, race.  X and W: device
+ * double, n_h x ncols, ld >= n_h, may alias.  Work is issued on the handle's
+ * stream; asynchronous.  ST_ENOTSUP without the tensor-grid heat solver. */
+int st_shift_solve_noalloc(st_problem* p, double s, const double* X, int ldx, int ncols, double* W, int ldw);
+
+/* st_shift_solve_noalloc_max -- capacity of that scratch array in doubles. */
+unsigned long st_shift_solve_noalloc_max(void);
+
 /* st_solve -- rational Krylov Galerkin projection (RKSM) for (1) (Section 4):
  * compress F to a full-column-rank F1 (QR + SVD), grow an orthonormal basis
  * V of the rational Krylov space of the pencil (A, M) started from M^{-1} F1

@@ -31,6 +31,7 @@ ABI_SYMBOLS = (
     "st_setup", "st_destroy", "st_problem_info", "st_get_csr", "st_apply", "st_rhs_manufactured",
     "st_shift_solve", "st_solve", "st_residual", "st_residual_lowrank", "st_timestep_cn",
     "st_error_string", "st_last_error", "st_launch_count", "st_profile_begin", "st_profile_end",
+    "st_shift_solve_noalloc", "st_shift_solve_noalloc_max",
 )
 
 
@@ -95,6 +96,8 @@ def lib() -> C.CDLL:
         "st_error_string": ([i], C.c_char_p),
         "st_last_error": ([], C.c_char_p),
         "st_launch_count": ([], C.c_ulonglong),
+        "st_shift_solve_noalloc": ([vp, d, vp, i, i, vp, i], i),
+        "st_shift_solve_noalloc_max": ([], C.c_ulong),
         "st_profile_begin": ([], i),
         "st_profile_end": ([C.POINTER(StKernelTime), i, C.POINTER(i)], i),
     }

@@ -25,6 +25,7 @@
     do { int s__ = (expr); if (s__ != ST_OK) return s__; } while (0)
 
 void st_note_cuda(cudaError_t e, const char* what, const char* file, int line);
+void st_note_msg(const char* msg);   // sets the text returned by st_last_error
 
 // launch accounting and optional event timing (st_profile.cu)
 void st_count_launch();

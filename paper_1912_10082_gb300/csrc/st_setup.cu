@@ -15,6 +15,8 @@ void st_note_cuda(cudaError_t e, const char* what, const char* file, int line) {
     std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
+void st_note_msg(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 extern "C" const char* st_last_error(void) { return g_last_error; }
 
 extern "C" const char* st_error_string(int status) {
