@@ -112,7 +112,8 @@ typedef struct st_stats {
                              iteration (Section 5, Table 1: mu_mem = Its + 1 for a rank-1 load) */
     double relres;        /* final relative residual, FP64 */
     double ms_total;      /* wall time of the call (host clock) */
-    double ms_phase[8];   /* 0 compress, 1 shifted solves, 2 orthogonalisation, 3 projection,
+    double ms_phase[8];   /* host clock between synchronisation points: 0 compress, 1 shifted solves and
+                             block Gram-Schmidt, 2 block QR, 3 products of the new block,
                              4 projected solve, 5 residual, 6 output, 7 other */
     double shift_min, shift_max;  /* extremes of the shifts s used, as (A + s M)^{-1} */
 } st_stats;
@@ -222,11 +223,86 @@ int st_residual_lowrank(st_problem* p, const double* V, int ldv, const double* Y
 int st_timestep_cn(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
                    double* U, int ldu);
 
+/* st_set_coefficients -- change the operator and its coefficients of a box
+ * problem in place (same grid, time grid and controls): op ST_HEAT with
+ * kappa (> 0; 0 means 1.0), or ST_CONVDIFF with eps > 0 and beta[3]
+ * (beta may be NULL for zero velocity).  Re-runs the device assembly of
+ * M, A, P = M + dt/2 A, N = M - dt/2 A (Section 3) on the handle's stream;
+ * the grid-only fast-diagonalisation tables are kept.  Asynchronous.
+ * ST_ENOTSUP for user CSR problems (dim == 0). */
+int st_set_coefficients(st_problem* p, int op, double kappa, double eps, const double* beta);
+
 /* st_error_string -- static text for a status code. */
 const char* st_error_string(int status);
 
 /* st_last_error -- text of the last CUDA failure seen by this thread. */
 const char* st_last_error(void);
+
+/* ---- many independent solves on one GPU: batched and served workloads ----
+ * The paper solves one problem at a time; the executor runs many solves of
+ * the Section 4 method at once.  `slots` worker threads each own a CUDA
+ * stream and a cache of problem handles keyed by geometry (operators and
+ * fast-diagonalisation tables stay on the device between requests; a new
+ * coefficient re-runs the assembly only).  Requests are admitted in arrival
+ * order as long as their estimated device footprint (st_request_bytes) fits
+ * the free part of the HBM budget; a request that does not fit is passed
+ * over until memory frees up, and one larger than the whole budget runs when
+ * nothing else does.  A slot takes the next admissible request as soon as its
+ * previous one finishes (continuous batching): work of requests that arrived
+ * at different times overlaps on the device.  A solve reads and writes only
+ * its own handle, so its result is the same alone and in a mix. */
+typedef struct st_executor st_executor;
+
+typedef struct st_request {
+    st_desc desc;            /* box problem (dim 1..3) and solver controls; desc.stream is ignored */
+    const double* F1;        /* n_h x p load factor, host or device; valid until the result is returned */
+    int ldf1;
+    const double* F2;        /* n_t x p load factor, host or device */
+    int ldf2;
+    int p;                   /* 1 <= p <= 16 */
+    double* U_out;           /* optional n_h x n_t buffer (host or device) receiving U = V Y; NULL: none */
+    int ldu;                 /* leading dimension of U_out (>= n_h) */
+    unsigned long long tag;  /* the caller's identifier, returned with the result */
+} st_request;
+
+typedef struct st_result {
+    unsigned long long tag;  /* st_request.tag */
+    int status;              /* status of the solve (ST_OK, ST_ENOTCONV, ...) or of its set-up */
+    int slot;                /* worker slot that ran the request */
+    int k;                   /* basis columns of the solution */
+    double bytes_reserved;   /* admission estimate held while the request ran */
+    double t_submit, t_start, t_end;   /* seconds on the executor clock (st_executor_now) */
+    st_stats stats;          /* statistics of the solve */
+} st_result;
+
+/* st_request_bytes -- admission estimate of a request's device footprint:
+ * operators, tables, a basis V and M V of min(max_basis, p (min(maxit,80)+1))
+ * columns, the N_h-sized work blocks and Y.  0 for invalid descriptors. */
+double st_request_bytes(const st_desc* d, int p);
+
+/* st_executor_create -- start `slots` (1..256) worker threads on the current
+ * device with an HBM budget in bytes (<= 0: 80% of the free memory). */
+int st_executor_create(int slots, double hbm_budget_bytes, st_executor** out);
+
+/* st_executor_submit -- queue a request (copied; the F1, F2 and U_out
+ * buffers it points to must stay valid until its result is returned).
+ * ST_EINVAL for bad sizes or after st_executor_destroy began. */
+int st_executor_submit(st_executor* ex, const st_request* req);
+
+/* st_executor_wait -- move up to `max` finished results into out[] (out may be
+ * NULL to discard them), waiting up to timeout_s seconds for the first one
+ * (<= 0: do not wait).  *count receives the number moved. */
+int st_executor_wait(st_executor* ex, st_result* out, int max, int* count, double timeout_s);
+
+/* st_executor_pending -- requests still queued and running (host outputs, may be NULL). */
+int st_executor_pending(st_executor* ex, int* queued, int* running);
+
+/* st_executor_now -- seconds since the executor was created (its clock). */
+double st_executor_now(st_executor* ex);
+
+/* st_executor_destroy -- drop queued requests, let running ones finish, join
+ * the workers and free their handles.  NULL is accepted. */
+int st_executor_destroy(st_executor* ex);
 
 /* ---- launch accounting and kernel timing (tracing; no counterpart in the paper) ---- */
 

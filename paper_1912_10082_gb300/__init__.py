@@ -31,7 +31,9 @@ ABI_SYMBOLS = (
     "st_setup", "st_destroy", "st_problem_info", "st_get_csr", "st_apply", "st_rhs_manufactured",
     "st_shift_solve", "st_solve", "st_residual", "st_residual_lowrank", "st_timestep_cn",
     "st_error_string", "st_last_error", "st_launch_count", "st_profile_begin", "st_profile_end",
-    "st_shift_solve_noalloc", "st_shift_solve_noalloc_max",
+    "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
+    "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
+    "st_executor_destroy",
 )
 
 
@@ -60,6 +62,22 @@ class StStats(C.Structure):
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "ms_phase"}
         d["ms_phase"] = list(self.ms_phase)
+        return d
+
+
+class StRequest(C.Structure):
+    _fields_ = [("desc", StDesc), ("F1", C.c_void_p), ("ldf1", C.c_int), ("F2", C.c_void_p), ("ldf2", C.c_int),
+                ("p", C.c_int), ("U_out", C.c_void_p), ("ldu", C.c_int), ("tag", C.c_ulonglong)]
+
+
+class StResult(C.Structure):
+    _fields_ = [("tag", C.c_ulonglong), ("status", C.c_int), ("slot", C.c_int), ("k", C.c_int),
+                ("bytes_reserved", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_end", C.c_double), ("stats", StStats)]
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "stats"}
+        d["stats"] = self.stats.as_dict()
         return d
 
 
@@ -98,6 +116,14 @@ def lib() -> C.CDLL:
         "st_launch_count": ([], C.c_ulonglong),
         "st_shift_solve_noalloc": ([vp, d, vp, i, i, vp, i], i),
         "st_shift_solve_noalloc_max": ([], C.c_ulong),
+        "st_set_coefficients": ([vp, i, d, d, vp], i),
+        "st_request_bytes": ([C.POINTER(StDesc), i], d),
+        "st_executor_create": ([i, d, C.POINTER(vp)], i),
+        "st_executor_submit": ([vp, C.POINTER(StRequest)], i),
+        "st_executor_wait": ([vp, C.POINTER(StResult), i, C.POINTER(i), d], i),
+        "st_executor_pending": ([vp, C.POINTER(i), C.POINTER(i)], i),
+        "st_executor_now": ([vp], d),
+        "st_executor_destroy": ([vp], i),
         "st_profile_begin": ([], i),
         "st_profile_end": ([C.POINTER(StKernelTime), i, C.POINTER(i)], i),
     }
@@ -168,6 +194,23 @@ def empty_colmajor(rows: int, cols: int, dtype=None, device="cuda"):
     return torch.empty((cols, rows), dtype=dtype, device=device).t()
 
 
+def make_desc(dim: int, n, n_t: int, T: float = 1.0, kappa: float = 1.0, *, length=None, op: int = ST_HEAT,
+              eps: float = 0.0, beta=(0.0, 0.0, 0.0), precision: int = ST_FP64, tol: float = 1e-8,
+              maxit: int = 0, max_basis: int = 0) -> StDesc:
+    """An st_desc for a box problem (see include/st.h for every field)."""
+    d = StDesc()
+    d.dim = int(dim)
+    ns = [int(n)] * 3 if np.isscalar(n) else list(n) + [1] * (3 - len(n))
+    for i in range(3):
+        d.n[i] = int(ns[i]) if i < max(dim, 1) else 1
+        d.length[i] = float(length[i]) if length is not None and i < len(length) else 1.0
+        d.beta[i] = float(beta[i]) if i < len(beta) else 0.0
+    d.op, d.kappa, d.eps = int(op), float(kappa), float(eps)
+    d.n_t, d.T = int(n_t), float(T)
+    d.precision, d.tol, d.maxit, d.max_basis = int(precision), float(tol), int(maxit), int(max_basis)
+    return d
+
+
 class Problem:
     """Owns one st_problem handle (see include/st.h for every argument)."""
 
@@ -175,16 +218,8 @@ class Problem:
                  op: int = ST_HEAT, eps: float = 0.0, beta=(0.0, 0.0, 0.0), precision: int = ST_FP64,
                  tol: float = 1e-8, maxit: int = 0, max_basis: int = 0, stream=None, csr=None):
         L = lib()
-        d = StDesc()
-        d.dim = int(dim)
-        ns = [int(n)] * 3 if np.isscalar(n) else list(n) + [1] * (3 - len(n))
-        for i in range(3):
-            d.n[i] = int(ns[i]) if i < max(dim, 1) else 1
-            d.length[i] = float(length[i]) if length is not None and i < len(length) else 1.0
-            d.beta[i] = float(beta[i]) if i < len(beta) else 0.0
-        d.op, d.kappa, d.eps = int(op), float(kappa), float(eps)
-        d.n_t, d.T = int(n_t), float(T)
-        d.precision, d.tol, d.maxit, d.max_basis = int(precision), float(tol), int(maxit), int(max_basis)
+        d = make_desc(dim, n, n_t, T, kappa, length=length, op=op, eps=eps, beta=beta, precision=precision,
+                      tol=tol, maxit=maxit, max_basis=max_basis)
         self._keep = []
         if csr is not None:
             row_ptr, col, mv, av = (np.ascontiguousarray(csr[0], dtype=np.int32),
@@ -222,6 +257,10 @@ class Problem:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_coefficients(self, op: int = ST_HEAT, kappa: float = 1.0, eps: float = 0.0, beta=(0.0, 0.0, 0.0)):
+        b = (C.c_double * 3)(*[float(x) for x in (list(beta) + [0.0] * 3)[:3]])
+        _check(lib().st_set_coefficients(self.h, int(op), float(kappa), float(eps), b), "st_set_coefficients")
 
     # -- set-up data ---------------------------------------------------------
     def get_csr(self):
@@ -304,6 +343,75 @@ class Problem:
         pu, lu, _, _ = _ptr_ld(U)
         _check(lib().st_timestep_cn(self.h, p1, l1, p2, l2, m, pu, lu), "st_timestep_cn")
         return U
+
+
+def request_bytes(desc: StDesc, p: int) -> float:
+    """Admission estimate of one request's device footprint in bytes."""
+    return float(lib().st_request_bytes(C.byref(desc), int(p)))
+
+
+class Executor:
+    """Many independent solves on one GPU (st_executor_*; see include/st.h).
+
+    ``submit`` copies the request; the load factors (and the optional output
+    buffer) are kept alive here until their result has been collected by
+    ``wait``.
+    """
+
+    def __init__(self, slots: int = 16, hbm_budget_bytes: float = 0.0):
+        h = C.c_void_p()
+        _check(lib().st_executor_create(int(slots), float(hbm_budget_bytes), C.byref(h)), "st_executor_create")
+        self.h = h
+        self._live = {}
+
+    def now(self) -> float:
+        return float(lib().st_executor_now(self.h))
+
+    def submit(self, desc: StDesc, F1, F2, tag: int, U_out=None):
+        r = StRequest()
+        r.desc = desc
+        p1, l1, _, m = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        r.F1, r.ldf1, r.F2, r.ldf2, r.p, r.tag = p1, l1, p2, l2, m, int(tag)
+        if U_out is not None:
+            pu, lu, _, _ = _ptr_ld(U_out)
+            r.U_out, r.ldu = pu, lu
+        self._live[int(tag)] = (F1, F2, U_out)
+        _check(lib().st_executor_submit(self.h, C.byref(r)), "st_executor_submit")
+
+    def wait(self, max_results: int = 256, timeout: float = 0.05):
+        arr = (StResult * max_results)()
+        cnt = C.c_int()
+        _check(lib().st_executor_wait(self.h, arr, max_results, C.byref(cnt), float(timeout)), "st_executor_wait")
+        out = []
+        for i in range(cnt.value):
+            d = arr[i].as_dict()
+            self._live.pop(int(d["tag"]), None)
+            out.append(d)
+        return out
+
+    def pending(self):
+        q, r = C.c_int(), C.c_int()
+        _check(lib().st_executor_pending(self.h, C.byref(q), C.byref(r)), "st_executor_pending")
+        return q.value, r.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().st_executor_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

@@ -66,7 +66,9 @@ struct st_problem {
     double *m64 = nullptr, *a64 = nullptr, *p64 = nullptr, *q64 = nullptr;   // M, A, P=M+dt/2A, N=M-dt/2A
     float *m32 = nullptr, *a32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     FdAxis ax[3];
-    double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M)
+    double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M), or of its diffusion part
+    double fd_lam_min = 0.0, fd_lam_max = 0.0;   // the same for unit diffusion (sums of 1D sine-mode eigenvalues)
+    double fd_kappa = 1.0;                 // diffusion the fast-diagonalisation transforms use
     std::vector<void*> owned;              // every device allocation of the handle
     // solution of the last st_solve (device, owned)
     double* V = nullptr;
@@ -84,6 +86,12 @@ struct st_problem {
     // grow-only device workspace slots
     void* slot_ptr[24] = {};
     size_t slot_bytes[24] = {};
+    // staging area of the solver's synchronisation points: sm_dev holds
+    // [download region | upload region] of sm_cap doubles each on the device,
+    // sm_host the pinned host mirror of both
+    double* sm_dev = nullptr;
+    double* sm_host = nullptr;
+    size_t sm_cap = 0;
 };
 
 // Returns a device buffer of at least `bytes` for slot `id` (contents not kept on growth).
@@ -128,6 +136,9 @@ int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, co
                  double beta, double* W, int ldw, cudaStream_t s);
 // W = W * R^{-1} for upper triangular R (m x m, device), in place
 int st_trsm_right_upper(int n, int m, const double* R, int ldr, double* W, int ldw, cudaStream_t s);
+// R (upper, m x m, ld ldr, device) with R^T R = G (m x m, ld ldg, device), m <= 16, by one warp.
+// On a non-positive pivot *flag (device) is set to 1 and R to the identity; else *flag = 0.
+int st_chol_small(int m, const double* G, int ldg, double* R, int ldr, double* flag, cudaStream_t s);
 
 // small vector helpers
 int st_copy_cols64(int n, int m, const double* X, int ldx, double* Y, int ldy, cudaStream_t s);

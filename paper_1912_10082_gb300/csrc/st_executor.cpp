@@ -1,0 +1,295 @@
+// Executor for many independent space-time solves on one GPU: the batched and
+// served workloads of the library (no counterpart in the paper, which solves
+// one problem at a time; each solve here is the paper's Section 4 method).
+//
+// Design.  `slots` worker threads each own a CUDA stream and a small cache of
+// problem handles keyed by geometry, so operators and fast-diagonalisation
+// tables stay on the device between requests; a new diffusion coefficient
+// only re-runs the assembly kernel.  Requests wait in one queue and are
+// admitted in arrival order, skipping ahead past requests whose estimated
+// device footprint does not fit the free part of the HBM budget (a request
+// larger than the whole budget runs when nothing else does).  A slot takes
+// the next admissible request as soon as its previous one finishes, so work
+// of requests that arrived at different times overlaps on the device
+// (continuous batching).  Each solve touches only its own handle, so a
+// result does not depend on what else is running.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "st_common.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    st_request req;
+    double t_submit = 0.0;
+    double est = 0.0;
+};
+
+struct GeomKey {
+    int dim, n0, n1, n2, n_t, precision, maxit, max_basis;
+    double l0, l1, l2, T, tol;
+    bool operator==(const GeomKey& o) const { return std::memcmp(this, &o, sizeof(GeomKey)) == 0; }
+};
+
+GeomKey key_of(const st_desc& d) {
+    GeomKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.dim = d.dim;
+    k.n0 = d.n[0];
+    k.n1 = d.dim > 1 ? d.n[1] : 1;
+    k.n2 = d.dim > 2 ? d.n[2] : 1;
+    k.n_t = d.n_t;
+    k.precision = d.precision;
+    k.maxit = d.maxit;
+    k.max_basis = d.max_basis;
+    k.l0 = d.length[0];
+    k.l1 = d.dim > 1 ? d.length[1] : 0.0;
+    k.l2 = d.dim > 2 ? d.length[2] : 0.0;
+    k.T = d.T;
+    k.tol = d.tol;
+    return k;
+}
+
+}  // namespace
+
+struct st_executor {
+    int device = 0;
+    int nslots = 0;
+    double budget = 0.0, used = 0.0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Job> queue;
+    std::deque<st_result> done;
+    std::vector<std::thread> threads;
+    bool stop = false;
+    int running = 0;
+    Clock::time_point t0;
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+// Estimated device bytes of one solve: operators, fast-diagonalisation tables,
+// a basis V and M V of k_est columns, the N_h-sized work blocks and Y.
+extern "C" double st_request_bytes(const st_desc* d, int p) {
+    if (!d || d->dim < 1 || d->dim > 3 || p < 1) return 0.0;
+    double nh = 1.0, nnz = 1.0, tab = 0.0;
+    for (int i = 0; i < d->dim; ++i) {
+        nh *= d->n[i];
+        nnz *= 3.0 * d->n[i] - 2.0;
+        tab += 12.0 * d->n[i] * d->n[i] + 16.0 * d->n[i];
+    }
+    int maxit = d->maxit > 0 ? d->maxit : 400;
+    int maxb = d->max_basis > 0 ? d->max_basis : 2048;
+    double k_est = std::min<double>(maxb + 16, (double)p * (std::min(maxit, 80) + 1));
+    double csr = nnz * (4.0 + 4 * 8.0 + 4 * 4.0) + 4.0 * (nh + 1);
+    double blocks = 8.0 * nh * (2.0 * k_est + 12.0 * p);
+    double y = 8.0 * k_est * d->n_t;
+    return csr + tab + blocks + y;
+}
+
+namespace {
+
+bool pick(st_executor* ex, size_t* idx) {
+    for (size_t i = 0; i < ex->queue.size(); ++i) {
+        if (ex->used + ex->queue[i].est <= ex->budget) {
+            *idx = i;
+            return true;
+        }
+    }
+    if (ex->running == 0 && !ex->queue.empty()) {
+        *idx = 0;
+        return true;
+    }
+    return false;
+}
+
+int run_one(st_executor* ex, cudaStream_t s, std::vector<std::pair<GeomKey, st_problem*>>& cache, const Job& job,
+            st_result& res) {
+    st_desc d = job.req.desc;
+    d.stream = s;
+    GeomKey key = key_of(d);
+    st_problem* h = nullptr;
+    for (size_t i = 0; i < cache.size(); ++i)
+        if (cache[i].first == key) {
+            h = cache[i].second;
+            std::rotate(cache.begin(), cache.begin() + i, cache.begin() + i + 1);   // most recent first
+            break;
+        }
+    if (h) {
+        ST_TRY(st_set_coefficients(h, d.op, d.kappa, d.eps, d.beta));
+    } else {
+        ST_TRY(st_setup(&d, &h));
+        // keep handles whose operators are small; large ones are rebuilt per request
+        if ((double)h->nnz * 52.0 <= 512.0 * 1024 * 1024) {
+            cache.insert(cache.begin(), {key, h});
+            if (cache.size() > 2) {
+                st_destroy(cache.back().second);
+                cache.pop_back();
+            }
+        }
+    }
+    bool cached = !cache.empty() && cache.front().second == h;
+    st_solution sol{};
+    double* Ud = nullptr;
+    bool host_out = false;
+    if (job.req.U_out) {
+        if (st_is_device_ptr(job.req.U_out)) {
+            Ud = job.req.U_out;
+            sol.ldu = job.req.ldu;
+        } else {
+            host_out = true;
+            int st = st_slot(h, 23, sizeof(double) * (size_t)h->n_h * h->n_t, (void**)&Ud);
+            if (st != ST_OK) {
+                if (!cached) st_destroy(h);
+                return st;
+            }
+            sol.ldu = h->n_h;
+        }
+        sol.U_dense = Ud;
+    }
+    int st = st_solve(h, job.req.F1, job.req.ldf1, job.req.F2, job.req.ldf2, job.req.p, &sol, &res.stats);
+    res.k = sol.k;
+    if (host_out && (st == ST_OK || st == ST_ENOTCONV)) {
+        cudaError_t e = cudaMemcpy2DAsync(job.req.U_out, sizeof(double) * job.req.ldu, Ud, sizeof(double) * h->n_h,
+                                          sizeof(double) * h->n_h, h->n_t, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st_note_cuda(e, "executor result copy", __FILE__, __LINE__);
+            st = ST_ECUDA;
+        }
+    }
+    if (!cached) st_destroy(h);
+    return st;
+}
+
+void worker(st_executor* ex, int slot) {
+    cudaSetDevice(ex->device);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    std::vector<std::pair<GeomKey, st_problem*>> cache;
+    while (true) {
+        Job job;
+        {
+            std::unique_lock<std::mutex> lk(ex->mu);
+            size_t idx = 0;
+            ex->cv_work.wait(lk, [&] { return ex->stop || pick(ex, &idx); });
+            if (ex->stop) break;
+            job = ex->queue[idx];
+            ex->queue.erase(ex->queue.begin() + (long)idx);
+            ex->used += job.est;
+            ex->running++;
+        }
+        st_result res{};
+        res.tag = job.req.tag;
+        res.slot = slot;
+        res.bytes_reserved = job.est;
+        res.t_submit = job.t_submit;
+        res.t_start = ex->now();
+        res.status = run_one(ex, s, cache, job, res);
+        res.t_end = ex->now();
+        {
+            std::lock_guard<std::mutex> lk(ex->mu);
+            ex->used -= job.est;
+            ex->running--;
+            ex->done.push_back(res);
+        }
+        ex->cv_done.notify_all();
+        ex->cv_work.notify_all();
+    }
+    for (auto& kv : cache) st_destroy(kv.second);
+    if (s) cudaStreamDestroy(s);
+}
+
+}  // namespace
+
+extern "C" int st_executor_create(int slots, double hbm_budget_bytes, st_executor** out) {
+    if (!out) return ST_EINVAL;
+    *out = nullptr;
+    if (slots < 1 || slots > 256) return ST_EINVAL;
+    st_executor* ex = new st_executor();
+    if (cudaGetDevice(&ex->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ex;
+        return ST_ECUDA;
+    }
+    if (hbm_budget_bytes <= 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            delete ex;
+            return ST_ECUDA;
+        }
+        hbm_budget_bytes = 0.8 * (double)fr;
+    }
+    ex->budget = hbm_budget_bytes;
+    ex->nslots = slots;
+    ex->t0 = Clock::now();
+    for (int i = 0; i < slots; ++i) ex->threads.emplace_back(worker, ex, i);
+    *out = ex;
+    return ST_OK;
+}
+
+extern "C" double st_executor_now(st_executor* ex) { return ex ? ex->now() : 0.0; }
+
+extern "C" int st_executor_submit(st_executor* ex, const st_request* req) {
+    if (!ex || !req || !req->F1 || !req->F2 || req->p < 1 || req->p > 16) return ST_EINVAL;
+    const st_desc& d = req->desc;
+    if (d.dim < 1 || d.dim > 3 || d.n_t < 1 || !(d.T > 0)) return ST_EINVAL;
+    Job job;
+    job.req = *req;
+    job.t_submit = ex->now();
+    job.est = st_request_bytes(&d, req->p);
+    {
+        std::lock_guard<std::mutex> lk(ex->mu);
+        if (ex->stop) return ST_EINVAL;
+        ex->queue.push_back(job);
+    }
+    ex->cv_work.notify_one();
+    return ST_OK;
+}
+
+extern "C" int st_executor_wait(st_executor* ex, st_result* out, int max, int* count, double timeout_s) {
+    if (!ex || !count || max < 0) return ST_EINVAL;
+    *count = 0;
+    std::unique_lock<std::mutex> lk(ex->mu);
+    auto ready = [&] { return !ex->done.empty(); };
+    if (timeout_s > 0)
+        ex->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready);
+    int n = 0;
+    while (n < max && !ex->done.empty()) {
+        if (out) out[n] = ex->done.front();
+        ex->done.pop_front();
+        ++n;
+    }
+    *count = n;
+    return ST_OK;
+}
+
+extern "C" int st_executor_pending(st_executor* ex, int* queued, int* running) {
+    if (!ex) return ST_EINVAL;
+    std::lock_guard<std::mutex> lk(ex->mu);
+    if (queued) *queued = (int)ex->queue.size();
+    if (running) *running = ex->running;
+    return ST_OK;
+}
+
+extern "C" int st_executor_destroy(st_executor* ex) {
+    if (!ex) return ST_OK;
+    {
+        std::lock_guard<std::mutex> lk(ex->mu);
+        ex->stop = true;
+        ex->queue.clear();
+    }
+    ex->cv_work.notify_all();
+    for (auto& t : ex->threads) t.join();
+    delete ex;
+    return ST_OK;
+}

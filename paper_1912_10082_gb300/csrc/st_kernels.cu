@@ -291,14 +291,30 @@ template <typename T>
 int launch_gemm_rr(int M, int N, int K, const T* A, long long lda, const T* B, long long ldb, T* C, long long ldc,
                    int batch, const Batch2& bt, const FdEpi& ep, cudaStream_t s, const char* tag) {
     if (M <= 0 || N <= 0 || batch <= 0) return ST_OK;
-    long long tiles64 = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
-    bool small = tiles64 < 2 * 152;
-    int bm = small ? 32 : 64;
+    // Tile edge 16, 32 or 64 (1, 2 or 4 outputs per thread and direction).
+    // The busiest of the 152 SMs computes about ceil(tiles / 152) * edge^2
+    // outputs.  FP64 FMAs are so slow on this chip (2 per clock per SM) that
+    // this balance alone decides an FP64 product's time; in FP32 a small tile
+    // also pays 2/TM shared loads per FMA, weighted in as 1/efficiency.  The
+    // cheapest wins; ties go to the larger tile.
+    int bm = 64;
+    double best = 1e300;
+    for (int e : {64, 32, 16}) {
+        long long tiles = (long long)((N + e - 1) / e) * ((M + e - 1) / e) * batch;
+        double eff = sizeof(T) == 8 ? 1.0 : (double)e / 64.0;
+        double share = (double)((tiles + 151) / 152) * e * e / eff;
+        if (share < 0.999 * best) {
+            best = share;
+            bm = e;
+        }
+    }
     dim3 grid((N + bm - 1) / bm, (M + bm - 1) / bm, batch);
     if (grid.y > 65535 || grid.z > 65535) return ST_EINVAL;
     double bytes = (double)sizeof(T) * ((double)M * K + ((double)K * N + (double)M * N) * batch);
     st_prof_begin(s, tag, bytes, 2.0 * M * N * (double)K * batch);
-    if (small)
+    if (bm == 16)
+        k_gemm_rr<T, 1><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bt, ep);
+    else if (bm == 32)
         k_gemm_rr<T, 2><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bt, ep);
     else
         k_gemm_rr<T, 4><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bt, ep);
@@ -358,14 +374,21 @@ __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_partial(int n, int k, int 
     }
 }
 
+// One warp per output entry: lanes take every 32nd chunk, then a fixed
+// butterfly sums the lanes, so the result does not depend on scheduling.
 __global__ void k_ts_reduce(int nchunks, int k, int m, const double* __restrict__ part, double* __restrict__ H,
                             long long ldh) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int idx = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x % 32;
     if (idx >= k * m) return;
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * k * m + idx];
-    int a = idx / m, b = idx % m;
-    H[(size_t)b * ldh + a] = s;
+    for (int c = lane; c < nchunks; c += 32) s += part[(size_t)c * k * m + idx];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        int a = idx / m, b = idx % m;
+        H[(size_t)b * ldh + a] = s;
+    }
 }
 
 // W = beta W + alpha V H, thread per row, H staged through shared memory.
@@ -426,6 +449,41 @@ __global__ void k_trsm_right_upper(int n, int m, const double* __restrict__ R, l
 #pragma unroll
     for (int j = 0; j < kMaxCols; ++j)
         if (j < m) W[(size_t)j * ldw + r] = x[j];
+}
+
+// Cholesky factor of a small SPD matrix by one warp, lane i owning row i of
+// the lower factor L (R = L^T): column j is scaled by its pivot, then each
+// lane updates its row of the trailing block.
+__global__ void k_chol_small(int m, const double* __restrict__ G, long long ldg, double* __restrict__ R,
+                             long long ldr, double* __restrict__ flag) {
+    __shared__ double a[kMaxCols][kMaxCols + 1];
+    int t = threadIdx.x;
+    for (int idx = t; idx < m * m; idx += 32) a[idx % m][idx / m] = G[(size_t)(idx / m) * ldg + idx % m];
+    __syncwarp();
+    bool bad = false;
+    for (int j = 0; j < m; ++j) {
+        double d = a[j][j];   // the same shared value in every lane: uniform branch
+        if (!(d > 0.0)) {
+            bad = true;
+            break;
+        }
+        double rj = sqrt(d);
+        __syncwarp();
+        if (t > j && t < m) a[t][j] /= rj;
+        if (t == j) a[j][j] = rj;
+        __syncwarp();
+        if (t > j && t < m) {
+            double aij = a[t][j];
+            for (int l = j + 1; l <= t; ++l) a[t][l] -= aij * a[l][j];
+        }
+        __syncwarp();
+    }
+    for (int idx = t; idx < m * m; idx += 32) {
+        int i = idx % m, j = idx / m;   // R(i, j) = L(j, i) for i <= j
+        double v = bad ? (i == j ? 1.0 : 0.0) : (i <= j ? a[j][i] : 0.0);
+        R[(size_t)j * ldr + i] = v;
+    }
+    if (t == 0) *flag = bad ? 1.0 : 0.0;
 }
 
 template <typename S, typename D>
@@ -576,7 +634,7 @@ static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, 
     sc.c1 = dim > 1 ? p->ax[1].c2 : p->ax[0].c2;
     sc.c2 = dim > 2 ? p->ax[2].c2 : p->ax[0].c2;
     sc.kind = kind;
-    sc.kappa = p->kappa;
+    sc.kappa = p->fd_kappa;
     sc.shift = shift;
     sc.coef = 1.0;
     if (kind == FD_MASS_RESOLVENT)
@@ -620,14 +678,14 @@ static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, 
 
 int st_fd_apply64(st_problem* p, FdKind kind, double shift, double coef, const double* X, int ldx, int ncols,
                   double* W, int ldw, double* tmp, cudaStream_t s) {
-    if (!p->tensor_heat) return ST_ENOTSUP;
+    if (p->dim < 1) return ST_ENOTSUP;
     const double* Q[3] = {p->ax[0].Q64, p->ax[1].Q64, p->ax[2].Q64};
     return fd_apply_impl<double>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, "fd_gemm64");
 }
 
 int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const float* X, int ldx, int ncols, float* W,
                   int ldw, float* tmp, cudaStream_t s) {
-    if (!p->tensor_heat) return ST_ENOTSUP;
+    if (p->dim < 1) return ST_ENOTSUP;
     const float* Q[3] = {p->ax[0].Q32, p->ax[1].Q32, p->ax[2].Q32};
     return fd_apply_impl<float>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, "fd_gemm32");
 }
@@ -657,10 +715,10 @@ int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W,
     }
     st_prof_begin(s, "ts_tn", 8.0 * (double)n * (k + m) + 8.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
     k_ts_tn_partial<<<nch, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, partial);
-    st_prof_end(s);
     ST_LAUNCH_CHECK();
     int tot = k * m;
-    k_ts_reduce<<<(tot + 255) / 256, 256, 0, s>>>(nch, k, m, partial, H, ldh);
+    k_ts_reduce<<<(tot + 7) / 8, 256, 0, s>>>(nch, k, m, partial, H, ldh);
+    st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;
 }
@@ -684,6 +742,14 @@ int st_trsm_right_upper(int n, int m, const double* R, int ldr, double* W, int l
     if (n <= 0 || m <= 0) return ST_OK;
     if (m > kMaxCols) return ST_EINVAL;
     k_trsm_right_upper<<<(n + 255) / 256, 256, 0, s>>>(n, m, R, ldr, W, ldw);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_chol_small(int m, const double* G, int ldg, double* R, int ldr, double* flag, cudaStream_t s) {
+    if (m <= 0) return ST_OK;
+    if (m > kMaxCols) return ST_EINVAL;
+    k_chol_small<<<1, 32, 0, s>>>(m, G, ldg, R, ldr, flag);
     ST_LAUNCH_CHECK();
     return ST_OK;
 }

@@ -220,6 +220,37 @@ static int alloc_csr(st_problem* p) {
     return ST_OK;
 }
 
+// Values of M, A, P, N for the problem's current operator and coefficients
+// (pattern and values are written together by one kernel).
+static int assemble_tensor(st_problem* p) {
+    const st_desc& d = p->d;
+    Axis1D a1[3];
+    for (int i = 0; i < 3; ++i) {
+        double h = p->len[i] / (p->n[i] + 1);
+        a1[i].m0 = 4.0 * h / 6.0;
+        a1[i].m1 = h / 6.0;
+        a1[i].k0 = 2.0 / h;
+        a1[i].k1 = -1.0 / h;
+    }
+    int threads = 256;
+    int blocks = (p->n_h + threads - 1) / threads;
+    k_assemble_tensor<<<blocks, threads, 0, p->stream>>>(
+        d.dim, p->n[0], p->n[1], p->n[2], a1[0], a1[1], a1[2], d.op, p->kappa, d.eps, d.beta[0], d.beta[1],
+        d.beta[2], 0.5 * p->dt, p->n_h, p->nnz, p->row_ptr, p->col, p->m64, p->a64, p->p64, p->q64, p->m32,
+        p->a32, p->p32, p->q32);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+// Spectrum bounds of the pencil (A, M) (heat) or of its symmetric diffusion
+// part (convection-diffusion), from the 1D sine-mode eigenvalues.
+static void set_spectrum(st_problem* p) {
+    p->tensor_heat = p->d.op == ST_HEAT;
+    p->fd_kappa = p->d.op == ST_HEAT ? p->kappa : p->d.eps;
+    p->lam_min = p->fd_kappa * p->fd_lam_min;
+    p->lam_max = p->fd_kappa * p->fd_lam_max;
+}
+
 static int setup_tensor(st_problem* p) {
     const st_desc& d = p->d;
     p->dim = d.dim;
@@ -237,25 +268,10 @@ static int setup_tensor(st_problem* p) {
     p->nnz = (int)nnz;
     p->max_row_nnz = d.dim == 1 ? 3 : (d.dim == 2 ? 9 : 27);
     ST_TRY(alloc_csr(p));
-    Axis1D a1[3];
-    for (int i = 0; i < 3; ++i) {
-        double h = p->len[i] / (p->n[i] + 1);
-        a1[i].m0 = 4.0 * h / 6.0;
-        a1[i].m1 = h / 6.0;
-        a1[i].k0 = 2.0 / h;
-        a1[i].k1 = -1.0 / h;
-    }
-    int threads = 256;
-    int blocks = (p->n_h + threads - 1) / threads;
-    k_assemble_tensor<<<blocks, threads, 0, p->stream>>>(
-        d.dim, p->n[0], p->n[1], p->n[2], a1[0], a1[1], a1[2], d.op, p->kappa, d.eps, d.beta[0], d.beta[1],
-        d.beta[2], 0.5 * p->dt, p->n_h, p->nnz, p->row_ptr, p->col, p->m64, p->a64, p->p64, p->q64, p->m32,
-        p->a32, p->p32, p->q32);
-    ST_LAUNCH_CHECK();
-    if (d.op == ST_HEAT) {
-        p->tensor_heat = true;
-        p->lam_min = 0.0;
-        p->lam_max = 0.0;
+    ST_TRY(assemble_tensor(p));
+    {
+        p->fd_lam_min = 0.0;
+        p->fd_lam_max = 0.0;
         for (int i = 0; i < d.dim; ++i) {
             FdAxis& ax = p->ax[i];
             ax.n = p->n[i];
@@ -274,12 +290,11 @@ static int setup_tensor(st_problem* p) {
                 double c = std::cos(M_PI * j / (ax.n + 1.0));
                 return (6.0 / (h * h)) * (2.0 * s * s) / (2.0 + c);
             };
-            p->lam_min += lamj(1);
-            p->lam_max += lamj(ax.n);
+            p->fd_lam_min += lamj(1);
+            p->fd_lam_max += lamj(ax.n);
         }
-        p->lam_min *= p->kappa;
-        p->lam_max *= p->kappa;
     }
+    set_spectrum(p);
     return ST_OK;
 }
 
@@ -316,9 +331,35 @@ static int setup_user_csr(st_problem* p, const st_desc& d) {
 extern "C" int st_destroy(st_problem* p) {
     if (!p) return ST_OK;
     if (p->cn_graph) cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
+    if (p->sm_host) cudaFreeHost(p->sm_host);
     for (void* ptr : p->owned) cudaFree(ptr);
     p->owned.clear();
     delete p;
+    return ST_OK;
+}
+
+extern "C" int st_set_coefficients(st_problem* p, int op, double kappa, double eps, const double* beta) {
+    if (!p) return ST_EINVAL;
+    if (p->dim < 1) return ST_ENOTSUP;
+    if (op != ST_HEAT && op != ST_CONVDIFF) return ST_EINVAL;
+    if (op == ST_CONVDIFF && !(eps > 0)) return ST_EINVAL;
+    if (kappa < 0) return ST_EINVAL;
+    double kap = kappa > 0 ? kappa : 1.0;
+    bool same = op == p->d.op && kap == p->kappa && (op == ST_HEAT || eps == p->d.eps);
+    for (int i = 0; i < 3 && same && op == ST_CONVDIFF; ++i) same = (beta ? beta[i] : 0.0) == p->d.beta[i];
+    if (same) return ST_OK;
+    p->d.op = op;
+    p->kappa = kap;
+    p->d.kappa = kap;
+    p->d.eps = eps;
+    for (int i = 0; i < 3; ++i) p->d.beta[i] = beta ? beta[i] : 0.0;
+    // the captured Crank-Nicolson graph holds the old coefficients
+    if (p->cn_graph) {
+        cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
+        p->cn_graph = nullptr;
+    }
+    ST_TRY(assemble_tensor(p));
+    set_spectrum(p);
     return ST_OK;
 }
 

@@ -366,6 +366,252 @@ struct HostSym {
     double& operator()(int i, int j) { return a[(size_t)j * ld + i]; }
 };
 
+// ---- staging of the small results of one synchronisation point ----
+// The device buffer sm_dev holds a download region [0, cap) that collects the
+// small products the host needs after the next synchronisation, and an upload
+// region [cap, 2 cap) for small host matrices.  The host mirror is pinned, so
+// every synchronisation point costs one device-to-host copy.
+int stage_reserve(st_problem* p, size_t need) {
+    if (p->sm_cap >= need) return ST_OK;
+    size_t cap = std::max<size_t>({need, 2 * p->sm_cap, (size_t)8192});
+    if (p->sm_dev || p->sm_host) ST_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (p->sm_dev) st_free_one(p, p->sm_dev);
+    if (p->sm_host) cudaFreeHost(p->sm_host);
+    p->sm_dev = nullptr;
+    p->sm_host = nullptr;
+    p->sm_cap = 0;
+    ST_TRY(st_alloc(p, (void**)&p->sm_dev, sizeof(double) * 2 * cap));
+    cudaError_t e = cudaMallocHost((void**)&p->sm_host, sizeof(double) * 2 * cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        st_note_cuda(e, "cudaMallocHost", __FILE__, __LINE__);
+        p->sm_host = nullptr;
+        return ST_ENOMEM;
+    }
+    p->sm_cap = cap;
+    return ST_OK;
+}
+
+inline size_t pad32(size_t m) { return (m + 31) & ~size_t(31); }
+
+struct Stage {
+    Ctx& c;
+    size_t down = 0, up = 0;
+    bool overflow = false;
+    explicit Stage(Ctx& cc) : c(cc) {}
+    // device address of the next m doubles of the download region.  Every
+    // caller reserves its phase's total first; if that sizing were ever short,
+    // the request is redirected to the start of the region (in bounds) and
+    // the next fetch reports the error.
+    double* out(size_t m) {
+        if (down + pad32(m) > c.p->sm_cap) {
+            overflow = true;
+            return c.p->sm_dev;
+        }
+        double* d = c.p->sm_dev + down;
+        down += pad32(m);
+        return d;
+    }
+    bool fits() const { return !overflow && down <= c.p->sm_cap && up <= c.p->sm_cap; }
+    const double* host_of(const double* d) const { return c.p->sm_host + (d - c.p->sm_dev); }
+    // copies m host doubles to the device through the pinned upload region
+    int in(const double* h, size_t m, double** d) {
+        size_t off = c.p->sm_cap + up;
+        if (up + pad32(m) > c.p->sm_cap) {
+            st_note_msg("internal error: solver upload area sized too small");
+            return ST_EINVAL;
+        }
+        up += pad32(m);
+        std::memcpy(c.p->sm_host + off, h, sizeof(double) * m);
+        ST_CUDA_TRY(cudaMemcpyAsync(c.p->sm_dev + off, c.p->sm_host + off, sizeof(double) * m,
+                                    cudaMemcpyHostToDevice, c.s));
+        *d = c.p->sm_dev + off;
+        return ST_OK;
+    }
+    // one copy of the download region, then wait for the stream
+    int fetch() {
+        if (!fits()) {
+            st_note_msg("internal error: solver staging area sized too small");
+            return ST_EINVAL;
+        }
+        if (down) ST_CUDA_TRY(cudaMemcpyAsync(c.p->sm_host, c.p->sm_dev, sizeof(double) * down,
+                                              cudaMemcpyDeviceToHost, c.s));
+        ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+        down = 0;
+        up = 0;
+        return ST_OK;
+    }
+};
+
+// H (device, k x m, ld ldh) = V^T W over the n rows.
+int ts_tn_dev(Ctx& c, int k, int m, const double* V, int ldv, const double* W, int ldw, double* H, int ldh) {
+    if (k == 0 || m == 0) return ST_OK;
+    double* part;
+    ST_TRY(st_slot(c.p, S_PART, sizeof(double) * st_tsgemm_partial_elems(c.n, k, m), (void**)&part));
+    return st_tsgemm_tn(c.n, k, m, V, ldv, W, ldw, H, ldh, part, c.s);
+}
+
+// Rank of a block from its Gram matrix G = W^T W (host, m x m) and, when it
+// has full rank and a Cholesky factor, the first CholQR factor R1 = L^T.
+// The rank counts the eigenvalues above drop^2 max(lambda_max, ref2), the
+// rule of block_qr, which handles every block that is not of full rank.
+struct QrPlan {
+    int rank = 0;
+    bool fast = false;
+    std::vector<double> R1;   // m x m upper, ld m
+};
+
+void qr_plan(const double* G, int m, double ref2, double drop, QrPlan& q) {
+    std::vector<double> E(G, G + (size_t)m * m), w(m);
+    dense::sym_eigvals(m, E.data(), m, w.data());
+    double lmax = std::max(w[m - 1], 0.0);
+    double thr = drop * drop * std::max(lmax, ref2);
+    q.rank = 0;
+    for (int i = 0; i < m; ++i) q.rank += w[i] > thr;
+    q.fast = false;
+    if (q.rank == m && w[0] > 1e-24 * lmax) {
+        std::vector<double> L(G, G + (size_t)m * m);
+        if (dense::cholesky(m, L.data(), m)) {
+            q.R1.assign((size_t)m * m, 0.0);
+            for (int j = 0; j < m; ++j)
+                for (int i = 0; i <= j; ++i) q.R1[(size_t)j * m + i] = L[(size_t)i * m + j];
+            q.fast = true;
+        }
+    }
+}
+
+// Device part of CholQR2 for a full-rank block: W <- W R1^{-1}, then the
+// second Gram matrix, its Cholesky factor R2 by one warp, W <- W R2^{-1}.
+// R2 and the pivot flag land in the download region.
+int qr_fast_launch(Ctx& c, Stage& sg, double* W, int ldw, int m, const std::vector<double>& R1, double** dR2,
+                   double** dflag) {
+    double* dR1;
+    ST_TRY(sg.in(R1.data(), (size_t)m * m, &dR1));
+    ST_TRY(st_trsm_right_upper(c.n, m, dR1, m, W, ldw, c.s));
+    double* dG2 = sg.out((size_t)m * m);
+    ST_TRY(ts_tn_dev(c, m, m, W, ldw, W, ldw, dG2, m));
+    *dR2 = sg.out((size_t)m * m);
+    *dflag = sg.out(1);
+    ST_TRY(st_chol_small(m, dG2, m, *dR2, m, *dflag, c.s));
+    ST_TRY(st_trsm_right_upper(c.n, m, *dR2, m, W, ldw, c.s));
+    return ST_OK;
+}
+
+// R = R2 R1 for upper triangular m x m factors (ld m).
+std::vector<double> upper_product(int m, const double* R2, const double* R1) {
+    std::vector<double> R((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i <= j; ++i) {
+            double s = 0.0;
+            for (int q = i; q <= j; ++q) s += R2[(size_t)q * m + i] * R1[(size_t)j * m + q];
+            R[(size_t)j * m + i] = s;
+        }
+    return R;
+}
+
+// Gram matrix Gb = b^T b of the residual direction b = w_hat - M V Mm^{-1} V^T w_hat,
+// w_hat = -(s M q + A q) R_q, evaluated on the device (one extra synchronisation).
+int residual_gram_explicit(Ctx& c, int k, int pn, int pl, double s, const double* MAq, const double* MV,
+                           const std::vector<double>& X1, const HostSym& Mm, const std::vector<double>& Rq,
+                           std::vector<double>& Gb) {
+    st_problem* p = c.p;
+    const int n = c.n;
+    double* Wh;
+    double* Wh2;
+    ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n * pl, (void**)&Wh));
+    ST_TRY(st_slot(p, S_WH2, sizeof(double) * (size_t)n * pl, (void**)&Wh2));
+    std::vector<double> negR((size_t)pn * pl);
+    for (int j = 0; j < pl; ++j)
+        for (int i = 0; i < pn; ++i) negR[(size_t)j * pn + i] = -Rq[(size_t)j * pl + i];
+    ST_TRY(st_copy_cols64(n, pn, MAq + (size_t)n * pn, n, Wh, n, c.s));
+    ST_TRY(st_axpby64(n, pn, s, MAq, n, 1.0, Wh, n, c.s));   // Wh = s Mq + Aq
+    ST_TRY(ts_nn_host(c, pn, pl, 1.0, Wh, n, negR.data(), 0.0, Wh2, n));
+    std::vector<double> Vw((size_t)k * pl, 0.0);
+    for (int j = 0; j < pl; ++j)
+        for (int q = 0; q < pn; ++q) {
+            double rq = -Rq[(size_t)j * pl + q];
+            for (int i = 0; i < k; ++i)
+                Vw[(size_t)j * k + i] += (s * X1[(size_t)q * k + i] + X1[(size_t)(pn + q) * k + i]) * rq;
+        }
+    std::vector<double> L((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) L[(size_t)j * k + i] = Mm.a[(size_t)j * Mm.ld + i];
+    if (!dense::cholesky(k, L.data(), k)) return ST_EBREAKDOWN;
+    dense::chol_solve(k, L.data(), k, Vw.data(), k, pl);
+    ST_TRY(ts_nn_host(c, k, pl, -1.0, MV, n, Vw.data(), 1.0, Wh2, n));
+    Gb.assign((size_t)pl * pl, 0.0);
+    return ts_tn_host(c, pl, pl, Wh2, n, Wh2, n, Gb.data());
+}
+
+// The same Gram matrix from products that phase B already computed:
+// with Wh = s M q + A q and c = Mm^{-1} V^T Wh, b = -(Wh - M V c) R_q and
+// Z^T Z = Wh^T Wh - (MV^T Wh)^T c - c^T (MV^T Wh) + c^T (MV^T MV) c.
+// Returns false when cancellation could spoil it (trace(Z^T Z) tiny next to
+// trace(Wh^T Wh)); the caller then takes the explicit route.
+bool residual_gram_products(int k, int pn, int pl, double s, const std::vector<double>& X1,
+                            const std::vector<double>& X1b, const std::vector<double>& Gq, const HostSym& Mm,
+                            const HostSym& Gmv, const std::vector<double>& Rq, std::vector<double>& Gb) {
+    const int q2 = 2 * pn;
+    std::vector<double> VtWh((size_t)k * pn), MVtWh((size_t)k * pn), WhWh((size_t)pn * pn);
+    for (int j = 0; j < pn; ++j)
+        for (int i = 0; i < k; ++i) {
+            VtWh[(size_t)j * k + i] = s * X1[(size_t)j * k + i] + X1[(size_t)(pn + j) * k + i];
+            MVtWh[(size_t)j * k + i] = s * X1b[(size_t)j * k + i] + X1b[(size_t)(pn + j) * k + i];
+        }
+    for (int j = 0; j < pn; ++j)
+        for (int i = 0; i < pn; ++i)
+            WhWh[(size_t)j * pn + i] = s * s * Gq[(size_t)j * q2 + i] +
+                                       s * (Gq[(size_t)(pn + j) * q2 + i] + Gq[(size_t)j * q2 + pn + i]) +
+                                       Gq[(size_t)(pn + j) * q2 + pn + i];
+    std::vector<double> L((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) L[(size_t)j * k + i] = Mm.a[(size_t)j * Mm.ld + i];
+    if (!dense::cholesky(k, L.data(), k)) return false;
+    std::vector<double> C = VtWh;
+    dense::chol_solve(k, L.data(), k, C.data(), k, pn);
+    std::vector<double> GC((size_t)k * pn, 0.0);   // Gmv C
+    for (int j = 0; j < pn; ++j)
+        for (int q = 0; q < k; ++q) {
+            double cq = C[(size_t)j * k + q];
+            const double* g = &Gmv.a[(size_t)q * Gmv.ld];
+            for (int i = 0; i < k; ++i) GC[(size_t)j * k + i] += g[i] * cq;
+        }
+    std::vector<double> ZZ((size_t)pn * pn);
+    double tz = 0.0, tw = 0.0;
+    for (int j = 0; j < pn; ++j)
+        for (int i = 0; i < pn; ++i) {
+            double a = 0.0, b = 0.0, d = 0.0;
+            for (int q = 0; q < k; ++q) {
+                a += MVtWh[(size_t)i * k + q] * C[(size_t)j * k + q];
+                b += C[(size_t)i * k + q] * MVtWh[(size_t)j * k + q];
+                d += C[(size_t)i * k + q] * GC[(size_t)j * k + q];
+            }
+            ZZ[(size_t)j * pn + i] = WhWh[(size_t)j * pn + i] - a - b + d;
+        }
+    for (int i = 0; i < pn; ++i) {
+        tz += ZZ[(size_t)i * pn + i];
+        tw += WhWh[(size_t)i * pn + i];
+    }
+    if (!(tz > 1e-6 * tw)) return false;
+    Gb.assign((size_t)pl * pl, 0.0);
+    for (int b2 = 0; b2 < pl; ++b2)
+        for (int a2 = 0; a2 < pl; ++a2) {
+            double acc = 0.0;
+            for (int j = 0; j < pn; ++j) {
+                double t = 0.0;
+                for (int i = 0; i < pn; ++i) t += Rq[(size_t)a2 * pl + i] * ZZ[(size_t)j * pn + i];
+                acc += t * Rq[(size_t)b2 * pl + j];
+            }
+            Gb[(size_t)b2 * pl + a2] = acc;
+        }
+    return true;
+}
+
+// RKSM driver.  Each iteration synchronises twice: after phase A (shifted
+// solve, block CGS2 with its coefficients kept on the device, Gram matrices
+// of the new block) and after phase B (CholQR2 finished on the device,
+// products of the new block with V, MV, itself and F1).  Everything k x k
+// runs on the host between the two.
 int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int p0, st_solution* sol,
                st_stats* st) {
     auto t_start = Clock::now();
@@ -376,22 +622,58 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     const double tol = p->d.tol;
     st_stats S{};
     auto tp = Clock::now();
+    Stage sg(c);
 
     // ---- A1: rank compression of F = F1 F2^T ----
     double* F1d;
     ST_TRY(st_slot(p, S_F1D, sizeof(double) * (size_t)n * p0, (void**)&F1d));
     ST_TRY(st_stage_matrix(p, F1, ldf1, n, p0, F1d));
+    const bool f2dev = st_is_device_ptr(F2);
+    ST_TRY(stage_reserve(p, pad32((size_t)p0 * p0) + pad32((size_t)nt * p0)));
+    double* dGF = sg.out((size_t)p0 * p0);
+    ST_TRY(ts_tn_dev(c, p0, p0, F1d, n, F1d, n, dGF, p0));
+    double* dF2 = nullptr;
+    if (f2dev) {
+        dF2 = sg.out((size_t)nt * p0);
+        ST_CUDA_TRY(cudaMemcpy2DAsync(dF2, sizeof(double) * nt, F2, sizeof(double) * ldf2, sizeof(double) * nt, p0,
+                                      cudaMemcpyDeviceToDevice, c.s));
+    }
+    ST_TRY(sg.fetch());
     std::vector<double> F2h((size_t)nt * p0);
-    if (st_is_device_ptr(F2)) {
-        ST_CUDA_TRY(cudaMemcpy2DAsync(F2h.data(), sizeof(double) * nt, F2, sizeof(double) * ldf2, sizeof(double) * nt,
-                                      p0, cudaMemcpyDeviceToHost, c.s));
-        ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+    if (f2dev) {
+        std::memcpy(F2h.data(), sg.host_of(dF2), sizeof(double) * (size_t)nt * p0);
     } else {
         for (int j = 0; j < p0; ++j) std::memcpy(&F2h[(size_t)j * nt], F2 + (size_t)j * ldf2, sizeof(double) * nt);
     }
-    std::vector<double> R1;
-    int r1 = 0;
-    ST_TRY(block_qr(c, F1d, n, p0, 0.0, 1e-14, R1, &r1));   // F1d <- Q1 (n x r1), F1 = Q1 R1
+    // F1 = Q1 R1 from F1^T F1 = E diag(w) E^T: Q1 = F1 E_r w_r^{-1/2}, R1 = w_r^{1/2} E_r^T
+    // over the kept directions.  One Gram product loses orthogonality like
+    // eps cond(F1)^2, so a condition number above 1e4 takes the CholQR2 route.
+    std::vector<double> R1((size_t)p0 * p0, 0.0), T1;   // R1: r1 x p0 in a p0 x p0 array (ld p0)
+    int r1 = 0, src_cols = 0;
+    {
+        std::vector<double> E(sg.host_of(dGF), sg.host_of(dGF) + (size_t)p0 * p0), w(p0);
+        dense::sym_eig(p0, E.data(), p0, w.data());
+        double wmax = std::max(w[p0 - 1], 0.0);
+        for (int i = 0; i < p0; ++i) r1 += (wmax > 0.0 && w[i] > 1e-28 * wmax);
+        bool gram = r1 > 0 && w[p0 - r1] > 1e-8 * wmax;
+        if (gram) {
+            T1.assign((size_t)p0 * r1, 0.0);
+            for (int t = 0; t < r1; ++t) {
+                int e = p0 - r1 + t;
+                double sw = std::sqrt(w[e]);
+                for (int q = 0; q < p0; ++q) {
+                    R1[(size_t)q * p0 + t] = sw * E[(size_t)e * p0 + q];
+                    T1[(size_t)t * p0 + q] = E[(size_t)e * p0 + q] / sw;
+                }
+            }
+            src_cols = p0;
+        } else if (r1 > 0) {
+            ST_TRY(block_qr(c, F1d, n, p0, 0.0, 1e-14, R1, &r1));   // F1d <- Q1 (n x r1), F1 = Q1 R1
+            T1.assign((size_t)r1 * r1, 0.0);
+            for (int t = 0; t < r1; ++t) T1[(size_t)t * r1 + t] = 1.0;
+            src_cols = r1;
+        }
+    }
     // F2 = Q2 R2 (host Householder)
     std::vector<double> Q2 = F2h, R2((size_t)p0 * p0);
     dense::thin_qr(nt, p0, Q2.data(), nt, R2.data(), p0);
@@ -406,16 +688,12 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     int r = 0;
     std::vector<double> Ub, sb, Vbt;
     if (r1 > 0) {
-        Ub.resize((size_t)r1 * p0);
-        sb.resize(p0);
-        Vbt.resize((size_t)p0 * p0);
-        // SVD of B^T (p0 x r1) is easier to pass as m >= n: use B^T when p0 >= r1
+        // SVD of B^T (p0 x r1): B = V2 diag(s2) U2^T
         std::vector<double> Bt((size_t)p0 * r1);
         for (int j = 0; j < p0; ++j)
             for (int i = 0; i < r1; ++i) Bt[(size_t)i * p0 + j] = B[(size_t)j * r1 + i];
         std::vector<double> U2((size_t)p0 * r1), s2(r1), V2t((size_t)r1 * r1);
         dense::svd_small(p0, r1, Bt.data(), p0, U2.data(), s2.data(), V2t.data());
-        // B = V2 diag(s2) U2^T
         for (int i = 0; i < r1; ++i)
             if (s2[i] > 1e-14 * s2[0]) ++r;
         // F1c = Q1 V2[:, :r], F2c = Q2 U2[:, :r] diag(s)
@@ -452,7 +730,19 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     }
     double* F1c;
     ST_TRY(st_slot(p, S_F1C, sizeof(double) * (size_t)n * r, (void**)&F1c));
-    ST_TRY(ts_nn_host(c, r1, r, 1.0, F1d, n, Ub.data(), 0.0, F1c, n));
+    {
+        // F1c = source Tc with source = F1 (Gram route) or Q1 (CholQR2 route)
+        std::vector<double> Tc((size_t)src_cols * r, 0.0);
+        for (int j = 0; j < r; ++j)
+            for (int t = 0; t < r1; ++t) {
+                double u = Ub[(size_t)j * r1 + t];
+                for (int q = 0; q < src_cols; ++q) Tc[(size_t)j * src_cols + q] += T1[(size_t)t * src_cols + q] * u;
+            }
+        ST_TRY(stage_reserve(p, pad32(Tc.size())));
+        double* dTc;
+        ST_TRY(sg.in(Tc.data(), Tc.size(), &dTc));
+        ST_TRY(st_tsgemm_nn(n, src_cols, r, 1.0, F1d, n, dTc, src_cols, 0.0, F1c, n, c.s));
+    }
     std::vector<double> F2c((size_t)nt * r, 0.0);   // Q2 U2 diag(s)
     for (int j = 0; j < r; ++j)
         for (int i = 0; i < nt; ++i) {
@@ -466,36 +756,65 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     const int pmax = r;
     double* MV = nullptr;
     ST_TRY(ensure_basis(p, c, std::min(2 * pmax + 8, p->d.max_basis + 16), 0, &MV));
-    tp = Clock::now();
-    ST_TRY(mass_inverse(c, prec, F1c, n, r, p->V, n));
-    S.ms_phase[1] += ms_since(tp);
-    std::vector<double> Rx;
-    int k = 0;
-    ST_TRY(block_qr(c, p->V, n, r, 0.0, 1e-12, Rx, &k));
-    if (k == 0) return ST_EBREAKDOWN;
     double* MAq;   // [M q, A q] staging, n x 2 pmax
     ST_TRY(st_slot(p, S_MAQ, sizeof(double) * (size_t)n * 2 * pmax, (void**)&MAq));
+    tp = Clock::now();
+    ST_TRY(stage_reserve(p, 3 * pad32((size_t)r * r) + pad32(1) + pad32((size_t)2 * r * r) + pad32((size_t)r * r) +
+                                pad32((size_t)r * r)));
+    ST_TRY(mass_inverse(c, prec, F1c, n, r, p->V, n));
+    double* dG = sg.out((size_t)r * r);
+    ST_TRY(ts_tn_dev(c, r, r, p->V, n, p->V, n, dG, r));
+    ST_TRY(sg.fetch());
+    S.ms_phase[1] += ms_since(tp);
+    tp = Clock::now();
+    int k = 0;
+    double* dflag = nullptr;
+    {
+        QrPlan qp;
+        qr_plan(sg.host_of(dG), r, 0.0, 1e-12, qp);
+        if (qp.rank == 0) return ST_EBREAKDOWN;
+        if (qp.fast) {
+            double* dR2;
+            ST_TRY(qr_fast_launch(c, sg, p->V, n, r, qp.R1, &dR2, &dflag));
+            k = r;
+        } else {
+            std::vector<double> Rx;
+            ST_TRY(block_qr(c, p->V, n, r, 0.0, 1e-12, Rx, &k));
+            if (k == 0) return ST_EBREAKDOWN;
+        }
+    }
     ST_TRY(st_spmm_ma<double>(p, p->V, n, k, MAq, n, MAq + (size_t)n * k, n, c.s));
+    double* dX0 = sg.out((size_t)k * 2 * k);
+    ST_TRY(ts_tn_dev(c, k, 2 * k, p->V, n, MAq, n, dX0, k));
+    double* dG1 = sg.out((size_t)k * r);
+    ST_TRY(ts_tn_dev(c, k, r, p->V, n, F1c, n, dG1, k));
+    double* dGmv = sg.out((size_t)k * k);
+    ST_TRY(ts_tn_dev(c, k, k, MAq, n, MAq, n, dGmv, k));
     ST_CUDA_TRY(cudaMemcpyAsync(MV, MAq, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, c.s));
-    HostSym Mm, Am, Hb;
-    std::vector<double> Gm;   // k x r, ld = kcap_h
+    ST_TRY(sg.fetch());
+    if (dflag && sg.host_of(dflag)[0] != 0.0) return ST_EBREAKDOWN;
+    HostSym Mm, Am, Hb, Gmv;
+    std::vector<double> Gm;   // k x r, ld = ldg
     int ldg = 0;
     {
-        std::vector<double> X((size_t)k * 2 * k), G((size_t)k * r);
-        ST_TRY(ts_tn_host(c, k, 2 * k, p->V, n, MAq, n, X.data()));
-        ST_TRY(ts_tn_host(c, k, r, p->V, n, F1c, n, G.data()));
+        const double* X = sg.host_of(dX0);
+        const double* G = sg.host_of(dG1);
+        const double* Gv = sg.host_of(dGmv);
         Mm.grow(k);
         Am.grow(k);
+        Gmv.grow(k);
         for (int j = 0; j < k; ++j)
             for (int i = 0; i < k; ++i) {
                 Mm(i, j) = 0.5 * (X[(size_t)j * k + i] + X[(size_t)i * k + j]);
                 Am(i, j) = 0.5 * (X[(size_t)(k + j) * k + i] + X[(size_t)(k + i) * k + j]);
+                Gmv(i, j) = 0.5 * (Gv[(size_t)j * k + i] + Gv[(size_t)i * k + j]);
             }
         ldg = std::max(64, 2 * k);
         Gm.assign((size_t)ldg * r, 0.0);
         for (int j = 0; j < r; ++j)
             for (int i = 0; i < k; ++i) Gm[(size_t)j * ldg + i] = G[(size_t)j * k + i];
     }
+    S.ms_phase[3] += ms_since(tp);
     std::vector<int> boff{0}, bsz{k};
     std::vector<double> shifts, ritz, Y;
     int last_ritz_k = -1;
@@ -505,12 +824,11 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     int next_check = 1;
     int mu_extra = 0;
     const double a_int = p->lam_min, b_int = p->lam_max;
-    std::vector<double> hist;
 
     while (true) {
         if (it >= p->d.maxit) break;
-        int pl = bsz.back();
-        int lo = boff.back();
+        const int pl = bsz.back();
+        const int lo = boff.back();
         if (k + pl > p->d.max_basis) break;
         ST_TRY(ensure_basis(p, c, k + pl, k, &MV));
         // ---- shift ----
@@ -524,36 +842,76 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         shifts.push_back(s);
         S.ms_phase[7] += ms_since(tp);
         ++it;
-        // ---- A3 shifted solve into the next basis slot ----
+        size_t needA = 2 * pad32((size_t)pl * pl) + 2 * pad32((size_t)k * pl);
+        size_t needB = 2 * pad32((size_t)k * 2 * pl) + pad32((size_t)pl * 2 * pl) + pad32((size_t)4 * pl * pl) +
+                       pad32((size_t)pl * r) + 2 * pad32((size_t)pl * pl) + pad32(1);
+        ST_TRY(stage_reserve(p, std::max(needA, needB)));
+        // ---- phase A: A3 shifted solve into the next basis slot, A4 block CGS2 ----
         tp = Clock::now();
         double* W = p->V + (size_t)k * n;
         ST_TRY(shifted_solve(c, prec, s, p->V + (size_t)lo * n, n, MV + (size_t)lo * n, n, pl, W, n));
-        ST_CUDA_TRY(cudaStreamSynchronize(c.s));
-        S.ms_phase[1] += ms_since(tp);
-        // ---- A4 block CGS2 + QR ----
-        tp = Clock::now();
-        std::vector<double> G0((size_t)pl * pl);
-        ST_TRY(ts_tn_host(c, pl, pl, W, n, W, n, G0.data()));
-        double ref2 = 0.0;
-        for (int i = 0; i < pl; ++i) ref2 = std::max(ref2, G0[(size_t)i * pl + i]);
-        std::vector<double> Hcol((size_t)k * pl, 0.0), h((size_t)k * pl);
+        double* dG0 = sg.out((size_t)pl * pl);
+        ST_TRY(ts_tn_dev(c, pl, pl, W, n, W, n, dG0, pl));
+        double* dh[2];
         for (int pass = 0; pass < 2; ++pass) {
-            ST_TRY(ts_tn_host(c, k, pl, p->V, n, W, n, h.data()));
-            ST_TRY(ts_nn_host(c, k, pl, -1.0, p->V, n, h.data(), 1.0, W, n));
-            for (size_t i = 0; i < h.size(); ++i) Hcol[i] += h[i];
+            dh[pass] = sg.out((size_t)k * pl);
+            ST_TRY(ts_tn_dev(c, k, pl, p->V, n, W, n, dh[pass], k));
+            ST_TRY(st_tsgemm_nn(n, k, pl, -1.0, p->V, n, dh[pass], k, 1.0, W, n, c.s));
         }
-        std::vector<double> Rq;
-        int pn = 0;
-        ST_TRY(block_qr(c, W, n, pl, ref2, 1e-10, Rq, &pn));
-        S.ms_phase[2] += ms_since(tp);
-        // ---- A5 products of the new block ----
+        double* dGw = sg.out((size_t)pl * pl);
+        ST_TRY(ts_tn_dev(c, pl, pl, W, n, W, n, dGw, pl));
+        ST_TRY(sg.fetch());
+        S.ms_phase[1] += ms_since(tp);
         tp = Clock::now();
-        std::vector<double> X1((size_t)k * 2 * pn), X2((size_t)pn * 2 * pn), X3((size_t)pn * r);
+        std::vector<double> Hcol((size_t)k * pl);
+        {
+            const double* h0 = sg.host_of(dh[0]);
+            const double* h1 = sg.host_of(dh[1]);
+            for (size_t i = 0; i < Hcol.size(); ++i) Hcol[i] = h0[i] + h1[i];
+        }
+        double ref2 = 0.0;
+        for (int i = 0; i < pl; ++i) ref2 = std::max(ref2, sg.host_of(dG0)[(size_t)i * pl + i]);
+        QrPlan qp;
+        qr_plan(sg.host_of(dGw), pl, ref2, 1e-10, qp);
+        int pn = 0;
+        std::vector<double> Rq((size_t)pl * pl, 0.0);
+        double* dR2 = nullptr;
+        dflag = nullptr;
+        if (qp.rank > 0) {
+            if (qp.fast) {
+                ST_TRY(qr_fast_launch(c, sg, W, n, pl, qp.R1, &dR2, &dflag));
+                pn = pl;
+            } else {
+                ST_TRY(block_qr(c, W, n, pl, ref2, 1e-10, Rq, &pn));
+            }
+        }
+        S.ms_phase[2] += ms_since(tp);
+        // ---- phase B: A5 products of the new block ----
+        tp = Clock::now();
+        std::vector<double> X1, X1b, X2, X3, Gq;
         if (pn > 0) {
             ST_TRY(st_spmm_ma<double>(p, W, n, pn, MAq, n, MAq + (size_t)n * pn, n, c.s));
-            ST_TRY(ts_tn_host(c, k, 2 * pn, p->V, n, MAq, n, X1.data()));
-            ST_TRY(ts_tn_host(c, pn, 2 * pn, W, n, MAq, n, X2.data()));
-            ST_TRY(ts_tn_host(c, pn, r, W, n, F1c, n, X3.data()));
+            double* dX1 = sg.out((size_t)k * 2 * pn);
+            ST_TRY(ts_tn_dev(c, k, 2 * pn, p->V, n, MAq, n, dX1, k));
+            double* dX1b = sg.out((size_t)k * 2 * pn);
+            ST_TRY(ts_tn_dev(c, k, 2 * pn, MV, n, MAq, n, dX1b, k));
+            double* dX2 = sg.out((size_t)pn * 2 * pn);
+            ST_TRY(ts_tn_dev(c, pn, 2 * pn, W, n, MAq, n, dX2, pn));
+            double* dGq = sg.out((size_t)4 * pn * pn);
+            ST_TRY(ts_tn_dev(c, 2 * pn, 2 * pn, MAq, n, MAq, n, dGq, 2 * pn));
+            double* dX3 = sg.out((size_t)pn * r);
+            ST_TRY(ts_tn_dev(c, pn, r, W, n, F1c, n, dX3, pn));
+            ST_TRY(sg.fetch());
+            if (qp.fast) {
+                if (sg.host_of(dflag)[0] != 0.0) return ST_EBREAKDOWN;
+                Rq = upper_product(pl, sg.host_of(dR2), qp.R1.data());
+            }
+            auto grab = [&](const double* d, size_t m) { return std::vector<double>(sg.host_of(d), sg.host_of(d) + m); };
+            X1 = grab(dX1, (size_t)k * 2 * pn);
+            X1b = grab(dX1b, (size_t)k * 2 * pn);
+            X2 = grab(dX2, (size_t)pn * 2 * pn);
+            Gq = grab(dGq, (size_t)4 * pn * pn);
+            X3 = grab(dX3, (size_t)pn * r);
         }
         S.ms_phase[3] += ms_since(tp);
         mu_extra = pn;
@@ -580,35 +938,9 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
             tp = Clock::now();
             double rr = 0.0;
             if (pn > 0) {
-                // w_hat = -(s M q + A q) R_q  (n x pl); V^T w_hat from X1
-                double* Wh;
-                double* Wh2;
-                ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n * pl, (void**)&Wh));
-                ST_TRY(st_slot(p, S_WH2, sizeof(double) * (size_t)n * pl, (void**)&Wh2));
-                // -R_q as pn x pl col-major: element (i, j) = -Rq[j*pl + i]
-                std::vector<double> negR((size_t)pn * pl);
-                for (int j = 0; j < pl; ++j)
-                    for (int i = 0; i < pn; ++i) negR[(size_t)j * pn + i] = -Rq[(size_t)j * pl + i];
-                ST_TRY(st_copy_cols64(n, pn, MAq + (size_t)n * pn, n, Wh, n, c.s));
-                ST_TRY(st_axpby64(n, pn, s, MAq, n, 1.0, Wh, n, c.s));   // Wh = s Mq + Aq
-                ST_TRY(ts_nn_host(c, pn, pl, 1.0, Wh, n, negR.data(), 0.0, Wh2, n));
-                // Vt w_hat = -(s X1_M + X1_A) R_q   (k x pl)
-                std::vector<double> Vw((size_t)k * pl, 0.0);
-                for (int j = 0; j < pl; ++j)
-                    for (int q = 0; q < pn; ++q) {
-                        double rq = -Rq[(size_t)j * pl + q];
-                        for (int i = 0; i < k; ++i)
-                            Vw[(size_t)j * k + i] += (s * X1[(size_t)q * k + i] + X1[(size_t)(pn + q) * k + i]) * rq;
-                    }
-                // c = Mm^{-1} Vw ; b = w_hat - M V c
-                std::vector<double> L((size_t)k * k);
-                for (int j = 0; j < k; ++j)
-                    for (int i = 0; i < k; ++i) L[(size_t)j * k + i] = Mm(i, j);
-                if (!dense::cholesky(k, L.data(), k)) return ST_EBREAKDOWN;
-                dense::chol_solve(k, L.data(), k, Vw.data(), k, pl);
-                ST_TRY(ts_nn_host(c, k, pl, -1.0, MV, n, Vw.data(), 1.0, Wh2, n));
-                std::vector<double> Gb((size_t)pl * pl);
-                ST_TRY(ts_tn_host(c, pl, pl, Wh2, n, Wh2, n, Gb.data()));
+                std::vector<double> Gb;
+                if (!residual_gram_products(k, pn, pl, s, X1, X1b, Gq, Mm, Gmv, Rq, Gb))
+                    ST_TRY(residual_gram_explicit(c, k, pn, pl, s, MAq, MV, X1, Mm, Rq, Gb));
                 // f = H^{-T} E_last  (k x pl)
                 std::vector<double> H((size_t)k * k), f((size_t)k * pl, 0.0);
                 for (int j = 0; j < k; ++j)
@@ -633,17 +965,15 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
                 }
             }
             res = std::sqrt(std::max(rr, 0.0)) / normF;
-            hist.push_back(res);
             S.ms_phase[5] += ms_since(tp);
             if (res <= tol || pn == 0) {
                 status = res <= tol ? ST_OK : ST_ENOTCONV;
                 if (pn == 0 && res > tol) status = ST_EBREAKDOWN;
                 break;
             }
-            // schedule the next check: every iteration while the projected solve is cheap
+            // next check: every iteration while the projected solve is cheap
             double cost = (double)k * k * nt;
             int gap = (int)std::max(1.0, std::min(16.0, cost / 4e6));
-            // when far from tol and converging geometrically, skip ahead
             next_check = it + gap;
         }
         if (pn == 0) {
@@ -654,17 +984,21 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         tp = Clock::now();
         ST_CUDA_TRY(cudaMemcpyAsync(MV + (size_t)k * n, MAq, sizeof(double) * (size_t)n * pn, cudaMemcpyDeviceToDevice,
                                     c.s));
-        int kn = k + pn;
+        const int kn = k + pn;
+        const int q2 = 2 * pn;
         Mm.grow(kn);
         Am.grow(kn);
+        Gmv.grow(kn);
         for (int j = 0; j < pn; ++j) {
             for (int i = 0; i < k; ++i) {
                 Mm(i, k + j) = Mm(k + j, i) = X1[(size_t)j * k + i];
                 Am(i, k + j) = Am(k + j, i) = X1[(size_t)(pn + j) * k + i];
+                Gmv(i, k + j) = Gmv(k + j, i) = X1b[(size_t)j * k + i];
             }
             for (int i = 0; i < pn; ++i) {
                 Mm(k + i, k + j) = 0.5 * (X2[(size_t)j * pn + i] + X2[(size_t)i * pn + j]);
                 Am(k + i, k + j) = 0.5 * (X2[(size_t)(pn + j) * pn + i] + X2[(size_t)(pn + i) * pn + j]);
+                Gmv(k + i, k + j) = 0.5 * (Gq[(size_t)j * q2 + i] + Gq[(size_t)i * q2 + j]);
             }
         }
         if (kn > ldg) {
