@@ -99,6 +99,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest value over all ranks (the slowest rank's time); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's timed region."""
+    return world * units_per_rank * steps / (max_ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -147,10 +162,62 @@ def roofline_of(prof, hbm_gbs):
     return out
 
 
+def run_reference_many(args, wl, world, rank):
+    """The oracle on a bounded sample of a batched or served workload: exact direct solves
+    (block forward substitution of the assembled system) of its instances in order, each step
+    stopping once about 10 s of CPU work is done."""
+    if rank != 0:
+        return None
+    from oracle import fem, kron, timefe
+    import workloads
+    if wl["kind"] == "batched":
+        insts = workloads.batched_instances(count=wl["count"], seed=wl["seed"], p=wl["p"])
+        insts = [dict(r, op="heat") for r in insts]
+    else:
+        insts = workloads.served_requests(count=wl["count"], seed=wl["seed"], mean_gap_s=wl["mean_gap_s"],
+                                          p=wl["p"])
+    times, units_all = [], []
+    done = 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        units = 0
+        i = 0
+        while time.perf_counter() - t0 < 10.0 and i < len(insts):
+            r = insts[i]
+            i += 1
+            if r["op"] == "heat":
+                M, A = fem.tensor_operators(r["dim"], r["n"], kappa=r.get("kappa", r.get("eps", 1.0)))
+            else:
+                M, A = fem.tensor_operators(r["dim"], r["n"], op="convdiff", eps=r["eps"], beta=r["beta"])
+            if "F1" in r:
+                F1, F2 = r["F1"], r["F2"]
+            else:
+                F1, F2 = workloads.request_factors(r)
+            D, C = timefe.time_matrices(r["n_t"], r.get("T", 1.0))
+            kron.forward_substitution(M, A, D, C, F1 @ F2.T)
+            units += M.shape[0] * r["n_t"]
+        el = time.perf_counter() - t0
+        done = i
+        if it >= args.warmup:
+            times.append(el)
+            units_all.append(units)
+    value = sum(units_all) / sum(times)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = f"direct oracle solves of the first {done} instances of the {wl['kind']} workload (about 10 s)"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"]},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, wl, world, rank):
     """The oracle (CPU, FP64) as it stands on a bounded sample of the workload."""
     if rank != 0:
         return None
+    if wl.get("kind"):
+        return run_reference_many(args, wl, world, rank)
     from oracle import fem, kron, rhs as orhs, rksm as orksm, timefe
     import workloads
     dim, n, nt = wl["dim"], wl["n"], wl["n_t"]
@@ -196,6 +263,142 @@ def cpu_baseline(wl):
     return line["cpu_baseline"]
 
 
+def bench_batched(args, wl, rank, world, local):
+    """Batched workload: many 2D instances of mixed sizes solved at once through the executor."""
+    import torch
+    import paper_1912_10082_gb300 as st
+    from paper_1912_10082_gb300 import serve
+    import workloads
+
+    torch.cuda.set_device(local)
+    insts = workloads.batched_instances(count=wl["count"], seed=wl["seed"], p=wl["p"])
+    dev = []
+    for r in insts:
+        d = dict(r)
+        for key in ("F1", "F2"):
+            t = st.empty_colmajor(*r[key].shape)
+            t.copy_(torch.from_numpy(r[key]))
+            d[key] = t
+        dev.append(d)
+    torch.cuda.synchronize()
+    slots = args.slots
+    dof = sum(r["n"] ** 2 * r["n_t"] for r in insts)
+
+    def timed(prec, method, steps, warmup, data):
+        res = None
+        for _ in range(warmup):
+            serve.run_batch(data, precision=prec, slots=slots, method=method)
+        torch.cuda.synchronize()
+        ms, lc = [], st.launch_count()
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = serve.run_batch(data, precision=prec, slots=slots, method=method)
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t0))
+        return ms, res, st.launch_count() - lc
+
+    with ClockSampler(local) as clk:
+        ms, res, launches = timed(st.ST_MIXED, st.ST_METHOD_RKSM, args.steps, args.warmup, dev)
+    print(f"[bench] batched mixed RKSM: {ms} ms per batch", file=sys.stderr, flush=True)
+    ms_step = statistics.mean(ms)
+    value = world * dof / (ms_step * 1e-3)
+    bad = [r for r in res["results"] if r["status"] != st.ST_OK]
+    its = [r["stats"]["iterations"] for r in res["results"]]
+    comps = {}
+    ms64, _, _ = timed(st.ST_FP64, st.ST_METHOD_RKSM, 1, 0, dev)
+    comps["fp64_rksm_batched"] = {"value": dof / (ms64[0] * 1e-3), "ms_per_step": ms64[0]}
+    mscn, _, _ = timed(st.ST_FP64, st.ST_METHOD_CN, 1, 0, dev)
+    comps["cn_fp64_batched"] = {"value": dof / (mscn[0] * 1e-3), "ms_per_step": mscn[0]}
+    print(f"[bench] batched fp64 RKSM {ms64[0]:.1f} ms, CN {mscn[0]:.1f} ms", file=sys.stderr, flush=True)
+    # one instance at a time on one stream (no batching), mixed precision
+    t0 = time.perf_counter()
+    serve.run_batch(dev[:32], precision=st.ST_MIXED, slots=1)
+    el = time.perf_counter() - t0
+    comps["mixed_rksm_one_at_a_time_first32"] = {
+        "value": sum(r["n"] ** 2 * r["n_t"] for r in insts[:32]) / el, "ms_per_step": 1e3 * el}
+    # end to end: host factors staged inside every solve; results = per-instance statistics
+    host = [dict(r) for r in insts]
+    for r in host:
+        for key in ("F1", "F2"):
+            t = torch.empty((r[key].shape[1], r[key].shape[0]), dtype=torch.float64).pin_memory().t()
+            t.copy_(torch.from_numpy(r[key]))
+            r[key] = t
+    mse, rese, _ = timed(st.ST_MIXED, st.ST_METHOD_RKSM, 1, 0, host)
+    h2d = sum((r["F1"].size + r["F2"].size) * 8 for r in insts)
+    from paper_1912_10082_gb300 import StResult
+    import ctypes
+    e2e = {"value": world * dof / (mse[0] * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(len(insts) * ctypes.sizeof(StResult))}
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batched: {len(insts)} 2D heat instances, grid side from (63,127,255), n_t from "
+                               f"(64,128,256,512), kappa 10^U(-1,1), rank-{wl['p']} Gaussian load, mixed precision",
+                   "instances": len(insts), "dof": dof, "slots": slots, "tol": 1e-8,
+                   "l2": "inputs of the batch (%.0f MB) exceed L2" % (sum(r['F1'].nbytes for r in insts) / 1e6),
+                   "parallelism": f"replicas{world}"},
+        "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its))},
+        "cpu_baseline": None, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+        "comparators": comps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_served(args, wl, rank, world, local):
+    """Served workload: a Poisson stream of heat and convection-diffusion requests of mixed sizes,
+    replayed at its arrival times through the executor (continuous batching)."""
+    import torch
+    import paper_1912_10082_gb300 as st
+    from paper_1912_10082_gb300 import serve
+    import workloads
+
+    torch.cuda.set_device(local)
+    count = args.requests or wl["count"]
+    warm = min(wl["warmup"], count // 10)
+    gap = wl["mean_gap_s"] * args.gap_scale
+    reqs = workloads.served_requests(count=count, seed=wl["seed"], mean_gap_s=gap, p=wl["p"])
+    facs = [tuple(np.asfortranarray(x) for x in workloads.request_factors(r)) for r in reqs]
+    lc = st.launch_count()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        out = serve.run_stream(reqs, facs, precision=st.ST_MIXED, slots=args.slots, warmup=warm)
+        wall = time.perf_counter() - t0
+    launches = st.launch_count() - lc
+    recs = out.pop("records")
+    kinds = {}
+    for j in range(warm, count):
+        r, res = reqs[j], recs[j]
+        key = f"{r['op']}{r['dim']}d"
+        d = kinds.setdefault(key, {"n": 0, "lat": [], "failed": 0})
+        d["n"] += 1
+        d["lat"].append(res["t_end"] - res["t_submit"])
+        d["failed"] += res["status"] != st.ST_OK
+    per_kind = {k: {"requests": v["n"], "failed": v["failed"], "p50_s": float(np.percentile(v["lat"], 50)),
+                    "p99_s": float(np.percentile(v["lat"], 99))} for k, v in sorted(kinds.items())}
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": out["dof_per_s"] * world, "unit": "DoF/s", "n_gpus": world, "steps": 1,
+        "warmup": warm, "ms_per_step": 1e3 * out["makespan_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"served: Poisson stream of {count} requests (first {warm} warm-up), mean gap "
+                               f"{1e3 * gap:.2f} ms, heat and convection-diffusion, 1D/2D/3D n 63..127^3, "
+                               f"n_t 64..512, rank-{wl['p']} Gaussian loads, mixed precision, tol 1e-8",
+                   "slots": args.slots, "gap_scale": args.gap_scale, "parallelism": f"replicas{world}"},
+        "latency": {"p50_s": out["p50_s"], "p99_s": out["p99_s"], "per_kind": per_kind},
+        "served": {"measured": out["measured"], "ok": out["ok"], "not_converged": out["not_converged"],
+                   "wall_s": wall},
+        "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,6 +407,9 @@ def main():
     ap.add_argument("--workload", default="heat2d")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slots", type=int, default=16, help="executor slots of the batched and served workloads")
+    ap.add_argument("--requests", type=int, default=0, help="served workload: number of requests (0: all)")
+    ap.add_argument("--gap-scale", type=float, default=1.0, help="served workload: scale of the mean arrival gap")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -211,6 +417,10 @@ def main():
     wl = dict(workloads.WORKLOADS[args.workload])
     wl["name"] = args.workload
     rank, world, local = dist_env()
+    if wl.get("kind") == "batched" and args.impl == "ours":
+        return bench_batched(args, wl, rank, world, local)
+    if wl.get("kind") == "served" and args.impl == "ours":
+        return bench_served(args, wl, rank, world, local)
 
     if args.impl == "reference":
         line = run_reference(args, wl, world, rank)
@@ -276,13 +486,9 @@ def main():
 
     with ClockSampler(local) as clk:
         ms, launches = timed(step, args.steps, args.warmup)
-    tot_ms = sum(ms)
-    if pg:
-        t = torch.tensor([tot_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(ms), pg, device="cuda")
     ms_per_step = tot_ms / args.steps
-    value = world * units * args.steps / (tot_ms * 1e-3)
+    value = job_throughput(units, world, args.steps, tot_ms)
 
     # certification of the last solution, outside the timed region (FP64, independent formula)
     V, Y, stats, status = prob.solve(f1, f2)
@@ -338,6 +544,34 @@ def main():
     comps["cn_fp64"] = {"value": units / (statistics.mean(ms3) * 1e-3), "ms_per_step": statistics.mean(ms3)}
     prob2.close()
 
+    # fused space-time apply (st_apply) on a dense U of the workload's size, L2 flushed before each launch
+    apply_stats = {}
+    for dtype_, tag in ((torch.float32, "apply32"), (torch.float64, "apply64")):
+        Ua = st.empty_colmajor(prob.n_h, prob.n_t, dtype=dtype_)
+        Ya = st.empty_colmajor(prob.n_h, prob.n_t, dtype=dtype_)
+        with torch.cuda.stream(stream):
+            Ua.normal_()
+            for _ in range(3):
+                prob.apply(Ua, Ya)
+            evs = []
+            for _ in range(20):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                prob.apply(Ua, Ya)
+                e1.record(stream)
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms_a = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        s_ = Ua.element_size()
+        nnz = prob.nnz
+        byts = 2.0 * s_ * prob.n_h * prob.n_t + nnz * (4.0 + 2.0 * s_) + 4.0 * (prob.n_h + 1)
+        apply_stats[tag] = {"ms_per_launch": ms_a, "bytes_per_launch": byts, "achieved_gbs": byts / (ms_a * 1e-3) / 1e9,
+                            "frac_of_hbm": byts / (ms_a * 1e-3) / 1e9 / pk["hbm_gbs"],
+                            "dof_per_s": prob.n_h * prob.n_t / (ms_a * 1e-3)}
+        del Ua, Ya
+
     if rank != 0:
         return 0
     cb = None
@@ -357,7 +591,7 @@ def main():
                    "mu_mem": s["mu_mem"]},
         "roofline": roof, "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()},
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
-        "comparators": comps,
+        "comparators": comps, "apply": apply_stats,
     }
     print(json.dumps(line), flush=True)
     prob.close()

@@ -116,6 +116,7 @@ typedef struct st_stats {
                              block Gram-Schmidt, 2 block QR, 3 products of the new block,
                              4 projected solve, 5 residual, 6 output, 7 other */
     double shift_min, shift_max;  /* extremes of the shifts s used, as (A + s M)^{-1} */
+    int inner_iterations; /* convection-diffusion: preconditioned FGMRES steps of all shifted solves */
 } st_stats;
 
 /* st_setup -- build a problem handle (Section 3: spatial matrices M_h, A_h;
@@ -196,7 +197,15 @@ unsigned long st_shift_solve_noalloc_max(void);
  * F1: n_h x p (ld ldf1), F2: n_t x p (ld ldf2), double, host OR device.
  * 1 <= p <= 16.  Output in *sol (V, Y owned by the handle; U_dense filled if
  * given).  stats may be NULL.  Synchronises.  Returns ST_OK, ST_ENOTCONV
- * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL. */
+ * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL.
+ * Heat (ST_HEAT): the shifted solves are exact fast-diagonalisation
+ * transforms.  Convection-diffusion (ST_CONVDIFF, A nonsymmetric): each
+ * shifted solve is flexible GMRES right-preconditioned by the
+ * fast-diagonalisation solve of eps K + s M, to 1e-3 tol relative (at least
+ * 1e-13); the projected matrices are not symmetrised and the projected time
+ * recurrence uses LU.  ST_MIXED: FP32 transforms (refined to FP64 accuracy,
+ * or inside FGMRES as the preconditioner) and basis products in double-float
+ * arithmetic on the FP32 pipes (about 48 significant bits). */
 int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
              st_solution* sol, st_stats* stats);
 
@@ -260,10 +269,15 @@ typedef struct st_request {
     const double* F2;        /* n_t x p load factor, host or device */
     int ldf2;
     int p;                   /* 1 <= p <= 16 */
-    double* U_out;           /* optional n_h x n_t buffer (host or device) receiving U = V Y; NULL: none */
+    double* U_out;           /* optional n_h x n_t buffer (host or device) receiving U; NULL: none */
     int ldu;                 /* leading dimension of U_out (>= n_h) */
     unsigned long long tag;  /* the caller's identifier, returned with the result */
+    int method;              /* ST_METHOD_RKSM (st_solve) or ST_METHOD_CN (st_timestep_cn; U is
+                                written to U_out, or to a buffer of the slot when U_out is NULL) */
 } st_request;
+
+#define ST_METHOD_RKSM 0
+#define ST_METHOD_CN   1
 
 typedef struct st_result {
     unsigned long long tag;  /* st_request.tag */

@@ -25,6 +25,7 @@ ST_OK, ST_EINVAL, ST_ENOMEM, ST_ENOTCONV, ST_EBREAKDOWN, ST_ECUDA, ST_ETIMEOUT, 
 ST_FP64, ST_MIXED = 0, 1
 ST_F64, ST_F32 = 0, 1
 ST_HEAT, ST_CONVDIFF = 0, 1
+ST_METHOD_RKSM, ST_METHOD_CN = 0, 1
 
 # every symbol include/st.h declares
 ABI_SYMBOLS = (
@@ -57,7 +58,7 @@ class StStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("basis_cols", C.c_int), ("rank", C.c_int), ("p", C.c_int),
                 ("converged", C.c_int), ("residual_checks", C.c_int), ("mu_mem", C.c_int),
                 ("relres", C.c_double), ("ms_total", C.c_double), ("ms_phase", C.c_double * 8),
-                ("shift_min", C.c_double), ("shift_max", C.c_double)]
+                ("shift_min", C.c_double), ("shift_max", C.c_double), ("inner_iterations", C.c_int)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name != "ms_phase"}
@@ -67,7 +68,8 @@ class StStats(C.Structure):
 
 class StRequest(C.Structure):
     _fields_ = [("desc", StDesc), ("F1", C.c_void_p), ("ldf1", C.c_int), ("F2", C.c_void_p), ("ldf2", C.c_int),
-                ("p", C.c_int), ("U_out", C.c_void_p), ("ldu", C.c_int), ("tag", C.c_ulonglong)]
+                ("p", C.c_int), ("U_out", C.c_void_p), ("ldu", C.c_int), ("tag", C.c_ulonglong),
+                ("method", C.c_int)]
 
 
 class StResult(C.Structure):
@@ -367,9 +369,10 @@ class Executor:
     def now(self) -> float:
         return float(lib().st_executor_now(self.h))
 
-    def submit(self, desc: StDesc, F1, F2, tag: int, U_out=None):
+    def submit(self, desc: StDesc, F1, F2, tag: int, U_out=None, method: int = ST_METHOD_RKSM):
         r = StRequest()
         r.desc = desc
+        r.method = int(method)
         p1, l1, _, m = _ptr_ld(F1)
         p2, l2, _, _ = _ptr_ld(F2)
         r.F1, r.ldf1, r.F2, r.ldf2, r.p, r.tag = p1, l1, p2, l2, m, int(tag)

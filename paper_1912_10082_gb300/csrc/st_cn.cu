@@ -28,14 +28,10 @@ extern "C" int st_timestep_cn(st_problem* p, const double* F1, int ldf1, const d
     ST_TRY(st_stage_matrix(p, F1, ldf1, n, ncols, f1));
     ST_TRY(st_stage_matrix(p, F2, ldf2, nt, ncols, f2));
     const void* key[4] = {U, (const void*)(size_t)ldu, (const void*)(size_t)ncols, f1};
-    bool hit = p->cn_graph != nullptr;
+    bool hit = p->cn_graph != nullptr && !p->cn_stale;
     for (int i = 0; i < 4 && hit; ++i) hit = key[i] == p->cn_key[i];
     hit = hit && (p->cn_buf == f2);
     if (!hit) {
-        if (p->cn_graph) {
-            cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
-            p->cn_graph = nullptr;
-        }
         cudaStream_t cs;
         ST_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
@@ -56,7 +52,18 @@ extern "C" int st_timestep_cn(st_problem* p, const double* F1, int ldf1, const d
             st = ST_ECUDA;
         }
         cudaGraphExec_t ex = nullptr;
-        if (st == ST_OK) {
+        if (st == ST_OK && p->cn_graph) {
+            // same topology with new parameters (coefficients or buffers): update in place
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate((cudaGraphExec_t)p->cn_graph, g, &info) == cudaSuccess) {
+                ex = (cudaGraphExec_t)p->cn_graph;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
+            }
+            p->cn_graph = nullptr;
+        }
+        if (st == ST_OK && !ex) {
             e = cudaGraphInstantiate(&ex, g, 0);
             if (e != cudaSuccess) {
                 st_note_cuda(e, "cudaGraphInstantiate", __FILE__, __LINE__);
@@ -72,6 +79,7 @@ extern "C" int st_timestep_cn(st_problem* p, const double* F1, int ldf1, const d
             return st;
         }
         p->cn_graph = ex;
+        p->cn_stale = false;
         p->cn_nodes = nodes;
         for (int i = 0; i < 4; ++i) p->cn_key[i] = key[i];
         p->cn_buf = f2;

@@ -64,6 +64,7 @@ struct st_problem {
     int* row_ptr = nullptr;
     int* col = nullptr;
     double *m64 = nullptr, *a64 = nullptr, *p64 = nullptr, *q64 = nullptr;   // M, A, P=M+dt/2A, N=M-dt/2A
+    double* at64 = nullptr;     // A^T on the same (symmetric) pattern; box problems only
     float *m32 = nullptr, *a32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     FdAxis ax[3];
     double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M), or of its diffusion part
@@ -72,6 +73,7 @@ struct st_problem {
     std::vector<void*> owned;              // every device allocation of the handle
     // solution of the last st_solve (device, owned)
     double* V = nullptr;
+    float2* Vdf = nullptr;      // double-float copy of V (mixed precision), same capacity
     double* Y = nullptr;
     int k = 0;
     size_t V_cap_cols = 0, Y_cap = 0;
@@ -80,6 +82,7 @@ struct st_problem {
     size_t work_bytes = 0;
     // CN graph cache
     void* cn_graph = nullptr;   // cudaGraphExec_t
+    bool cn_stale = false;      // coefficients changed since the capture: recapture and update
     size_t cn_nodes = 0;        // kernel nodes in the CN graph
     double* cn_buf = nullptr;
     const void* cn_key[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -108,6 +111,8 @@ int st_stage_matrix(st_problem* p, const double* src, int ld, int rows, int cols
 // Out1 = M X, Out2 = A X for ncols columns (either output may be NULL).
 template <typename T>
 int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OutM, int ldm, T* OutA, int lda, cudaStream_t s);
+// Out = A^T X (box problems: A^T is stored on the shared pattern)
+int st_spmm_at64(st_problem* p, const double* X, int ldx, int ncols, double* Out, int ldo, cudaStream_t s);
 // Out = alpha * (Mv * M + Av * A) X + beta * Out
 int st_spmm_comb64(st_problem* p, double cm, double ca, const double* X, int ldx, int ncols,
                    double beta, double* Out, int ldo, cudaStream_t s);
@@ -134,6 +139,13 @@ int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W,
 // W = beta * W + alpha * V H   (V n x k, H k x m device, W n x m)
 int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, const double* H, int ldh,
                  double beta, double* W, int ldw, cudaStream_t s);
+// Double-float variants for a basis V stored as (hi, lo) float pairs: FP64-accurate
+// to about 48 bits, computed on the FP32 pipes.
+int st_to_df(int n, int m, const double* X, int ldx, float2* Y, int ldy, cudaStream_t s);
+int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const double* W, int ldw,
+                    double* H, int ldh, double* partial, cudaStream_t s);
+int st_tsgemm_nn_df(int n, int k, int m, double alpha, const float2* V, int ldv, const double* H, int ldh,
+                    double beta, double* W, int ldw, cudaStream_t s);
 // W = W * R^{-1} for upper triangular R (m x m, device), in place
 int st_trsm_right_upper(int n, int m, const double* R, int ldr, double* W, int ldw, cudaStream_t s);
 // R (upper, m x m, ld ldr, device) with R^T R = G (m x m, ld ldg, device), m <= 16, by one warp.

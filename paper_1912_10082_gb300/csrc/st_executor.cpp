@@ -140,7 +140,15 @@ int run_one(st_executor* ex, cudaStream_t s, std::vector<std::pair<GeomKey, st_p
     st_solution sol{};
     double* Ud = nullptr;
     bool host_out = false;
-    if (job.req.U_out) {
+    const bool cn = job.req.method == ST_METHOD_CN;
+    if (!job.req.U_out && cn) {
+        int st = st_slot(h, 23, sizeof(double) * (size_t)h->n_h * h->n_t, (void**)&Ud);
+        if (st != ST_OK) {
+            if (!cached) st_destroy(h);
+            return st;
+        }
+        sol.ldu = h->n_h;
+    } else if (job.req.U_out) {
         if (st_is_device_ptr(job.req.U_out)) {
             Ud = job.req.U_out;
             sol.ldu = job.req.ldu;
@@ -155,8 +163,19 @@ int run_one(st_executor* ex, cudaStream_t s, std::vector<std::pair<GeomKey, st_p
         }
         sol.U_dense = Ud;
     }
-    int st = st_solve(h, job.req.F1, job.req.ldf1, job.req.F2, job.req.ldf2, job.req.p, &sol, &res.stats);
-    res.k = sol.k;
+    int st;
+    if (cn) {
+        st = st_timestep_cn(h, job.req.F1, job.req.ldf1, job.req.F2, job.req.ldf2, job.req.p, Ud, sol.ldu);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (st == ST_OK && e != cudaSuccess) {
+            st_note_cuda(e, "executor CN", __FILE__, __LINE__);
+            st = ST_ECUDA;
+        }
+        res.k = 0;
+    } else {
+        st = st_solve(h, job.req.F1, job.req.ldf1, job.req.F2, job.req.ldf2, job.req.p, &sol, &res.stats);
+        res.k = sol.k;
+    }
     if (host_out && (st == ST_OK || st == ST_ENOTCONV)) {
         cudaError_t e = cudaMemcpy2DAsync(job.req.U_out, sizeof(double) * job.req.ldu, Ud, sizeof(double) * h->n_h,
                                           sizeof(double) * h->n_h, h->n_t, cudaMemcpyDeviceToHost, s);
@@ -241,12 +260,17 @@ extern "C" double st_executor_now(st_executor* ex) { return ex ? ex->now() : 0.0
 
 extern "C" int st_executor_submit(st_executor* ex, const st_request* req) {
     if (!ex || !req || !req->F1 || !req->F2 || req->p < 1 || req->p > 16) return ST_EINVAL;
+    if (req->method != ST_METHOD_RKSM && req->method != ST_METHOD_CN) return ST_EINVAL;
     const st_desc& d = req->desc;
     if (d.dim < 1 || d.dim > 3 || d.n_t < 1 || !(d.T > 0)) return ST_EINVAL;
     Job job;
     job.req = *req;
     job.t_submit = ex->now();
     job.est = st_request_bytes(&d, req->p);
+    // a dense U staged on the device: CN's output, or U = V Y bound for host memory
+    double nh = 1.0;
+    for (int i = 0; i < d.dim; ++i) nh *= d.n[i];
+    if (req->method == ST_METHOD_CN || (req->U_out && !st_is_device_ptr(req->U_out))) job.est += 8.0 * nh * d.n_t;
     {
         std::lock_guard<std::mutex> lk(ex->mu);
         if (ex->stop) return ST_EINVAL;

@@ -44,7 +44,31 @@ __global__ void __launch_bounds__(128) k_apply_reg(int n_h, int n_t, int chunk, 
 #pragma unroll
         for (int e = 0; e < MAXNNZ; ++e) prevN += N[e] * u[c[e]];
     }
-    for (int l = l0; l < l1; ++l) {
+    // STEPS time columns per pass: all their gathers are issued before the
+    // FMAs, so a thread keeps STEPS x MAXNNZ loads in flight
+    constexpr int STEPS = MAXNNZ <= 9 ? 4 : (sizeof(T) == 4 ? 2 : 1);
+    int l = l0;
+    for (; l + STEPS <= l1; l += STEPS) {
+        T x[STEPS][MAXNNZ];
+#pragma unroll
+        for (int q = 0; q < STEPS; ++q) {
+            const T* u = U + (size_t)(l + q) * ldu;
+#pragma unroll
+            for (int e = 0; e < MAXNNZ; ++e) x[q][e] = u[c[e]];
+        }
+#pragma unroll
+        for (int q = 0; q < STEPS; ++q) {
+            T tP = T(0), tN = T(0);
+#pragma unroll
+            for (int e = 0; e < MAXNNZ; ++e) {
+                tP += P[e] * x[q][e];
+                tN += N[e] * x[q][e];
+            }
+            Y[(size_t)(l + q) * ldy + r] = tP - prevN;
+            prevN = tN;
+        }
+    }
+    for (; l < l1; ++l) {
         const T* u = U + (size_t)l * ldu;
         T tP = T(0), tN = T(0);
 #pragma unroll
@@ -329,46 +353,63 @@ int launch_gemm_rr(int M, int N, int K, const T* A, long long lda, const T* B, l
 // kernel sums the partials in chunk order (deterministic).
 // ---------------------------------------------------------------------------
 constexpr int TS_THREADS = 256;
+constexpr int TS_CG = 16;      // basis columns per CTA of H = V^T W
+constexpr int TS_UNROLL = 8;   // independent loads in flight per lane
 
-__host__ __device__ inline int ts_rows_per_cta(int n) {
-    // enough CTAs to fill the GPU: about 4 per SM of 152 SMs
-    int r = (n + 607) / 608;
-    r = ((r + 31) / 32) * 32;
-    return r < 64 ? 64 : (r > 512 ? 512 : r);
-}
+// Rows of one chunk of H = V^T W: the chunk of W staged in shared memory
+// holds rows x m <= 8192 doubles.
+__host__ __device__ inline int ts_rows(int m) { return m <= 8 ? 1024 : 512; }
 
+// Partial products of H = V^T W over one chunk of rows and a group of TS_CG
+// basis columns.  Each warp takes a column at a time; its lanes stride over
+// the chunk's rows (coalesced loads of V, TS_UNROLL of them issued before the
+// FMAs that use them) against the chunk of W in shared memory, then a fixed
+// xor butterfly sums the lanes.  With 32+ rows per lane the butterfly's FP64
+// adds are a small fraction of the FMAs (FP64 is the scarce unit).
+template <int MAXM>
 __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_partial(int n, int k, int m, int rows,
                                                               const double* __restrict__ V, long long ldv,
                                                               const double* __restrict__ W, long long ldw,
                                                               double* __restrict__ part) {
     extern __shared__ double Ws[];   // [m][rows]
-    int chunk = blockIdx.x;
-    int r0 = chunk * rows;
-    int nr = min(rows, n - r0);
+    const int chunk = blockIdx.x;
+    const int r0 = chunk * rows;
+    const int nr = min(rows, n - r0);
     for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
         int b = idx / rows, rr = idx % rows;
         Ws[idx] = rr < nr ? W[(size_t)b * ldw + r0 + rr] : 0.0;
     }
     __syncthreads();
-    int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     double* out = part + (size_t)chunk * k * m;
-    for (int a = warp; a < k; a += TS_THREADS / 32) {
+    for (int cc = warp; cc < TS_CG; cc += TS_THREADS / 32) {
+        const int a = blockIdx.y * TS_CG + cc;
+        if (a >= k) break;
         const double* v = V + (size_t)a * ldv + r0;
-        double acc[kMaxCols];
+        double acc[MAXM];
 #pragma unroll
-        for (int b = 0; b < kMaxCols; ++b) acc[b] = 0.0;
-        for (int rr = lane; rr < nr; rr += 32) {
-            double x = v[rr];
+        for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
+        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
+            double x[TS_UNROLL];
 #pragma unroll
-            for (int b = 0; b < kMaxCols; ++b)
-                if (b < m) acc[b] += x * Ws[b * rows + rr];
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = base + 32 * u;
+                x[u] = rr < nr ? v[rr] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = min(base + 32 * u, rows - 1);
+#pragma unroll
+                for (int b = 0; b < MAXM; ++b)
+                    if (b < m) acc[b] += x[u] * Ws[b * rows + rr];
+            }
         }
 #pragma unroll
-        for (int b = 0; b < kMaxCols; ++b) {
+        for (int b = 0; b < MAXM; ++b) {
             if (b >= m) break;
             double t = acc[b];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
             if (lane == 0) out[(size_t)a * m + b] = t;
         }
     }
@@ -391,36 +432,203 @@ __global__ void k_ts_reduce(int nchunks, int k, int m, const double* __restrict_
     }
 }
 
-// W = beta W + alpha V H, thread per row, H staged through shared memory.
+// W = beta W + alpha V H, one thread per row, H staged through shared memory;
+// TS_UNROLL basis entries of the row are loaded before the FMAs that use them.
+template <int MAXM>
 __global__ void __launch_bounds__(256) k_ts_nn(int n, int k, int m, double alpha, const double* __restrict__ V,
                                                long long ldv, const double* __restrict__ H, long long ldh,
                                                double beta, double* __restrict__ W, long long ldw) {
     constexpr int KT = 128;
-    __shared__ double Hs[KT * kMaxCols];
+    __shared__ double Hs[KT * MAXM];
     int r = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[kMaxCols];
+    double acc[MAXM];
 #pragma unroll
-    for (int b = 0; b < kMaxCols; ++b) acc[b] = 0.0;
+    for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
     for (int a0 = 0; a0 < k; a0 += KT) {
         int kt = min(KT, k - a0);
         __syncthreads();
         for (int idx = threadIdx.x; idx < kt * m; idx += blockDim.x) {
             int a = idx / m, b = idx % m;
-            Hs[idx] = H[(size_t)b * ldh + a0 + a];
+            Hs[a * MAXM + b] = H[(size_t)b * ldh + a0 + a];
         }
         __syncthreads();
         if (r < n) {
-            for (int a = 0; a < kt; ++a) {
-                double x = V[(size_t)(a0 + a) * ldv + r];
+            for (int a = 0; a < kt; a += TS_UNROLL) {
+                double x[TS_UNROLL];
 #pragma unroll
-                for (int b = 0; b < kMaxCols; ++b)
-                    if (b < m) acc[b] += x * Hs[a * m + b];
+                for (int u = 0; u < TS_UNROLL; ++u) x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : 0.0;
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u) {
+                    if (a + u >= kt) break;
+#pragma unroll
+                    for (int b = 0; b < MAXM; ++b)
+                        if (b < m) acc[b] += x[u] * Hs[(a + u) * MAXM + b];
+                }
             }
         }
     }
     if (r >= n) return;
 #pragma unroll
-    for (int b = 0; b < kMaxCols; ++b) {
+    for (int b = 0; b < MAXM; ++b) {
+        if (b >= m) break;
+        double* w = W + (size_t)b * ldw + r;
+        *w = beta == 0.0 ? alpha * acc[b] : beta * (*w) + alpha * acc[b];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float tall-skinny products.  FP64 runs at 1/64 of the FP32 rate on
+// this chip, so the basis products of the mixed-precision solve use
+// double-float arithmetic on the FP32 pipes instead (Dekker, "A floating-point
+// technique for extending the available precision", 1971; Knuth, TAOCP
+// vol. 2, 4.2.2, two-sum): a value is hi + lo with two floats, a product
+// a*b = p + e with e = fma(a, b, -p) exact, and a running sum keeps its
+// rounding error by two-sum.  Every 32 terms the pair is folded into an FP64
+// accumulator.  The result carries about 48 significant bits, with no FP64
+// instruction in the inner loops.  All FP32 operations are explicitly rounded
+// intrinsics so that the compiler cannot contract them.  The basis is kept as
+// (hi, lo) pairs (float2, 8 bytes per entry: the same traffic as FP64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return make_float2(hi, lo);
+}
+
+// (sh, sl) += a * b for double-floats a, b.
+__device__ __forceinline__ void df_madd(float& sh, float& sl, float2 a, float2 b) {
+    float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    float s = __fadd_rn(sh, p);
+    float z = __fsub_rn(s, sh);
+    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+    sh = s;
+}
+
+__global__ void k_to_df(int n, int m, const double* __restrict__ X, long long ldx, float2* __restrict__ Y,
+                        long long ldy) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * m) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    Y[(size_t)j * ldy + i] = df_split(X[(size_t)j * ldx + i]);
+}
+
+// (sh, sl) += (oh, ol) for two double-float partial sums (two-sum on the heads).
+__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
+    float s = __fadd_rn(sh, oh);
+    float z = __fsub_rn(s, sh);
+    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(oh, z));
+    sl = __fadd_rn(sl, __fadd_rn(t, ol));
+    sh = s;
+}
+
+// Partial H = V^T W as k_ts_tn_partial, with V in double-float and the chunk
+// of W split into double-float pairs in shared memory.  The lanes' partial
+// sums are combined by a double-float butterfly, so no FP64 instruction runs
+// before lane 0 folds the pair into the partial.
+template <int MAXM>
+__global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, int m, int rows,
+                                                                 const float2* __restrict__ V, long long ldv,
+                                                                 const double* __restrict__ W, long long ldw,
+                                                                 double* __restrict__ part) {
+    extern __shared__ double sm[];
+    float2* Ws = reinterpret_cast<float2*>(sm);   // [m][rows]
+    const int chunk = blockIdx.x;
+    const int r0 = chunk * rows;
+    const int nr = min(rows, n - r0);
+    for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
+        int b = idx / rows, rr = idx % rows;
+        Ws[idx] = rr < nr ? df_split(W[(size_t)b * ldw + r0 + rr]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double* out = part + (size_t)chunk * k * m;
+    for (int cc = warp; cc < TS_CG; cc += TS_THREADS / 32) {
+        const int a = blockIdx.y * TS_CG + cc;
+        if (a >= k) break;
+        const float2* v = V + (size_t)a * ldv + r0;
+        float sh[MAXM], sl[MAXM];
+#pragma unroll
+        for (int b = 0; b < MAXM; ++b) sh[b] = sl[b] = 0.f;
+        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
+            float2 x[TS_UNROLL];
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = base + 32 * u;
+                x[u] = rr < nr ? v[rr] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = min(base + 32 * u, rows - 1);
+#pragma unroll
+                for (int b = 0; b < MAXM; ++b)
+                    if (b < m) df_madd(sh[b], sl[b], x[u], Ws[b * rows + rr]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < MAXM; ++b) {
+            if (b >= m) break;
+            float h = sh[b], l = sl[b];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                float oh = __shfl_xor_sync(0xffffffffu, h, off);
+                float ol = __shfl_xor_sync(0xffffffffu, l, off);
+                df_add(h, l, oh, ol);
+            }
+            if (lane == 0) out[(size_t)a * m + b] = (double)h + (double)l;
+        }
+    }
+}
+
+// W = beta W + alpha V H with V in double-float, one thread per row; H is
+// split once per CTA into shared memory and the double-float sums are folded
+// into FP64 every 32 basis columns.
+template <int MAXM>
+__global__ void __launch_bounds__(256) k_ts_nn_df(int n, int k, int m, double alpha, const float2* __restrict__ V,
+                                                  long long ldv, const double* __restrict__ H, long long ldh,
+                                                  double beta, double* __restrict__ W, long long ldw) {
+    constexpr int KT = 32;
+    __shared__ float2 Hs[KT * MAXM];
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[MAXM];
+#pragma unroll
+    for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
+    for (int a0 = 0; a0 < k; a0 += KT) {
+        int kt = min(KT, k - a0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kt * m; idx += blockDim.x) {
+            int a = idx / m, b = idx % m;
+            Hs[a * MAXM + b] = df_split(H[(size_t)b * ldh + a0 + a]);
+        }
+        __syncthreads();
+        if (r < n) {
+            float sh[MAXM], sl[MAXM];
+#pragma unroll
+            for (int b = 0; b < MAXM; ++b) sh[b] = sl[b] = 0.f;
+            for (int a = 0; a < kt; a += TS_UNROLL) {
+                float2 x[TS_UNROLL];
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u)
+                    x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u) {
+                    if (a + u >= kt) break;
+#pragma unroll
+                    for (int b = 0; b < MAXM; ++b)
+                        if (b < m) df_madd(sh[b], sl[b], x[u], Hs[(a + u) * MAXM + b]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < MAXM; ++b)
+                if (b < m) acc[b] += (double)sh[b] + (double)sl[b];
+        }
+    }
+    if (r >= n) return;
+#pragma unroll
+    for (int b = 0; b < MAXM; ++b) {
         if (b >= m) break;
         double* w = W + (size_t)b * ldw + r;
         *w = beta == 0.0 ? alpha * acc[b] : beta * (*w) + alpha * acc[b];
@@ -582,6 +790,29 @@ int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OM, int ldm, T*
 template int st_spmm_ma<double>(st_problem*, const double*, int, int, double*, int, double*, int, cudaStream_t);
 template int st_spmm_ma<float>(st_problem*, const float*, int, int, float*, int, float*, int, cudaStream_t);
 
+int st_spmm_at64(st_problem* p, const double* X, int ldx, int ncols, double* Out, int ldo, cudaStream_t s) {
+    if (ncols <= 0) return ST_OK;
+    if (!p->at64) return ST_ENOTSUP;
+    int blocks = (p->n_h + 127) / 128;
+    st_prof_begin(s, "spmm_at64", (double)p->nnz * 12.0 + 4.0 * (p->n_h + 1) + 16.0 * (double)p->n_h * ncols,
+                  2.0 * (double)p->nnz * ncols);
+    if (p->max_row_nnz <= 3)
+        k_spmm_ma_reg<double, 3><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
+                                                         Out, ldo, nullptr, 0);
+    else if (p->max_row_nnz <= 9)
+        k_spmm_ma_reg<double, 9><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
+                                                         Out, ldo, nullptr, 0);
+    else if (p->max_row_nnz <= 27)
+        k_spmm_ma_reg<double, 27><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
+                                                          Out, ldo, nullptr, 0);
+    else
+        k_spmm_ma_generic<double><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
+                                                          Out, ldo, nullptr, 0);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
 int st_spmm_comb64(st_problem* p, double cm, double ca, const double* X, int ldx, int ncols, double beta, double* Out,
                    int ldo, cudaStream_t s) {
     if (ncols <= 0) return ST_OK;
@@ -691,33 +922,83 @@ int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const f
 }
 
 size_t st_tsgemm_partial_elems(int n, int k, int m) {
-    int rows = ts_rows_per_cta(n);
-    size_t nch = (size_t)((n + rows - 1) / rows);
-    return nch * (size_t)k * (size_t)m;
+    // the largest partial buffer any column chunk of at most kMaxCols needs
+    int mm = m < kMaxCols ? m : kMaxCols;
+    size_t nch = (size_t)((n + ts_rows(mm) - 1) / ts_rows(mm));
+    size_t nch1 = (size_t)((n + ts_rows(1) - 1) / ts_rows(1));
+    return (nch > nch1 ? nch : nch1) * (size_t)k * (size_t)mm;
 }
+
+namespace {
+// Launch the templated kernel whose MAXM (2, 4, 8 or 16) covers m.
+template <template <int> class L, typename... Args>
+void dispatch_m(int m, Args... args) {
+    if (m <= 2) L<2>::go(args...);
+    else if (m <= 4) L<4>::go(args...);
+    else if (m <= 8) L<8>::go(args...);
+    else L<16>::go(args...);
+}
+
+template <int MAXM> struct LaunchTn {
+    static void go(dim3 grid, size_t smem, cudaStream_t s, int n, int k, int m, int rows, const double* V, int ldv,
+                   const double* W, int ldw, double* part) {
+        static const bool set = [] {
+            cudaFuncSetAttribute(k_ts_tn_partial<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
+            return true;
+        }();
+        (void)set;
+        k_ts_tn_partial<MAXM><<<grid, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, part);
+    }
+};
+template <int MAXM> struct LaunchTnDf {
+    static void go(dim3 grid, size_t smem, cudaStream_t s, int n, int k, int m, int rows, const float2* V, int ldv,
+                   const double* W, int ldw, double* part) {
+        static const bool set = [] {
+            cudaFuncSetAttribute(k_ts_tn_df_partial<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
+            return true;
+        }();
+        (void)set;
+        k_ts_tn_df_partial<MAXM><<<grid, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, part);
+    }
+};
+template <int MAXM> struct LaunchNn {
+    static void go(int blocks, cudaStream_t s, int n, int k, int m, double alpha, const double* V, int ldv,
+                   const double* H, int ldh, double beta, double* W, int ldw) {
+        k_ts_nn<MAXM><<<blocks, 256, 0, s>>>(n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw);
+    }
+};
+template <int MAXM> struct LaunchNnDf {
+    static void go(int blocks, cudaStream_t s, int n, int k, int m, double alpha, const float2* V, int ldv,
+                   const double* H, int ldh, double beta, double* W, int ldw) {
+        k_ts_nn_df<MAXM><<<blocks, 256, 0, s>>>(n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw);
+    }
+};
+}  // namespace
 
 int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W, int ldw, double* H, int ldh,
                  double* partial, cudaStream_t s) {
     if (k <= 0 || m <= 0) return ST_OK;
-    if (m > kMaxCols) return ST_EINVAL;
+    if (m > kMaxCols) {   // wider blocks in chunks of kMaxCols columns
+        for (int j0 = 0; j0 < m; j0 += kMaxCols) {
+            int mm = m - j0 < kMaxCols ? m - j0 : kMaxCols;
+            ST_TRY(st_tsgemm_tn(n, k, mm, V, ldv, W + (size_t)j0 * ldw, ldw, H + (size_t)j0 * ldh, ldh, partial, s));
+        }
+        return ST_OK;
+    }
     if (n <= 0) {
         // empty sum
         for (int b = 0; b < m; ++b) ST_CUDA_TRY(cudaMemsetAsync(H + (size_t)b * ldh, 0, sizeof(double) * k, s));
         return ST_OK;
     }
-    int rows = ts_rows_per_cta(n);
-    int nch = (n + rows - 1) / rows;
-    size_t smem = sizeof(double) * (size_t)m * rows;
-    static bool smem_set = false;
-    if (!smem_set) {
-        cudaFuncSetAttribute(k_ts_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        smem_set = true;
-    }
-    st_prof_begin(s, "ts_tn", 8.0 * (double)n * (k + m) + 8.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
-    k_ts_tn_partial<<<nch, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, partial);
+    const int rows = ts_rows(m);
+    const int nch = (n + rows - 1) / rows;
+    const size_t smem = sizeof(double) * (size_t)m * rows;
+    dim3 grid(nch, (k + TS_CG - 1) / TS_CG);
+    if (grid.y > 65535) return ST_EINVAL;
+    st_prof_begin(s, "ts_tn", 8.0 * (double)n * (k + m) + 16.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
+    dispatch_m<LaunchTn>(m, grid, smem, s, n, k, m, rows, V, ldv, W, ldw, partial);
     ST_LAUNCH_CHECK();
-    int tot = k * m;
-    k_ts_reduce<<<(tot + 7) / 8, 256, 0, s>>>(nch, k, m, partial, H, ldh);
+    k_ts_reduce<<<(k * m + 7) / 8, 256, 0, s>>>(nch, k, m, partial, H, ldh);
     st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;
@@ -726,13 +1007,76 @@ int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W,
 int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, const double* H, int ldh, double beta,
                  double* W, int ldw, cudaStream_t s) {
     if (n <= 0 || m <= 0) return ST_OK;
-    if (m > kMaxCols) return ST_EINVAL;
+    if (m > kMaxCols) {   // wider blocks in chunks of kMaxCols columns
+        for (int j0 = 0; j0 < m; j0 += kMaxCols) {
+            int mm = m - j0 < kMaxCols ? m - j0 : kMaxCols;
+            ST_TRY(st_tsgemm_nn(n, k, mm, alpha, V, ldv, H + (size_t)j0 * ldh, ldh, beta, W + (size_t)j0 * ldw, ldw, s));
+        }
+        return ST_OK;
+    }
     if (k <= 0) {
         if (beta == 1.0) return ST_OK;
         return st_axpby64(n, m, 0.0, W, ldw, beta, W, ldw, s);
     }
     st_prof_begin(s, "ts_nn", 8.0 * (double)n * (k + m * (beta == 0.0 ? 1 : 2)), 2.0 * (double)n * k * m);
-    k_ts_nn<<<(n + 255) / 256, 256, 0, s>>>(n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw);
+    dispatch_m<LaunchNn>(m, (n + 255) / 256, s, n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_to_df(int n, int m, const double* X, int ldx, float2* Y, int ldy, cudaStream_t s) {
+    long long tot = (long long)n * m;
+    if (tot <= 0) return ST_OK;
+    k_to_df<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, X, ldx, Y, ldy);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const double* W, int ldw, double* H, int ldh,
+                    double* partial, cudaStream_t s) {
+    if (k <= 0 || m <= 0) return ST_OK;
+    if (m > kMaxCols) {   // wider blocks in chunks of kMaxCols columns
+        for (int j0 = 0; j0 < m; j0 += kMaxCols) {
+            int mm = m - j0 < kMaxCols ? m - j0 : kMaxCols;
+            ST_TRY(st_tsgemm_tn_df(n, k, mm, V, ldv, W + (size_t)j0 * ldw, ldw, H + (size_t)j0 * ldh, ldh, partial, s));
+        }
+        return ST_OK;
+    }
+    if (n <= 0) {
+        for (int b = 0; b < m; ++b) ST_CUDA_TRY(cudaMemsetAsync(H + (size_t)b * ldh, 0, sizeof(double) * k, s));
+        return ST_OK;
+    }
+    const int rows = ts_rows(m);
+    const int nch = (n + rows - 1) / rows;
+    const size_t smem = sizeof(double) * (size_t)m * rows;
+    dim3 grid(nch, (k + TS_CG - 1) / TS_CG);
+    if (grid.y > 65535) return ST_EINVAL;
+    st_prof_begin(s, "ts_tn_df", 8.0 * (double)n * (k + m) + 16.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
+    dispatch_m<LaunchTnDf>(m, grid, smem, s, n, k, m, rows, V, ldv, W, ldw, partial);
+    ST_LAUNCH_CHECK();
+    k_ts_reduce<<<(k * m + 7) / 8, 256, 0, s>>>(nch, k, m, partial, H, ldh);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_tsgemm_nn_df(int n, int k, int m, double alpha, const float2* V, int ldv, const double* H, int ldh,
+                    double beta, double* W, int ldw, cudaStream_t s) {
+    if (n <= 0 || m <= 0) return ST_OK;
+    if (m > kMaxCols) {   // wider blocks in chunks of kMaxCols columns
+        for (int j0 = 0; j0 < m; j0 += kMaxCols) {
+            int mm = m - j0 < kMaxCols ? m - j0 : kMaxCols;
+            ST_TRY(st_tsgemm_nn_df(n, k, mm, alpha, V, ldv, H + (size_t)j0 * ldh, ldh, beta, W + (size_t)j0 * ldw, ldw, s));
+        }
+        return ST_OK;
+    }
+    if (k <= 0) {
+        if (beta == 1.0) return ST_OK;
+        return st_axpby64(n, m, 0.0, W, ldw, beta, W, ldw, s);
+    }
+    st_prof_begin(s, "ts_nn_df", 8.0 * (double)n * (k + m * (beta == 0.0 ? 1 : 2)), 2.0 * (double)n * k * m);
+    dispatch_m<LaunchNnDf>(m, (n + 255) / 256, s, n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw);
     st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;

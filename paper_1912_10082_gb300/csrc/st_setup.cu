@@ -99,7 +99,7 @@ __device__ __forceinline__ double gval(int d) { return d == 0 ? 0.0 : 0.5 * d; }
 __global__ void k_assemble_tensor(int dim, int nx, int ny, int nz, Axis1D ax, Axis1D ay, Axis1D az,
                                   int op, double kappa, double eps, double bx, double by, double bz,
                                   double half_dt, int n_h, int nnz, int* __restrict__ row_ptr,
-                                  int* __restrict__ col, double* __restrict__ m64, double* __restrict__ a64,
+                                  int* __restrict__ col, double* __restrict__ m64, double* __restrict__ a64, double* __restrict__ at64,
                                   double* __restrict__ p64, double* __restrict__ q64,
                                   float* __restrict__ m32, float* __restrict__ a32, float* __restrict__ p32,
                                   float* __restrict__ q32) {
@@ -152,11 +152,15 @@ __global__ void k_assemble_tensor(int dim, int nx, int ny, int nz, Axis1D ax, Ax
                     conv = __dadd_rn(__dadd_rn(cxv, cyv), czv);
                 }
                 double av = op == ST_CONVDIFF ? __dadd_rn(__dmul_rn(eps, stiff), conv) : __dmul_rn(kappa, stiff);
+                // A^T on the same pattern: the stiffness and mass factors are
+                // symmetric in the offsets, the convection factor G is skew
+                double atv = op == ST_CONVDIFF ? __dsub_rn(__dmul_rn(eps, stiff), conv) : av;
                 double pv = __dadd_rn(mv, __dmul_rn(half_dt, av));
                 double qv = __dsub_rn(mv, __dmul_rn(half_dt, av));
                 col[e] = (jz * ny + jy) * nx + jx;
                 m64[e] = mv;
                 a64[e] = av;
+                at64[e] = atv;
                 p64[e] = pv;
                 q64[e] = qv;
                 m32[e] = (float)mv;
@@ -213,6 +217,7 @@ static int alloc_csr(st_problem* p) {
     size_t nnz = (size_t)p->nnz;
     ST_TRY(st_alloc(p, (void**)&p->row_ptr, sizeof(int) * (p->n_h + 1)));
     ST_TRY(st_alloc(p, (void**)&p->col, sizeof(int) * nnz));
+    ST_TRY(st_alloc(p, (void**)&p->at64, sizeof(double) * nnz));
     double** d64[4] = {&p->m64, &p->a64, &p->p64, &p->q64};
     float** d32[4] = {&p->m32, &p->a32, &p->p32, &p->q32};
     for (int i = 0; i < 4; ++i) ST_TRY(st_alloc(p, (void**)d64[i], sizeof(double) * nnz));
@@ -236,7 +241,7 @@ static int assemble_tensor(st_problem* p) {
     int blocks = (p->n_h + threads - 1) / threads;
     k_assemble_tensor<<<blocks, threads, 0, p->stream>>>(
         d.dim, p->n[0], p->n[1], p->n[2], a1[0], a1[1], a1[2], d.op, p->kappa, d.eps, d.beta[0], d.beta[1],
-        d.beta[2], 0.5 * p->dt, p->n_h, p->nnz, p->row_ptr, p->col, p->m64, p->a64, p->p64, p->q64, p->m32,
+        d.beta[2], 0.5 * p->dt, p->n_h, p->nnz, p->row_ptr, p->col, p->m64, p->a64, p->at64, p->p64, p->q64, p->m32,
         p->a32, p->p32, p->q32);
     ST_LAUNCH_CHECK();
     return ST_OK;
@@ -354,10 +359,7 @@ extern "C" int st_set_coefficients(st_problem* p, int op, double kappa, double e
     p->d.eps = eps;
     for (int i = 0; i < 3; ++i) p->d.beta[i] = beta ? beta[i] : 0.0;
     // the captured Crank-Nicolson graph holds the old coefficients
-    if (p->cn_graph) {
-        cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
-        p->cn_graph = nullptr;
-    }
+    p->cn_stale = true;
     ST_TRY(assemble_tensor(p));
     set_spectrum(p);
     return ST_OK;

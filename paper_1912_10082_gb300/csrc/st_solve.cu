@@ -37,8 +37,14 @@ inline double ms_since(Clock::time_point t0) {
 
 enum SlotId {
     S_F1D = 0, S_F1C, S_MAQ, S_WH, S_WH2, S_TMP, S_X32, S_W32, S_T32, S_SMALL, S_PART, S_COPY, S_MV,
-    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP
+    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT
 };
+
+// Records why the Krylov process broke down (text of st_last_error).
+int breakdown(const char* why) {
+    st_note_msg(why);
+    return ST_EBREAKDOWN;
+}
 
 struct Ctx {
     st_problem* p;
@@ -112,7 +118,7 @@ int block_qr(Ctx& c, double* W, int ldw, int m, double ref2, double drop, std::v
         ST_TRY(st_trsm_right_upper(c.n, m, dR, m, W, ldw, c.s));
         std::vector<double> G2((size_t)m * m);
         ST_TRY(ts_tn_host(c, m, m, W, ldw, W, ldw, G2.data()));
-        if (!dense::cholesky(m, G2.data(), m)) return ST_EBREAKDOWN;
+        if (!dense::cholesky(m, G2.data(), m)) return breakdown("block QR: second Gram matrix not positive definite");
         std::vector<double> R2((size_t)m * m, 0.0);
         for (int j = 0; j < m; ++j)
             for (int i = 0; i <= j; ++i) R2[(size_t)j * m + i] = G2[(size_t)i * m + j];
@@ -143,7 +149,7 @@ int block_qr(Ctx& c, double* W, int ldw, int m, double ref2, double drop, std::v
     for (int pass = 0; pass < 2; ++pass) {
         std::vector<double> G2((size_t)r * r);
         ST_TRY(ts_tn_host(c, r, r, W, ldw, W, ldw, G2.data()));
-        if (!dense::cholesky(r, G2.data(), r)) return ST_EBREAKDOWN;
+        if (!dense::cholesky(r, G2.data(), r)) return breakdown("block QR: Gram matrix of the kept directions not positive definite");
         std::vector<double> R2((size_t)r * r, 0.0);
         for (int j = 0; j < r; ++j)
             for (int i = 0; i <= j; ++i) R2[(size_t)j * r + i] = G2[(size_t)i * r + j];
@@ -292,34 +298,48 @@ bool ritz_values(int k, const double* Am, const double* Mm, int ld, std::vector<
     return true;
 }
 
-// Projected equation Mm Y D_t^T + Am Y C_t^T = GF (k x n_t), by the time
+// Projected equation Mm Y D_t^T + Am Y C_t^T = Gm F2c^T (k x n_t), by the time
 // recurrence of the lower-bidiagonal time pencil:
-// (Mm + dt/2 Am) y_l = GF_l + (Mm - dt/2 Am) y_{l-1}.
-bool projected_solve(int k, int n_t, double dt, const double* Mm, const double* Am, int ld, const double* GF,
-                     std::vector<double>& Y) {
-    std::vector<double> P((size_t)k * k), N((size_t)k * k);
+// (Mm + dt/2 Am) y_l = Gm F2c[l, :]^T + (Mm - dt/2 Am) y_{l-1}.
+// With P = Mm + dt/2 Am factored once, S = P^{-1}(Mm - dt/2 Am) and
+// G = P^{-1} Gm are formed first, so each step costs one k x k product.
+bool projected_solve(int k, int n_t, double dt, const double* Mm, const double* Am, int ld, const double* Gm,
+                     int ldg, int r, const double* F2c, std::vector<double>& Y, bool sym = true) {
+    std::vector<double> P((size_t)k * k), S((size_t)k * k), G((size_t)k * r);
     for (int j = 0; j < k; ++j)
         for (int i = 0; i < k; ++i) {
             double m = Mm[(size_t)j * ld + i], a = Am[(size_t)j * ld + i];
             P[(size_t)j * k + i] = m + 0.5 * dt * a;
-            N[(size_t)j * k + i] = m - 0.5 * dt * a;
+            S[(size_t)j * k + i] = m - 0.5 * dt * a;
         }
-    if (!dense::cholesky(k, P.data(), k)) return false;
+    for (int q = 0; q < r; ++q)
+        for (int i = 0; i < k; ++i) G[(size_t)q * k + i] = Gm[(size_t)q * ldg + i];
+    if (sym) {
+        if (!dense::cholesky(k, P.data(), k)) return false;
+        dense::chol_solve(k, P.data(), k, S.data(), k, k);
+        dense::chol_solve(k, P.data(), k, G.data(), k, r);
+    } else {
+        std::vector<int> piv(k);
+        if (!dense::lu(k, P.data(), k, piv.data())) return false;
+        dense::lu_solve(k, P.data(), k, piv.data(), S.data(), k, k);
+        dense::lu_solve(k, P.data(), k, piv.data(), G.data(), k, r);
+    }
     Y.assign((size_t)k * n_t, 0.0);
-    std::vector<double> r(k);
     for (int l = 0; l < n_t; ++l) {
-        const double* g = GF + (size_t)l * k;
-        for (int i = 0; i < k; ++i) r[i] = g[i];
+        double* y = &Y[(size_t)l * k];
+        for (int q = 0; q < r; ++q) {
+            double f = F2c[(size_t)q * n_t + l];
+            const double* gq = &G[(size_t)q * k];
+            for (int i = 0; i < k; ++i) y[i] += gq[i] * f;
+        }
         if (l > 0) {
-            const double* yp = &Y[(size_t)(l - 1) * k];
+            const double* yp = y - k;
             for (int j = 0; j < k; ++j) {
                 double t = yp[j];
-                const double* nc = &N[(size_t)j * k];
-                for (int i = 0; i < k; ++i) r[i] += nc[i] * t;
+                const double* sc = &S[(size_t)j * k];
+                for (int i = 0; i < k; ++i) y[i] += sc[i] * t;
             }
         }
-        dense::chol_solve(k, P.data(), k, r.data(), k, 1);
-        std::memcpy(&Y[(size_t)l * k], r.data(), sizeof(double) * k);
     }
     return true;
 }
@@ -333,16 +353,23 @@ int ensure_basis(st_problem* p, Ctx& c, int need_cols, int keep_cols, double** M
     cap = std::min<size_t>(cap, (size_t)p->d.max_basis + 16);
     if (cap < (size_t)need_cols) cap = need_cols;
     double *nv, *nmv;
+    float2* ndf = nullptr;
     ST_TRY(st_alloc(p, (void**)&nv, sizeof(double) * (size_t)c.n * cap));
     ST_TRY(st_alloc(p, (void**)&nmv, sizeof(double) * (size_t)c.n * cap));
+    if (p->d.precision == ST_MIXED) ST_TRY(st_alloc(p, (void**)&ndf, sizeof(float2) * (size_t)c.n * cap));
     if (keep_cols > 0) {
         ST_CUDA_TRY(cudaMemcpyAsync(nv, p->V, sizeof(double) * (size_t)c.n * keep_cols, cudaMemcpyDeviceToDevice, c.s));
         ST_CUDA_TRY(cudaMemcpyAsync(nmv, p->slot_ptr[S_MV], sizeof(double) * (size_t)c.n * keep_cols,
                                     cudaMemcpyDeviceToDevice, c.s));
+        if (ndf && p->Vdf)
+            ST_CUDA_TRY(cudaMemcpyAsync(ndf, p->Vdf, sizeof(float2) * (size_t)c.n * keep_cols,
+                                        cudaMemcpyDeviceToDevice, c.s));
     }
     ST_CUDA_TRY(cudaStreamSynchronize(c.s));
     if (p->V) st_free_one(p, p->V);
+    if (p->Vdf) st_free_one(p, p->Vdf);
     if (p->slot_ptr[S_MV]) st_free_one(p, p->slot_ptr[S_MV]);
+    p->Vdf = ndf;
     p->V = nv;
     p->V_cap_cols = cap;
     p->slot_ptr[S_MV] = nmv;
@@ -451,6 +478,21 @@ int ts_tn_dev(Ctx& c, int k, int m, const double* V, int ldv, const double* W, i
     return st_tsgemm_tn(c.n, k, m, V, ldv, W, ldw, H, ldh, part, c.s);
 }
 
+// H (device) = V^T W and W -= V H against the first k basis columns: FP64, or
+// double-float on the FP32 pipes when the solve is in mixed precision.
+int basis_tn(Ctx& c, bool df, int k, int m, const double* W, int ldw, double* H, int ldh) {
+    if (!df) return ts_tn_dev(c, k, m, c.p->V, c.n, W, ldw, H, ldh);
+    if (k == 0 || m == 0) return ST_OK;
+    double* part;
+    ST_TRY(st_slot(c.p, S_PART, sizeof(double) * st_tsgemm_partial_elems(c.n, k, m), (void**)&part));
+    return st_tsgemm_tn_df(c.n, k, m, c.p->Vdf, c.n, W, ldw, H, ldh, part, c.s);
+}
+
+int basis_nn_sub(Ctx& c, bool df, int k, int m, const double* H, int ldh, double* W, int ldw) {
+    if (!df) return st_tsgemm_nn(c.n, k, m, -1.0, c.p->V, c.n, H, ldh, 1.0, W, ldw, c.s);
+    return st_tsgemm_nn_df(c.n, k, m, -1.0, c.p->Vdf, c.n, H, ldh, 1.0, W, ldw, c.s);
+}
+
 // Rank of a block from its Gram matrix G = W^T W (host, m x m) and, when it
 // has full rank and a Cholesky factor, the first CholQR factor R1 = L^T.
 // The rank counts the eigenvalues above drop^2 max(lambda_max, ref2), the
@@ -458,6 +500,7 @@ int ts_tn_dev(Ctx& c, int k, int m, const double* V, int ldv, const double* W, i
 struct QrPlan {
     int rank = 0;
     bool fast = false;
+    bool severe = false;      // a kept direction lost more than 6 digits to Gram-Schmidt
     std::vector<double> R1;   // m x m upper, ld m
 };
 
@@ -467,7 +510,13 @@ void qr_plan(const double* G, int m, double ref2, double drop, QrPlan& q) {
     double lmax = std::max(w[m - 1], 0.0);
     double thr = drop * drop * std::max(lmax, ref2);
     q.rank = 0;
-    for (int i = 0; i < m; ++i) q.rank += w[i] > thr;
+    double wkept = 0.0;
+    for (int i = 0; i < m; ++i)
+        if (w[i] > thr) {
+            wkept = q.rank == 0 ? w[i] : std::min(wkept, w[i]);
+            ++q.rank;
+        }
+    q.severe = q.rank > 0 && wkept < 1e-12 * std::max(lmax, ref2);
     q.fast = false;
     if (q.rank == m && w[0] > 1e-24 * lmax) {
         std::vector<double> L(G, G + (size_t)m * m);
@@ -510,7 +559,8 @@ std::vector<double> upper_product(int m, const double* R2, const double* R1) {
 }
 
 // Gram matrix Gb = b^T b of the residual direction b = w_hat - M V Mm^{-1} V^T w_hat,
-// w_hat = -(s M q + A q) R_q, evaluated on the device (one extra synchronisation).
+// w_hat = -(s M q + A q) R_q (the rational Arnoldi residual), evaluated on the
+// device (one extra synchronisation, taken only at residual checks).
 int residual_gram_explicit(Ctx& c, int k, int pn, int pl, double s, const double* MAq, const double* MV,
                            const std::vector<double>& X1, const HostSym& Mm, const std::vector<double>& Rq,
                            std::vector<double>& Gb) {
@@ -536,75 +586,143 @@ int residual_gram_explicit(Ctx& c, int k, int pn, int pl, double s, const double
     std::vector<double> L((size_t)k * k);
     for (int j = 0; j < k; ++j)
         for (int i = 0; i < k; ++i) L[(size_t)j * k + i] = Mm.a[(size_t)j * Mm.ld + i];
-    if (!dense::cholesky(k, L.data(), k)) return ST_EBREAKDOWN;
+    if (!dense::cholesky(k, L.data(), k)) return breakdown("residual: projected mass matrix not positive definite");
     dense::chol_solve(k, L.data(), k, Vw.data(), k, pl);
     ST_TRY(ts_nn_host(c, k, pl, -1.0, MV, n, Vw.data(), 1.0, Wh2, n));
     Gb.assign((size_t)pl * pl, 0.0);
     return ts_tn_host(c, pl, pl, Wh2, n, Wh2, n, Gb.data());
 }
 
-// The same Gram matrix from products that phase B already computed:
-// with Wh = s M q + A q and c = Mm^{-1} V^T Wh, b = -(Wh - M V c) R_q and
-// Z^T Z = Wh^T Wh - (MV^T Wh)^T c - c^T (MV^T Wh) + c^T (MV^T MV) c.
-// Returns false when cancellation could spoil it (trace(Z^T Z) tiny next to
-// trace(Wh^T Wh)); the caller then takes the explicit route.
-bool residual_gram_products(int k, int pn, int pl, double s, const std::vector<double>& X1,
-                            const std::vector<double>& X1b, const std::vector<double>& Gq, const HostSym& Mm,
-                            const HostSym& Gmv, const std::vector<double>& Rq, std::vector<double>& Gb) {
-    const int q2 = 2 * pn;
-    std::vector<double> VtWh((size_t)k * pn), MVtWh((size_t)k * pn), WhWh((size_t)pn * pn);
-    for (int j = 0; j < pn; ++j)
-        for (int i = 0; i < k; ++i) {
-            VtWh[(size_t)j * k + i] = s * X1[(size_t)j * k + i] + X1[(size_t)(pn + j) * k + i];
-            MVtWh[(size_t)j * k + i] = s * X1b[(size_t)j * k + i] + X1b[(size_t)(pn + j) * k + i];
-        }
-    for (int j = 0; j < pn; ++j)
-        for (int i = 0; i < pn; ++i)
-            WhWh[(size_t)j * pn + i] = s * s * Gq[(size_t)j * q2 + i] +
-                                       s * (Gq[(size_t)(pn + j) * q2 + i] + Gq[(size_t)j * q2 + pn + i]) +
-                                       Gq[(size_t)(pn + j) * q2 + pn + i];
-    std::vector<double> L((size_t)k * k);
-    for (int j = 0; j < k; ++j)
-        for (int i = 0; i < k; ++i) L[(size_t)j * k + i] = Mm.a[(size_t)j * Mm.ld + i];
-    if (!dense::cholesky(k, L.data(), k)) return false;
-    std::vector<double> C = VtWh;
-    dense::chol_solve(k, L.data(), k, C.data(), k, pn);
-    std::vector<double> GC((size_t)k * pn, 0.0);   // Gmv C
-    for (int j = 0; j < pn; ++j)
-        for (int q = 0; q < k; ++q) {
-            double cq = C[(size_t)j * k + q];
-            const double* g = &Gmv.a[(size_t)q * Gmv.ld];
-            for (int i = 0; i < k; ++i) GC[(size_t)j * k + i] += g[i] * cq;
-        }
-    std::vector<double> ZZ((size_t)pn * pn);
-    double tz = 0.0, tw = 0.0;
-    for (int j = 0; j < pn; ++j)
-        for (int i = 0; i < pn; ++i) {
-            double a = 0.0, b = 0.0, d = 0.0;
-            for (int q = 0; q < k; ++q) {
-                a += MVtWh[(size_t)i * k + q] * C[(size_t)j * k + q];
-                b += C[(size_t)i * k + q] * MVtWh[(size_t)j * k + q];
-                d += C[(size_t)i * k + q] * GC[(size_t)j * k + q];
-            }
-            ZZ[(size_t)j * pn + i] = WhWh[(size_t)j * pn + i] - a - b + d;
-        }
-    for (int i = 0; i < pn; ++i) {
-        tz += ZZ[(size_t)i * pn + i];
-        tw += WhWh[(size_t)i * pn + i];
+// Iterations until the next residual check.  The projected solve of a check
+// costs about k^2 n_t flops on the host.  Once two checks exist, the observed
+// geometric rate predicts how many iterations remain to reach tol; the next
+// check comes after about half of them, so the solve overshoots by little
+// while checks stay rare.  Before that, or when the residual stagnates, a
+// cost rule spaces the checks.
+int check_gap(const std::vector<int>& hist_it, const std::vector<double>& hist_res, int it, double res, double tol,
+              double cost) {
+    int gap_cost = (int)std::max(1.0, std::min(16.0, cost / 4e6));
+    if (hist_it.empty() || !(res > 0.0)) return gap_cost;
+    double prev = hist_res.back();
+    int dit = it - hist_it.back();
+    if (dit <= 0 || !(prev > res)) return gap_cost;
+    double rate = std::pow(res / prev, 1.0 / dit);   // per iteration, < 1
+    double need = std::log(tol / res) / std::log(rate);
+    int gap = (int)std::floor(0.5 * need);
+    return std::max(1, std::min(gap, 24));
+}
+
+// Shifted solve (A + s M) W = M X for a nonsymmetric A (convection-diffusion):
+// flexible GMRES per column, right-preconditioned by the fast-diagonalisation
+// solve of the symmetric part eps K + s M.  The preconditioned directions T_j
+// are kept, so W = T y has exactly the GMRES residual whatever the
+// preconditioner's precision: FP64 transforms, or FP32 ones in mixed
+// precision.  Classical Gram-Schmidt twice, Givens rotations on the host,
+// restarts after J steps; stops at ||b - (A + sM) w|| <= rtol ||b||.
+int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx,
+                         int ncols, double* W, int ldw, double rtol, int* iters_out) {
+    st_problem* p = c.p;
+    const int n = c.n;
+    constexpr int J = 40, CYCLES = 12;
+    double *Z, *T, *bb;
+    ST_TRY(st_slot(p, S_GZ, sizeof(double) * (size_t)n * (J + 1), (void**)&Z));
+    ST_TRY(st_slot(p, S_GT, sizeof(double) * (size_t)n * J, (void**)&T));
+    ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n, (void**)&bb));
+    double* tmp;
+    float *x32 = nullptr, *w32 = nullptr, *t32 = nullptr;
+    ST_TRY(st_slot(p, S_TMP, sizeof(double) * (size_t)n, (void**)&tmp));
+    if (prec == ST_MIXED) {
+        ST_TRY(st_slot(p, S_X32, sizeof(float) * (size_t)n, (void**)&x32));
+        ST_TRY(st_slot(p, S_W32, sizeof(float) * (size_t)n, (void**)&w32));
+        ST_TRY(st_slot(p, S_T32, sizeof(float) * (size_t)n, (void**)&t32));
     }
-    if (!(tz > 1e-6 * tw)) return false;
-    Gb.assign((size_t)pl * pl, 0.0);
-    for (int b2 = 0; b2 < pl; ++b2)
-        for (int a2 = 0; a2 < pl; ++a2) {
-            double acc = 0.0;
-            for (int j = 0; j < pn; ++j) {
-                double t = 0.0;
-                for (int i = 0; i < pn; ++i) t += Rq[(size_t)a2 * pl + i] * ZZ[(size_t)j * pn + i];
-                acc += t * Rq[(size_t)b2 * pl + j];
-            }
-            Gb[(size_t)b2 * pl + a2] = acc;
+    auto precond = [&](const double* z, double* t) -> int {
+        if (prec != ST_MIXED) return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, 1, t, n, tmp, c.s);
+        ST_TRY(st_convert_64_32(n, 1, z, n, x32, n, c.s));
+        ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, 1, w32, n, t32, c.s));
+        return st_convert_32_64_add(n, 1, w32, n, t, n, 0.0, c.s);
+    };
+    ST_TRY(stage_reserve(p, 3 * pad32(J + 1)));
+    Stage sg(c);
+    int total = 0;
+    std::vector<double> H((size_t)(J + 1) * J), cs(J), sn(J), g(J + 1), y(J);
+    for (int col = 0; col < ncols; ++col) {
+        double* w = W + (size_t)col * ldw;
+        if (MX) {
+            ST_TRY(st_copy_cols64(n, 1, MX + (size_t)col * ldmx, ldmx, bb, n, c.s));
+        } else {
+            ST_TRY(st_spmm_ma<double>(p, X + (size_t)col * ldx, ldx, 1, bb, n, (double*)nullptr, n, c.s));
         }
-    return true;
+        ST_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * n, c.s));
+        ST_TRY(st_copy_cols64(n, 1, bb, n, Z, n, c.s));   // r = b
+        double bnorm = -1.0;
+        for (int cyc = 0; cyc < CYCLES; ++cyc) {
+            double* dn = sg.out(1);
+            ST_TRY(ts_tn_dev(c, 1, 1, Z, n, Z, n, dn, 1));
+            ST_TRY(sg.fetch());
+            double beta = std::sqrt(std::max(sg.host_of(dn)[0], 0.0));
+            if (bnorm < 0) bnorm = beta;
+            if (!(beta > rtol * bnorm) || beta == 0.0) break;
+            ST_TRY(st_axpby64(n, 1, 1.0 / beta, Z, n, 0.0, Z, n, c.s));
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            int j = 0;
+            bool done = false;
+            for (; j < J && !done; ++j) {
+                double* zj = Z + (size_t)j * n;
+                double* tj = T + (size_t)j * n;
+                double* u = Z + (size_t)(j + 1) * n;
+                ST_TRY(precond(zj, tj));
+                ST_TRY(st_spmm_comb64(p, shift, 1.0, tj, n, 1, 0.0, u, n, c.s));
+                double* dh[2];
+                for (int pass = 0; pass < 2; ++pass) {
+                    dh[pass] = sg.out(j + 1);
+                    ST_TRY(ts_tn_dev(c, j + 1, 1, Z, n, u, n, dh[pass], j + 1));
+                    ST_TRY(st_tsgemm_nn(n, j + 1, 1, -1.0, Z, n, dh[pass], j + 1, 1.0, u, n, c.s));
+                }
+                double* du = sg.out(1);
+                ST_TRY(ts_tn_dev(c, 1, 1, u, n, u, n, du, 1));
+                ST_TRY(sg.fetch());
+                ++total;
+                double* hc = &H[(size_t)j * (J + 1)];
+                for (int i = 0; i <= j; ++i) hc[i] = sg.host_of(dh[0])[i] + sg.host_of(dh[1])[i];
+                double hn = std::sqrt(std::max(sg.host_of(du)[0], 0.0));
+                hc[j + 1] = hn;
+                for (int i = 0; i < j; ++i) {
+                    double t0 = cs[i] * hc[i] + sn[i] * hc[i + 1];
+                    hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+                    hc[i] = t0;
+                }
+                double rr = std::hypot(hc[j], hc[j + 1]);
+                cs[j] = rr > 0 ? hc[j] / rr : 1.0;
+                sn[j] = rr > 0 ? hc[j + 1] / rr : 0.0;
+                hc[j] = rr;
+                hc[j + 1] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                done = std::fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0;
+                if (!done && hn > 0) ST_TRY(st_axpby64(n, 1, 1.0 / hn, u, n, 0.0, u, n, c.s));
+            }
+            // y = R^{-1} g, w += T y
+            for (int i = j - 1; i >= 0; --i) {
+                double t0 = g[i];
+                for (int q = i + 1; q < j; ++q) t0 -= H[(size_t)q * (J + 1) + i] * y[q];
+                y[i] = t0 / H[(size_t)i * (J + 1) + i];
+            }
+            double* dy;
+            ST_TRY(sg.in(y.data(), j, &dy));
+            ST_TRY(st_tsgemm_nn(n, j, 1, 1.0, T, n, dy, j, 1.0, w, n, c.s));
+            if (done) {
+                ST_TRY(sg.fetch());   // the upload region is reused by the next column
+                break;
+            }
+            // restart from the true residual r = b - (A + s M) w
+            ST_TRY(st_spmm_comb64(p, -shift, -1.0, w, n, 1, 0.0, Z, n, c.s));
+            ST_TRY(st_axpby64(n, 1, 1.0, bb, n, 1.0, Z, n, c.s));
+        }
+    }
+    if (iters_out) *iters_out += total;
+    return ST_OK;
 }
 
 // RKSM driver.  Each iteration synchronises twice: after phase A (shifted
@@ -623,6 +741,15 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     st_stats S{};
     auto tp = Clock::now();
     Stage sg(c);
+    // heat: A symmetric, exact fast-diagonalisation shifted solves; convection-diffusion:
+    // A nonsymmetric, preconditioned FGMRES shifted solves and unsymmetrised projections
+    const bool sym = p->tensor_heat;
+    const double inner_tol = std::max(1e-13, 1e-3 * tol);
+    auto resolvent = [&](double s, const double* X, int ldx, const double* MX, int ldmx, int m, double* W,
+                         int ldw) -> int {
+        if (sym) return shifted_solve(c, prec, s, X, ldx, MX, ldmx, m, W, ldw);
+        return shifted_solve_fgmres(c, prec, s, X, ldx, MX, ldmx, m, W, ldw, inner_tol, &S.inner_iterations);
+    };
 
     // ---- A1: rank compression of F = F1 F2^T ----
     double* F1d;
@@ -757,10 +884,10 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     double* MV = nullptr;
     ST_TRY(ensure_basis(p, c, std::min(2 * pmax + 8, p->d.max_basis + 16), 0, &MV));
     double* MAq;   // [M q, A q] staging, n x 2 pmax
-    ST_TRY(st_slot(p, S_MAQ, sizeof(double) * (size_t)n * 2 * pmax, (void**)&MAq));
+    const int nmaq = sym ? 2 : 3;   // [M q, A q] or [M q, A q, A^T q]
+    ST_TRY(st_slot(p, S_MAQ, sizeof(double) * (size_t)n * nmaq * pmax, (void**)&MAq));
     tp = Clock::now();
-    ST_TRY(stage_reserve(p, 3 * pad32((size_t)r * r) + pad32(1) + pad32((size_t)2 * r * r) + pad32((size_t)r * r) +
-                                pad32((size_t)r * r)));
+    ST_TRY(stage_reserve(p, 3 * pad32((size_t)r * r) + pad32(1) + pad32((size_t)2 * r * r) + pad32((size_t)r * r)));
     ST_TRY(mass_inverse(c, prec, F1c, n, r, p->V, n));
     double* dG = sg.out((size_t)r * r);
     ST_TRY(ts_tn_dev(c, r, r, p->V, n, p->V, n, dG, r));
@@ -772,7 +899,7 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     {
         QrPlan qp;
         qr_plan(sg.host_of(dG), r, 0.0, 1e-12, qp);
-        if (qp.rank == 0) return ST_EBREAKDOWN;
+        if (qp.rank == 0) return breakdown("start block has rank 0");
         if (qp.fast) {
             double* dR2;
             ST_TRY(qr_fast_launch(c, sg, p->V, n, r, qp.R1, &dR2, &dflag));
@@ -780,34 +907,32 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         } else {
             std::vector<double> Rx;
             ST_TRY(block_qr(c, p->V, n, r, 0.0, 1e-12, Rx, &k));
-            if (k == 0) return ST_EBREAKDOWN;
+            if (k == 0) return breakdown("start block has rank 0");
         }
     }
+    const bool dfb = prec == ST_MIXED;
+    if (dfb) ST_TRY(st_to_df(n, k, p->V, n, p->Vdf, n, c.s));
     ST_TRY(st_spmm_ma<double>(p, p->V, n, k, MAq, n, MAq + (size_t)n * k, n, c.s));
     double* dX0 = sg.out((size_t)k * 2 * k);
     ST_TRY(ts_tn_dev(c, k, 2 * k, p->V, n, MAq, n, dX0, k));
     double* dG1 = sg.out((size_t)k * r);
     ST_TRY(ts_tn_dev(c, k, r, p->V, n, F1c, n, dG1, k));
-    double* dGmv = sg.out((size_t)k * k);
-    ST_TRY(ts_tn_dev(c, k, k, MAq, n, MAq, n, dGmv, k));
     ST_CUDA_TRY(cudaMemcpyAsync(MV, MAq, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, c.s));
     ST_TRY(sg.fetch());
-    if (dflag && sg.host_of(dflag)[0] != 0.0) return ST_EBREAKDOWN;
-    HostSym Mm, Am, Hb, Gmv;
+    if (dflag && sg.host_of(dflag)[0] != 0.0) return breakdown("start block: device Cholesky pivot not positive");
+    HostSym Mm, Am, Hb;
     std::vector<double> Gm;   // k x r, ld = ldg
     int ldg = 0;
     {
         const double* X = sg.host_of(dX0);
         const double* G = sg.host_of(dG1);
-        const double* Gv = sg.host_of(dGmv);
         Mm.grow(k);
         Am.grow(k);
-        Gmv.grow(k);
         for (int j = 0; j < k; ++j)
             for (int i = 0; i < k; ++i) {
                 Mm(i, j) = 0.5 * (X[(size_t)j * k + i] + X[(size_t)i * k + j]);
-                Am(i, j) = 0.5 * (X[(size_t)(k + j) * k + i] + X[(size_t)(k + i) * k + j]);
-                Gmv(i, j) = 0.5 * (Gv[(size_t)j * k + i] + Gv[(size_t)i * k + j]);
+                Am(i, j) = sym ? 0.5 * (X[(size_t)(k + j) * k + i] + X[(size_t)(k + i) * k + j])
+                               : X[(size_t)(k + j) * k + i];
             }
         ldg = std::max(64, 2 * k);
         Gm.assign((size_t)ldg * r, 0.0);
@@ -824,6 +949,8 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     int next_check = 1;
     int mu_extra = 0;
     const double a_int = p->lam_min, b_int = p->lam_max;
+    std::vector<int> hist_it;
+    std::vector<double> hist_res;
 
     while (true) {
         if (it >= p->d.maxit) break;
@@ -843,20 +970,20 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         S.ms_phase[7] += ms_since(tp);
         ++it;
         size_t needA = 2 * pad32((size_t)pl * pl) + 2 * pad32((size_t)k * pl);
-        size_t needB = 2 * pad32((size_t)k * 2 * pl) + pad32((size_t)pl * 2 * pl) + pad32((size_t)4 * pl * pl) +
-                       pad32((size_t)pl * r) + 2 * pad32((size_t)pl * pl) + pad32(1);
+        size_t needB = pad32((size_t)k * nmaq * pl) + pad32((size_t)pl * 2 * pl) + pad32((size_t)pl * r) +
+                       2 * pad32((size_t)pl * pl) + pad32(1);
         ST_TRY(stage_reserve(p, std::max(needA, needB)));
         // ---- phase A: A3 shifted solve into the next basis slot, A4 block CGS2 ----
         tp = Clock::now();
         double* W = p->V + (size_t)k * n;
-        ST_TRY(shifted_solve(c, prec, s, p->V + (size_t)lo * n, n, MV + (size_t)lo * n, n, pl, W, n));
+        ST_TRY(resolvent(s, p->V + (size_t)lo * n, n, MV + (size_t)lo * n, n, pl, W, n));
         double* dG0 = sg.out((size_t)pl * pl);
         ST_TRY(ts_tn_dev(c, pl, pl, W, n, W, n, dG0, pl));
         double* dh[2];
         for (int pass = 0; pass < 2; ++pass) {
             dh[pass] = sg.out((size_t)k * pl);
-            ST_TRY(ts_tn_dev(c, k, pl, p->V, n, W, n, dh[pass], k));
-            ST_TRY(st_tsgemm_nn(n, k, pl, -1.0, p->V, n, dh[pass], k, 1.0, W, n, c.s));
+            ST_TRY(basis_tn(c, dfb, k, pl, W, n, dh[pass], k));
+            ST_TRY(basis_nn_sub(c, dfb, k, pl, dh[pass], k, W, n));
         }
         double* dGw = sg.out((size_t)pl * pl);
         ST_TRY(ts_tn_dev(c, pl, pl, W, n, W, n, dGw, pl));
@@ -873,6 +1000,16 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         for (int i = 0; i < pl; ++i) ref2 = std::max(ref2, sg.host_of(dG0)[(size_t)i * pl + i]);
         QrPlan qp;
         qr_plan(sg.host_of(dGw), pl, ref2, 1e-10, qp);
+        if (qp.severe) {
+            // the block almost lies in range(V): its remainder carries the rounding
+            // of the two passes, so a third pass in FP64 cleans it before the QR
+            std::vector<double> h3((size_t)k * pl), G3((size_t)pl * pl);
+            ST_TRY(ts_tn_host(c, k, pl, p->V, n, W, n, h3.data()));
+            ST_TRY(ts_nn_host(c, k, pl, -1.0, p->V, n, h3.data(), 1.0, W, n));
+            for (size_t i = 0; i < Hcol.size(); ++i) Hcol[i] += h3[i];
+            ST_TRY(ts_tn_host(c, pl, pl, W, n, W, n, G3.data()));
+            qr_plan(G3.data(), pl, ref2, 1e-10, qp);
+        }
         int pn = 0;
         std::vector<double> Rq((size_t)pl * pl, 0.0);
         double* dR2 = nullptr;
@@ -888,29 +1025,25 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         S.ms_phase[2] += ms_since(tp);
         // ---- phase B: A5 products of the new block ----
         tp = Clock::now();
-        std::vector<double> X1, X1b, X2, X3, Gq;
+        std::vector<double> X1, X2, X3;
         if (pn > 0) {
             ST_TRY(st_spmm_ma<double>(p, W, n, pn, MAq, n, MAq + (size_t)n * pn, n, c.s));
-            double* dX1 = sg.out((size_t)k * 2 * pn);
-            ST_TRY(ts_tn_dev(c, k, 2 * pn, p->V, n, MAq, n, dX1, k));
-            double* dX1b = sg.out((size_t)k * 2 * pn);
-            ST_TRY(ts_tn_dev(c, k, 2 * pn, MV, n, MAq, n, dX1b, k));
+            if (!sym) ST_TRY(st_spmm_at64(p, W, n, pn, MAq + (size_t)2 * n * pn, n, c.s));
+            if (dfb) ST_TRY(st_to_df(n, pn, W, n, p->Vdf + (size_t)k * n, n, c.s));
+            double* dX1 = sg.out((size_t)k * nmaq * pn);
+            ST_TRY(basis_tn(c, dfb, k, nmaq * pn, MAq, n, dX1, k));
             double* dX2 = sg.out((size_t)pn * 2 * pn);
             ST_TRY(ts_tn_dev(c, pn, 2 * pn, W, n, MAq, n, dX2, pn));
-            double* dGq = sg.out((size_t)4 * pn * pn);
-            ST_TRY(ts_tn_dev(c, 2 * pn, 2 * pn, MAq, n, MAq, n, dGq, 2 * pn));
             double* dX3 = sg.out((size_t)pn * r);
             ST_TRY(ts_tn_dev(c, pn, r, W, n, F1c, n, dX3, pn));
             ST_TRY(sg.fetch());
             if (qp.fast) {
-                if (sg.host_of(dflag)[0] != 0.0) return ST_EBREAKDOWN;
+                if (sg.host_of(dflag)[0] != 0.0) return breakdown("new block: device Cholesky pivot not positive");
                 Rq = upper_product(pl, sg.host_of(dR2), qp.R1.data());
             }
             auto grab = [&](const double* d, size_t m) { return std::vector<double>(sg.host_of(d), sg.host_of(d) + m); };
-            X1 = grab(dX1, (size_t)k * 2 * pn);
-            X1b = grab(dX1b, (size_t)k * 2 * pn);
+            X1 = grab(dX1, (size_t)k * nmaq * pn);
             X2 = grab(dX2, (size_t)pn * 2 * pn);
-            Gq = grab(dGq, (size_t)4 * pn * pn);
             X3 = grab(dX3, (size_t)pn * r);
         }
         S.ms_phase[3] += ms_since(tp);
@@ -925,22 +1058,15 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         bool check = (pn == 0) || (it >= next_check) || (it >= p->d.maxit) || (k + pn + pn > p->d.max_basis);
         if (check) {
             tp = Clock::now();
-            std::vector<double> GF((size_t)k * nt, 0.0);
-            for (int l = 0; l < nt; ++l)
-                for (int q = 0; q < r; ++q) {
-                    double f = F2c[(size_t)q * nt + l];
-                    if (f == 0.0) continue;
-                    for (int i = 0; i < k; ++i) GF[(size_t)l * k + i] += Gm[(size_t)q * ldg + i] * f;
-                }
-            if (!projected_solve(k, nt, dt, Mm.a.data(), Am.a.data(), Mm.ld, GF.data(), Y)) return ST_EBREAKDOWN;
+            if (!projected_solve(k, nt, dt, Mm.a.data(), Am.a.data(), Mm.ld, Gm.data(), ldg, r, F2c.data(), Y, sym))
+                return breakdown("projected equation singular");
             S.ms_phase[4] += ms_since(tp);
             S.residual_checks++;
             tp = Clock::now();
             double rr = 0.0;
             if (pn > 0) {
                 std::vector<double> Gb;
-                if (!residual_gram_products(k, pn, pl, s, X1, X1b, Gq, Mm, Gmv, Rq, Gb))
-                    ST_TRY(residual_gram_explicit(c, k, pn, pl, s, MAq, MV, X1, Mm, Rq, Gb));
+                ST_TRY(residual_gram_explicit(c, k, pn, pl, s, MAq, MV, X1, Mm, Rq, Gb));
                 // f = H^{-T} E_last  (k x pl)
                 std::vector<double> H((size_t)k * k), f((size_t)k * pl, 0.0);
                 for (int j = 0; j < k; ++j)
@@ -948,7 +1074,7 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
                 std::vector<int> piv(k);
                 dense::lu(k, H.data(), k, piv.data());
                 for (int j = 0; j < pl; ++j) f[(size_t)j * k + lo + j] = 1.0;
-                if (!dense::lu_solve_transpose(k, H.data(), k, piv.data(), f.data(), k, pl)) return ST_EBREAKDOWN;
+                if (!dense::lu_solve_transpose(k, H.data(), k, piv.data(), f.data(), k, pl)) return breakdown("rational Arnoldi Hessenberg matrix singular");
                 // g_l = f^T (dt/2)(y_l + y_{l-1});  ||R||^2 = sum_l g_l^T Gb g_l
                 std::vector<double> gl(pl);
                 for (int l = 0; l < nt; ++l) {
@@ -971,10 +1097,9 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
                 if (pn == 0 && res > tol) status = ST_EBREAKDOWN;
                 break;
             }
-            // next check: every iteration while the projected solve is cheap
-            double cost = (double)k * k * nt;
-            int gap = (int)std::max(1.0, std::min(16.0, cost / 4e6));
-            next_check = it + gap;
+            next_check = it + check_gap(hist_it, hist_res, it, res, tol, (double)k * k * nt);
+            hist_it.push_back(it);
+            hist_res.push_back(res);
         }
         if (pn == 0) {
             status = ST_EBREAKDOWN;
@@ -985,20 +1110,18 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         ST_CUDA_TRY(cudaMemcpyAsync(MV + (size_t)k * n, MAq, sizeof(double) * (size_t)n * pn, cudaMemcpyDeviceToDevice,
                                     c.s));
         const int kn = k + pn;
-        const int q2 = 2 * pn;
         Mm.grow(kn);
         Am.grow(kn);
-        Gmv.grow(kn);
         for (int j = 0; j < pn; ++j) {
             for (int i = 0; i < k; ++i) {
                 Mm(i, k + j) = Mm(k + j, i) = X1[(size_t)j * k + i];
-                Am(i, k + j) = Am(k + j, i) = X1[(size_t)(pn + j) * k + i];
-                Gmv(i, k + j) = Gmv(k + j, i) = X1b[(size_t)j * k + i];
+                Am(i, k + j) = X1[(size_t)(pn + j) * k + i];
+                Am(k + j, i) = sym ? X1[(size_t)(pn + j) * k + i] : X1[(size_t)(2 * pn + j) * k + i];
             }
             for (int i = 0; i < pn; ++i) {
                 Mm(k + i, k + j) = 0.5 * (X2[(size_t)j * pn + i] + X2[(size_t)i * pn + j]);
-                Am(k + i, k + j) = 0.5 * (X2[(size_t)(pn + j) * pn + i] + X2[(size_t)(pn + i) * pn + j]);
-                Gmv(k + i, k + j) = 0.5 * (Gq[(size_t)j * q2 + i] + Gq[(size_t)i * q2 + j]);
+                Am(k + i, k + j) = sym ? 0.5 * (X2[(size_t)(pn + j) * pn + i] + X2[(size_t)(pn + i) * pn + j])
+                                       : X2[(size_t)(pn + j) * pn + i];
             }
         }
         if (kn > ldg) {
@@ -1018,11 +1141,8 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     }
     if (Y.empty() || (int)(Y.size() / std::max(1, nt)) != k) {
         // iterations ended without a check of the final basis
-        std::vector<double> GF((size_t)k * nt, 0.0);
-        for (int l = 0; l < nt; ++l)
-            for (int q = 0; q < r; ++q)
-                for (int i = 0; i < k; ++i) GF[(size_t)l * k + i] += Gm[(size_t)q * ldg + i] * F2c[(size_t)q * nt + l];
-        if (!projected_solve(k, nt, dt, Mm.a.data(), Am.a.data(), Mm.ld, GF.data(), Y)) return ST_EBREAKDOWN;
+        if (!projected_solve(k, nt, dt, Mm.a.data(), Am.a.data(), Mm.ld, Gm.data(), ldg, r, F2c.data(), Y, sym))
+            return breakdown("projected equation singular (final basis)");
         mu_extra = 0;
     }
     // ---- A9 output ----
@@ -1080,38 +1200,47 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     return status;
 }
 
-// ||L Z^T||_F for L (device n x m) and Z (host nt x m): block CGS2 QR of L
-// into R (m x m), then the small product on the host.
+// ||L Z^T||_F for L (device n x m, overwritten) and Z (host nt x m): QR of L one
+// column at a time, then the small product R Z^T on the host.  The factor
+// [F1, M V, A V] of a residual is far from full rank (F1 lies in range(M V),
+// A V mostly in range(M V) too) and its columns differ in norm by orders of
+// magnitude, so each column is re-projected until a pass no longer halves it
+// ("twice is enough" made adaptive, at most four passes), and a column whose
+// remainder falls below 1e-13 of its original norm adds no direction.  This
+// keeps the backward error per column near rounding, like a Householder QR.
 int lowrank_fro(Ctx& c, double* L, int m, const std::vector<double>& Z, int nt, double* out) {
+    const int n = c.n;
     std::vector<double> R((size_t)m * m, 0.0);
-    const int bs = 8;
-    for (int j0 = 0; j0 < m; j0 += bs) {
-        int mb = std::min(bs, m - j0);
-        double* Wb = L + (size_t)j0 * c.n;
-        std::vector<double> Hc((size_t)j0 * mb, 0.0), hh((size_t)j0 * mb);
-        for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
-            ST_TRY(ts_tn_host(c, j0, mb, L, c.n, Wb, c.n, hh.data()));
-            ST_TRY(ts_nn_host(c, j0, mb, -1.0, L, c.n, hh.data(), 1.0, Wb, c.n));
-            for (size_t i = 0; i < hh.size(); ++i) Hc[i] += hh[i];
+    int q = 0;
+    std::vector<double> nu2(1), h;
+    for (int j = 0; j < m; ++j) {
+        double* w = L + (size_t)j * n;
+        ST_TRY(ts_tn_host(c, 1, 1, w, n, w, n, nu2.data()));
+        const double nu0 = std::sqrt(std::max(nu2[0], 0.0));
+        double nu = nu0;
+        std::vector<double> coef((size_t)std::max(q, 1), 0.0);
+        for (int pass = 0; pass < 4 && q > 0 && nu > 0.0; ++pass) {
+            h.assign(q, 0.0);
+            ST_TRY(ts_tn_host(c, q, 1, L, n, w, n, h.data()));
+            ST_TRY(ts_nn_host(c, q, 1, -1.0, L, n, h.data(), 1.0, w, n));
+            for (int i = 0; i < q; ++i) coef[i] += h[i];
+            ST_TRY(ts_tn_host(c, 1, 1, w, n, w, n, nu2.data()));
+            double nu_new = std::sqrt(std::max(nu2[0], 0.0));
+            bool settled = nu_new > 0.5 * nu;
+            nu = nu_new;
+            if (settled) break;
         }
-        std::vector<double> Rb;
-        int rb = 0;
-        ST_TRY(block_qr(c, Wb, c.n, mb, 0.0, 1e-15, Rb, &rb));
-        if (rb < mb) {
-            // zero the dropped directions so later blocks ignore them
-            for (int j = rb; j < mb; ++j)
-                ST_CUDA_TRY(cudaMemsetAsync(Wb + (size_t)j * c.n, 0, sizeof(double) * c.n, c.s));
-        }
-        for (int j = 0; j < mb; ++j) {
-            for (int i = 0; i < j0; ++i) R[(size_t)(j0 + j) * m + i] = Hc[(size_t)j * j0 + i];
-            for (int i = 0; i < rb; ++i) R[(size_t)(j0 + j) * m + j0 + i] = Rb[(size_t)j * mb + i];
+        for (int i = 0; i < q; ++i) R[(size_t)j * m + i] = coef[i];
+        if (nu > 1e-13 * nu0 && nu > 0.0) {
+            double* dst = L + (size_t)q * n;
+            ST_TRY(st_axpby64(n, 1, 1.0 / nu, w, n, 0.0, dst, n, c.s));
+            R[(size_t)j * m + q] = nu;
+            ++q;
         }
     }
-    // R is block upper triangular with dense diagonal blocks (rank-deficient blocks
-    // give a dense r x m factor), so the product runs over every column.
     double s = 0.0;
     for (int l = 0; l < nt; ++l)
-        for (int i = 0; i < m; ++i) {
+        for (int i = 0; i < q; ++i) {
             double v = 0.0;
             for (int j = 0; j < m; ++j) v += R[(size_t)j * m + i] * Z[(size_t)j * nt + l];
             s += v * v;
@@ -1157,7 +1286,7 @@ extern "C" int st_solve(st_problem* p, const double* F1, int ldf1, const double*
                         st_solution* sol, st_stats* stats) {
     if (!p || !F1 || !F2) return ST_EINVAL;
     if (ncols < 1 || ncols > 16 || ldf1 < p->n_h || ldf2 < p->n_t) return ST_EINVAL;
-    if (!p->tensor_heat) return ST_ENOTSUP;
+    if (p->dim < 1) return ST_ENOTSUP;
     return solve_impl(p, F1, ldf1, F2, ldf2, ncols, sol, stats);
 }
 

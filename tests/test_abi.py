@@ -57,7 +57,8 @@ def test_struct_layouts_match_c(tmp_path):
     """sizeof/offsetof of the ABI structs seen by gcc equal the ctypes mirrors."""
     import paper_1912_10082_gb300 as st
 
-    fields = {"st_desc": st.StDesc, "st_solution": st.StSolution, "st_stats": st.StStats}
+    fields = {"st_desc": st.StDesc, "st_solution": st.StSolution, "st_stats": st.StStats,
+              "st_request": st.StRequest, "st_result": st.StResult, "st_kernel_time": st.StKernelTime}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "st.h"', "int main(void){"]
     for cname, cls in fields.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
