@@ -305,6 +305,11 @@ def bench_batched(args, wl, rank, world, local):
     value = world * dof / (ms_step * 1e-3)
     bad = [r for r in res["results"] if r["status"] != st.ST_OK]
     its = [r["stats"]["iterations"] for r in res["results"]]
+    # where the slots' time went (host clock between synchronisation points, summed over instances)
+    names = ["compress", "shift_solve_cgs", "block_qr", "products", "projected_solve", "residual", "output",
+             "shifts"]
+    phase_s = {nm: sum(r["stats"]["ms_phase"][i] for r in res["results"]) * 1e-3 for i, nm in enumerate(names)}
+    busy_s = sum(r["t_end"] - r["t_start"] for r in res["results"])
     comps = {}
     ms64, _, _ = timed(st.ST_FP64, st.ST_METHOD_RKSM, 1, 0, dev)
     comps["fp64_rksm_batched"] = {"value": dof / (ms64[0] * 1e-3), "ms_per_step": ms64[0]}
@@ -341,7 +346,8 @@ def bench_batched(args, wl, rank, world, local):
                    "instances": len(insts), "dof": dof, "slots": slots, "tol": 1e-8,
                    "l2": "inputs of the batch (%.0f MB) exceed L2" % (sum(r['F1'].nbytes for r in insts) / 1e6),
                    "parallelism": f"replicas{world}"},
-        "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its))},
+        "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its)),
+                   "slot_busy_s": busy_s, "phase_s": phase_s},
         "cpu_baseline": None, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
         "comparators": comps,
     }

@@ -960,8 +960,9 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         ST_TRY(ensure_basis(p, c, k + pl, k, &MV));
         // ---- shift ----
         tp = Clock::now();
-        int ritz_every = k <= 96 ? 1 : (k + 47) / 48;
-        if (last_ritz_k < 0 || it % ritz_every == 0) {
+        // Ritz values cost O(k^3) on the host: refresh them while the basis is
+        // small, then whenever it has grown by an eighth since the last refresh
+        if (last_ritz_k < 0 || k <= 16 || k >= last_ritz_k + std::max(2, last_ritz_k / 8)) {
             if (!ritz_values(k, Am.a.data(), Mm.a.data(), Mm.ld, ritz)) ritz.clear();
             last_ritz_k = k;
         }
