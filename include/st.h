@@ -250,9 +250,12 @@ const char* st_last_error(void);
 /* ---- many independent solves on one GPU: batched and served workloads ----
  * The paper solves one problem at a time; the executor runs many solves of
  * the Section 4 method at once.  `slots` worker threads each own a CUDA
- * stream and a cache of problem handles keyed by geometry (operators and
- * fast-diagonalisation tables stay on the device between requests; a new
- * coefficient re-runs the assembly only).  Requests are admitted in arrival
+ * stream; problem handles live in a pool shared by the slots and keyed by
+ * geometry (operators and fast-diagonalisation tables stay on the device
+ * between requests; a new coefficient re-runs the assembly only; at most
+ * 4 x slots handles are kept, and none whose operators exceed 512 MB).
+ * Device memory of handles comes from the stream-ordered allocator, so one
+ * slot's allocations never synchronise the others.  Requests are admitted in arrival
  * order as long as their estimated device footprint (st_request_bytes) fits
  * the free part of the HBM budget; a request that does not fit is passed
  * over until memory frees up, and one larger than the whole budget runs when

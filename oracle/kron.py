@@ -77,3 +77,43 @@ def forward_substitution(M, A, D, C, F: np.ndarray) -> np.ndarray:
             rhs -= D[l, l - 1] * (M @ U[:, l - 1]) + C[l, l - 1] * (A @ U[:, l - 1])
         U[:, l] = diag_blocks[key].solve(rhs)
     return U
+
+
+def forward_substitution_cg(M, A, D, C, F1: np.ndarray, F2: np.ndarray, steps: int, rtol: float = 1e-14):
+    """The first ``steps`` columns of the block forward substitution, each block solved by
+    conjugate gradients (the diagonal blocks D[l,l] M + C[l,l] A are symmetric positive
+    definite for the heat operator).  For grids whose direct factorisation does not fit:
+    forward substitution fixes the first columns exactly whatever the later ones are.
+    The load is given as factors, F[:, l] = F1 @ F2[l]."""
+    n_h = M.shape[0]
+    U = np.zeros((n_h, steps))
+    prev = None
+    for l in range(steps):
+        Bl = (D[l, l] * M + C[l, l] * A).tocsr()
+        rhs = F1 @ F2[l]
+        if l > 0:
+            rhs = rhs - (D[l, l - 1] * (M @ prev) + C[l, l - 1] * (A @ prev))
+        x = _cg(Bl, rhs, rtol, 20 * n_h)
+        U[:, l] = x
+        prev = x
+    return U
+
+
+def _cg(B, b: np.ndarray, rtol: float, maxiter: int) -> np.ndarray:
+    """Textbook conjugate gradients (Hestenes-Stiefel) from x = 0, stopping at ||r|| <= rtol ||b||."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    stop = (rtol * np.linalg.norm(b)) ** 2
+    for _ in range(maxiter):
+        if rr <= stop:
+            return x
+        q = B @ p
+        alpha = rr / float(p @ q)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = float(r @ r)
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    raise RuntimeError("CG did not reach the requested tolerance")

@@ -49,6 +49,10 @@ struct FdAxis {
     float* Q32 = nullptr;
     double* lam = nullptr;  // eigenvalues of K phi = lam M phi, j = 1..n
     double* c2 = nullptr;   // 2 / ((n+1) mu_j), mu_j the M eigenvalue of sine mode j
+    // folded half tables {H0, H1, G0, G1}: H_p[k][i'] = Q[k][2i'+p] (k, i' < K_p, K_0 = ceil(n/2),
+    // K_1 = floor(n/2)), G_p = H_p^T
+    double* fold64[4] = {};
+    float* fold32[4] = {};
 };
 
 struct st_problem {
@@ -67,6 +71,11 @@ struct st_problem {
     double* at64 = nullptr;     // A^T on the same (symmetric) pattern; box problems only
     float *m32 = nullptr, *a32 = nullptr, *p32 = nullptr, *q32 = nullptr;
     FdAxis ax[3];
+    // stencil of P and N on a box grid (every n_d >= 3): the 27 values of an interior
+    // row in (dz, dy, dx) order, copied from the assembled CSR (zeros beyond dim)
+    bool box_ok = false;
+    double box_p64[27] = {}, box_q64[27] = {};
+    float box_p32[27] = {}, box_q32[27] = {};
     double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M), or of its diffusion part
     double fd_lam_min = 0.0, fd_lam_max = 0.0;   // the same for unit diffusion (sums of 1D sine-mode eigenvalues)
     double fd_kappa = 1.0;                 // diffusion the fast-diagonalisation transforms use
@@ -87,8 +96,8 @@ struct st_problem {
     double* cn_buf = nullptr;
     const void* cn_key[4] = {nullptr, nullptr, nullptr, nullptr};
     // grow-only device workspace slots
-    void* slot_ptr[24] = {};
-    size_t slot_bytes[24] = {};
+    void* slot_ptr[32] = {};
+    size_t slot_bytes[32] = {};
     // staging area of the solver's synchronisation points: sm_dev holds
     // [download region | upload region] of sm_cap doubles each on the device,
     // sm_host the pinned host mirror of both
@@ -142,7 +151,7 @@ int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, co
 // Double-float variants for a basis V stored as (hi, lo) float pairs: FP64-accurate
 // to about 48 bits, computed on the FP32 pipes.
 int st_to_df(int n, int m, const double* X, int ldx, float2* Y, int ldy, cudaStream_t s);
-int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const double* W, int ldw,
+int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2* W, int ldw,
                     double* H, int ldh, double* partial, cudaStream_t s);
 int st_tsgemm_nn_df(int n, int k, int m, double alpha, const float2* V, int ldv, const double* H, int ldh,
                     double beta, double* W, int ldw, cudaStream_t s);

@@ -2,10 +2,12 @@
 // served workloads of the library (no counterpart in the paper, which solves
 // one problem at a time; each solve here is the paper's Section 4 method).
 //
-// Design.  `slots` worker threads each own a CUDA stream and a small cache of
-// problem handles keyed by geometry, so operators and fast-diagonalisation
-// tables stay on the device between requests; a new diffusion coefficient
-// only re-runs the assembly kernel.  Requests wait in one queue and are
+// Design.  `slots` worker threads each own a CUDA stream.  Problem handles
+// live in a pool shared by the slots and keyed by geometry, so operators and
+// fast-diagonalisation tables stay on the device between requests; a request
+// takes an idle handle of its geometry (rebound to the slot's stream) and a
+// new diffusion coefficient only re-runs the assembly kernel.  Handle memory
+// comes from the stream-ordered pool, so no slot's allocation stalls another.  Requests wait in one queue and are
 // admitted in arrival order, skipping ahead past requests whose estimated
 // device footprint does not fit the free part of the HBM budget (a request
 // larger than the whole budget runs when nothing else does).  A slot takes
@@ -27,6 +29,7 @@
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kExecutorUSlot = 31;   // workspace slot of a dense U staged for a request (ids below are the solver's)
 
 struct Job {
     st_request req;
@@ -61,8 +64,17 @@ GeomKey key_of(const st_desc& d) {
 
 }  // namespace
 
+struct PoolEntry {
+    GeomKey key;
+    st_problem* h = nullptr;
+    bool busy = false;
+    unsigned long long last_use = 0;
+};
+
 struct st_executor {
     int device = 0;
+    std::vector<PoolEntry> pool;      // problem handles shared by all slots, keyed by geometry
+    unsigned long long use_clock = 0;
     int nslots = 0;
     double budget = 0.0, used = 0.0;
     std::mutex mu;
@@ -111,42 +123,84 @@ bool pick(st_executor* ex, size_t* idx) {
     return false;
 }
 
-int run_one(st_executor* ex, cudaStream_t s, std::vector<std::pair<GeomKey, st_problem*>>& cache, const Job& job,
-            st_result& res) {
-    st_desc d = job.req.desc;
-    d.stream = s;
-    GeomKey key = key_of(d);
+// Take an idle pooled handle of this geometry (rebound to the slot's stream;
+// the slot that used it last synchronised its stream when it finished), or
+// build a new one.
+st_problem* checkout(st_executor* ex, const GeomKey& key, const st_desc& d, cudaStream_t s, int* status) {
+    *status = ST_OK;
+    {
+        std::lock_guard<std::mutex> lk(ex->mu);
+        for (auto& e : ex->pool)
+            if (!e.busy && e.key == key) {
+                e.busy = true;
+                e.h->stream = s;
+                e.h->d.stream = s;
+                return e.h;
+            }
+    }
     st_problem* h = nullptr;
-    for (size_t i = 0; i < cache.size(); ++i)
-        if (cache[i].first == key) {
-            h = cache[i].second;
-            std::rotate(cache.begin(), cache.begin() + i, cache.begin() + i + 1);   // most recent first
-            break;
+    *status = st_setup(&d, &h);
+    return *status == ST_OK ? h : nullptr;
+}
+
+// Return a handle to the pool.  Handles whose operators exceed 512 MB are not
+// kept; beyond 4 handles per slot the least recently used idle one goes.
+void checkin(st_executor* ex, const GeomKey& key, st_problem* h) {
+    st_problem* drop = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ex->mu);
+        bool found = false;
+        for (auto& e : ex->pool)
+            if (e.h == h) {
+                e.busy = false;
+                e.last_use = ++ex->use_clock;
+                found = true;
+            }
+        if (!found) {
+            if ((double)h->nnz * 52.0 > 512.0 * 1024 * 1024) {
+                drop = h;
+            } else {
+                ex->pool.push_back(PoolEntry{key, h, false, ++ex->use_clock});
+            }
         }
-    if (h) {
-        ST_TRY(st_set_coefficients(h, d.op, d.kappa, d.eps, d.beta));
-    } else {
-        ST_TRY(st_setup(&d, &h));
-        // keep handles whose operators are small; large ones are rebuilt per request
-        if ((double)h->nnz * 52.0 <= 512.0 * 1024 * 1024) {
-            cache.insert(cache.begin(), {key, h});
-            if (cache.size() > 2) {
-                st_destroy(cache.back().second);
-                cache.pop_back();
+        if (!drop && ex->pool.size() > (size_t)4 * ex->nslots) {
+            size_t victim = ex->pool.size();
+            for (size_t i = 0; i < ex->pool.size(); ++i)
+                if (!ex->pool[i].busy && (victim == ex->pool.size() || ex->pool[i].last_use < ex->pool[victim].last_use))
+                    victim = i;
+            if (victim < ex->pool.size()) {
+                drop = ex->pool[victim].h;
+                ex->pool.erase(ex->pool.begin() + (long)victim);
             }
         }
     }
-    bool cached = !cache.empty() && cache.front().second == h;
+    if (drop) st_destroy(drop);
+}
+
+int run_one(st_executor* ex, cudaStream_t s, const Job& job, st_result& res) {
+    st_desc d = job.req.desc;
+    d.stream = s;
+    GeomKey key = key_of(d);
+    int st0 = ST_OK;
+    st_problem* h = checkout(ex, key, d, s, &st0);
+    if (!h) return st0;
+    struct Release {
+        st_executor* ex;
+        const GeomKey& key;
+        st_problem* h;
+        ~Release() {
+            cudaStreamSynchronize(h->stream);   // nothing of this request in flight when another slot takes it
+            checkin(ex, key, h);
+        }
+    } release{ex, key, h};
+    ST_TRY(st_set_coefficients(h, d.op, d.kappa, d.eps, d.beta));
     st_solution sol{};
     double* Ud = nullptr;
     bool host_out = false;
     const bool cn = job.req.method == ST_METHOD_CN;
     if (!job.req.U_out && cn) {
-        int st = st_slot(h, 23, sizeof(double) * (size_t)h->n_h * h->n_t, (void**)&Ud);
-        if (st != ST_OK) {
-            if (!cached) st_destroy(h);
-            return st;
-        }
+        int st = st_slot(h, kExecutorUSlot, sizeof(double) * (size_t)h->n_h * h->n_t, (void**)&Ud);
+        if (st != ST_OK) return st;
         sol.ldu = h->n_h;
     } else if (job.req.U_out) {
         if (st_is_device_ptr(job.req.U_out)) {
@@ -154,11 +208,8 @@ int run_one(st_executor* ex, cudaStream_t s, std::vector<std::pair<GeomKey, st_p
             sol.ldu = job.req.ldu;
         } else {
             host_out = true;
-            int st = st_slot(h, 23, sizeof(double) * (size_t)h->n_h * h->n_t, (void**)&Ud);
-            if (st != ST_OK) {
-                if (!cached) st_destroy(h);
-                return st;
-            }
+            int st = st_slot(h, kExecutorUSlot, sizeof(double) * (size_t)h->n_h * h->n_t, (void**)&Ud);
+            if (st != ST_OK) return st;
             sol.ldu = h->n_h;
         }
         sol.U_dense = Ud;
@@ -185,7 +236,6 @@ int run_one(st_executor* ex, cudaStream_t s, std::vector<std::pair<GeomKey, st_p
             st = ST_ECUDA;
         }
     }
-    if (!cached) st_destroy(h);
     return st;
 }
 
@@ -193,7 +243,6 @@ void worker(st_executor* ex, int slot) {
     cudaSetDevice(ex->device);
     cudaStream_t s = nullptr;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    std::vector<std::pair<GeomKey, st_problem*>> cache;
     while (true) {
         Job job;
         {
@@ -212,7 +261,7 @@ void worker(st_executor* ex, int slot) {
         res.bytes_reserved = job.est;
         res.t_submit = job.t_submit;
         res.t_start = ex->now();
-        res.status = run_one(ex, s, cache, job, res);
+        res.status = run_one(ex, s, job, res);
         res.t_end = ex->now();
         {
             std::lock_guard<std::mutex> lk(ex->mu);
@@ -223,7 +272,6 @@ void worker(st_executor* ex, int slot) {
         ex->cv_done.notify_all();
         ex->cv_work.notify_all();
     }
-    for (auto& kv : cache) st_destroy(kv.second);
     if (s) cudaStreamDestroy(s);
 }
 
@@ -314,6 +362,13 @@ extern "C" int st_executor_destroy(st_executor* ex) {
     }
     ex->cv_work.notify_all();
     for (auto& t : ex->threads) t.join();
+    // the slots' streams are gone with their workers: release the pooled
+    // handles on the default stream
+    for (auto& e : ex->pool) {
+        e.h->stream = nullptr;
+        e.h->d.stream = nullptr;
+        st_destroy(e.h);
+    }
     delete ex;
     return ST_OK;
 }

@@ -82,6 +82,63 @@ __global__ void __launch_bounds__(128) k_apply_reg(int n_h, int n_t, int chunk, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused space-time apply on a uniform box grid (2D, 3D): the same
+// Y[:,l] = P u_l - N u_{l-1} without CSR gathers.  Every interior row of P and
+// N carries the same 9 (27) stencil values, taken from the assembled CSR at
+// set-up and passed as kernel parameters (constant bank, indexed at compile
+// time), so the sums below equal the CSR kernel's term for term (a neighbour
+// outside the box contributes an exact zero instead of a skipped entry).
+// A thread owns one grid point and STEPS consecutive time columns (plus the
+// column before them for N u_{l0-1}); all (STEPS+1) x 9 (27) loads are
+// independent and issued together, with no shared memory and no barrier, so
+// many CTAs per SM hide the latency.  Consecutive CTAs cover consecutive
+// points of the same time chunk: the few U columns they touch stay in L2, so
+// each U entry leaves HBM about once.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct BoxStencil {
+    T p[27];
+    T q[27];
+};
+
+template <typename T, int DIM, int STEPS>
+__global__ void __launch_bounds__(256) k_apply_box(int nx, int ny, int nz, int n_t, BoxStencil<T> S,
+                                                   const T* __restrict__ U, long long ldu, T* __restrict__ Y,
+                                                   long long ldy) {
+    const long long nxy = (long long)nx * ny;
+    const long long n_h = nxy * (DIM == 3 ? nz : 1);
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_h) return;
+    const int x = (int)(r % nx);
+    const long long t = r / nx;
+    const int y = (int)(t % ny);
+    const int z = DIM == 3 ? (int)(t / ny) : 0;
+    const int l0 = blockIdx.y * STEPS;
+    const int l1 = min(n_t, l0 + STEPS);
+    const int c0 = l0 > 0 ? l0 - 1 : 0;
+    T prevN = T(0);
+#pragma unroll
+    for (int q = 0; q <= STEPS; ++q) {
+        const int c = c0 + q;
+        if (c >= l1) break;
+        const T* u = U + (size_t)c * ldu + r;
+        T tP = T(0), tN = T(0);
+#pragma unroll
+        for (int e = 0; e < 27; ++e) {
+            const int dz = e / 9 - 1, dy = (e / 3) % 3 - 1, dx = e % 3 - 1;
+            if (DIM < 3 && dz != 0) continue;
+            const bool ok = (x + dx >= 0) && (x + dx < nx) && (y + dy >= 0) && (y + dy < ny) &&
+                            (DIM < 3 || ((z + dz >= 0) && (z + dz < nz)));
+            const T v = ok ? u[(long long)dz * nxy + (long long)dy * nx + dx] : T(0);
+            tP += S.p[e] * v;
+            tN += S.q[e] * v;
+        }
+        if (c >= l0) Y[(size_t)c * ldy + r] = tP - prevN;
+        prevN = tN;
+    }
+}
+
 // Generic CSR rows (any length): entries re-read from L1/L2 each step.
 template <typename T>
 __global__ void k_apply_generic(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
@@ -311,6 +368,150 @@ __global__ void __launch_bounds__(256) k_gemm_rr(int M, int N, int K, const T* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Folded mode product.  The sine matrix Q[j][i] = sin((j+1)(i+1) pi/(n+1)) of
+// the transforms satisfies Q[n-1-j][i] = (-1)^i Q[j][i], so an output of even
+// index i needs only the folded input X[j] + X[n-1-j] and one of odd index only
+// X[j] - X[n-1-j], for j below the middle (the middle entry of an odd n
+// enters the even outputs alone: there Q is 0 for odd i).  Each product then
+// becomes two half-size products (one per parity of the output index) with
+// the tables H_p[k][i'] = Q[k][2i'+p] and G_p = H_p^T: half the FMAs of the
+// full product.  blockIdx.z = 2 * batch + parity.
+//   SIDE 0: C[line][i] = sum_j X[line][j] Q[j][i]   (the x direction)
+//   SIDE 1: C[i][col]  = sum_j Q[i][j] X[j][col]    (the y and z directions)
+// ---------------------------------------------------------------------------
+template <typename T, int TM, int SIDE>
+__global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __restrict__ X, long long ldx,
+                                                   const T* __restrict__ H0, const T* __restrict__ H1,
+                                                   const T* __restrict__ G0, const T* __restrict__ G1,
+                                                   T* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep) {
+    constexpr int BM = 16 * TM, BN = 16 * TM, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN];
+    const int par = blockIdx.z & 1;
+    const int zb = blockIdx.z >> 1;
+    const int z1 = zb % bt.nb1, z2 = zb / bt.nb1;
+    const int K = par ? n / 2 : (n + 1) / 2;   // folded length = outputs of this parity
+    const int mid = (n & 1) ? (n - 1) / 2 : -1;
+    const T sgn = par ? T(-1) : T(1);
+    const int M = SIDE == 0 ? other : K;
+    const int N = SIDE == 0 ? K : other;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (m0 >= M || n0 >= N) return;   // the odd parity has one output fewer for odd n
+    if (SIDE == 0) {
+        X += (size_t)z1 * bt.sA1 + (size_t)z2 * bt.sA2;
+    } else {
+        X += (size_t)z1 * bt.sB1 + (size_t)z2 * bt.sB2;
+    }
+    C += (size_t)z1 * bt.sC1 + (size_t)z2 * bt.sC2;
+    const T* Hp = par ? H1 : H0;   // K x K' (k-major), SIDE 0 right operand
+    const T* Gp = par ? G1 : G0;   // K' x K (output-major), SIDE 1 left operand
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    T acc[TM][TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += 256) {
+            int mm = idx / BK, kk = idx % BK;
+            int gm = m0 + mm, gk = k0 + kk;
+            T v = T(0);
+            if (gm < M && gk < K) {
+                if (SIDE == 0) {
+                    const T* row = X + (size_t)gm * ldx;
+                    v = gk == mid ? row[gk] : row[gk] + sgn * row[n - 1 - gk];
+                } else {
+                    v = Gp[(size_t)gm * K + gk];
+                }
+            }
+            As[kk][mm] = v;
+        }
+        for (int idx = tid; idx < BK * BN; idx += 256) {
+            int kk = idx / BN, nn = idx % BN;
+            int gk = k0 + kk, gn = n0 + nn;
+            T v = T(0);
+            if (gk < K && gn < N) {
+                if (SIDE == 0) {
+                    v = Hp[(size_t)gk * K + gn];
+                } else {
+                    v = gk == mid ? X[(size_t)gk * ldx + gn]
+                                  : X[(size_t)gk * ldx + gn] + sgn * X[(size_t)(n - 1 - gk) * ldx + gn];
+                }
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], bb[TM];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TM; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TM; ++j) acc[i][j] += a[i] * bb[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            // output coordinates of the unfolded product
+            long long om = SIDE == 0 ? gm : 2LL * gm + par;
+            long long on = SIDE == 0 ? 2LL * gn + par : gn;
+            double f = ep.coef;
+            if (ep.scale) {
+                long long e = ep.left ? om * ep.J + on : on;
+                f *= fd_omega(ep, e);
+            }
+            C[(size_t)om * ldc + on] = (T)(f * (double)acc[i][j]);
+        }
+    }
+}
+
+template <typename T, int SIDE>
+int launch_gemm_fold(int n, int other, const T* X, long long ldx, const T* const* HG, T* C, long long ldc, int batch,
+                     const Batch2& bt, const FdEpi& ep, cudaStream_t s, const char* tag) {
+    if (n <= 0 || other <= 0 || batch <= 0) return ST_OK;
+    const int K0 = (n + 1) / 2, K1 = n / 2;
+    const int M = SIDE == 0 ? other : K0, N = SIDE == 0 ? K0 : other;
+    // tile choice as for the unfolded product, over both parities
+    int bm = 64;
+    double best = 1e300;
+    for (int e : {64, 32, 16}) {
+        long long tiles = (long long)((N + e - 1) / e) * ((M + e - 1) / e) * batch * 2;
+        double eff = sizeof(T) == 8 ? 1.0 : (double)e / 64.0;
+        double share = (double)((tiles + 151) / 152) * e * e / eff;
+        if (share < 0.999 * best) {
+            best = share;
+            bm = e;
+        }
+    }
+    dim3 grid((N + bm - 1) / bm, (M + bm - 1) / bm, 2 * batch);
+    if (grid.y > 65535 || grid.z > 65535) return ST_EINVAL;
+    double fma = (double)other * ((double)K0 * K0 + (double)K1 * K1) * batch;
+    double bytes = (double)sizeof(T) * ((double)K0 * K0 + (double)K1 * K1 + 2.0 * (double)other * n * batch);
+    st_prof_begin(s, tag, bytes, 2.0 * fma);
+    if (bm == 16)
+        k_gemm_fold<T, 1, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+    else if (bm == 32)
+        k_gemm_fold<T, 2, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+    else
+        k_gemm_fold<T, 4, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
 template <typename T>
 int launch_gemm_rr(int M, int N, int K, const T* A, long long lda, const T* B, long long ldb, T* C, long long ldc,
                    int batch, const Batch2& bt, const FdEpi& ep, cudaStream_t s, const char* tag) {
@@ -525,14 +726,14 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol)
     sh = s;
 }
 
-// Partial H = V^T W as k_ts_tn_partial, with V in double-float and the chunk
-// of W split into double-float pairs in shared memory.  The lanes' partial
+// Partial H = V^T W as k_ts_tn_partial, with V and W both in double-float
+// (W split once by the caller, not once per CTA: the split costs FP64).  The lanes' partial
 // sums are combined by a double-float butterfly, so no FP64 instruction runs
 // before lane 0 folds the pair into the partial.
 template <int MAXM>
 __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, int m, int rows,
                                                                  const float2* __restrict__ V, long long ldv,
-                                                                 const double* __restrict__ W, long long ldw,
+                                                                 const float2* __restrict__ W, long long ldw,
                                                                  double* __restrict__ part) {
     extern __shared__ double sm[];
     float2* Ws = reinterpret_cast<float2*>(sm);   // [m][rows]
@@ -541,7 +742,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, i
     const int nr = min(rows, n - r0);
     for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
         int b = idx / rows, rr = idx % rows;
-        Ws[idx] = rr < nr ? df_split(W[(size_t)b * ldw + r0 + rr]) : make_float2(0.f, 0.f);
+        Ws[idx] = rr < nr ? W[(size_t)b * ldw + r0 + rr] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -732,6 +933,28 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
         pv = (const T*)p->p32;
         nv = (const T*)p->q32;
     }
+    if (p->box_ok && (p->dim == 2 || p->dim == 3)) {
+        const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+        BoxStencil<T> S;
+        for (int e = 0; e < 27; ++e) {
+            S.p[e] = (T)(sizeof(T) == 8 ? p->box_p64[e] : p->box_p32[e]);
+            S.q[e] = (T)(sizeof(T) == 8 ? p->box_q64[e] : p->box_q32[e]);
+        }
+        // time columns per thread: 4 (2D) or 2 (3D), keeping the loads of a thread in registers
+        const int steps = p->dim == 2 ? 4 : 2;
+        dim3 grid((unsigned)((p->n_h + 255) / 256), (unsigned)((n_t + steps - 1) / steps));
+        if (grid.y > 65535) return ST_EINVAL;
+        double ts = (double)sizeof(T);
+        st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32", ts * 2.0 * (double)p->n_h * n_t,
+                      4.0 * (double)p->max_row_nnz * p->n_h * n_t);
+        if (p->dim == 2)
+            k_apply_box<T, 2, 4><<<grid, 256, 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+        else
+            k_apply_box<T, 3, 2><<<grid, 256, 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+        st_prof_end(s);
+        ST_LAUNCH_CHECK();
+        return ST_OK;
+    }
     int rows_blocks = (p->n_h + 127) / 128;
     // split time into chunks so that the grid holds about 300k threads
     long long want = 300000;
@@ -845,7 +1068,8 @@ int st_cn_rhs_step(st_problem* p, const double* u, const double* F1, int ldf1, c
 // products); X is read only by the first, so X and W may alias.
 template <typename T>
 static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, const T* X, int ldx, int ncols, T* W,
-                         int ldw, T* tmp, cudaStream_t s, const T* const* Q, const char* tag) {
+                         int ldw, T* tmp, cudaStream_t s, const T* const* Q, const T* const (*HG)[4],
+                         const char* tag) {
     int dim = p->dim;
     int nx = p->n[0], ny = p->n[1], nz = p->n[2];
     long long nh = p->n_h;
@@ -889,7 +1113,8 @@ static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, 
                 ep.left = 0;
                 ep.J = 1;
                 Batch2 bt{1, 0, lds, 0, 0, 0, ldd};   // one batch per column: z2 = column
-                ST_TRY(launch_gemm_rr<T>((int)R, nx, nx, src, nx, Q[0], nx, dst, nx, ncols, bt, ep, s, tag));
+                (void)Q;
+                ST_TRY((launch_gemm_fold<T, 0>(nx, (int)R, src, nx, HG[0], dst, nx, ncols, bt, ep, s, tag)));
             } else {
                 long long J = (d == 1) ? nx : (long long)nx * ny;
                 int nd = p->n[d];
@@ -897,7 +1122,7 @@ static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, 
                 ep.left = 1;
                 ep.J = J;
                 Batch2 bt{outer, 0, 0, (long long)nd * J, lds, (long long)nd * J, ldd};
-                ST_TRY(launch_gemm_rr<T>(nd, (int)J, nd, Q[d], nd, src, J, dst, J, outer * ncols, bt, ep, s, tag));
+                ST_TRY((launch_gemm_fold<T, 1>(nd, (int)J, src, J, HG[d], dst, J, outer * ncols, bt, ep, s, tag)));
             }
             src = dst;
             lds = ldd;
@@ -911,14 +1136,20 @@ int st_fd_apply64(st_problem* p, FdKind kind, double shift, double coef, const d
                   double* W, int ldw, double* tmp, cudaStream_t s) {
     if (p->dim < 1) return ST_ENOTSUP;
     const double* Q[3] = {p->ax[0].Q64, p->ax[1].Q64, p->ax[2].Q64};
-    return fd_apply_impl<double>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, "fd_gemm64");
+    const double* HG[3][4];
+    for (int d = 0; d < 3; ++d)
+        for (int t = 0; t < 4; ++t) HG[d][t] = p->ax[d].fold64[t];
+    return fd_apply_impl<double>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, HG, "fd_gemm64");
 }
 
 int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const float* X, int ldx, int ncols, float* W,
                   int ldw, float* tmp, cudaStream_t s) {
     if (p->dim < 1) return ST_ENOTSUP;
     const float* Q[3] = {p->ax[0].Q32, p->ax[1].Q32, p->ax[2].Q32};
-    return fd_apply_impl<float>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, "fd_gemm32");
+    const float* HG[3][4];
+    for (int d = 0; d < 3; ++d)
+        for (int t = 0; t < 4; ++t) HG[d][t] = p->ax[d].fold32[t];
+    return fd_apply_impl<float>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, HG, "fd_gemm32");
 }
 
 size_t st_tsgemm_partial_elems(int n, int k, int m) {
@@ -952,7 +1183,7 @@ template <int MAXM> struct LaunchTn {
 };
 template <int MAXM> struct LaunchTnDf {
     static void go(dim3 grid, size_t smem, cudaStream_t s, int n, int k, int m, int rows, const float2* V, int ldv,
-                   const double* W, int ldw, double* part) {
+                   const float2* W, int ldw, double* part) {
         static const bool set = [] {
             cudaFuncSetAttribute(k_ts_tn_df_partial<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
             return true;
@@ -1033,7 +1264,7 @@ int st_to_df(int n, int m, const double* X, int ldx, float2* Y, int ldy, cudaStr
     return ST_OK;
 }
 
-int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const double* W, int ldw, double* H, int ldh,
+int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2* W, int ldw, double* H, int ldh,
                     double* partial, cudaStream_t s) {
     if (k <= 0 || m <= 0) return ST_OK;
     if (m > kMaxCols) {   // wider blocks in chunks of kMaxCols columns

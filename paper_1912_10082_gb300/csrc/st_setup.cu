@@ -33,13 +33,37 @@ extern "C" const char* st_error_string(int status) {
     }
 }
 
+// Device memory of a handle comes from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the handle's stream): growing or
+// releasing a buffer never synchronises the device, so handles that run
+// concurrently on other streams (the executor's slots) are not stalled.  The
+// pool keeps freed memory for reuse instead of returning it to the driver.
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long keep = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
 int st_alloc(st_problem* p, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    cudaError_t e = cudaMallocAsync(ptr, bytes, p->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        st_note_cuda(e, "cudaMalloc", __FILE__, __LINE__);
+        st_note_cuda(e, "cudaMallocAsync", __FILE__, __LINE__);
         *ptr = nullptr;
         return e == cudaErrorMemoryAllocation ? ST_ENOMEM : ST_ECUDA;
     }
@@ -56,7 +80,7 @@ int st_free_one(st_problem* p, void* ptr) {
             break;
         }
     }
-    cudaFree(ptr);
+    cudaFreeAsync(ptr, p->stream);
     return ST_OK;
 }
 
@@ -197,6 +221,30 @@ __global__ void k_fd_tables(int n, double h, double* __restrict__ Q64, float* __
     }
 }
 
+// Folded half tables of the sine matrix for the mode products (see k_gemm_fold).
+__global__ void k_fd_fold_tables(int n, const double* __restrict__ Q, double* __restrict__ H0, double* __restrict__ H1,
+                                 double* __restrict__ G0, double* __restrict__ G1, float* __restrict__ h0,
+                                 float* __restrict__ h1, float* __restrict__ g0, float* __restrict__ g1) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int K0 = (n + 1) / 2, K1 = n / 2;
+    if (idx < K0 * K0) {
+        int k = idx / K0, i = idx % K0;
+        double v = Q[(size_t)k * n + 2 * i];
+        H0[(size_t)k * K0 + i] = v;
+        G0[(size_t)i * K0 + k] = v;
+        h0[(size_t)k * K0 + i] = (float)v;
+        g0[(size_t)i * K0 + k] = (float)v;
+    }
+    if (idx < K1 * K1) {
+        int k = idx / K1, i = idx % K1;
+        double v = Q[(size_t)k * n + 2 * i + 1];
+        H1[(size_t)k * K1 + i] = v;
+        G1[(size_t)i * K1 + k] = v;
+        h1[(size_t)k * K1 + i] = (float)v;
+        g1[(size_t)i * K1 + k] = (float)v;
+    }
+}
+
 __global__ void k_csr_copy_f32(int nnz, const double* __restrict__ m, const double* __restrict__ a, double half_dt,
                                double* __restrict__ p64, double* __restrict__ q64, float* __restrict__ m32,
                                float* __restrict__ a32, float* __restrict__ p32, float* __restrict__ q32) {
@@ -247,6 +295,43 @@ static int assemble_tensor(st_problem* p) {
     return ST_OK;
 }
 
+// Stencil of P and N for the box-grid apply: the values of an interior row, in
+// CSR (= (dz, dy, dx) lexicographic) order, placed at 27-point indices.
+static int read_box_stencil(st_problem* p) {
+    p->box_ok = false;
+    if (p->dim < 2) return ST_OK;
+    for (int d = 0; d < p->dim; ++d)
+        if (p->n[d] < 3) return ST_OK;
+    const int nx = p->n[0], ny = p->n[1];
+    const int r = p->dim == 2 ? 1 + nx : 1 + nx * (1 + ny);
+    int rp[2];
+    ST_CUDA_TRY(cudaMemcpyAsync(rp, p->row_ptr + r, sizeof(int) * 2, cudaMemcpyDeviceToHost, p->stream));
+    ST_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    const int cnt = rp[1] - rp[0];
+    const int want = p->dim == 2 ? 9 : 27;
+    if (cnt != want) return ST_OK;
+    double v64[2][27];
+    float v32[2][27];
+    ST_CUDA_TRY(cudaMemcpyAsync(v64[0], p->p64 + rp[0], sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync(v64[1], p->q64 + rp[0], sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync(v32[0], p->p32 + rp[0], sizeof(float) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    ST_CUDA_TRY(cudaMemcpyAsync(v32[1], p->q32 + rp[0], sizeof(float) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    ST_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    const int base = p->dim == 2 ? 9 : 0;   // 2D: the dz = 0 plane
+    for (int e = 0; e < 27; ++e) {
+        p->box_p64[e] = p->box_q64[e] = 0.0;
+        p->box_p32[e] = p->box_q32[e] = 0.f;
+    }
+    for (int i = 0; i < cnt; ++i) {
+        p->box_p64[base + i] = v64[0][i];
+        p->box_q64[base + i] = v64[1][i];
+        p->box_p32[base + i] = v32[0][i];
+        p->box_q32[base + i] = v32[1][i];
+    }
+    p->box_ok = true;
+    return ST_OK;
+}
+
 // Spectrum bounds of the pencil (A, M) (heat) or of its symmetric diffusion
 // part (convection-diffusion), from the 1D sine-mode eigenvalues.
 static void set_spectrum(st_problem* p) {
@@ -289,6 +374,19 @@ static int setup_tensor(st_problem* p) {
             int nb = (int)((nn + 255) / 256);
             k_fd_tables<<<nb, 256, 0, p->stream>>>(ax.n, ax.h, ax.Q64, ax.Q32, ax.lam, ax.c2);
             ST_LAUNCH_CHECK();
+            {
+                const size_t k0 = (size_t)(ax.n + 1) / 2, k1 = (size_t)ax.n / 2;
+                for (int t = 0; t < 4; ++t) {
+                    size_t cnt = t % 2 == 0 ? k0 * k0 : k1 * k1;
+                    ST_TRY(st_alloc(p, (void**)&ax.fold64[t], sizeof(double) * (cnt ? cnt : 1)));
+                    ST_TRY(st_alloc(p, (void**)&ax.fold32[t], sizeof(float) * (cnt ? cnt : 1)));
+                }
+                int nbf = (int)((k0 * k0 + 255) / 256);
+                k_fd_fold_tables<<<nbf, 256, 0, p->stream>>>(ax.n, ax.Q64, ax.fold64[0], ax.fold64[1], ax.fold64[2],
+                                                             ax.fold64[3], ax.fold32[0], ax.fold32[1], ax.fold32[2],
+                                                             ax.fold32[3]);
+                ST_LAUNCH_CHECK();
+            }
             double h = ax.h;
             auto lamj = [&](int j) {
                 double s = std::sin(M_PI * j / (2.0 * (ax.n + 1)));
@@ -300,7 +398,7 @@ static int setup_tensor(st_problem* p) {
         }
     }
     set_spectrum(p);
-    return ST_OK;
+    return read_box_stencil(p);
 }
 
 static int setup_user_csr(st_problem* p, const st_desc& d) {
@@ -337,7 +435,9 @@ extern "C" int st_destroy(st_problem* p) {
     if (!p) return ST_OK;
     if (p->cn_graph) cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
     if (p->sm_host) cudaFreeHost(p->sm_host);
-    for (void* ptr : p->owned) cudaFree(ptr);
+    for (void* ptr : p->owned) cudaFreeAsync(ptr, p->stream);
+    cudaStreamSynchronize(p->stream);
+    cudaGetLastError();
     p->owned.clear();
     delete p;
     return ST_OK;
@@ -362,7 +462,7 @@ extern "C" int st_set_coefficients(st_problem* p, int op, double kappa, double e
     p->cn_stale = true;
     ST_TRY(assemble_tensor(p));
     set_spectrum(p);
-    return ST_OK;
+    return read_box_stencil(p);
 }
 
 extern "C" int st_setup(const st_desc* d, st_problem** out) {
@@ -374,6 +474,7 @@ extern "C" int st_setup(const st_desc* d, st_problem** out) {
     if (d->op == ST_CONVDIFF && !(d->eps > 0)) return ST_EINVAL;
     if (d->kappa < 0) return ST_EINVAL;
     if (d->precision != ST_FP64 && d->precision != ST_MIXED) return ST_EINVAL;
+    keep_pool_memory();
     st_problem* p = new st_problem();
     p->d = *d;
     p->d.row_ptr = nullptr;

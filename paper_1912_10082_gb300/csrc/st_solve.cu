@@ -13,12 +13,10 @@
 #include "st_common.cuh"
 
 int st_slot(st_problem* p, int id, size_t bytes, void** out) {
-    if (id < 0 || id >= 24) return ST_EINVAL;
+    if (id < 0 || id >= 32) return ST_EINVAL;
     if (p->slot_bytes[id] < bytes) {
-        if (p->slot_ptr[id]) {
-            cudaStreamSynchronize(p->stream);
-            st_free_one(p, p->slot_ptr[id]);
-        }
+        // stream-ordered: work already issued on the stream finishes with the old buffer first
+        if (p->slot_ptr[id]) st_free_one(p, p->slot_ptr[id]);
         p->slot_ptr[id] = nullptr;
         p->slot_bytes[id] = 0;
         ST_TRY(st_alloc(p, &p->slot_ptr[id], bytes));
@@ -37,7 +35,7 @@ inline double ms_since(Clock::time_point t0) {
 
 enum SlotId {
     S_F1D = 0, S_F1C, S_MAQ, S_WH, S_WH2, S_TMP, S_X32, S_W32, S_T32, S_SMALL, S_PART, S_COPY, S_MV,
-    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT
+    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT, S_WDF
 };
 
 // Records why the Krylov process broke down (text of st_last_error).
@@ -365,7 +363,7 @@ int ensure_basis(st_problem* p, Ctx& c, int need_cols, int keep_cols, double** M
             ST_CUDA_TRY(cudaMemcpyAsync(ndf, p->Vdf, sizeof(float2) * (size_t)c.n * keep_cols,
                                         cudaMemcpyDeviceToDevice, c.s));
     }
-    ST_CUDA_TRY(cudaStreamSynchronize(c.s));
+    // stream-ordered frees: they take effect after the copies above
     if (p->V) st_free_one(p, p->V);
     if (p->Vdf) st_free_one(p, p->Vdf);
     if (p->slot_ptr[S_MV]) st_free_one(p, p->slot_ptr[S_MV]);
@@ -484,8 +482,11 @@ int basis_tn(Ctx& c, bool df, int k, int m, const double* W, int ldw, double* H,
     if (!df) return ts_tn_dev(c, k, m, c.p->V, c.n, W, ldw, H, ldh);
     if (k == 0 || m == 0) return ST_OK;
     double* part;
+    float2* W2;
     ST_TRY(st_slot(c.p, S_PART, sizeof(double) * st_tsgemm_partial_elems(c.n, k, m), (void**)&part));
-    return st_tsgemm_tn_df(c.n, k, m, c.p->Vdf, c.n, W, ldw, H, ldh, part, c.s);
+    ST_TRY(st_slot(c.p, S_WDF, sizeof(float2) * (size_t)c.n * m, (void**)&W2));
+    ST_TRY(st_to_df(c.n, m, W, ldw, W2, c.n, c.s));
+    return st_tsgemm_tn_df(c.n, k, m, c.p->Vdf, c.n, W2, c.n, H, ldh, part, c.s);
 }
 
 int basis_nn_sub(Ctx& c, bool df, int k, int m, const double* H, int ldh, double* W, int ldw) {

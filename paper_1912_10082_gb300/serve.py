@@ -48,12 +48,14 @@ def run_batch(instances, *, precision=ST_FP64, tol=1e-8, maxit=400, slots=16, me
 
 
 def run_stream(requests, factors, *, precision=ST_FP64, tol=1e-8, maxit=400, slots=16, hbm_budget_bytes=0.0,
-               warmup=0):
+               warmup=0, outputs=None):
     """Replay a request stream: request i is submitted at its ``arrival_s``.
 
     ``factors[i]`` = (F1, F2).  The first ``warmup`` requests are run but left
-    out of the statistics.  Returns dict with p50/p99 latency (s), DoF/s over
-    the measured requests' makespan and the per-request records.
+    out of the statistics.  ``outputs`` (optional dict index -> column-major
+    n_h x n_t buffer) receives the dense solution of those requests.  Returns
+    dict with p50/p99 latency (s), DoF/s over the measured requests' makespan
+    and the per-request records.
     """
     recs = {}
     with Executor(slots=slots, hbm_budget_bytes=hbm_budget_bytes) as ex:
@@ -64,7 +66,8 @@ def run_stream(requests, factors, *, precision=ST_FP64, tol=1e-8, maxit=400, slo
             now = ex.now() - start
             while i < n and requests[i]["arrival_s"] <= now:
                 F1, F2 = factors[i]
-                ex.submit(_desc_of(requests[i], precision, tol, maxit), F1, F2, tag=i)
+                U = outputs.get(i) if outputs else None
+                ex.submit(_desc_of(requests[i], precision, tol, maxit), F1, F2, tag=i, U_out=U)
                 i += 1
             wait = 0.0005
             if i < n:

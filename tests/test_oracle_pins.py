@@ -437,3 +437,14 @@ def test_planted_mass_mistake_is_caught(monkeypatch):
     bad = fem.p1_mass_1d(7).toarray()
     assert not np.allclose(bad, quad_1d(7, 1.0, "M"), atol=1e-15)
     assert np.allclose(good, quad_1d(7, 1.0, "M"), atol=1e-15)
+
+
+def test_cg_forward_substitution_equals_direct_elimination():
+    """The CG variant of block forward substitution (used where a factorisation does not fit)
+    reproduces the direct one on the first columns."""
+    M, A = fem.tensor_operators(3, 9)
+    D, C = timefe.time_matrices(7, 1.0)
+    F1, F2 = workloads.gaussian_factors(M.shape[0], 7, 3, seed=1)
+    U = kron.forward_substitution(M, A, D, C, F1 @ F2.T)
+    Uc = kron.forward_substitution_cg(M, A, D, C, F1, F2, 3, rtol=1e-14)
+    assert np.linalg.norm(Uc - U[:, :3]) <= 1e-12 * np.linalg.norm(U[:, :3])
