@@ -173,6 +173,7 @@ int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const doub
 namespace dense {
 bool cholesky(int n, double* A, int lda);                 // lower, in place
 void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs);
+void lower_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs);   // L X = B
 bool lu(int n, double* A, int lda, int* piv);
 void lu_solve(int n, const double* LU, int lda, const int* piv, double* B, int ldb, int nrhs);
 bool lu_solve_transpose(int n, const double* LU, int lda, const int* piv, double* B, int ldb, int nrhs);

@@ -11,35 +11,72 @@ namespace dense {
 
 #define A_(i, j) A[(size_t)(j) * lda + (i)]
 
+// Dot product with four independent partial sums (vectorisable without
+// reassociation flags; the summation order is fixed).
+static inline double dot(int n, const double* x, const double* y) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= n; i += 4) {
+        s0 += x[i] * y[i];
+        s1 += x[i + 1] * y[i + 1];
+        s2 += x[i + 2] * y[i + 2];
+        s3 += x[i + 3] * y[i + 3];
+    }
+    for (; i < n; ++i) s0 += x[i] * y[i];
+    return (s0 + s1) + (s2 + s3);
+}
+
+// Lower Cholesky factor in place, right-looking: each step scales one column
+// and updates the trailing columns with contiguous (vectorisable) loops.
 bool cholesky(int n, double* A, int lda) {
     for (int j = 0; j < n; ++j) {
-        double s = A_(j, j);
-        for (int k = 0; k < j; ++k) s -= A_(j, k) * A_(j, k);
+        double* cj = A + (size_t)j * lda;
+        double s = cj[j];
         if (!(s > 0.0)) return false;
         double d = std::sqrt(s);
-        A_(j, j) = d;
-        for (int i = j + 1; i < n; ++i) {
-            double t = A_(i, j);
-            for (int k = 0; k < j; ++k) t -= A_(i, k) * A_(j, k);
-            A_(i, j) = t / d;
+        cj[j] = d;
+        for (int i = j + 1; i < n; ++i) cj[i] /= d;
+        for (int c = j + 1; c < n; ++c) {
+            double t = cj[c];
+            if (t == 0.0) continue;
+            double* cc = A + (size_t)c * lda;
+            for (int i = c; i < n; ++i) cc[i] -= cj[i] * t;
         }
-        for (int i = 0; i < j; ++i) A_(i, j) = 0.0;
     }
+    for (int j = 1; j < n; ++j)
+        for (int i = 0; i < j; ++i) A_(i, j) = 0.0;
     return true;
 }
 
+// L L^T X = B: forward substitution by columns of L (axpy), back substitution
+// with L^T by dot products with columns of L; both contiguous.
 void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
     for (int c = 0; c < nrhs; ++c) {
         double* b = B + (size_t)c * ldb;
-        for (int i = 0; i < n; ++i) {
-            double s = b[i];
-            for (int k = 0; k < i; ++k) s -= L[(size_t)k * ldl + i] * b[k];
-            b[i] = s / L[(size_t)i * ldl + i];
+        for (int j = 0; j < n; ++j) {
+            const double* lj = L + (size_t)j * ldl;
+            double t = b[j] / lj[j];
+            b[j] = t;
+            if (t == 0.0) continue;
+            for (int i = j + 1; i < n; ++i) b[i] -= lj[i] * t;
         }
         for (int i = n - 1; i >= 0; --i) {
-            double s = b[i];
-            for (int k = i + 1; k < n; ++k) s -= L[(size_t)i * ldl + k] * b[k];
-            b[i] = s / L[(size_t)i * ldl + i];
+            const double* li = L + (size_t)i * ldl;
+            b[i] = (b[i] - dot(n - i - 1, li + i + 1, b + i + 1)) / li[i];
+        }
+    }
+}
+
+// L X = B for lower triangular L (forward substitution by columns of L).
+void lower_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
+    for (int c = 0; c < nrhs; ++c) {
+        double* b = B + (size_t)c * ldb;
+        for (int j = 0; j < n; ++j) {
+            const double* lj = L + (size_t)j * ldl;
+            double t = b[j] / lj[j];
+            b[j] = t;
+            if (t == 0.0) continue;
+            for (int i = j + 1; i < n; ++i) b[i] -= lj[i] * t;
         }
     }
 }
@@ -98,16 +135,11 @@ bool lu_solve_transpose(int n, const double* A, int lda, const int* piv, double*
     for (int c = 0; c < nrhs; ++c) {
         double* b = B + (size_t)c * ldb;
         for (int j = 0; j < n; ++j) {   // U^T y = b (lower triangular)
-            double s = b[j];
-            for (int i = 0; i < j; ++i) s -= A_(i, j) * b[i];
             if (A_(j, j) == 0.0) return false;
-            b[j] = s / A_(j, j);
+            b[j] = (b[j] - dot(j, &A_(0, j), b)) / A_(j, j);
         }
-        for (int j = n - 1; j >= 0; --j) {   // L^T z = y (unit upper)
-            double s = b[j];
-            for (int i = j + 1; i < n; ++i) s -= A_(i, j) * b[i];
-            b[j] = s;
-        }
+        for (int j = n - 1; j >= 0; --j)   // L^T z = y (unit upper)
+            b[j] -= dot(n - j - 1, &A_(j + 1, j), b + j + 1);
         for (int i = n - 1; i >= 0; --i)
             if (piv[i] != i) std::swap(b[i], b[piv[i]]);
     }
@@ -139,12 +171,14 @@ static void tridiagonalize(int n, double* A, int lda, double* d, double* e, bool
         for (int i = 0; i < m; ++i) vv += v[i] * v[i];
         double tau = 2.0 / vv;
         taus[j] = tau;
-        // p = tau * A22 v (symmetric, full storage)
-        for (int i = 0; i < m; ++i) {
-            double s = 0.0;
-            for (int k = 0; k < m; ++k) s += A_(j + 1 + i, j + 1 + k) * v[k];
-            p[i] = tau * s;
+        // p = tau * A22 v (symmetric, full storage), by columns of A22
+        for (int i = 0; i < m; ++i) p[i] = 0.0;
+        for (int k = 0; k < m; ++k) {
+            const double* col = &A_(j + 1, j + 1 + k);
+            double vk = v[k];
+            for (int i = 0; i < m; ++i) p[i] += col[i] * vk;
         }
+        for (int i = 0; i < m; ++i) p[i] *= tau;
         double pv = 0.0;
         for (int i = 0; i < m; ++i) pv += p[i] * v[i];
         double K = 0.5 * tau * pv;

@@ -102,40 +102,92 @@ struct BoxStencil {
     T q[27];
 };
 
-template <typename T, int DIM, int STEPS>
+// Register blocking: a thread owns YB x ZB grid points stacked in y (and z) at
+// one x, so the (YB+2)(ZB+2) x 3 loads of a time column serve YB x ZB
+// outputs (2D: 18 loads for 4 outputs instead of 36; 3D: 48 for 4 instead of
+// 108).  A warp spans 32 consecutive x, so every load is coalesced.  The
+// thread walks STEPS time columns, carrying N u_{l-1} per output, and loads
+// the next column while it computes the current one.
+template <typename T, int DIM, int YB, int ZB, int STEPS>
 __global__ void __launch_bounds__(256) k_apply_box(int nx, int ny, int nz, int n_t, BoxStencil<T> S,
                                                    const T* __restrict__ U, long long ldu, T* __restrict__ Y,
                                                    long long ldy) {
+    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
+    constexpr int NV = RY * RZ * 3;
+    const int nxs = (nx + 31) / 32, nyb = (ny + 8 * YB - 1) / (8 * YB);
+    int b = blockIdx.x;
+    const int xs = b % nxs;
+    b /= nxs;
+    const int yb = b % nyb;
+    const int zb = b / nyb;
+    const int x = xs * 32 + threadIdx.x;
+    const int y0 = (yb * 8 + threadIdx.y) * YB;
+    const int z0 = zb * ZB;
+    if (x >= nx || y0 >= ny || (DIM == 3 && z0 >= nz)) return;
     const long long nxy = (long long)nx * ny;
-    const long long n_h = nxy * (DIM == 3 ? nz : 1);
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_h) return;
-    const int x = (int)(r % nx);
-    const long long t = r / nx;
-    const int y = (int)(t % ny);
-    const int z = DIM == 3 ? (int)(t / ny) : 0;
     const int l0 = blockIdx.y * STEPS;
     const int l1 = min(n_t, l0 + STEPS);
     const int c0 = l0 > 0 ? l0 - 1 : 0;
-    T prevN = T(0);
+    // validity of the loaded rows and x neighbours
+    bool okx[3], oky[RY], okz[RZ];
 #pragma unroll
-    for (int q = 0; q <= STEPS; ++q) {
-        const int c = c0 + q;
-        if (c >= l1) break;
-        const T* u = U + (size_t)c * ldu + r;
-        T tP = T(0), tN = T(0);
+    for (int i = 0; i < 3; ++i) okx[i] = x + i - 1 >= 0 && x + i - 1 < nx;
 #pragma unroll
-        for (int e = 0; e < 27; ++e) {
-            const int dz = e / 9 - 1, dy = (e / 3) % 3 - 1, dx = e % 3 - 1;
-            if (DIM < 3 && dz != 0) continue;
-            const bool ok = (x + dx >= 0) && (x + dx < nx) && (y + dy >= 0) && (y + dy < ny) &&
-                            (DIM < 3 || ((z + dz >= 0) && (z + dz < nz)));
-            const T v = ok ? u[(long long)dz * nxy + (long long)dy * nx + dx] : T(0);
-            tP += S.p[e] * v;
-            tN += S.q[e] * v;
+    for (int i = 0; i < RY; ++i) oky[i] = y0 + i - 1 >= 0 && y0 + i - 1 < ny;
+#pragma unroll
+    for (int i = 0; i < RZ; ++i) okz[i] = DIM < 3 || (z0 + i - 1 >= 0 && z0 + i - 1 < nz);
+    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
+    auto load = [&](int c, T* v) {
+        const T* u = U + (size_t)c * ldu + base;
+#pragma unroll
+        for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+            for (int iy = 0; iy < RY; ++iy)
+#pragma unroll
+                for (int ix = 0; ix < 3; ++ix) {
+                    const bool ok = okx[ix] && oky[iy] && okz[iz];
+                    const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx + ix - 1;
+                    v[(iz * RY + iy) * 3 + ix] = ok ? u[off] : T(0);
+                }
+    };
+    // with prefetch (PF), column c+1 is loaded into the other buffer while c is computed
+    constexpr bool PF = !(DIM == 3 && sizeof(T) == 8);   // FP64 3D: registers allow one buffer
+    T va[NV], vb[PF ? NV : 1];
+    T pn[YB * ZB];
+#pragma unroll
+    for (int o = 0; o < YB * ZB; ++o) pn[o] = T(0);
+    if (PF) load(c0, va);
+#pragma unroll 1
+    for (int c = c0; c < l1; c += 2) {
+        // column c in va; prefetch c + 1 into vb
+        if (PF && c + 1 < l1) load(c + 1, vb);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int cc = c + h;
+            if (cc >= l1) break;
+            if (!PF) load(cc, va);
+            const T* v = (h == 0 || !PF) ? va : vb;
+            if (PF && h == 1 && cc + 1 < l1) load(cc + 1, va);   // the next pair's first column
+#pragma unroll
+            for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+                for (int oy = 0; oy < YB; ++oy) {
+                    const int o = oz * YB + oy;
+                    if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
+                    T tP = T(0), tN = T(0);
+#pragma unroll
+                    for (int e = 0; e < 27; ++e) {
+                        const int dz = e / 9 - 1, dy = (e / 3) % 3 - 1, dx = e % 3 - 1;
+                        if (DIM < 3 && dz != 0) continue;
+                        const T w = v[((DIM == 3 ? oz + 1 + dz : 0) * RY + oy + 1 + dy) * 3 + dx + 1];
+                        tP += S.p[e] * w;
+                        tN += S.q[e] * w;
+                    }
+                    if (cc >= l0) Y[(size_t)cc * ldy + base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx] =
+                        tP - pn[o];
+                    pn[o] = tN;
+                }
         }
-        if (c >= l0) Y[(size_t)c * ldy + r] = tP - prevN;
-        prevN = tN;
     }
 }
 
@@ -557,9 +609,19 @@ constexpr int TS_THREADS = 256;
 constexpr int TS_CG = 16;      // basis columns per CTA of H = V^T W
 constexpr int TS_UNROLL = 8;   // independent loads in flight per lane
 
-// Rows of one chunk of H = V^T W: the chunk of W staged in shared memory
-// holds rows x m <= 8192 doubles.
-__host__ __device__ inline int ts_rows(int m) { return m <= 8 ? 1024 : 512; }
+// Rows of one chunk of H = V^T W: enough chunks that chunks x column groups
+// fill the GPU about four CTAs deep (a few basis columns need many short
+// chunks to keep enough loads in flight), at least 128 rows, and a staged
+// chunk of W of rows x m <= 8192 doubles.
+__host__ __device__ inline int ts_rows(int n, int k, int m) {
+    const int maxr = m <= 8 ? 1024 : 512;
+    const long long groups = (k + 15) / 16;
+    const long long want = 4 * 152;
+    long long nch = (want + groups - 1) / groups;
+    long long r = (n + nch - 1) / nch;
+    r = ((r + 31) / 32) * 32;
+    return (int)(r < 128 ? 128 : (r > maxr ? maxr : r));
+}
 
 // Partial products of H = V^T W over one chunk of rows and a group of TS_CG
 // basis columns.  Each warp takes a column at a time; its lanes stride over
@@ -940,17 +1002,20 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
             S.p[e] = (T)(sizeof(T) == 8 ? p->box_p64[e] : p->box_p32[e]);
             S.q[e] = (T)(sizeof(T) == 8 ? p->box_q64[e] : p->box_q32[e]);
         }
-        // time columns per thread: 4 (2D) or 2 (3D), keeping the loads of a thread in registers
-        const int steps = p->dim == 2 ? 4 : 2;
-        dim3 grid((unsigned)((p->n_h + 255) / 256), (unsigned)((n_t + steps - 1) / steps));
-        if (grid.y > 65535) return ST_EINVAL;
+        // blocks of 32 x-points by 8 thread rows; each thread YB (x ZB) points and STEPS columns
+        constexpr int STEPS = 16;
+        const int YB = p->dim == 2 ? 4 : 2, ZB = p->dim == 2 ? 1 : 2;
+        long long blocks = (long long)((nx + 31) / 32) * ((ny + 8 * YB - 1) / (8 * YB)) *
+                           (p->dim == 3 ? (nz + ZB - 1) / ZB : 1);
+        dim3 grid((unsigned)blocks, (unsigned)((n_t + STEPS - 1) / STEPS));
+        if (blocks > 0x7fffffffLL || grid.y > 65535) return ST_EINVAL;
         double ts = (double)sizeof(T);
         st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32", ts * 2.0 * (double)p->n_h * n_t,
                       4.0 * (double)p->max_row_nnz * p->n_h * n_t);
         if (p->dim == 2)
-            k_apply_box<T, 2, 4><<<grid, 256, 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            k_apply_box<T, 2, 4, 1, STEPS><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
         else
-            k_apply_box<T, 3, 2><<<grid, 256, 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            k_apply_box<T, 3, 2, 2, STEPS><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
         st_prof_end(s);
         ST_LAUNCH_CHECK();
         return ST_OK;
@@ -1155,8 +1220,8 @@ int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const f
 size_t st_tsgemm_partial_elems(int n, int k, int m) {
     // the largest partial buffer any column chunk of at most kMaxCols needs
     int mm = m < kMaxCols ? m : kMaxCols;
-    size_t nch = (size_t)((n + ts_rows(mm) - 1) / ts_rows(mm));
-    size_t nch1 = (size_t)((n + ts_rows(1) - 1) / ts_rows(1));
+    size_t nch = (size_t)((n + ts_rows(n, k, mm) - 1) / ts_rows(n, k, mm));
+    size_t nch1 = (size_t)((n + ts_rows(n, k, 1) - 1) / ts_rows(n, k, 1));
     return (nch > nch1 ? nch : nch1) * (size_t)k * (size_t)mm;
 }
 
@@ -1221,7 +1286,7 @@ int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W,
         for (int b = 0; b < m; ++b) ST_CUDA_TRY(cudaMemsetAsync(H + (size_t)b * ldh, 0, sizeof(double) * k, s));
         return ST_OK;
     }
-    const int rows = ts_rows(m);
+    const int rows = ts_rows(n, k, m);
     const int nch = (n + rows - 1) / rows;
     const size_t smem = sizeof(double) * (size_t)m * rows;
     dim3 grid(nch, (k + TS_CG - 1) / TS_CG);
@@ -1278,7 +1343,7 @@ int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2*
         for (int b = 0; b < m; ++b) ST_CUDA_TRY(cudaMemsetAsync(H + (size_t)b * ldh, 0, sizeof(double) * k, s));
         return ST_OK;
     }
-    const int rows = ts_rows(m);
+    const int rows = ts_rows(n, k, m);
     const int nch = (n + rows - 1) / rows;
     const size_t smem = sizeof(double) * (size_t)m * rows;
     dim3 grid(nch, (k + TS_CG - 1) / TS_CG);

@@ -225,39 +225,57 @@ int mass_inverse(Ctx& c, int prec, const double* X, int ldx, int ncols, double* 
     return ST_OK;
 }
 
+// log of prod_j |s - s_j| / prod_i |s + theta_i| (products renormalised to avoid overflow).
+double shift_objective(double s, double b, const std::vector<double>& used, const std::vector<double>& ritz) {
+    double prod = 1.0;
+    long long ex = 0;
+    int cnt = 0;
+    for (double sj : used) {
+        prod *= std::fabs(s - sj) / b;
+        if (++cnt == 16) {
+            int e;
+            prod = std::frexp(prod, &e);
+            ex += e;
+            cnt = 0;
+        }
+    }
+    for (double th : ritz) {
+        prod /= std::fabs(s + th) / b;
+        if (++cnt == 16) {
+            int e;
+            prod = std::frexp(prod, &e);
+            ex += e;
+            cnt = 0;
+        }
+    }
+    if (!(prod > 0.0)) return -1e300;
+    return std::log(prod) + (double)ex * std::log(2.0);
+}
+
 // Next shift by the adaptive rule: maximise prod_j |s - s_j| / prod_i |s + theta_i|
-// over a log-spaced grid of [a, b] (products renormalised to avoid overflow).
+// over [a, b] on a log scale: a coarse grid of `grid` points, then a finer one
+// over the two coarse cells around the best point.
 double next_shift(double a, double b, const std::vector<double>& used, const std::vector<double>& ritz, int grid) {
-    double best = a, bestv = -1e300;
     double la = std::log(a), lb = std::log(b);
+    double step = (lb - la) / (grid - 1);
+    int gbest = 0;
+    double bestv = -1e300;
     for (int g = 0; g < grid; ++g) {
-        double s = std::exp(la + (lb - la) * g / (grid - 1));
-        double prod = 1.0;
-        long long ex = 0;
-        int cnt = 0;
-        for (double sj : used) {
-            prod *= std::fabs(s - sj) / b;
-            if (++cnt == 16) {
-                int e;
-                prod = std::frexp(prod, &e);
-                ex += e;
-                cnt = 0;
-            }
-        }
-        for (double th : ritz) {
-            prod /= std::fabs(s + th) / b;
-            if (++cnt == 16) {
-                int e;
-                prod = std::frexp(prod, &e);
-                ex += e;
-                cnt = 0;
-            }
-        }
-        if (prod <= 0.0) continue;
-        double v = std::log(prod) + ex * std::log(2.0);
+        double v = shift_objective(std::exp(la + step * g), b, used, ritz);
         if (v > bestv) {
             bestv = v;
-            best = s;
+            gbest = g;
+        }
+    }
+    double best = std::exp(la + step * gbest);
+    double lo = la + step * std::max(0, gbest - 1), hi = la + step * std::min(grid - 1, gbest + 1);
+    const int fine = 48;
+    for (int g = 0; g <= fine; ++g) {
+        double sv = std::exp(lo + (hi - lo) * g / fine);
+        double v = shift_objective(sv, b, used, ritz);
+        if (v > bestv) {
+            bestv = v;
+            best = sv;
         }
     }
     return best;
@@ -274,14 +292,7 @@ bool ritz_values(int k, const double* Am, const double* Mm, int ld, std::vector<
     if (!dense::cholesky(k, L.data(), k)) return false;
     // X = L^{-1} C (column by column), then C = L^{-1} X^T
     for (int pass = 0; pass < 2; ++pass) {
-        for (int j = 0; j < k; ++j) {
-            double* b = &C[(size_t)j * k];
-            for (int i = 0; i < k; ++i) {
-                double s = b[i];
-                for (int q = 0; q < i; ++q) s -= L[(size_t)q * k + i] * b[q];
-                b[i] = s / L[(size_t)i * k + i];
-            }
-        }
+        dense::lower_solve(k, L.data(), k, C.data(), k, k);
         for (int j = 0; j < k; ++j)
             for (int i = j + 1; i < k; ++i) std::swap(C[(size_t)j * k + i], C[(size_t)i * k + j]);
     }
@@ -967,7 +978,7 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
             if (!ritz_values(k, Am.a.data(), Mm.a.data(), Mm.ld, ritz)) ritz.clear();
             last_ritz_k = k;
         }
-        double s = next_shift(a_int, b_int, shifts, ritz, 600);
+        double s = next_shift(a_int, b_int, shifts, ritz, 150);
         shifts.push_back(s);
         S.ms_phase[7] += ms_since(tp);
         ++it;

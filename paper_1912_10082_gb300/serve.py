@@ -33,9 +33,14 @@ def run_batch(instances, *, precision=ST_FP64, tol=1e-8, maxit=400, slots=16, me
     Returns dict(makespan_s, dof, results) where results[i] is the executor's
     result of instance i.  ``outputs[i]``, if given, receives the dense U.
     """
+    # largest instances first (longest-processing-time order): the small ones fill the slots at
+    # the end instead of one large solve running alone
+    order = sorted(range(len(instances)),
+                   key=lambda i: (-(int(instances[i]["n"]) ** int(instances[i]["dim"])), -int(instances[i]["n_t"]), i))
     with Executor(slots=slots, hbm_budget_bytes=hbm_budget_bytes) as ex:
         t0 = ex.now()
-        for i, r in enumerate(instances):
+        for i in order:
+            r = instances[i]
             U = outputs[i] if outputs is not None else None
             ex.submit(_desc_of(r, precision, tol, maxit), r["F1"], r["F2"], tag=i, U_out=U, method=method)
         got = {}

@@ -32,6 +32,8 @@ WORKLOADS = {
     "heat2d": dict(dim=2, n=255, n_t=256, T=1.0, kappa=1.0, rhs="manufactured"),
     "heat2d_gauss": dict(dim=2, n=255, n_t=256, T=1.0, kappa=1.0, rhs="gaussian", p=2, seed=2),
     "heat3d": dict(dim=3, n=127, n_t=512, T=1.0, kappa=1.0, rhs="gaussian", p=4, seed=3),
+    # a smaller 3D case of the same kind (profiling captures)
+    "heat3d_small": dict(dim=3, n=63, n_t=128, T=1.0, kappa=1.0, rhs="gaussian", p=4, seed=3),
     # many instances: drawn by batched_instances / served_requests
     "batched": dict(kind="batched", count=256, seed=4, p=2),
     "served": dict(kind="served", count=2200, warmup=200, seed=5, mean_gap_s=2e-3, p=2),
