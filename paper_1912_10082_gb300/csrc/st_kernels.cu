@@ -109,7 +109,7 @@ struct BoxStencil {
 // thread walks STEPS time columns, carrying N u_{l-1} per output, and loads
 // the next column while it computes the current one.
 template <typename T, int DIM, int YB, int ZB, int STEPS>
-__global__ void __launch_bounds__(256) k_apply_box(int nx, int ny, int nz, int n_t, BoxStencil<T> S,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && DIM == 2) ? 3 : 1) k_apply_box(int nx, int ny, int nz, int n_t, BoxStencil<T> S,
                                                    const T* __restrict__ U, long long ldu, T* __restrict__ Y,
                                                    long long ldy) {
     constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
@@ -1003,7 +1003,7 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
             S.q[e] = (T)(sizeof(T) == 8 ? p->box_q64[e] : p->box_q32[e]);
         }
         // blocks of 32 x-points by 8 thread rows; each thread YB (x ZB) points and STEPS columns
-        constexpr int STEPS = 16;
+        constexpr int STEPS = 8;
         const int YB = p->dim == 2 ? 4 : 2, ZB = p->dim == 2 ? 1 : 2;
         long long blocks = (long long)((nx + 31) / 32) * ((ny + 8 * YB - 1) / (8 * YB)) *
                            (p->dim == 3 ? (nz + ZB - 1) / ZB : 1);

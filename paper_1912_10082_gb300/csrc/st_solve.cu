@@ -654,7 +654,7 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
         ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, 1, w32, n, t32, c.s));
         return st_convert_32_64_add(n, 1, w32, n, t, n, 0.0, c.s);
     };
-    ST_TRY(stage_reserve(p, 3 * pad32(J + 1)));
+    ST_TRY(stage_reserve(p, 3 * pad32(J + 2)));
     Stage sg(c);
     int total = 0;
     std::vector<double> H((size_t)(J + 1) * J), cs(J), sn(J), g(J + 1), y(J);
@@ -686,19 +686,33 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
                 double* u = Z + (size_t)(j + 1) * n;
                 ST_TRY(precond(zj, tj));
                 ST_TRY(st_spmm_comb64(p, shift, 1.0, tj, n, 1, 0.0, u, n, c.s));
+                // u is column j+1 of Z: one product [Z_0..Z_j, u]^T u per pass gives the
+                // coefficients and u^T u before the pass's update
                 double* dh[2];
                 for (int pass = 0; pass < 2; ++pass) {
-                    dh[pass] = sg.out(j + 1);
-                    ST_TRY(ts_tn_dev(c, j + 1, 1, Z, n, u, n, dh[pass], j + 1));
-                    ST_TRY(st_tsgemm_nn(n, j + 1, 1, -1.0, Z, n, dh[pass], j + 1, 1.0, u, n, c.s));
+                    dh[pass] = sg.out(j + 2);
+                    ST_TRY(ts_tn_dev(c, j + 2, 1, Z, n, u, n, dh[pass], j + 2));
+                    ST_TRY(st_tsgemm_nn(n, j + 1, 1, -1.0, Z, n, dh[pass], j + 2, 1.0, u, n, c.s));
                 }
-                double* du = sg.out(1);
-                ST_TRY(ts_tn_dev(c, 1, 1, u, n, u, n, du, 1));
                 ST_TRY(sg.fetch());
                 ++total;
                 double* hc = &H[(size_t)j * (J + 1)];
-                for (int i = 0; i <= j; ++i) hc[i] = sg.host_of(dh[0])[i] + sg.host_of(dh[1])[i];
-                double hn = std::sqrt(std::max(sg.host_of(du)[0], 0.0));
+                const double* h0 = sg.host_of(dh[0]);
+                const double* h1 = sg.host_of(dh[1]);
+                double hh = 0.0;
+                for (int i = 0; i <= j; ++i) {
+                    hc[i] = h0[i] + h1[i];
+                    hh += h1[i] * h1[i];
+                }
+                // ||u||^2 after the second pass: before it, minus what it removed
+                double nu2 = h1[j + 1] - hh;
+                if (!(nu2 > 1e-6 * h1[j + 1])) {
+                    double* du = sg.out(1);
+                    ST_TRY(ts_tn_dev(c, 1, 1, u, n, u, n, du, 1));
+                    ST_TRY(sg.fetch());
+                    nu2 = sg.host_of(du)[0];
+                }
+                double hn = std::sqrt(std::max(nu2, 0.0));
                 hc[j + 1] = hn;
                 for (int i = 0; i < j; ++i) {
                     double t0 = cs[i] * hc[i] + sn[i] * hc[i + 1];
@@ -982,37 +996,60 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         shifts.push_back(s);
         S.ms_phase[7] += ms_since(tp);
         ++it;
-        size_t needA = 2 * pad32((size_t)pl * pl) + 2 * pad32((size_t)k * pl);
-        size_t needB = pad32((size_t)k * nmaq * pl) + pad32((size_t)pl * 2 * pl) + pad32((size_t)pl * r) +
-                       2 * pad32((size_t)pl * pl) + pad32(1);
+        size_t needA = 2 * pad32((size_t)(k + pl) * pl);
+        size_t needB = pad32((size_t)(k + pl) * nmaq * pl) + pad32((size_t)pl * r) + 2 * pad32((size_t)pl * pl) +
+                       pad32(1);
         ST_TRY(stage_reserve(p, std::max(needA, needB)));
         // ---- phase A: A3 shifted solve into the next basis slot, A4 block CGS2 ----
         tp = Clock::now();
         double* W = p->V + (size_t)k * n;
         ST_TRY(resolvent(s, p->V + (size_t)lo * n, n, MV + (size_t)lo * n, n, pl, W, n));
-        double* dG0 = sg.out((size_t)pl * pl);
-        ST_TRY(ts_tn_dev(c, pl, pl, W, n, W, n, dG0, pl));
+        // each pass is one product [V, W]^T W: its first k rows are the Gram-Schmidt
+        // coefficients, its last pl rows the Gram matrix of W before the update
+        const int kk = k + pl;
         double* dh[2];
         for (int pass = 0; pass < 2; ++pass) {
-            dh[pass] = sg.out((size_t)k * pl);
-            ST_TRY(basis_tn(c, dfb, k, pl, W, n, dh[pass], k));
-            ST_TRY(basis_nn_sub(c, dfb, k, pl, dh[pass], k, W, n));
+            dh[pass] = sg.out((size_t)kk * pl);
+            if (dfb) {
+                ST_TRY(st_to_df(n, pl, W, n, p->Vdf + (size_t)k * n, n, c.s));
+                double* part;
+                ST_TRY(st_slot(p, S_PART, sizeof(double) * st_tsgemm_partial_elems(n, kk, pl), (void**)&part));
+                ST_TRY(st_tsgemm_tn_df(n, kk, pl, p->Vdf, n, p->Vdf + (size_t)k * n, n, dh[pass], kk, part, c.s));
+            } else {
+                ST_TRY(ts_tn_dev(c, kk, pl, p->V, n, W, n, dh[pass], kk));
+            }
+            ST_TRY(basis_nn_sub(c, dfb, k, pl, dh[pass], kk, W, n));
         }
-        double* dGw = sg.out((size_t)pl * pl);
-        ST_TRY(ts_tn_dev(c, pl, pl, W, n, W, n, dGw, pl));
         ST_TRY(sg.fetch());
         S.ms_phase[1] += ms_since(tp);
         tp = Clock::now();
-        std::vector<double> Hcol((size_t)k * pl);
+        std::vector<double> Hcol((size_t)k * pl), Gw((size_t)pl * pl);
+        double ref2 = 0.0, tr1 = 0.0, tr2 = 0.0;
         {
             const double* h0 = sg.host_of(dh[0]);
             const double* h1 = sg.host_of(dh[1]);
-            for (size_t i = 0; i < Hcol.size(); ++i) Hcol[i] = h0[i] + h1[i];
+            for (int j = 0; j < pl; ++j)
+                for (int i = 0; i < k; ++i) Hcol[(size_t)j * k + i] = h0[(size_t)j * kk + i] + h1[(size_t)j * kk + i];
+            // Gram of W after the second pass: G1 - h2^T h2 (V orthonormal), G1 the Gram before it
+            for (int j = 0; j < pl; ++j) {
+                ref2 = std::max(ref2, h0[(size_t)j * kk + k + j]);
+                for (int i = 0; i < pl; ++i) {
+                    double g = h1[(size_t)j * kk + k + i], hh = 0.0;
+                    for (int q = 0; q < k; ++q) hh += h1[(size_t)i * kk + q] * h1[(size_t)j * kk + q];
+                    Gw[(size_t)j * pl + i] = g - hh;
+                    if (i == j) {
+                        tr1 += g;
+                        tr2 += hh;
+                    }
+                }
+            }
         }
-        double ref2 = 0.0;
-        for (int i = 0; i < pl; ++i) ref2 = std::max(ref2, sg.host_of(dG0)[(size_t)i * pl + i]);
+        if (!(tr2 <= 1e-4 * tr1)) {
+            // the second pass removed a visible part: take the Gram matrix explicitly
+            ST_TRY(ts_tn_host(c, pl, pl, W, n, W, n, Gw.data()));
+        }
         QrPlan qp;
-        qr_plan(sg.host_of(dGw), pl, ref2, 1e-10, qp);
+        qr_plan(Gw.data(), pl, ref2, 1e-10, qp);
         if (qp.severe) {
             // the block almost lies in range(V): its remainder carries the rounding
             // of the two passes, so a third pass in FP64 cleans it before the QR
@@ -1043,10 +1080,10 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
             ST_TRY(st_spmm_ma<double>(p, W, n, pn, MAq, n, MAq + (size_t)n * pn, n, c.s));
             if (!sym) ST_TRY(st_spmm_at64(p, W, n, pn, MAq + (size_t)2 * n * pn, n, c.s));
             if (dfb) ST_TRY(st_to_df(n, pn, W, n, p->Vdf + (size_t)k * n, n, c.s));
-            double* dX1 = sg.out((size_t)k * nmaq * pn);
-            ST_TRY(basis_tn(c, dfb, k, nmaq * pn, MAq, n, dX1, k));
-            double* dX2 = sg.out((size_t)pn * 2 * pn);
-            ST_TRY(ts_tn_dev(c, pn, 2 * pn, W, n, MAq, n, dX2, pn));
+            // one product [V, q]^T [M q, A q (, A^T q)]: rows 0..k-1 = V^T (.), rows k.. = q^T (.)
+            const int kq = k + pn;
+            double* dX12 = sg.out((size_t)kq * nmaq * pn);
+            ST_TRY(basis_tn(c, dfb, kq, nmaq * pn, MAq, n, dX12, kq));
             double* dX3 = sg.out((size_t)pn * r);
             ST_TRY(ts_tn_dev(c, pn, r, W, n, F1c, n, dX3, pn));
             ST_TRY(sg.fetch());
@@ -1055,8 +1092,15 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
                 Rq = upper_product(pl, sg.host_of(dR2), qp.R1.data());
             }
             auto grab = [&](const double* d, size_t m) { return std::vector<double>(sg.host_of(d), sg.host_of(d) + m); };
-            X1 = grab(dX1, (size_t)k * nmaq * pn);
-            X2 = grab(dX2, (size_t)pn * 2 * pn);
+            {
+                const double* x12 = sg.host_of(dX12);
+                X1.resize((size_t)k * nmaq * pn);
+                X2.resize((size_t)pn * 2 * pn);
+                for (int j = 0; j < nmaq * pn; ++j)
+                    for (int i = 0; i < k; ++i) X1[(size_t)j * k + i] = x12[(size_t)j * kq + i];
+                for (int j = 0; j < 2 * pn; ++j)
+                    for (int i = 0; i < pn; ++i) X2[(size_t)j * pn + i] = x12[(size_t)j * kq + k + i];
+            }
             X3 = grab(dX3, (size_t)pn * r);
         }
         S.ms_phase[3] += ms_since(tp);
