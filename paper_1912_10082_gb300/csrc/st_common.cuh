@@ -76,6 +76,8 @@ struct st_problem {
     bool box_ok = false;
     double box_p64[27] = {}, box_q64[27] = {};
     float box_p32[27] = {}, box_q32[27] = {};
+    double box_m64[27] = {}, box_a64[27] = {};   // M and A (Aᵀ = A reversed) for the spatial products
+    float box_m32[27] = {}, box_a32[27] = {};
     double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M), or of its diffusion part
     double fd_lam_min = 0.0, fd_lam_max = 0.0;   // the same for unit diffusion (sums of 1D sine-mode eigenvalues)
     double fd_kappa = 1.0;                 // diffusion the fast-diagonalisation transforms use

@@ -191,6 +191,69 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && DIM == 2) ? 3 : 1) k_a
     }
 }
 
+// Spatial products with a constant box stencil: O1[:,c] = S1 * X[:,c] (+ beta
+// O1[:,c]) and, when O2 is given, O2[:,c] = S2 * X[:,c] from the same loads.
+// Same thread layout and register blocking as the apply (a warp spans 32
+// consecutive x; a thread owns YB x ZB points), one column per blockIdx.y.
+// Only the vectors move: the stencil travels in the kernel parameters.
+template <typename T>
+struct BoxPair {
+    T s[2][27];
+};
+
+template <typename T, int DIM, int YB, int ZB>
+__global__ void __launch_bounds__(256) k_stencil_box(int nx, int ny, int nz, BoxPair<T> S, const T* __restrict__ X,
+                                                     long long ldx, T beta, T* __restrict__ O1, long long ld1,
+                                                     T* __restrict__ O2, long long ld2) {
+    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
+    constexpr int NV = RY * RZ * 3;
+    const int nxs = (nx + 31) / 32, nyb = (ny + 8 * YB - 1) / (8 * YB);
+    int b = blockIdx.x;
+    const int xs = b % nxs;
+    b /= nxs;
+    const int yb = b % nyb;
+    const int zb = b / nyb;
+    const int x = xs * 32 + threadIdx.x;
+    const int y0 = (yb * 8 + threadIdx.y) * YB;
+    const int z0 = zb * ZB;
+    if (x >= nx || y0 >= ny || (DIM == 3 && z0 >= nz)) return;
+    const long long nxy = (long long)nx * ny;
+    const int c = blockIdx.y;
+    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
+    const T* u = X + (size_t)c * ldx + base;
+    T v[NV];
+#pragma unroll
+    for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < RY; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < 3; ++ix) {
+                const bool ok = x + ix - 1 >= 0 && x + ix - 1 < nx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny &&
+                                (DIM < 3 || (z0 + iz - 1 >= 0 && z0 + iz - 1 < nz));
+                const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx + ix - 1;
+                v[(iz * RY + iy) * 3 + ix] = ok ? u[off] : T(0);
+            }
+#pragma unroll
+    for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+        for (int oy = 0; oy < YB; ++oy) {
+            if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
+            T t1 = T(0), t2 = T(0);
+#pragma unroll
+            for (int e = 0; e < 27; ++e) {
+                const int dz = e / 9 - 1, dy = (e / 3) % 3 - 1, dx = e % 3 - 1;
+                if (DIM < 3 && dz != 0) continue;
+                const T w = v[((DIM == 3 ? oz + 1 + dz : 0) * RY + oy + 1 + dy) * 3 + dx + 1];
+                t1 += S.s[0][e] * w;
+                if (O2) t2 += S.s[1][e] * w;
+            }
+            const long long at = base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx;
+            T* o1 = O1 + (size_t)c * ld1 + at;
+            *o1 = beta == T(0) ? t1 : t1 + beta * *o1;
+            if (O2) O2[(size_t)c * ld2 + at] = t2;
+        }
+}
+
 // Generic CSR rows (any length): entries re-read from L1/L2 each step.
 template <typename T>
 __global__ void k_apply_generic(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
@@ -1003,19 +1066,20 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
             S.q[e] = (T)(sizeof(T) == 8 ? p->box_q64[e] : p->box_q32[e]);
         }
         // blocks of 32 x-points by 8 thread rows; each thread YB (x ZB) points and STEPS columns
-        constexpr int STEPS = 8;
+        // 2D: 4 rows x 8 time columns per thread; 3D: 2 x 2 points x 16 columns
         const int YB = p->dim == 2 ? 4 : 2, ZB = p->dim == 2 ? 1 : 2;
         long long blocks = (long long)((nx + 31) / 32) * ((ny + 8 * YB - 1) / (8 * YB)) *
                            (p->dim == 3 ? (nz + ZB - 1) / ZB : 1);
-        dim3 grid((unsigned)blocks, (unsigned)((n_t + STEPS - 1) / STEPS));
+        const int steps = p->dim == 2 ? 8 : 16;
+        dim3 grid((unsigned)blocks, (unsigned)((n_t + steps - 1) / steps));
         if (blocks > 0x7fffffffLL || grid.y > 65535) return ST_EINVAL;
         double ts = (double)sizeof(T);
         st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32", ts * 2.0 * (double)p->n_h * n_t,
                       4.0 * (double)p->max_row_nnz * p->n_h * n_t);
         if (p->dim == 2)
-            k_apply_box<T, 2, 4, 1, STEPS><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            k_apply_box<T, 2, 4, 1, 8><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
         else
-            k_apply_box<T, 3, 2, 2, STEPS><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            k_apply_box<T, 3, 2, 2, 16><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
         st_prof_end(s);
         ST_LAUNCH_CHECK();
         return ST_OK;
@@ -1046,6 +1110,25 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
 template int st_apply_kernel<double>(st_problem*, const double*, int, double*, int, int, cudaStream_t);
 template int st_apply_kernel<float>(st_problem*, const float*, int, float*, int, int, cudaStream_t);
 
+// Launch k_stencil_box over the problem's box grid (2D: 2 points per thread
+// in y; 3D: 2 x 2 in y, z).
+template <typename T>
+static void launch_stencil_box(st_problem* p, const BoxPair<T>& S, const T* X, int ldx, int ncols, T beta, T* O1,
+                               int ld1, T* O2, int ld2, cudaStream_t s) {
+    const int nx = p->n[0], ny = p->n[1], nz = p->dim == 3 ? p->n[2] : 1;
+    const int YB = 2, ZB = p->dim == 2 ? 1 : 2;
+    const long long blocks = (long long)((nx + 31) / 32) * ((ny + 8 * YB - 1) / (8 * YB)) * ((nz + ZB - 1) / ZB);
+    dim3 grid((unsigned)blocks, (unsigned)ncols);
+    if (p->dim == 2)
+        k_stencil_box<T, 2, 2, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, S, X, ldx, beta, O1, ld1, O2, ld2);
+    else
+        k_stencil_box<T, 3, 2, 2><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, S, X, ldx, beta, O1, ld1, O2, ld2);
+}
+
+static bool use_box(const st_problem* p, int ncols) {
+    return p->box_ok && (p->dim == 2 || p->dim == 3) && ncols <= 65535;
+}
+
 template <typename T>
 int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OM, int ldm, T* OA, int lda, cudaStream_t s) {
     if (ncols <= 0) return ST_OK;
@@ -1060,6 +1143,21 @@ int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OM, int ldm, T*
     int blocks = (p->n_h + 127) / 128;
     double ts = (double)sizeof(T);
     int nout = (OM ? 1 : 0) + (OA ? 1 : 0);
+    if (nout > 0 && use_box(p, ncols)) {
+        BoxPair<T> S;
+        for (int e = 0; e < 27; ++e) {
+            T m = sizeof(T) == 8 ? (T)p->box_m64[e] : (T)p->box_m32[e];
+            T a = sizeof(T) == 8 ? (T)p->box_a64[e] : (T)p->box_a32[e];
+            S.s[0][e] = OM ? m : a;
+            S.s[1][e] = a;
+        }
+        st_prof_begin(s, sizeof(T) == 8 ? "spmm64_box" : "spmm32_box", ts * (double)p->n_h * ncols * (1 + nout),
+                      2.0 * (p->dim == 2 ? 9 : 27) * (double)p->n_h * ncols * nout);
+        launch_stencil_box<T>(p, S, X, ldx, ncols, T(0), OM ? OM : OA, OM ? ldm : lda, OM ? OA : nullptr, lda, s);
+        st_prof_end(s);
+        ST_LAUNCH_CHECK();
+        return ST_OK;
+    }
     st_prof_begin(s, sizeof(T) == 8 ? "spmm64" : "spmm32",
                   (double)p->nnz * (4.0 + 2.0 * ts) + 4.0 * (p->n_h + 1) + ts * (double)p->n_h * ncols * (1 + nout),
                   4.0 * (double)p->nnz * ncols);
@@ -1081,6 +1179,17 @@ template int st_spmm_ma<float>(st_problem*, const float*, int, int, float*, int,
 int st_spmm_at64(st_problem* p, const double* X, int ldx, int ncols, double* Out, int ldo, cudaStream_t s) {
     if (ncols <= 0) return ST_OK;
     if (!p->at64) return ST_ENOTSUP;
+    if (use_box(p, ncols)) {
+        // a constant stencil's transpose is the stencil reflected through its centre
+        BoxPair<double> S;
+        for (int e = 0; e < 27; ++e) S.s[0][e] = S.s[1][e] = p->box_a64[26 - e];
+        st_prof_begin(s, "spmm_at64_box", 16.0 * (double)p->n_h * ncols,
+                      2.0 * (p->dim == 2 ? 9 : 27) * (double)p->n_h * ncols);
+        launch_stencil_box<double>(p, S, X, ldx, ncols, 0.0, Out, ldo, nullptr, 0, s);
+        st_prof_end(s);
+        ST_LAUNCH_CHECK();
+        return ST_OK;
+    }
     int blocks = (p->n_h + 127) / 128;
     st_prof_begin(s, "spmm_at64", (double)p->nnz * 12.0 + 4.0 * (p->n_h + 1) + 16.0 * (double)p->n_h * ncols,
                   2.0 * (double)p->nnz * ncols);
@@ -1104,6 +1213,16 @@ int st_spmm_at64(st_problem* p, const double* X, int ldx, int ncols, double* Out
 int st_spmm_comb64(st_problem* p, double cm, double ca, const double* X, int ldx, int ncols, double beta, double* Out,
                    int ldo, cudaStream_t s) {
     if (ncols <= 0) return ST_OK;
+    if (use_box(p, ncols)) {
+        BoxPair<double> S;
+        for (int e = 0; e < 27; ++e) S.s[0][e] = S.s[1][e] = cm * p->box_m64[e] + ca * p->box_a64[e];
+        st_prof_begin(s, "spmm_comb64_box", 8.0 * (double)p->n_h * ncols * (beta == 0.0 ? 2 : 3),
+                      2.0 * (p->dim == 2 ? 9 : 27) * (double)p->n_h * ncols);
+        launch_stencil_box<double>(p, S, X, ldx, ncols, beta, Out, ldo, nullptr, 0, s);
+        st_prof_end(s);
+        ST_LAUNCH_CHECK();
+        return ST_OK;
+    }
     int blocks = (p->n_h + 127) / 128;
     st_prof_begin(s, "spmm_comb64", (double)p->nnz * 20.0 + 4.0 * (p->n_h + 1) + 8.0 * p->n_h * ncols * (beta == 0.0 ? 2 : 3),
                   4.0 * (double)p->nnz * ncols);

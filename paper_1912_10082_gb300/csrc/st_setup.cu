@@ -310,24 +310,23 @@ static int read_box_stencil(st_problem* p) {
     const int cnt = rp[1] - rp[0];
     const int want = p->dim == 2 ? 9 : 27;
     if (cnt != want) return ST_OK;
-    double v64[2][27];
-    float v32[2][27];
-    ST_CUDA_TRY(cudaMemcpyAsync(v64[0], p->p64 + rp[0], sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
-    ST_CUDA_TRY(cudaMemcpyAsync(v64[1], p->q64 + rp[0], sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
-    ST_CUDA_TRY(cudaMemcpyAsync(v32[0], p->p32 + rp[0], sizeof(float) * cnt, cudaMemcpyDeviceToHost, p->stream));
-    ST_CUDA_TRY(cudaMemcpyAsync(v32[1], p->q32 + rp[0], sizeof(float) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    double v64[4][27];
+    float v32[4][27];
+    const double* s64[4] = {p->p64, p->q64, p->m64, p->a64};
+    const float* s32[4] = {p->p32, p->q32, p->m32, p->a32};
+    for (int j = 0; j < 4; ++j) {
+        ST_CUDA_TRY(cudaMemcpyAsync(v64[j], s64[j] + rp[0], sizeof(double) * cnt, cudaMemcpyDeviceToHost, p->stream));
+        ST_CUDA_TRY(cudaMemcpyAsync(v32[j], s32[j] + rp[0], sizeof(float) * cnt, cudaMemcpyDeviceToHost, p->stream));
+    }
     ST_CUDA_TRY(cudaStreamSynchronize(p->stream));
     const int base = p->dim == 2 ? 9 : 0;   // 2D: the dz = 0 plane
-    for (int e = 0; e < 27; ++e) {
-        p->box_p64[e] = p->box_q64[e] = 0.0;
-        p->box_p32[e] = p->box_q32[e] = 0.f;
-    }
-    for (int i = 0; i < cnt; ++i) {
-        p->box_p64[base + i] = v64[0][i];
-        p->box_q64[base + i] = v64[1][i];
-        p->box_p32[base + i] = v32[0][i];
-        p->box_q32[base + i] = v32[1][i];
-    }
+    double* d64[4] = {p->box_p64, p->box_q64, p->box_m64, p->box_a64};
+    float* d32[4] = {p->box_p32, p->box_q32, p->box_m32, p->box_a32};
+    for (int j = 0; j < 4; ++j)
+        for (int e = 0; e < 27; ++e) {
+            d64[j][e] = e >= base && e < base + cnt ? v64[j][e - base] : 0.0;
+            d32[j][e] = e >= base && e < base + cnt ? v32[j][e - base] : 0.f;
+        }
     p->box_ok = true;
     return ST_OK;
 }

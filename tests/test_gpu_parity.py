@@ -121,7 +121,7 @@ def test_manufactured_loads_match_oracle(dim, n, nt):
 
 # ---------------------------------------------------------------- A3 shifted solve (K2)
 
-@pytest.mark.parametrize("dim,n", [(1, 15), (2, (9, 6)), (3, 5), (3, (4, 6, 3))])
+@pytest.mark.parametrize("dim,n", [(1, 15), (2, (9, 6)), (3, 5), (3, (4, 6, 3)), (2, (40, 37)), (3, (35, 18, 5))])
 @pytest.mark.parametrize("prec,tol", [(st.ST_FP64, 1e-12), (st.ST_MIXED, 1e-10)])
 def test_shift_solve_matches_sparse_lu(dim, n, prec, tol):
     M, A = ops(dim, n, kappa=0.8)
@@ -179,7 +179,7 @@ def test_solve_matches_direct_solution(dim, n, nt, p, seed, prec):
 
 
 @pytest.mark.parametrize("dim,n,nt,eps", [(1, 31, 24, 0.05), (2, 15, 16, 0.05), (2, (12, 9), 20, 0.5),
-                                           (3, 7, 10, 0.2)])
+                                           (3, 7, 10, 0.2), (2, (40, 21), 12, 0.05), (3, (33, 9, 5), 8, 0.2)])
 @pytest.mark.parametrize("prec", [st.ST_FP64, st.ST_MIXED])
 def test_solve_convdiff_matches_direct_solution(dim, n, nt, eps, prec):
     """Convection-diffusion (nonsymmetric A): FGMRES shifted solves, unsymmetrised projections."""
