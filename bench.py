@@ -372,20 +372,27 @@ def bench_served(args, wl, rank, world, local):
     lc = st.launch_count()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
-        out = serve.run_stream(reqs, facs, precision=st.ST_MIXED, slots=args.slots, warmup=warm)
+        policy = st.ST_SCHED_HRRN if args.policy == "hrrn" else st.ST_SCHED_FIFO
+        out = serve.run_stream(reqs, facs, precision=st.ST_MIXED, slots=args.slots, warmup=warm, policy=policy)
         wall = time.perf_counter() - t0
     launches = st.launch_count() - lc
     recs = out.pop("records")
     kinds = {}
+    failures = []
     for j in range(warm, count):
         r, res = reqs[j], recs[j]
+        if res["status"] != st.ST_OK and len(failures) < 10:
+            failures.append({"request": j, "status": res["status"], "op": r["op"], "dim": r["dim"], "n": r["n"],
+                             "n_t": r["n_t"], "eps": r.get("eps"), "message": res["message"]})
         key = f"{r['op']}{r['dim']}d"
-        d = kinds.setdefault(key, {"n": 0, "lat": [], "failed": 0})
+        d = kinds.setdefault(key, {"n": 0, "lat": [], "svc": [], "failed": 0})
         d["n"] += 1
         d["lat"].append(res["t_end"] - res["t_submit"])
+        d["svc"].append(res["t_end"] - res["t_start"])
         d["failed"] += res["status"] != st.ST_OK
     per_kind = {k: {"requests": v["n"], "failed": v["failed"], "p50_s": float(np.percentile(v["lat"], 50)),
-                    "p99_s": float(np.percentile(v["lat"], 99))} for k, v in sorted(kinds.items())}
+                    "p99_s": float(np.percentile(v["lat"], 99)), "service_p50_s": float(np.percentile(v["svc"], 50)),
+                    "service_sum_s": float(np.sum(v["svc"]))} for k, v in sorted(kinds.items())}
     if rank != 0:
         return 0
     line = {
@@ -395,10 +402,11 @@ def bench_served(args, wl, rank, world, local):
         "config": {"workload": f"served: Poisson stream of {count} requests (first {warm} warm-up), mean gap "
                                f"{1e3 * gap:.2f} ms, heat and convection-diffusion, 1D/2D/3D n 63..127^3, "
                                f"n_t 64..512, rank-{wl['p']} Gaussian loads, mixed precision, tol 1e-8",
-                   "slots": args.slots, "gap_scale": args.gap_scale, "parallelism": f"replicas{world}"},
+                   "slots": args.slots, "gap_scale": args.gap_scale, "policy": args.policy,
+                   "parallelism": f"replicas{world}"},
         "latency": {"p50_s": out["p50_s"], "p99_s": out["p99_s"], "per_kind": per_kind},
         "served": {"measured": out["measured"], "ok": out["ok"], "not_converged": out["not_converged"],
-                   "wall_s": wall},
+                   "wall_s": wall, "failures": failures},
         "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
@@ -416,6 +424,8 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="executor slots of the batched and served workloads")
     ap.add_argument("--requests", type=int, default=0, help="served workload: number of requests (0: all)")
     ap.add_argument("--gap-scale", type=float, default=1.0, help="served workload: scale of the mean arrival gap")
+    ap.add_argument("--policy", default="hrrn", choices=["fifo", "hrrn"],
+                    help="served workload: admission order of the executor")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

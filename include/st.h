@@ -158,11 +158,16 @@ int st_apply(st_problem* p, int dtype, const void* U, int ldu, void* Y, int ldy)
 int st_rhs_manufactured(st_problem* p, double* F1, int ldf1, double* F2, int ldf2);
 
 /* st_shift_solve -- W = (A + s M)^{-1} M X for p columns (Section 4: the
- * resolvent (A_h - sigma M_h)^{-1} M_h with sigma = -s < 0), by fast
- * diagonalisation on the tensor grid.  precision ST_FP64 computes the
- * transforms in FP64; ST_MIXED computes them in FP32 and refines once with an
- * FP64 residual.  X, W: device double, n_h x p, ld >= n_h; may alias.
- * s > -lambda_min.  Asynchronous. */
+ * resolvent (A_h - sigma M_h)^{-1} M_h with sigma = -s < 0).  Heat: fast
+ * diagonalisation on the tensor grid; precision ST_FP64 computes the
+ * transforms in FP64, ST_MIXED computes them in FP32 and refines once with an
+ * FP64 residual.  Asynchronous.  Convection-diffusion: flexible GMRES
+ * right-preconditioned by the fast-diagonalisation solve of eps K + s M (its
+ * transforms in FP64, or FP32 under ST_MIXED), all columns advanced together,
+ * stopped at a relative residual of 1e-12 per column; synchronises with the
+ * host every few steps.  X, W: device double, n_h x p, ld >= n_h; may alias.
+ * s > -lambda_min (of eps K for convection-diffusion).  ST_ENOTSUP for
+ * problems given by user matrices. */
 int st_shift_solve(st_problem* p, double s, const double* X, int ldx, int ncols,
                    double* W, int ldw, int precision);
 
@@ -290,18 +295,25 @@ typedef struct st_result {
     double bytes_reserved;   /* admission estimate held while the request ran */
     double t_submit, t_start, t_end;   /* seconds on the executor clock (st_executor_now) */
     st_stats stats;          /* statistics of the solve */
+    char message[160];       /* on failure, the worker's st_last_error text ("" on success) */
 } st_result;
 
 /* st_request_bytes -- admission estimate of a request's device footprint:
  * operators, tables, a basis V and M V of min(max_basis, p (min(maxit,80)+1))
- * columns, the N_h-sized work blocks and Y.  0 for invalid descriptors. */
+ * columns, the N_h-sized work blocks and Y; for convection-diffusion also
+ * the flexible GMRES blocks (84 N_h doubles per column, at most 16 columns
+ * and 4 GB).  0 for invalid descriptors. */
 double st_request_bytes(const st_desc* d, int p);
 
 /* st_executor_create -- start `slots` (1..256) worker threads on the current
  * device with an HBM budget in bytes (<= 0: 80% of the free memory). */
 int st_executor_create(int slots, double hbm_budget_bytes, st_executor** out);
 
-/* st_executor_submit -- queue a request (copied; the F1, F2 and U_out
+/* A request that runs out of device memory (ST_ENOMEM) while other requests
+ * run is queued again, at most twice, with an estimate of the whole budget,
+ * so that it runs alone; its result is reported only then.
+ *
+ * st_executor_submit -- queue a request (copied; the F1, F2 and U_out
  * buffers it points to must stay valid until its result is returned).
  * ST_EINVAL for bad sizes or after st_executor_destroy began. */
 int st_executor_submit(st_executor* ex, const st_request* req);
@@ -310,6 +322,22 @@ int st_executor_submit(st_executor* ex, const st_request* req);
  * NULL to discard them), waiting up to timeout_s seconds for the first one
  * (<= 0: do not wait).  *count receives the number moved. */
 int st_executor_wait(st_executor* ex, st_result* out, int max, int* count, double timeout_s);
+
+/* st_executor_set_policy -- order in which waiting requests are admitted.
+ * ST_SCHED_FIFO (the default): arrival order, skipping requests that do not
+ * fit the free HBM.  ST_SCHED_HRRN: the request with the highest response
+ * ratio (wait + estimated service) / estimated service, admitted when it
+ * fits the free HBM (until then nothing else is admitted), so short requests
+ * overtake long ones while no request waits for ever (its ratio grows with
+ * its wait).  The service estimate of a request
+ * is 2 ms plus n_h * n_t times a rate per class (operator, method,
+ * dimension), learned from the finished requests of that class (prior rate
+ * 3e-9 s for heat RKSM, 2e-8 s for convection-diffusion RKSM, 1e-9 s for
+ * CN).  Takes effect from the next admission; ST_EINVAL for an unknown
+ * policy. */
+#define ST_SCHED_FIFO 0
+#define ST_SCHED_HRRN 1
+int st_executor_set_policy(st_executor* ex, int policy);
 
 /* st_executor_pending -- requests still queued and running (host outputs, may be NULL). */
 int st_executor_pending(st_executor* ex, int* queued, int* running);

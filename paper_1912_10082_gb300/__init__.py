@@ -26,6 +26,7 @@ ST_FP64, ST_MIXED = 0, 1
 ST_F64, ST_F32 = 0, 1
 ST_HEAT, ST_CONVDIFF = 0, 1
 ST_METHOD_RKSM, ST_METHOD_CN = 0, 1
+ST_SCHED_FIFO, ST_SCHED_HRRN = 0, 1
 
 # every symbol include/st.h declares
 ABI_SYMBOLS = (
@@ -34,7 +35,7 @@ ABI_SYMBOLS = (
     "st_error_string", "st_last_error", "st_launch_count", "st_profile_begin", "st_profile_end",
     "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
-    "st_executor_destroy",
+    "st_executor_destroy", "st_executor_set_policy",
 )
 
 
@@ -75,11 +76,12 @@ class StRequest(C.Structure):
 class StResult(C.Structure):
     _fields_ = [("tag", C.c_ulonglong), ("status", C.c_int), ("slot", C.c_int), ("k", C.c_int),
                 ("bytes_reserved", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
-                ("t_end", C.c_double), ("stats", StStats)]
+                ("t_end", C.c_double), ("stats", StStats), ("message", C.c_char * 160)]
 
     def as_dict(self):
-        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "stats"}
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stats", "message")}
         d["stats"] = self.stats.as_dict()
+        d["message"] = self.message.decode(errors="replace")
         return d
 
 
@@ -125,6 +127,7 @@ def lib() -> C.CDLL:
         "st_executor_wait": ([vp, C.POINTER(StResult), i, C.POINTER(i), d], i),
         "st_executor_pending": ([vp, C.POINTER(i), C.POINTER(i)], i),
         "st_executor_now": ([vp], d),
+        "st_executor_set_policy": ([vp, i], i),
         "st_executor_destroy": ([vp], i),
         "st_profile_begin": ([], i),
         "st_profile_end": ([C.POINTER(StKernelTime), i, C.POINTER(i)], i),
@@ -360,11 +363,16 @@ class Executor:
     ``wait``.
     """
 
-    def __init__(self, slots: int = 16, hbm_budget_bytes: float = 0.0):
+    def __init__(self, slots: int = 16, hbm_budget_bytes: float = 0.0, policy: int = ST_SCHED_FIFO):
         h = C.c_void_p()
         _check(lib().st_executor_create(int(slots), float(hbm_budget_bytes), C.byref(h)), "st_executor_create")
         self.h = h
         self._live = {}
+        if policy != ST_SCHED_FIFO:
+            self.set_policy(policy)
+
+    def set_policy(self, policy: int):
+        _check(lib().st_executor_set_policy(self.h, int(policy)), "st_executor_set_policy")
 
     def now(self) -> float:
         return float(lib().st_executor_now(self.h))

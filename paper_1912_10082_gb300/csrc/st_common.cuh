@@ -1,6 +1,8 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <atomic>
+#include <functional>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -145,6 +147,12 @@ int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const f
 // Tall-skinny products.  H (k x m, ld ldh, device) = V^T W for V n x k, W n x m.
 // partial must hold tsgemm_partial_elems(n, k, m) doubles.
 size_t st_tsgemm_partial_elems(int n, int k, int m);
+// batched flexible GMRES (m independent Arnoldi processes, vectors interleaved)
+size_t st_gm_partial_elems(int n, int kk, int m);
+int st_gm_dots(int n, int kk, int m, const double* Z, double* part, double* H, int ldh, cudaStream_t s);
+int st_gm_update(int n, int nb, int m, double* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
+                 long long ldhd, int jcol, int J, cudaStream_t s);
+int st_scale_cols_dev(int n, int m, double* X, int ldx, const double* f, cudaStream_t s);
 int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W, int ldw,
                  double* H, int ldh, double* partial, cudaStream_t s);
 // W = beta * W + alpha * V H   (V n x k, H k x m device, W n x m)
@@ -172,6 +180,28 @@ int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const doub
                      double* U, int ldu, cudaStream_t s);
 
 // ---- host dense algebra (st_dense.cpp), column-major, FP64 ----
+// Host threads for the projected problems (st_dense.cpp).  Parallel loops
+// give each output element to one thread and keep its serial summation order,
+// so results do not depend on the thread count.
+namespace hostpar {
+struct ActiveSolve {   // counts solves in flight; they share the host cores
+    ActiveSolve();
+    ~ActiveSolve();
+};
+int threads_for(double flops);   // 1 .. 8 threads for a job of this size
+class Barrier {
+   public:
+    explicit Barrier(int count) : n(count) {}
+    void wait();
+
+   private:
+    std::atomic<int> arrived{0};
+    std::atomic<unsigned> gen{0};
+    int n;
+};
+void run(int T, const std::function<void(int, Barrier&)>& body);   // body(t, barrier), t = 0 on the caller
+}  // namespace hostpar
+
 namespace dense {
 bool cholesky(int n, double* A, int lda);                 // lower, in place
 void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs);

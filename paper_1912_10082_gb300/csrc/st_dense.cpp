@@ -1,11 +1,61 @@
 // Small dense FP64 algebra for the projected problems (k x k, k <= a few
 // thousand), run on the host cores next to the GPU.  Column-major storage.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "st_common.cuh"
+
+// ---------------------------------------------------------------------------
+// Host threads for the projected problems.  Every parallel loop below gives
+// each output element to one thread and keeps the serial order of its sum, so
+// results are bitwise the same for any thread count (a solve gives the same
+// numbers alone and next to others).
+// ---------------------------------------------------------------------------
+namespace hostpar {
+
+static std::atomic<int> g_active{0};
+
+ActiveSolve::ActiveSolve() { g_active.fetch_add(1); }
+ActiveSolve::~ActiveSolve() { g_active.fetch_sub(1); }
+
+int threads_for(double flops) {
+    static const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+    if (flops < 4e6) return 1;
+    const int share = std::max(1, hw / std::max(1, g_active.load()));
+    return std::max(1, std::min({8, share, (int)(flops / 2e6)}));
+}
+
+void Barrier::wait() {
+    if (n <= 1) return;
+    const unsigned g = gen.load(std::memory_order_acquire);
+    if (arrived.fetch_add(1, std::memory_order_acq_rel) + 1 == n) {
+        arrived.store(0, std::memory_order_relaxed);
+        gen.fetch_add(1, std::memory_order_release);
+        return;
+    }
+    int spins = 0;
+    while (gen.load(std::memory_order_acquire) == g)
+        if (++spins > 2000) std::this_thread::yield();
+}
+
+void run(int T, const std::function<void(int, Barrier&)>& body) {
+    Barrier b(std::max(1, T));
+    if (T <= 1) {
+        body(0, b);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T - 1);
+    for (int t = 1; t < T; ++t) th.emplace_back([&body, &b, t] { body(t, b); });
+    body(0, b);
+    for (auto& x : th) x.join();
+}
+
+}  // namespace hostpar
 
 namespace dense {
 
@@ -29,20 +79,51 @@ static inline double dot(int n, const double* x, const double* y) {
 // Lower Cholesky factor in place, right-looking: each step scales one column
 // and updates the trailing columns with contiguous (vectorisable) loops.
 bool cholesky(int n, double* A, int lda) {
-    for (int j = 0; j < n; ++j) {
-        double* cj = A + (size_t)j * lda;
-        double s = cj[j];
-        if (!(s > 0.0)) return false;
-        double d = std::sqrt(s);
-        cj[j] = d;
-        for (int i = j + 1; i < n; ++i) cj[i] /= d;
-        for (int c = j + 1; c < n; ++c) {
-            double t = cj[c];
-            if (t == 0.0) continue;
-            double* cc = A + (size_t)c * lda;
-            for (int i = c; i < n; ++i) cc[i] -= cj[i] * t;
+    // Blocked right-looking order: thread 0 factors a panel of NB columns (each
+    // scaled, then applied to the panel's later columns), then the threads apply
+    // the panel's columns, in ascending order, to the trailing columns (dealt
+    // cyclically).  Every entry receives its updates in ascending column order,
+    // so the factor does not depend on the thread count.
+    constexpr int NB = 32;
+    const int T = hostpar::threads_for((double)n * n * n / 3.0);
+    bool ok = true;
+    hostpar::run(T, [&](int t, hostpar::Barrier& bar) {
+        for (int jb = 0; jb < n; jb += NB) {
+            const int je = std::min(n, jb + NB);
+            if (t == 0) {
+                for (int j = jb; j < je && ok; ++j) {
+                    double* cj = A + (size_t)j * lda;
+                    const double s = cj[j];
+                    if (!(s > 0.0)) {
+                        ok = false;
+                        break;
+                    }
+                    const double d = std::sqrt(s);
+                    cj[j] = d;
+                    for (int i = j + 1; i < n; ++i) cj[i] /= d;
+                    for (int c = j + 1; c < je; ++c) {
+                        const double tc = cj[c];
+                        if (tc == 0.0) continue;
+                        double* cc = A + (size_t)c * lda;
+                        for (int i = c; i < n; ++i) cc[i] -= cj[i] * tc;
+                    }
+                }
+            }
+            bar.wait();
+            if (!ok) return;   // read after the barrier: every thread leaves at the same panel
+            for (int c = je + t; c < n; c += T) {
+                double* cc = A + (size_t)c * lda;
+                for (int j = jb; j < je; ++j) {
+                    const double* cj = A + (size_t)j * lda;
+                    const double tc = cj[c];
+                    if (tc == 0.0) continue;
+                    for (int i = c; i < n; ++i) cc[i] -= cj[i] * tc;
+                }
+            }
+            bar.wait();
         }
-    }
+    });
+    if (!ok) return false;
     for (int j = 1; j < n; ++j)
         for (int i = 0; i < j; ++i) A_(i, j) = 0.0;
     return true;
@@ -50,8 +131,8 @@ bool cholesky(int n, double* A, int lda) {
 
 // L L^T X = B: forward substitution by columns of L (axpy), back substitution
 // with L^T by dot products with columns of L; both contiguous.
-void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
-    for (int c = 0; c < nrhs; ++c) {
+static void chol_solve_cols(int n, const double* L, int ldl, double* B, int ldb, int c0, int c1) {
+    for (int c = c0; c < c1; ++c) {
         double* b = B + (size_t)c * ldb;
         for (int j = 0; j < n; ++j) {
             const double* lj = L + (size_t)j * ldl;
@@ -67,18 +148,30 @@ void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
     }
 }
 
+// right-hand sides split over the threads
+void chol_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
+    const int T = std::min(nrhs, hostpar::threads_for(2.0 * n * n * nrhs));
+    hostpar::run(T, [&](int t, hostpar::Barrier&) {
+        chol_solve_cols(n, L, ldl, B, ldb, (int)((long long)nrhs * t / T), (int)((long long)nrhs * (t + 1) / T));
+    });
+}
+
 // L X = B for lower triangular L (forward substitution by columns of L).
 void lower_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) {
-    for (int c = 0; c < nrhs; ++c) {
-        double* b = B + (size_t)c * ldb;
-        for (int j = 0; j < n; ++j) {
-            const double* lj = L + (size_t)j * ldl;
-            double t = b[j] / lj[j];
-            b[j] = t;
-            if (t == 0.0) continue;
-            for (int i = j + 1; i < n; ++i) b[i] -= lj[i] * t;
+    const int T = std::min(nrhs, hostpar::threads_for((double)n * n * nrhs));
+    hostpar::run(T, [&](int th, hostpar::Barrier&) {
+        const int c0 = (int)((long long)nrhs * th / T), c1 = (int)((long long)nrhs * (th + 1) / T);
+        for (int c = c0; c < c1; ++c) {
+            double* b = B + (size_t)c * ldb;
+            for (int j = 0; j < n; ++j) {
+                const double* lj = L + (size_t)j * ldl;
+                double t = b[j] / lj[j];
+                b[j] = t;
+                if (t == 0.0) continue;
+                for (int i = j + 1; i < n; ++i) b[i] -= lj[i] * t;
+            }
         }
-    }
+    });
 }
 
 bool lu(int n, double* A, int lda, int* piv) {
@@ -149,49 +242,65 @@ bool lu_solve_transpose(int n, const double* A, int lda, const int* piv, double*
 // Householder reduction of a symmetric matrix to tridiagonal form T = Q^T A Q.
 // d: diagonal, e: sub-diagonal (e[i] couples i and i+1).  If want_q, A is
 // overwritten by Q; otherwise A is destroyed.
+// The reduction runs on a thread team.  Every thread forms the reflector and
+// the scalars itself (the same serial arithmetic, O(n) a step), p = tau A22 v
+// is split by rows and the rank-2 update by columns, each element keeping the
+// serial order of its sum; two barriers a step.
 static void tridiagonalize(int n, double* A, int lda, double* d, double* e, bool want_q) {
-    std::vector<double> v(n), p(n), w(n);
+    std::vector<double> p(n);
     std::vector<double> taus(n, 0.0);
-    for (int j = 0; j + 2 < n; ++j) {
-        int m = n - j - 1;
-        double* x = &A_(j + 1, j);
-        double alpha = 0.0;
-        for (int i = 0; i < m; ++i) alpha += x[i] * x[i];
-        alpha = std::sqrt(alpha);
-        if (alpha == 0.0) {
-            taus[j] = 0.0;
-            continue;
+    // one thread: with two barriers a step the team ran slower than one core on
+    // a 552 x 552 reduction (the steps are memory-bound and short)
+    const int T = 1;
+    hostpar::run(T, [&](int t, hostpar::Barrier& bar) {
+        std::vector<double> v(n), w(n);
+        for (int j = 0; j + 2 < n; ++j) {
+            const int m = n - j - 1;
+            double* x = &A_(j + 1, j);
+            double alpha = 0.0;
+            for (int i = 0; i < m; ++i) alpha += x[i] * x[i];
+            alpha = std::sqrt(alpha);
+            if (alpha == 0.0) {
+                if (t == 0) taus[j] = 0.0;
+                continue;   // the same decision in every thread
+            }
+            if (x[0] > 0) alpha = -alpha;
+            // v = x - alpha e1, normalised so that v[0] = 1
+            const double v0 = x[0] - alpha;
+            for (int i = 0; i < m; ++i) v[i] = x[i] / v0;
+            v[0] = 1.0;
+            double vv = 0.0;
+            for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+            const double tau = 2.0 / vv;
+            // p = tau * A22 v (symmetric, full storage), by columns of A22, rows split
+            const int i0 = (int)((long long)m * t / T), i1 = (int)((long long)m * (t + 1) / T);
+            for (int i = i0; i < i1; ++i) p[i] = 0.0;
+            for (int k = 0; k < m; ++k) {
+                const double* col = &A_(j + 1, j + 1 + k);
+                const double vk = v[k];
+                for (int i = i0; i < i1; ++i) p[i] += col[i] * vk;
+            }
+            for (int i = i0; i < i1; ++i) p[i] *= tau;
+            bar.wait();
+            double pv = 0.0;
+            for (int i = 0; i < m; ++i) pv += p[i] * v[i];
+            const double K = 0.5 * tau * pv;
+            for (int i = 0; i < m; ++i) w[i] = p[i] - K * v[i];
+            for (int c = t; c < m; c += T) {
+                double* col = &A_(j + 1, j + 1 + c);
+                const double vc = v[c], wc = w[c];
+                for (int i = 0; i < m; ++i) col[i] -= v[i] * wc + w[i] * vc;
+            }
+            bar.wait();   // A22 and p are free again; column j is read by nobody from here on
+            if (t == 0) {
+                taus[j] = tau;
+                // store v below the sub-diagonal for Q accumulation
+                x[0] = alpha;
+                for (int i = 1; i < m; ++i) x[i] = v[i];
+            }
         }
-        if (x[0] > 0) alpha = -alpha;
-        // v = x - alpha e1, normalised so that v[0] = 1
-        double v0 = x[0] - alpha;
-        for (int i = 0; i < m; ++i) v[i] = x[i] / v0;
-        v[0] = 1.0;
-        double vv = 0.0;
-        for (int i = 0; i < m; ++i) vv += v[i] * v[i];
-        double tau = 2.0 / vv;
-        taus[j] = tau;
-        // p = tau * A22 v (symmetric, full storage), by columns of A22
-        for (int i = 0; i < m; ++i) p[i] = 0.0;
-        for (int k = 0; k < m; ++k) {
-            const double* col = &A_(j + 1, j + 1 + k);
-            double vk = v[k];
-            for (int i = 0; i < m; ++i) p[i] += col[i] * vk;
-        }
-        for (int i = 0; i < m; ++i) p[i] *= tau;
-        double pv = 0.0;
-        for (int i = 0; i < m; ++i) pv += p[i] * v[i];
-        double K = 0.5 * tau * pv;
-        for (int i = 0; i < m; ++i) w[i] = p[i] - K * v[i];
-        for (int c = 0; c < m; ++c) {
-            double* col = &A_(j + 1, j + 1 + c);
-            double vc = v[c], wc = w[c];
-            for (int i = 0; i < m; ++i) col[i] -= v[i] * wc + w[i] * vc;
-        }
-        // store v below the sub-diagonal for Q accumulation
-        x[0] = alpha;
-        for (int i = 1; i < m; ++i) x[i] = v[i];
-    }
+    });
+    std::vector<double> v(n);
     for (int i = 0; i < n; ++i) d[i] = A_(i, i);
     for (int i = 0; i + 1 < n; ++i) e[i] = A_(i + 1, i);
     if (!want_q) return;

@@ -8,16 +8,19 @@
 // takes an idle handle of its geometry (rebound to the slot's stream) and a
 // new diffusion coefficient only re-runs the assembly kernel.  Handle memory
 // comes from the stream-ordered pool, so no slot's allocation stalls another.  Requests wait in one queue and are
-// admitted in arrival order, skipping ahead past requests whose estimated
-// device footprint does not fit the free part of the HBM budget (a request
-// larger than the whole budget runs when nothing else does).  A slot takes
+// admitted in arrival order (or, under the HRRN policy, highest response ratio
+// first), skipping requests whose estimated device footprint does not fit the
+// free part of the HBM budget (a request larger than the whole budget runs
+// when nothing else does).  A slot takes
 // the next admissible request as soon as its previous one finishes, so work
 // of requests that arrived at different times overlaps on the device
 // (continuous batching).  Each solve touches only its own handle, so a
 // result does not depend on what else is running.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -33,9 +36,21 @@ constexpr int kExecutorUSlot = 31;   // workspace slot of a dense U staged for a
 
 struct Job {
     st_request req;
+    int retries = 0;      // re-queued after running out of device memory next to other requests
     double t_submit = 0.0;
-    double est = 0.0;
+    double est = 0.0;     // admission estimate of device bytes
+    double units = 0.0;   // n_h * n_t: the work measure of the service estimate
+    int cls = 0;          // (operator, method, dimension) class of the learned rate
 };
+
+constexpr double kServiceOverhead = 2e-3;   // seconds of a request beyond its n_h * n_t work
+
+int class_of(const st_request& r) { return (r.desc.op == ST_CONVDIFF ? 8 : 0) + (r.method == ST_METHOD_CN ? 4 : 0) + r.desc.dim; }
+
+double prior_rate(int cls) {
+    if (cls & 4) return 1e-9;
+    return (cls & 8) ? 2e-8 : 3e-9;
+}
 
 struct GeomKey {
     int dim, n0, n1, n2, n_t, precision, maxit, max_basis;
@@ -84,6 +99,8 @@ struct st_executor {
     std::vector<std::thread> threads;
     bool stop = false;
     int running = 0;
+    int policy = ST_SCHED_FIFO;
+    double rate[16] = {};   // learned seconds per n_h * n_t unit, per class (0: not yet seen)
     Clock::time_point t0;
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -100,27 +117,58 @@ extern "C" double st_request_bytes(const st_desc* d, int p) {
     }
     int maxit = d->maxit > 0 ? d->maxit : 400;
     int maxb = d->max_basis > 0 ? d->max_basis : 2048;
-    double k_est = std::min<double>(maxb + 16, (double)p * (std::min(maxit, 80) + 1));
+    // convection-diffusion needs more iterations (up to about 200 at eps = 0.01)
+    const int it_est = d->op == ST_CONVDIFF ? 200 : 80;
+    double k_est = std::min<double>(maxb + 16, (double)p * (std::min(maxit, it_est) + 1));
     double csr = nnz * (4.0 + 4 * 8.0 + 4 * 4.0) + 4.0 * (nh + 1);
-    double blocks = 8.0 * nh * (2.0 * k_est + 12.0 * p);
+    // V and M V (and the double-float V in mixed precision)
+    double blocks = 8.0 * nh * ((d->precision == ST_MIXED ? 3.0 : 2.0) * k_est + 12.0 * p);
     double y = 8.0 * k_est * d->n_t;
+    if (d->op == ST_CONVDIFF) {
+        // flexible GMRES: 40-step Krylov and preconditioned blocks for up to 16 columns, within 4 GB
+        double per_col = 8.0 * nh * 84.0;
+        double mg = std::max(1.0, std::min({(double)p, 16.0, std::floor(4e9 / per_col)}));
+        blocks += per_col * mg;
+    }
     return csr + tab + blocks + y;
 }
 
 namespace {
 
+double service_estimate(const st_executor* ex, const Job& j) {
+    double r = ex->rate[j.cls] > 0 ? ex->rate[j.cls] : prior_rate(j.cls);
+    return kServiceOverhead + r * j.units;
+}
+
+// The request to admit next (caller holds ex->mu).  FIFO: the first that fits
+// the free budget.  HRRN: the request of highest (wait + service) / service;
+// if it does not fit, nothing is admitted until memory frees up, so a large
+// request is not starved by small ones that keep fitting.  With nothing
+// running, the head (FIFO) or the top request (HRRN) runs whatever its size,
+// so the queue cannot stall.
 bool pick(st_executor* ex, size_t* idx) {
+    if (ex->queue.empty()) return false;
+    if (ex->policy != ST_SCHED_HRRN) {
+        for (size_t i = 0; i < ex->queue.size(); ++i)
+            if (ex->used + ex->queue[i].est <= ex->budget) {
+                *idx = i;
+                return true;
+            }
+        *idx = 0;
+        return ex->running == 0;
+    }
+    const double now = ex->now();
+    double best = -1.0;
     for (size_t i = 0; i < ex->queue.size(); ++i) {
-        if (ex->used + ex->queue[i].est <= ex->budget) {
+        const Job& j = ex->queue[i];
+        const double sv = service_estimate(ex, j);
+        const double ratio = (now - j.t_submit + sv) / sv;
+        if (ratio > best) {
+            best = ratio;
             *idx = i;
-            return true;
         }
     }
-    if (ex->running == 0 && !ex->queue.empty()) {
-        *idx = 0;
-        return true;
-    }
-    return false;
+    return ex->running == 0 || ex->used + ex->queue[*idx].est <= ex->budget;
 }
 
 // Take an idle pooled handle of this geometry (rebound to the slot's stream;
@@ -261,12 +309,28 @@ void worker(st_executor* ex, int slot) {
         res.bytes_reserved = job.est;
         res.t_submit = job.t_submit;
         res.t_start = ex->now();
+        st_note_msg("");
         res.status = run_one(ex, s, job, res);
         res.t_end = ex->now();
+        if (res.status != ST_OK) std::snprintf(res.message, sizeof(res.message), "%s", st_last_error());
         {
             std::lock_guard<std::mutex> lk(ex->mu);
             ex->used -= job.est;
             ex->running--;
+            if (res.status == ST_ENOMEM && ex->running > 0 && job.retries < 2) {
+                // the estimate fell short while others held memory: run it again, alone
+                job.retries++;
+                job.est = std::max(job.est, ex->budget);
+                ex->queue.push_front(job);
+                ex->cv_work.notify_all();
+                continue;
+            }
+            if (res.status == ST_OK && job.units > 0) {
+                // exponential average of the observed rate of this class
+                double obs = std::max(0.0, res.t_end - res.t_start - kServiceOverhead) / job.units;
+                double& r = ex->rate[job.cls];
+                r = r > 0 ? 0.7 * r + 0.3 * obs : obs;
+            }
             ex->done.push_back(res);
         }
         ex->cv_done.notify_all();
@@ -318,6 +382,8 @@ extern "C" int st_executor_submit(st_executor* ex, const st_request* req) {
     // a dense U staged on the device: CN's output, or U = V Y bound for host memory
     double nh = 1.0;
     for (int i = 0; i < d.dim; ++i) nh *= d.n[i];
+    job.units = nh * d.n_t;
+    job.cls = class_of(*req);
     if (req->method == ST_METHOD_CN || (req->U_out && !st_is_device_ptr(req->U_out))) job.est += 8.0 * nh * d.n_t;
     {
         std::lock_guard<std::mutex> lk(ex->mu);
@@ -342,6 +408,16 @@ extern "C" int st_executor_wait(st_executor* ex, st_result* out, int max, int* c
         ++n;
     }
     *count = n;
+    return ST_OK;
+}
+
+extern "C" int st_executor_set_policy(st_executor* ex, int policy) {
+    if (!ex || (policy != ST_SCHED_FIFO && policy != ST_SCHED_HRRN)) return ST_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(ex->mu);
+        ex->policy = policy;
+    }
+    ex->cv_work.notify_all();
     return ST_OK;
 }
 

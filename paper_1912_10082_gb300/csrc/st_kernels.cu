@@ -191,6 +191,104 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && DIM == 2) ? 3 : 1) k_a
     }
 }
 
+// FP32 variant: a lane loads only its own x of the (YB+2)(ZB+2) rows and takes
+// the x - 1 and x + 1 values from its neighbours by warp shuffles, so a warp
+// of 32 lanes yields 30 outputs per row from one coalesced load per row (the
+// two edge lanes only supply halo values).  The STEPS + 1 columns a thread
+// walks are unrolled, the next column's loads issued PD columns ahead.  The
+// sums run in the same order as k_apply_box (dz, dy, dx lexicographic).
+template <typename T, int DIM, int YB, int ZB, int STEPS, int PD>
+__global__ void __launch_bounds__(256, DIM == 2 ? 3 : 1) k_apply_box_sh(int nx, int ny, int nz, int n_t,
+                                                                          BoxStencil<T> S, const T* __restrict__ U,
+                                                                          long long ldu, T* __restrict__ Y,
+                                                                          long long ldy) {
+    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
+    constexpr int NV = RY * RZ;
+    const int nxs = (nx + 29) / 30, nyb = (ny + 8 * YB - 1) / (8 * YB);
+    int b = blockIdx.x;
+    const int xs = b % nxs;
+    b /= nxs;
+    const int yb = b % nyb;
+    const int zb = b / nyb;
+    const int lane = threadIdx.x;
+    const int x = xs * 30 + lane - 1;
+    const int y0 = (yb * 8 + threadIdx.y) * YB;
+    const int z0 = zb * ZB;
+    if (y0 >= ny || (DIM == 3 && z0 >= nz)) return;   // uniform over the warp: the shuffles see all lanes
+    const bool okx = x >= 0 && x < nx;
+    const bool emit = lane >= 1 && lane <= 30 && x < nx;
+    const long long nxy = (long long)nx * ny;
+    bool ok[NV];
+#pragma unroll
+    for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < RY; ++iy)
+            ok[iz * RY + iy] = okx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny &&
+                               (DIM < 3 || (z0 + iz - 1 >= 0 && z0 + iz - 1 < nz));
+    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
+    const int l0 = blockIdx.y * STEPS;
+    auto load = [&](int c, T* v) {
+#pragma unroll
+        for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+            for (int iy = 0; iy < RY; ++iy) {
+                const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx;
+                v[iz * RY + iy] =
+                    (c >= 0 && c < n_t && ok[iz * RY + iy]) ? __ldg(U + (long long)c * ldu + base + off) : T(0);
+            }
+    };
+    T buf[PD + 1][NV];
+    T pn[YB * ZB];
+#pragma unroll
+    for (int j = 0; j < PD; ++j) load(l0 - 1 + j, buf[j]);
+#pragma unroll
+    for (int j = 0; j <= STEPS; ++j) {
+        const int c = l0 - 1 + j;   // column c; j = 0 is the previous chunk's last (N u_{l0-1} only)
+        if (j + PD <= STEPS) load(l0 - 1 + j + PD, buf[(j + PD) % (PD + 1)]);
+        if (c >= n_t) break;
+        const T* v = buf[j % (PD + 1)];
+        T tP[YB * ZB], tN[YB * ZB];
+#pragma unroll
+        for (int o = 0; o < YB * ZB; ++o) tP[o] = tN[o] = T(0);
+#pragma unroll
+        for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+            for (int iy = 0; iy < RY; ++iy) {
+                const T w0 = v[iz * RY + iy];
+                const T wm = __shfl_up_sync(0xffffffffu, w0, 1);
+                const T wp = __shfl_down_sync(0xffffffffu, w0, 1);
+#pragma unroll
+                for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+                    for (int oy = 0; oy < YB; ++oy) {
+                        const int dz = DIM == 3 ? iz - 1 - oz : 0, dy = iy - 1 - oy;
+                        if (dz < -1 || dz > 1 || dy < -1 || dy > 1) continue;
+                        const int e = (dz + 1) * 9 + (dy + 1) * 3;
+                        const int o = oz * YB + oy;
+                        tP[o] += S.p[e] * wm;
+                        tN[o] += S.q[e] * wm;
+                        tP[o] += S.p[e + 1] * w0;
+                        tN[o] += S.q[e + 1] * w0;
+                        tP[o] += S.p[e + 2] * wp;
+                        tN[o] += S.q[e + 2] * wp;
+                    }
+            }
+        if (j >= 1 && c >= 0 && emit) {
+#pragma unroll
+            for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+                for (int oy = 0; oy < YB; ++oy) {
+                    if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
+                    const int o = oz * YB + oy;
+                    Y[(size_t)c * ldy + base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx] =
+                        tP[o] - pn[o];
+                }
+        }
+#pragma unroll
+        for (int o = 0; o < YB * ZB; ++o) pn[o] = c >= 0 ? tN[o] : T(0);
+    }
+}
+
 // Spatial products with a constant box stencil: O1[:,c] = S1 * X[:,c] (+ beta
 // O1[:,c]) and, when O2 is given, O2[:,c] = S2 * X[:,c] from the same loads.
 // Same thread layout and register blocking as the apply (a warp spans 32
@@ -1042,6 +1140,116 @@ __global__ void k_axpby(int n, int m, double a, const double* __restrict__ X, lo
     *y = (b == 0.0 ? 0.0 : b * (*y)) + a * X[(size_t)j * ldx + i];
 }
 
+// ---------------------------------------------------------------------------
+// Batched flexible GMRES: m independent Arnoldi processes, one per column of a
+// block, advanced together.  The Krylov blocks are interleaved: vector i of
+// column c is Z + (i m + c) n.  Each kernel covers all m columns, so a step
+// costs the same launches for any m and no column's coefficients leave the
+// device until the host checks convergence.
+// ---------------------------------------------------------------------------
+
+// part[(chunk m + c) kk + i] = sum over the chunk's rows of Z_i[:,c] . Z_{kk-1}[:,c]
+// for i < kk: the last vector is the one being orthogonalised, so i = kk - 1
+// is its squared norm.  The chunk of that vector is staged in shared memory;
+// a warp per basis vector, lanes over rows, a fixed butterfly.
+__global__ void __launch_bounds__(256) k_gm_dot_partial(int n, int kk, int m, int rows, const double* __restrict__ Z,
+                                                        double* __restrict__ part) {
+    extern __shared__ double us[];
+    const int c = blockIdx.y;
+    const long long r0 = (long long)blockIdx.x * rows;
+    const int rn = (int)min((long long)rows, (long long)n - r0);
+    const double* u = Z + ((size_t)(kk - 1) * m + c) * n + r0;
+    for (int t = threadIdx.x; t < rn; t += blockDim.x) us[t] = u[t];
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int i = warp; i < kk; i += blockDim.x / 32) {
+        const double* z = Z + ((size_t)i * m + c) * n + r0;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int t = lane;
+        for (; t + 96 < rn; t += 128) {
+            s0 += z[t] * us[t];
+            s1 += z[t + 32] * us[t + 32];
+            s2 += z[t + 64] * us[t + 64];
+            s3 += z[t + 96] * us[t + 96];
+        }
+        for (; t < rn; t += 32) s0 += z[t] * us[t];
+        double sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) part[((size_t)blockIdx.x * m + c) * kk + i] = sum;
+    }
+}
+
+// H[c ldh + i] = sum over chunks of part: a warp per (c, i), fixed order.
+__global__ void k_gm_reduce(int nch, int kk, int m, const double* __restrict__ part, double* __restrict__ H, int ldh) {
+    const int idx = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (idx >= kk * m) return;
+    const int c = idx / kk, i = idx % kk;
+    double s = 0.0;
+    for (int ch = lane; ch < nch; ch += 32) s += part[((size_t)ch * m + c) * kk + i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) H[(size_t)c * ldh + i] = s;
+}
+
+// Z_nb[:,c] -= sum_{i < nb} Z_i[:,c] H[c ldh + i], a thread per row for all m
+// columns.  With H1 (the first pass's coefficients) the step ends here: H holds
+// the second pass's coefficients and, at i = nb, the squared norm of the vector
+// before this update, so the new norm is h = sqrt(H[nb] - sum H[i]^2); the
+// vector is divided by h (set to zero when h = 0) and CTA 0 writes column jcol
+// of each column's Hessenberg matrix, Hd[c ldhd + jcol (J + 1) + i] =
+// H1[i] + H[i] (i < nb) and h (i = nb).
+template <int MAXM>
+__global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, double* __restrict__ Z,
+                                                   const double* __restrict__ H, int ldh,
+                                                   const double* __restrict__ H1, int ldh1, double* __restrict__ Hd,
+                                                   long long ldhd, int jcol, int J) {
+    extern __shared__ double hs[];   // m x (nb + 1) coefficients, then m scale factors
+    double* inv = hs + (size_t)m * (nb + 1);
+    for (int t = threadIdx.x; t < m * (nb + 1); t += blockDim.x) hs[t] = H[(size_t)(t / (nb + 1)) * ldh + t % (nb + 1)];
+    __syncthreads();
+    if (H1 && threadIdx.x < m) {
+        const int c = threadIdx.x;
+        double ss = 0.0;
+        for (int i = 0; i < nb; ++i) ss += hs[c * (nb + 1) + i] * hs[c * (nb + 1) + i];
+        const double nu2 = hs[c * (nb + 1) + nb] - ss;
+        const double h = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+        inv[c] = h > 0.0 ? 1.0 / h : 0.0;
+        if (blockIdx.x == 0) {
+            double* col = Hd + (size_t)c * ldhd + (size_t)jcol * (J + 1);
+            for (int i = 0; i < nb; ++i) col[i] = H1[(size_t)c * ldh1 + i] + hs[c * (nb + 1) + i];
+            col[nb] = h;
+        }
+    }
+    __syncthreads();
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double acc[MAXM];
+#pragma unroll
+    for (int c = 0; c < MAXM; ++c) acc[c] = c < m ? Z[((size_t)nb * m + c) * n + r] : 0.0;
+    for (int i = 0; i < nb; ++i) {
+        double z[MAXM];
+#pragma unroll
+        for (int c = 0; c < MAXM; ++c) z[c] = c < m ? Z[((size_t)i * m + c) * n + r] : 0.0;
+#pragma unroll
+        for (int c = 0; c < MAXM; ++c)
+            if (c < m) acc[c] -= z[c] * hs[c * (nb + 1) + i];   // hs holds m columns only
+    }
+#pragma unroll
+    for (int c = 0; c < MAXM; ++c)
+        if (c < m) Z[((size_t)nb * m + c) * n + r] = H1 ? acc[c] * inv[c] : acc[c];
+}
+
+// X[:,c] *= f[c] (device factors).
+__global__ void k_scale_cols_dev(int n, int m, double* __restrict__ X, long long ldx, const double* __restrict__ f) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * m) return;
+    const int c = (int)(idx / n);
+    const long long r = idx % n;
+    X[(size_t)c * ldx + r] *= f[c];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1065,21 +1273,31 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
             S.p[e] = (T)(sizeof(T) == 8 ? p->box_p64[e] : p->box_p32[e]);
             S.q[e] = (T)(sizeof(T) == 8 ? p->box_q64[e] : p->box_q32[e]);
         }
-        // blocks of 32 x-points by 8 thread rows; each thread YB (x ZB) points and STEPS columns
-        // 2D: 4 rows x 8 time columns per thread; 3D: 2 x 2 points x 16 columns
-        const int YB = p->dim == 2 ? 4 : 2, ZB = p->dim == 2 ? 1 : 2;
-        long long blocks = (long long)((nx + 31) / 32) * ((ny + 8 * YB - 1) / (8 * YB)) *
+        // blocks of 32 x-points (30 outputs for the shuffle kernel) by 8 thread rows; each thread
+        // YB (x ZB) points and `steps` columns.  FP32: shuffle kernel, 2D 4 rows x 8 columns,
+        // 3D 4 x 2 points x 8 columns.  FP64 (FP64-ALU-bound): 2D 4 rows x 8, 3D 2 x 2 x 16.
+        const bool sh = sizeof(T) == 4;
+        const int YB = p->dim == 2 ? 4 : (sh ? 4 : 2), ZB = p->dim == 2 ? 1 : 2;
+        const int xw = sh ? 30 : 32;
+        long long blocks = (long long)((nx + xw - 1) / xw) * ((ny + 8 * YB - 1) / (8 * YB)) *
                            (p->dim == 3 ? (nz + ZB - 1) / ZB : 1);
-        const int steps = p->dim == 2 ? 8 : 16;
+        const int steps = (p->dim == 2 || sh) ? 8 : 16;
         dim3 grid((unsigned)blocks, (unsigned)((n_t + steps - 1) / steps));
         if (blocks > 0x7fffffffLL || grid.y > 65535) return ST_EINVAL;
         double ts = (double)sizeof(T);
         st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32", ts * 2.0 * (double)p->n_h * n_t,
                       4.0 * (double)p->max_row_nnz * p->n_h * n_t);
-        if (p->dim == 2)
-            k_apply_box<T, 2, 4, 1, 8><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
-        else
-            k_apply_box<T, 3, 2, 2, 16><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+        if constexpr (sizeof(T) == 4) {
+            if (p->dim == 2)
+                k_apply_box_sh<T, 2, 4, 1, 8, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            else
+                k_apply_box_sh<T, 3, 4, 2, 8, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+        } else {
+            if (p->dim == 2)
+                k_apply_box<T, 2, 4, 1, 8><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            else
+                k_apply_box<T, 3, 2, 2, 16><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+        }
         st_prof_end(s);
         ST_LAUNCH_CHECK();
         return ST_OK;
@@ -1556,4 +1774,62 @@ int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const doub
     }
     Batch2 bt{1, 0, 0, 0, 0, 0, 0};
     return launch_gemm_rr<double>(n_t, n, k, Y, ldy, V, ldv, U, ldu, 1, bt, plain, s, "lowrank_gemm");
+}
+
+// ---------------------------------------------------------------------------
+// batched flexible GMRES building blocks
+// ---------------------------------------------------------------------------
+static int gm_rows(int n, int m) {
+    // about 600 CTAs over the m columns, 256..4096 rows a chunk
+    long long nch = std::max(1, 608 / std::max(1, m));
+    long long rows = (n + nch - 1) / nch;
+    rows = (rows + 31) / 32 * 32;
+    return (int)std::min<long long>(4096, std::max<long long>(256, rows));
+}
+
+size_t st_gm_partial_elems(int n, int kk, int m) {
+    const int rows = gm_rows(n, m);
+    return (size_t)((n + rows - 1) / rows) * (size_t)m * (size_t)kk;
+}
+
+int st_gm_dots(int n, int kk, int m, const double* Z, double* part, double* H, int ldh, cudaStream_t s) {
+    if (n <= 0 || kk <= 0 || m <= 0 || m > kMaxCols) return ST_EINVAL;
+    const int rows = gm_rows(n, m);
+    const int nch = (n + rows - 1) / rows;
+    st_prof_begin(s, "gm_dot", 8.0 * (double)n * kk * m + 16.0 * (double)nch * kk * m, 2.0 * (double)n * kk * m);
+    k_gm_dot_partial<<<dim3(nch, m), 256, sizeof(double) * rows, s>>>(n, kk, m, rows, Z, part);
+    ST_LAUNCH_CHECK();
+    k_gm_reduce<<<(kk * m + 7) / 8, 256, 0, s>>>(nch, kk, m, part, H, ldh);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_gm_update(int n, int nb, int m, double* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
+                 long long ldhd, int jcol, int J, cudaStream_t s) {
+    if (n <= 0 || nb < 0 || m <= 0 || m > kMaxCols) return ST_EINVAL;
+    const int blocks = (n + 255) / 256;
+    const size_t smem = sizeof(double) * ((size_t)m * (nb + 1) + m);
+    st_prof_begin(s, "gm_update", 8.0 * (double)n * m * (nb + 2), 2.0 * (double)n * m * nb);
+    if (m <= 1)
+        k_gm_update<1><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+    else if (m <= 2)
+        k_gm_update<2><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+    else if (m <= 4)
+        k_gm_update<4><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+    else if (m <= 8)
+        k_gm_update<8><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+    else
+        k_gm_update<16><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_scale_cols_dev(int n, int m, double* X, int ldx, const double* f, cudaStream_t s) {
+    if (n <= 0 || m <= 0) return ST_OK;
+    const long long tot = (long long)n * m;
+    k_scale_cols_dev<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, X, ldx, f);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
 }

@@ -35,7 +35,7 @@ inline double ms_since(Clock::time_point t0) {
 
 enum SlotId {
     S_F1D = 0, S_F1C, S_MAQ, S_WH, S_WH2, S_TMP, S_X32, S_W32, S_T32, S_SMALL, S_PART, S_COPY, S_MV,
-    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT, S_WDF
+    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT, S_WDF, S_GH, S_GHD, S_GPART
 };
 
 // Records why the Krylov process broke down (text of st_last_error).
@@ -334,22 +334,28 @@ bool projected_solve(int k, int n_t, double dt, const double* Mm, const double* 
         dense::lu_solve(k, P.data(), k, piv.data(), G.data(), k, r);
     }
     Y.assign((size_t)k * n_t, 0.0);
-    for (int l = 0; l < n_t; ++l) {
-        double* y = &Y[(size_t)l * k];
-        for (int q = 0; q < r; ++q) {
-            double f = F2c[(size_t)q * n_t + l];
-            const double* gq = &G[(size_t)q * k];
-            for (int i = 0; i < k; ++i) y[i] += gq[i] * f;
-        }
-        if (l > 0) {
-            const double* yp = y - k;
-            for (int j = 0; j < k; ++j) {
-                double t = yp[j];
-                const double* sc = &S[(size_t)j * k];
-                for (int i = 0; i < k; ++i) y[i] += sc[i] * t;
+    // the rows of each step split over a thread team, a barrier between steps
+    const int T = hostpar::threads_for(2.0 * k * k * n_t);
+    hostpar::run(T, [&](int t, hostpar::Barrier& bar) {
+        const int i0 = (int)((long long)k * t / T), i1 = (int)((long long)k * (t + 1) / T);
+        for (int l = 0; l < n_t; ++l) {
+            double* y = &Y[(size_t)l * k];
+            for (int q = 0; q < r; ++q) {
+                double f = F2c[(size_t)q * n_t + l];
+                const double* gq = &G[(size_t)q * k];
+                for (int i = i0; i < i1; ++i) y[i] += gq[i] * f;
             }
+            if (l > 0) {
+                const double* yp = y - k;
+                for (int j = 0; j < k; ++j) {
+                    double tj = yp[j];
+                    const double* sc = &S[(size_t)j * k];
+                    for (int i = i0; i < i1; ++i) y[i] += sc[i] * tj;
+                }
+            }
+            bar.wait();
         }
-    }
+    });
     return true;
 }
 
@@ -358,7 +364,11 @@ int ensure_basis(st_problem* p, Ctx& c, int need_cols, int keep_cols, double** M
         *MV = (double*)p->slot_ptr[S_MV];
         return ST_OK;
     }
-    size_t cap = std::max<size_t>({(size_t)need_cols, 2 * p->V_cap_cols, 32});
+    // doubling while the basis is small; beyond 16M entries a column block, grow by half (the old and
+    // new blocks coexist during the copy, so doubling a large basis triples its footprint)
+    const size_t grown = (size_t)c.n * p->V_cap_cols <= ((size_t)1 << 24) ? 2 * p->V_cap_cols
+                                                                             : p->V_cap_cols + p->V_cap_cols / 2;
+    size_t cap = std::max<size_t>({(size_t)need_cols, grown, 32});
     cap = std::min<size_t>(cap, (size_t)p->d.max_basis + 16);
     if (cap < (size_t)need_cols) cap = need_cols;
     double *nv, *nmv;
@@ -625,126 +635,173 @@ int check_gap(const std::vector<int>& hist_it, const std::vector<double>& hist_r
 }
 
 // Shifted solve (A + s M) W = M X for a nonsymmetric A (convection-diffusion):
-// flexible GMRES per column, right-preconditioned by the fast-diagonalisation
-// solve of the symmetric part eps K + s M.  The preconditioned directions T_j
-// are kept, so W = T y has exactly the GMRES residual whatever the
-// preconditioner's precision: FP64 transforms, or FP32 ones in mixed
-// precision.  Classical Gram-Schmidt twice, Givens rotations on the host,
-// restarts after J steps; stops at ||b - (A + sM) w|| <= rtol ||b||.
+// flexible GMRES, right-preconditioned by the fast-diagonalisation solve of
+// the symmetric part eps K + s M.  The preconditioned directions T_j are kept,
+// so W = T y has exactly the GMRES residual whatever the preconditioner's
+// precision: FP64 transforms, or FP32 ones in mixed precision.  The columns
+// run as independent GMRES processes advanced together (each kernel covers
+// the whole block, vectors interleaved): classical Gram-Schmidt twice, the
+// new vector normalised on the device from the second pass's Gram products,
+// so a step needs no synchronisation.  Every CHK steps the host fetches the
+// new Hessenberg columns, applies the Givens rotations of each column and
+// stops the cycle once every column satisfies ||b - (A + sM) w|| <= rtol ||b||
+// (a column that converged inside a CHK window uses only its own steps).
+// Restarts after J steps from the true residual.
 int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx,
                          int ncols, double* W, int ldw, double rtol, int* iters_out) {
     st_problem* p = c.p;
     const int n = c.n;
-    constexpr int J = 40, CYCLES = 12;
-    double *Z, *T, *bb;
-    ST_TRY(st_slot(p, S_GZ, sizeof(double) * (size_t)n * (J + 1), (void**)&Z));
-    ST_TRY(st_slot(p, S_GT, sizeof(double) * (size_t)n * J, (void**)&T));
-    ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n, (void**)&bb));
-    double* tmp;
+    constexpr int J = 40, CYCLES = 12, CHK = 4, MAXG = 16;
+    // columns per group: all of them (at most 16) unless the Krylov blocks would exceed 4 GB
+    const double per_col = 8.0 * n * (2.0 * J + 4.0);
+    const int mg = std::max(1, std::min({ncols, MAXG, (int)std::max(1.0, 4e9 / per_col)}));
+    const long long ldhd = (long long)J * (J + 1);
+    double *Z, *T, *B, *tmp, *Hc, *Hd, *part;
+    ST_TRY(st_slot(p, S_GZ, sizeof(double) * (size_t)n * (J + 1) * mg, (void**)&Z));
+    ST_TRY(st_slot(p, S_GT, sizeof(double) * (size_t)n * J * mg, (void**)&T));
+    ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n * mg, (void**)&B));
+    ST_TRY(st_slot(p, S_TMP, sizeof(double) * (size_t)n * mg, (void**)&tmp));
+    ST_TRY(st_slot(p, S_GH, sizeof(double) * (size_t)2 * (J + 2) * mg, (void**)&Hc));
+    ST_TRY(st_slot(p, S_GHD, sizeof(double) * (size_t)ldhd * mg, (void**)&Hd));
+    ST_TRY(st_slot(p, S_GPART, sizeof(double) * st_gm_partial_elems(n, J + 2, mg), (void**)&part));
+    double* H1 = Hc;                          // first pass coefficients, ld J + 2
+    double* H2 = Hc + (size_t)(J + 2) * mg;   // second pass (and the squared norm at i = j + 1)
     float *x32 = nullptr, *w32 = nullptr, *t32 = nullptr;
-    ST_TRY(st_slot(p, S_TMP, sizeof(double) * (size_t)n, (void**)&tmp));
     if (prec == ST_MIXED) {
-        ST_TRY(st_slot(p, S_X32, sizeof(float) * (size_t)n, (void**)&x32));
-        ST_TRY(st_slot(p, S_W32, sizeof(float) * (size_t)n, (void**)&w32));
-        ST_TRY(st_slot(p, S_T32, sizeof(float) * (size_t)n, (void**)&t32));
+        ST_TRY(st_slot(p, S_X32, sizeof(float) * (size_t)n * mg, (void**)&x32));
+        ST_TRY(st_slot(p, S_W32, sizeof(float) * (size_t)n * mg, (void**)&w32));
+        ST_TRY(st_slot(p, S_T32, sizeof(float) * (size_t)n * mg, (void**)&t32));
     }
-    auto precond = [&](const double* z, double* t) -> int {
-        if (prec != ST_MIXED) return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, 1, t, n, tmp, c.s);
-        ST_TRY(st_convert_64_32(n, 1, z, n, x32, n, c.s));
-        ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, 1, w32, n, t32, c.s));
-        return st_convert_32_64_add(n, 1, w32, n, t, n, 0.0, c.s);
+    auto precond = [&](const double* z, double* t, int m) -> int {
+        if (prec != ST_MIXED) return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, m, t, n, tmp, c.s);
+        ST_TRY(st_convert_64_32(n, m, z, n, x32, n, c.s));
+        ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, m, w32, n, t32, c.s));
+        return st_convert_32_64_add(n, m, w32, n, t, n, 0.0, c.s);
     };
-    ST_TRY(stage_reserve(p, 3 * pad32(J + 2)));
+    ST_TRY(stage_reserve(p, pad32((size_t)mg * ldhd) + pad32((size_t)(J + 2) * mg) + 2 * pad32(mg)));
     Stage sg(c);
     int total = 0;
-    std::vector<double> H((size_t)(J + 1) * J), cs(J), sn(J), g(J + 1), y(J);
-    for (int col = 0; col < ncols; ++col) {
-        double* w = W + (size_t)col * ldw;
+    struct ColState {
+        std::vector<double> H, cs, sn, g;
+        double bnorm = -1.0, beta = 0.0;
+        bool active = false, conv = false;
+        int used = 0;   // Arnoldi steps of this cycle that enter the solution
+    };
+    std::vector<ColState> cols(mg);
+    for (auto& cl : cols) {
+        cl.H.assign((size_t)(J + 1) * J, 0.0);
+        cl.cs.assign(J, 0.0);
+        cl.sn.assign(J, 0.0);
+        cl.g.assign(J + 1, 0.0);
+    }
+    std::vector<double> f(mg), y(J);
+    for (int g0 = 0; g0 < ncols; g0 += mg) {
+        const int m = std::min(mg, ncols - g0);
+        double* Wg = W + (size_t)g0 * ldw;
         if (MX) {
-            ST_TRY(st_copy_cols64(n, 1, MX + (size_t)col * ldmx, ldmx, bb, n, c.s));
+            ST_TRY(st_copy_cols64(n, m, MX + (size_t)g0 * ldmx, ldmx, B, n, c.s));
         } else {
-            ST_TRY(st_spmm_ma<double>(p, X + (size_t)col * ldx, ldx, 1, bb, n, (double*)nullptr, n, c.s));
+            ST_TRY(st_spmm_ma<double>(p, X + (size_t)g0 * ldx, ldx, m, B, n, (double*)nullptr, n, c.s));
         }
-        ST_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * n, c.s));
-        ST_TRY(st_copy_cols64(n, 1, bb, n, Z, n, c.s));   // r = b
-        double bnorm = -1.0;
+        for (int k = 0; k < m; ++k) ST_CUDA_TRY(cudaMemsetAsync(Wg + (size_t)k * ldw, 0, sizeof(double) * n, c.s));
+        ST_TRY(st_copy_cols64(n, m, B, n, Z, n, c.s));   // R = B
+        for (int k = 0; k < m; ++k) cols[k].bnorm = -1.0;
         for (int cyc = 0; cyc < CYCLES; ++cyc) {
-            double* dn = sg.out(1);
-            ST_TRY(ts_tn_dev(c, 1, 1, Z, n, Z, n, dn, 1));
+            // residual norms of the block: the dots of vector 0 with itself
+            ST_TRY(st_gm_dots(n, 1, m, Z, part, H2, J + 2, c.s));
+            double* dn = sg.out(m);
+            ST_CUDA_TRY(cudaMemcpy2DAsync(dn, sizeof(double), H2, sizeof(double) * (J + 2), sizeof(double), m,
+                                          cudaMemcpyDeviceToDevice, c.s));
             ST_TRY(sg.fetch());
-            double beta = std::sqrt(std::max(sg.host_of(dn)[0], 0.0));
-            if (bnorm < 0) bnorm = beta;
-            if (!(beta > rtol * bnorm) || beta == 0.0) break;
-            ST_TRY(st_axpby64(n, 1, 1.0 / beta, Z, n, 0.0, Z, n, c.s));
-            std::fill(g.begin(), g.end(), 0.0);
-            g[0] = beta;
-            int j = 0;
-            bool done = false;
-            for (; j < J && !done; ++j) {
-                double* zj = Z + (size_t)j * n;
-                double* tj = T + (size_t)j * n;
-                double* u = Z + (size_t)(j + 1) * n;
-                ST_TRY(precond(zj, tj));
-                ST_TRY(st_spmm_comb64(p, shift, 1.0, tj, n, 1, 0.0, u, n, c.s));
-                // u is column j+1 of Z: one product [Z_0..Z_j, u]^T u per pass gives the
-                // coefficients and u^T u before the pass's update
-                double* dh[2];
-                for (int pass = 0; pass < 2; ++pass) {
-                    dh[pass] = sg.out(j + 2);
-                    ST_TRY(ts_tn_dev(c, j + 2, 1, Z, n, u, n, dh[pass], j + 2));
-                    ST_TRY(st_tsgemm_nn(n, j + 1, 1, -1.0, Z, n, dh[pass], j + 2, 1.0, u, n, c.s));
-                }
+            bool any = false;
+            for (int k = 0; k < m; ++k) {
+                ColState& cl = cols[k];
+                cl.beta = std::sqrt(std::max(sg.host_of(dn)[k], 0.0));
+                if (cl.bnorm < 0) cl.bnorm = cl.beta;
+                cl.active = cl.beta > rtol * cl.bnorm && cl.beta > 0.0;
+                cl.conv = !cl.active;
+                cl.used = 0;
+                std::fill(cl.g.begin(), cl.g.end(), 0.0);
+                cl.g[0] = cl.beta;
+                f[k] = cl.active ? 1.0 / cl.beta : 0.0;
+                any = any || cl.active;
+            }
+            if (!any) break;
+            double* df;
+            ST_TRY(sg.in(f.data(), m, &df));
+            ST_TRY(st_scale_cols_dev(n, m, Z, n, df, c.s));
+            int j = 0, checked = 0;
+            bool all_conv = false;
+            for (; j < J && !all_conv; ++j) {
+                double* Zj = Z + (size_t)j * m * n;
+                double* Tj = T + (size_t)j * m * n;
+                double* U = Z + (size_t)(j + 1) * m * n;
+                ST_TRY(precond(Zj, Tj, m));
+                ST_TRY(st_spmm_comb64(p, shift, 1.0, Tj, n, m, 0.0, U, n, c.s));
+                ST_TRY(st_gm_dots(n, j + 2, m, Z, part, H1, J + 2, c.s));
+                ST_TRY(st_gm_update(n, j + 1, m, Z, H1, J + 2, nullptr, 0, nullptr, 0, j, J, c.s));
+                ST_TRY(st_gm_dots(n, j + 2, m, Z, part, H2, J + 2, c.s));
+                ST_TRY(st_gm_update(n, j + 1, m, Z, H2, J + 2, H1, J + 2, Hd, ldhd, j, J, c.s));
+                if ((j + 1) % CHK != 0 && j + 1 < J) continue;
+                // Hessenberg columns checked..j of every column of the block
+                const int nc = j + 1 - checked;
+                double* dh = sg.out((size_t)m * ldhd);
+                for (int k = 0; k < m; ++k)
+                    ST_CUDA_TRY(cudaMemcpyAsync(dh + (size_t)k * ldhd + (size_t)checked * (J + 1),
+                                                Hd + (size_t)k * ldhd + (size_t)checked * (J + 1),
+                                                sizeof(double) * (size_t)nc * (J + 1), cudaMemcpyDeviceToDevice, c.s));
                 ST_TRY(sg.fetch());
-                ++total;
-                double* hc = &H[(size_t)j * (J + 1)];
-                const double* h0 = sg.host_of(dh[0]);
-                const double* h1 = sg.host_of(dh[1]);
-                double hh = 0.0;
-                for (int i = 0; i <= j; ++i) {
-                    hc[i] = h0[i] + h1[i];
-                    hh += h1[i] * h1[i];
+                all_conv = true;
+                for (int k = 0; k < m; ++k) {
+                    ColState& cl = cols[k];
+                    if (!cl.active || cl.conv) continue;
+                    const double* hk = sg.host_of(dh) + (size_t)k * ldhd;
+                    for (int jj = checked; jj <= j && !cl.conv; ++jj) {
+                        double* hc = &cl.H[(size_t)jj * (J + 1)];
+                        for (int i = 0; i <= jj + 1; ++i) hc[i] = hk[(size_t)jj * (J + 1) + i];
+                        const double hn = hc[jj + 1];
+                        for (int i = 0; i < jj; ++i) {
+                            double t0 = cl.cs[i] * hc[i] + cl.sn[i] * hc[i + 1];
+                            hc[i + 1] = -cl.sn[i] * hc[i] + cl.cs[i] * hc[i + 1];
+                            hc[i] = t0;
+                        }
+                        double rr = std::hypot(hc[jj], hc[jj + 1]);
+                        cl.cs[jj] = rr > 0 ? hc[jj] / rr : 1.0;
+                        cl.sn[jj] = rr > 0 ? hc[jj + 1] / rr : 0.0;
+                        hc[jj] = rr;
+                        hc[jj + 1] = 0.0;
+                        cl.g[jj + 1] = -cl.sn[jj] * cl.g[jj];
+                        cl.g[jj] = cl.cs[jj] * cl.g[jj];
+                        cl.used = jj + 1;
+                        total++;
+                        cl.conv = std::fabs(cl.g[jj + 1]) <= rtol * cl.bnorm || hn == 0.0;
+                    }
+                    all_conv = all_conv && cl.conv;
                 }
-                // ||u||^2 after the second pass: before it, minus what it removed
-                double nu2 = h1[j + 1] - hh;
-                if (!(nu2 > 1e-6 * h1[j + 1])) {
-                    double* du = sg.out(1);
-                    ST_TRY(ts_tn_dev(c, 1, 1, u, n, u, n, du, 1));
-                    ST_TRY(sg.fetch());
-                    nu2 = sg.host_of(du)[0];
+                checked = j + 1;
+            }
+            // y = R^{-1} g per column, w += T y over that column's own steps
+            bool done = true;
+            for (int k = 0; k < m; ++k) {
+                ColState& cl = cols[k];
+                if (!cl.active || cl.used == 0) continue;
+                const int ju = cl.used;
+                for (int i = ju - 1; i >= 0; --i) {
+                    double t0 = cl.g[i];
+                    for (int q = i + 1; q < ju; ++q) t0 -= cl.H[(size_t)q * (J + 1) + i] * y[q];
+                    y[i] = t0 / cl.H[(size_t)i * (J + 1) + i];
                 }
-                double hn = std::sqrt(std::max(nu2, 0.0));
-                hc[j + 1] = hn;
-                for (int i = 0; i < j; ++i) {
-                    double t0 = cs[i] * hc[i] + sn[i] * hc[i + 1];
-                    hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-                    hc[i] = t0;
-                }
-                double rr = std::hypot(hc[j], hc[j + 1]);
-                cs[j] = rr > 0 ? hc[j] / rr : 1.0;
-                sn[j] = rr > 0 ? hc[j + 1] / rr : 0.0;
-                hc[j] = rr;
-                hc[j + 1] = 0.0;
-                g[j + 1] = -sn[j] * g[j];
-                g[j] = cs[j] * g[j];
-                done = std::fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0;
-                if (!done && hn > 0) ST_TRY(st_axpby64(n, 1, 1.0 / hn, u, n, 0.0, u, n, c.s));
+                double* dy;
+                ST_TRY(sg.in(y.data(), ju, &dy));
+                ST_TRY(st_tsgemm_nn(n, ju, 1, 1.0, T + (size_t)k * n, m * n, dy, ju, 1.0, Wg + (size_t)k * ldw, ldw,
+                                    c.s));
+                done = done && cl.conv;
             }
-            // y = R^{-1} g, w += T y
-            for (int i = j - 1; i >= 0; --i) {
-                double t0 = g[i];
-                for (int q = i + 1; q < j; ++q) t0 -= H[(size_t)q * (J + 1) + i] * y[q];
-                y[i] = t0 / H[(size_t)i * (J + 1) + i];
-            }
-            double* dy;
-            ST_TRY(sg.in(y.data(), j, &dy));
-            ST_TRY(st_tsgemm_nn(n, j, 1, 1.0, T, n, dy, j, 1.0, w, n, c.s));
-            if (done) {
-                ST_TRY(sg.fetch());   // the upload region is reused by the next column
-                break;
-            }
-            // restart from the true residual r = b - (A + s M) w
-            ST_TRY(st_spmm_comb64(p, -shift, -1.0, w, n, 1, 0.0, Z, n, c.s));
-            ST_TRY(st_axpby64(n, 1, 1.0, bb, n, 1.0, Z, n, c.s));
+            ST_TRY(sg.fetch());   // the upload region is reused by the next cycle
+            if (done) break;
+            // restart from the true residual R = B - (A + s M) W
+            ST_TRY(st_spmm_comb64(p, -shift, -1.0, Wg, ldw, m, 0.0, Z, n, c.s));
+            ST_TRY(st_axpby64(n, m, 1.0, B, n, 1.0, Z, n, c.s));
         }
     }
     if (iters_out) *iters_out += total;
@@ -758,6 +815,7 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
 // runs on the host between the two.
 int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int p0, st_solution* sol,
                st_stats* st) {
+    hostpar::ActiveSolve active;   // solves in flight share the host cores
     auto t_start = Clock::now();
     Ctx c{p, p->stream, p->n_h};
     const int n = p->n_h, nt = p->n_t;
@@ -987,8 +1045,10 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         // ---- shift ----
         tp = Clock::now();
         // Ritz values cost O(k^3) on the host: refresh them while the basis is
-        // small, then whenever it has grown by an eighth since the last refresh
-        if (last_ritz_k < 0 || k <= 16 || k >= last_ritz_k + std::max(2, last_ritz_k / 8)) {
+        // small, then whenever it has grown by an eighth (a quarter beyond 128
+        // columns) since the last refresh
+        if (last_ritz_k < 0 || k <= 16 ||
+            k >= last_ritz_k + std::max(2, last_ritz_k / (last_ritz_k > 128 ? 4 : 8))) {
             if (!ritz_values(k, Am.a.data(), Mm.a.data(), Mm.ld, ritz)) ritz.clear();
             last_ritz_k = k;
         }
@@ -1358,7 +1418,7 @@ extern "C" int st_shift_solve(st_problem* p, double s, const double* X, int ldx,
                               int precision) {
     if (!p || !X || !W || ncols < 1 || ldx < p->n_h || ldw < p->n_h) return ST_EINVAL;
     if (precision != ST_FP64 && precision != ST_MIXED) return ST_EINVAL;
-    if (!p->tensor_heat) return ST_ENOTSUP;
+    if (!p->tensor_heat && !(p->dim >= 1 && p->d.op == ST_CONVDIFF)) return ST_ENOTSUP;
     if (!(s > -p->lam_min)) return ST_EINVAL;
     Ctx c{p, p->stream, p->n_h};
     // process in column groups of at most 16 through a private buffer (X and W may alias)
@@ -1366,7 +1426,11 @@ extern "C" int st_shift_solve(st_problem* p, double s, const double* X, int ldx,
         int m = std::min(16, ncols - j0);
         double* buf;
         ST_TRY(st_slot(p, S_COPY, sizeof(double) * (size_t)p->n_h * m, (void**)&buf));
-        ST_TRY(shifted_solve(c, precision, s, X + (size_t)j0 * ldx, ldx, nullptr, 0, m, buf, p->n_h));
+        if (p->tensor_heat)
+            ST_TRY(shifted_solve(c, precision, s, X + (size_t)j0 * ldx, ldx, nullptr, 0, m, buf, p->n_h));
+        else
+            ST_TRY(shifted_solve_fgmres(c, precision, s, X + (size_t)j0 * ldx, ldx, nullptr, 0, m, buf, p->n_h, 1e-12,
+                                        nullptr));
         ST_TRY(st_copy_cols64(p->n_h, m, buf, p->n_h, W + (size_t)j0 * ldw, ldw, p->stream));
     }
     return ST_OK;

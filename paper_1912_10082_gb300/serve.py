@@ -15,7 +15,8 @@ import time
 
 import numpy as np
 
-from . import (ST_CONVDIFF, ST_FP64, ST_HEAT, ST_METHOD_RKSM, ST_OK, ST_ENOTCONV, Executor, make_desc)
+from . import (ST_CONVDIFF, ST_FP64, ST_HEAT, ST_METHOD_RKSM, ST_OK, ST_ENOTCONV, ST_SCHED_FIFO, Executor,
+               make_desc)
 
 
 def _desc_of(r, precision, tol, maxit):
@@ -53,17 +54,18 @@ def run_batch(instances, *, precision=ST_FP64, tol=1e-8, maxit=400, slots=16, me
 
 
 def run_stream(requests, factors, *, precision=ST_FP64, tol=1e-8, maxit=400, slots=16, hbm_budget_bytes=0.0,
-               warmup=0, outputs=None):
+               warmup=0, outputs=None, policy=ST_SCHED_FIFO):
     """Replay a request stream: request i is submitted at its ``arrival_s``.
 
     ``factors[i]`` = (F1, F2).  The first ``warmup`` requests are run but left
     out of the statistics.  ``outputs`` (optional dict index -> column-major
     n_h x n_t buffer) receives the dense solution of those requests.  Returns
     dict with p50/p99 latency (s), DoF/s over the measured requests' makespan
-    and the per-request records.
+    and the per-request records.  ``policy`` is the executor's admission order
+    (ST_SCHED_FIFO or ST_SCHED_HRRN).
     """
     recs = {}
-    with Executor(slots=slots, hbm_budget_bytes=hbm_budget_bytes) as ex:
+    with Executor(slots=slots, hbm_budget_bytes=hbm_budget_bytes, policy=policy) as ex:
         start = ex.now()
         i = 0
         n = len(requests)

@@ -132,3 +132,40 @@ def test_set_coefficients_matches_fresh_setup():
             Ub2 = b.timestep_cn(F1, F2)
             torch.cuda.synchronize()
             assert torch.equal(Ua2, Ub2)
+
+
+@pytest.mark.parametrize("policy", [st.ST_SCHED_FIFO, st.ST_SCHED_HRRN])
+def test_admission_policy_orders_waiting_requests(policy):
+    """One slot, busy with a long solve while a large request and three small ones queue up behind it:
+    FIFO admits them in arrival order, HRRN admits the small ones (higher response ratio) first."""
+    def req(n, nt, seed):
+        F1, F2 = workloads.gaussian_factors(n * n, nt, 2, seed=seed)
+        return st.make_desc(2, n, nt, 1.0, 1.0), np.asfortranarray(F1), np.asfortranarray(F2)
+
+    blocker = req(127, 256, 1)
+    big = req(63, 256, 2)
+    small = [req(7, 8, 3 + i) for i in range(3)]
+    with st.Executor(slots=1, policy=policy) as ex:
+        ex.submit(*blocker, tag=0)
+        while ex.pending()[0] > 0:   # the blocker is admitted before the others arrive
+            pass
+        ex.submit(*big, tag=1)
+        for i, s in enumerate(small):
+            ex.submit(*s, tag=2 + i)
+        got = {}
+        while len(got) < 5:
+            for res in ex.wait(8, timeout=1.0):
+                got[res["tag"]] = res
+    assert all(g["status"] == st.ST_OK for g in got.values())
+    starts = {t: g["t_start"] for t, g in got.items()}
+    assert all(starts[0] < starts[t] for t in range(1, 5))
+    if policy == st.ST_SCHED_FIFO:
+        assert all(starts[1] < starts[t] for t in range(2, 5))
+    else:
+        assert all(starts[t] < starts[1] for t in range(2, 5))
+
+
+def test_set_policy_rejects_unknown_policy():
+    with st.Executor(slots=1) as ex:
+        with pytest.raises(st.StError):
+            ex.set_policy(7)

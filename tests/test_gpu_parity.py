@@ -133,6 +133,27 @@ def test_shift_solve_matches_sparse_lu(dim, n, prec, tol):
         assert relerr(out, ref) <= tol, (s, relerr(out, ref))
 
 
+@pytest.mark.parametrize("dim,n,eps", [(1, 31, 0.05), (2, (40, 21), 0.01), (2, 15, 0.5), (3, (33, 9, 5), 0.05)])
+@pytest.mark.parametrize("prec", [st.ST_FP64, st.ST_MIXED])
+def test_shift_solve_convdiff_matches_sparse_lu(dim, n, eps, prec):
+    """Convection-diffusion resolvent: batched flexible GMRES (five columns advanced together)."""
+    beta = (1.0, 0.5, 0.25)[:dim]
+    M, A = fem.tensor_operators(dim, n, op="convdiff", eps=eps, beta=beta)
+    X = np.random.default_rng(6).standard_normal((M.shape[0], 5))
+    X[:, 3] = 0.0   # a zero column converges at once
+    for s in (0.3, 40.0, 1e4):
+        ref = np.linalg.solve((A + s * M).toarray(), M @ X)
+        with st.Problem(dim, n, 4, 1.0, op=st.ST_CONVDIFF, eps=eps, beta=beta) as prob:
+            out = host(prob.shift_solve(s, dev(X), precision=prec))
+        assert np.all(out[:, 3] == 0.0)
+        # each column stops at a relative residual of 1e-12; the error is at most cond(A + sM) times that
+        K, B = (A + s * M).toarray(), M @ X
+        for j in (0, 1, 2, 4):
+            res = np.linalg.norm(B[:, j] - K @ out[:, j]) / np.linalg.norm(B[:, j])
+            assert res <= 5e-12, (s, j, res)
+        assert relerr(out, ref) <= 1e-8, (s, relerr(out, ref))
+
+
 # ---------------------------------------------------------------- A10 Crank-Nicolson (K10)
 
 @pytest.mark.parametrize("dim,n,nt,p", [(1, 63, 64, 2), (2, 15, 40, 3), (3, 7, 12, 1)])
