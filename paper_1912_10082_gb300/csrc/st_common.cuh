@@ -80,6 +80,13 @@ struct st_problem {
     float box_p32[27] = {}, box_q32[27] = {};
     double box_m64[27] = {}, box_a64[27] = {};   // M and A (Aᵀ = A reversed) for the spatial products
     float box_m32[27] = {}, box_a32[27] = {};
+    // x-line preconditioner of convection-diffusion: Thomas factors of
+    // eps Kx + beta_x Gx + mu Mx for every mode of the transformed directions,
+    // for the shift line_shift (n_h entries each)
+    double *line_cp64 = nullptr, *line_ip64 = nullptr;
+    float *line_cp32 = nullptr, *line_ip32 = nullptr;
+    double line_shift = -1.0;
+    bool line_valid = false;
     double lam_min = 0.0, lam_max = 0.0;   // spectrum of the pencil (A, M), or of its diffusion part
     double fd_lam_min = 0.0, fd_lam_max = 0.0;   // the same for unit diffusion (sums of 1D sine-mode eigenvalues)
     double fd_kappa = 1.0;                 // diffusion the fast-diagonalisation transforms use
@@ -141,6 +148,16 @@ int st_cn_rhs_step(st_problem* p, const double* u, const double* F1, int ldf1, c
 enum FdKind { FD_MASS_RESOLVENT = 0, FD_RESOLVENT = 1, FD_MASS_INVERSE = 2 };
 int st_fd_apply64(st_problem* p, FdKind kind, double shift, double coef, const double* X, int ldx,
                   int ncols, double* W, int ldw, double* tmp, cudaStream_t s);
+// x-line preconditioner (convection-diffusion with |beta_x| the largest
+// component): W = coef (eps K + beta_x Gx (x) M_rest + s M)^{-1} X, exact in
+// 1D; y (and z) by sine transforms, x by Thomas sweeps with the factors of
+// st_line_factor (call it for the shift first).
+bool st_line_usable(const st_problem* p);
+int st_line_factor(st_problem* p, double shift, cudaStream_t s);
+int st_line_apply64(st_problem* p, double coef, const double* X, int ldx, int ncols, double* W, int ldw, double* tmp,
+                    cudaStream_t s);
+int st_line_apply32(st_problem* p, double coef, const float* X, int ldx, int ncols, float* W, int ldw, float* tmp,
+                    cudaStream_t s);
 int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const float* X, int ldx,
                   int ncols, float* W, int ldw, float* tmp, cudaStream_t s);
 

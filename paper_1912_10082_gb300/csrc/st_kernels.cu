@@ -949,34 +949,63 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol)
     sh = s;
 }
 
+// Two double-float multiply-adds at once, (SH, SL)[c] += a * b_c for the two
+// columns c of a pair, with the packed FP32 instructions of sm_100+ (each lane
+// of a packed operation rounds exactly as the scalar one, so the results are
+// those of df_madd).  b = (b0.hi, b1.hi, b0.lo, b1.lo).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void df_madd2(float2& SH, float2& SL, float2 a, float4 b) {
+    const float2 Ax = make_float2(a.x, a.x), Ay = make_float2(a.y, a.y);
+    const float2 Bx = make_float2(b.x, b.y), By = make_float2(b.z, b.w);
+    const float2 P = __fmul2_rn(Ax, Bx);
+    float2 E = __ffma2_rn(Ax, Bx, neg2(P));
+    E = __ffma2_rn(Ax, By, E);
+    E = __ffma2_rn(Ay, Bx, E);
+    const float2 S = __fadd2_rn(SH, P);
+    const float2 Z = __fadd2_rn(S, neg2(SH));
+    const float2 T = __fadd2_rn(__fadd2_rn(SH, neg2(__fadd2_rn(S, neg2(Z)))), __fadd2_rn(P, neg2(Z)));
+    SL = __fadd2_rn(SL, __fadd2_rn(T, E));
+    SH = S;
+}
+
 // Partial H = V^T W as k_ts_tn_partial, with V and W both in double-float
-// (W split once by the caller, not once per CTA: the split costs FP64).  The lanes' partial
-// sums are combined by a double-float butterfly, so no FP64 instruction runs
-// before lane 0 folds the pair into the partial.
+// (W split once by the caller, not once per CTA: the split costs FP64).  W's
+// chunk is staged as column pairs (hi, hi, lo, lo) so that one 16-byte shared
+// load feeds a packed df_madd2 for two columns.  The lanes' partial sums are
+// combined by a double-float butterfly and stored as (hi, lo) float pairs: no
+// FP64 instruction runs here (FP64 is 1/64 of FP32); k_ts_reduce_df folds
+// them.
 template <int MAXM>
 __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, int m, int rows,
                                                                  const float2* __restrict__ V, long long ldv,
                                                                  const float2* __restrict__ W, long long ldw,
-                                                                 double* __restrict__ part) {
+                                                                 float2* __restrict__ part) {
+    constexpr int MP = (MAXM + 1) / 2;
     extern __shared__ double sm[];
-    float2* Ws = reinterpret_cast<float2*>(sm);   // [m][rows]
+    float4* Ws = reinterpret_cast<float4*>(sm);   // [pairs][rows]
     const int chunk = blockIdx.x;
     const int r0 = chunk * rows;
     const int nr = min(rows, n - r0);
-    for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
-        int b = idx / rows, rr = idx % rows;
-        Ws[idx] = rr < nr ? W[(size_t)b * ldw + r0 + rr] : make_float2(0.f, 0.f);
+    const int np = (m + 1) / 2;
+    for (int idx = threadIdx.x; idx < np * rows; idx += TS_THREADS) {
+        const int q = idx / rows, rr = idx % rows;
+        float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+        if (rr < nr) {
+            w0 = W[(size_t)(2 * q) * ldw + r0 + rr];
+            if (2 * q + 1 < m) w1 = W[(size_t)(2 * q + 1) * ldw + r0 + rr];
+        }
+        Ws[idx] = make_float4(w0.x, w1.x, w0.y, w1.y);
     }
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    double* out = part + (size_t)chunk * k * m;
+    float2* out = part + (size_t)chunk * k * m;
     for (int cc = warp; cc < TS_CG; cc += TS_THREADS / 32) {
         const int a = blockIdx.y * TS_CG + cc;
         if (a >= k) break;
         const float2* v = V + (size_t)a * ldv + r0;
-        float sh[MAXM], sl[MAXM];
+        float2 SH[MP], SL[MP];
 #pragma unroll
-        for (int b = 0; b < MAXM; ++b) sh[b] = sl[b] = 0.f;
+        for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
         for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
             float2 x[TS_UNROLL];
 #pragma unroll
@@ -988,34 +1017,61 @@ __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, i
             for (int u = 0; u < TS_UNROLL; ++u) {
                 int rr = min(base + 32 * u, rows - 1);
 #pragma unroll
-                for (int b = 0; b < MAXM; ++b)
-                    if (b < m) df_madd(sh[b], sl[b], x[u], Ws[b * rows + rr]);
+                for (int q = 0; q < MP; ++q)
+                    if (q < np) df_madd2(SH[q], SL[q], x[u], Ws[q * rows + rr]);
             }
         }
 #pragma unroll
-        for (int b = 0; b < MAXM; ++b) {
-            if (b >= m) break;
-            float h = sh[b], l = sl[b];
+        for (int q = 0; q < MP; ++q) {
+            if (q >= np) break;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                float oh = __shfl_xor_sync(0xffffffffu, h, off);
-                float ol = __shfl_xor_sync(0xffffffffu, l, off);
-                df_add(h, l, oh, ol);
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int b = 2 * q + h2;
+                if (b >= m) break;
+                float h = h2 ? SH[q].y : SH[q].x, l = h2 ? SL[q].y : SL[q].x;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    float oh = __shfl_xor_sync(0xffffffffu, h, off);
+                    float ol = __shfl_xor_sync(0xffffffffu, l, off);
+                    df_add(h, l, oh, ol);
+                }
+                if (lane == 0) out[(size_t)a * m + b] = make_float2(h, l);
             }
-            if (lane == 0) out[(size_t)a * m + b] = (double)h + (double)l;
         }
     }
 }
 
+// H = sum over chunks of the (hi, lo) partials, each folded to FP64 first:
+// a warp per output, fixed order (as k_ts_reduce).
+__global__ void k_ts_reduce_df(int nchunks, int k, int m, const float2* __restrict__ part, double* __restrict__ H,
+                               long long ldh) {
+    int idx = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x % 32;
+    if (idx >= k * m) return;
+    double s = 0.0;
+    for (int c = lane; c < nchunks; c += 32) {
+        const float2 hl = part[(size_t)c * k * m + idx];
+        s += (double)hl.x + (double)hl.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        int a = idx / m, b = idx % m;
+        H[(size_t)b * ldh + a] = s;
+    }
+}
+
 // W = beta W + alpha V H with V in double-float, one thread per row; H is
-// split once per CTA into shared memory and the double-float sums are folded
-// into FP64 every 32 basis columns.
+// split once per CTA into shared memory as column pairs (hi, hi, lo, lo), the
+// double-float sums run two columns at a time (df_madd2) and are folded into
+// FP64 every 128 basis columns.
 template <int MAXM>
 __global__ void __launch_bounds__(256) k_ts_nn_df(int n, int k, int m, double alpha, const float2* __restrict__ V,
                                                   long long ldv, const double* __restrict__ H, long long ldh,
                                                   double beta, double* __restrict__ W, long long ldw) {
-    constexpr int KT = 32;
-    __shared__ float2 Hs[KT * MAXM];
+    constexpr int KT = 128, MP = (MAXM + 1) / 2;
+    __shared__ float4 Hs[KT * MP];
+    const int np = (m + 1) / 2;
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[MAXM];
 #pragma unroll
@@ -1023,15 +1079,17 @@ __global__ void __launch_bounds__(256) k_ts_nn_df(int n, int k, int m, double al
     for (int a0 = 0; a0 < k; a0 += KT) {
         int kt = min(KT, k - a0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < kt * m; idx += blockDim.x) {
-            int a = idx / m, b = idx % m;
-            Hs[a * MAXM + b] = df_split(H[(size_t)b * ldh + a0 + a]);
+        for (int idx = threadIdx.x; idx < kt * np; idx += blockDim.x) {
+            const int a = idx / np, q = idx % np;
+            const float2 h0 = df_split(H[(size_t)(2 * q) * ldh + a0 + a]);
+            const float2 h1 = 2 * q + 1 < m ? df_split(H[(size_t)(2 * q + 1) * ldh + a0 + a]) : make_float2(0.f, 0.f);
+            Hs[a * MP + q] = make_float4(h0.x, h1.x, h0.y, h1.y);
         }
         __syncthreads();
         if (r < n) {
-            float sh[MAXM], sl[MAXM];
+            float2 SH[MP], SL[MP];
 #pragma unroll
-            for (int b = 0; b < MAXM; ++b) sh[b] = sl[b] = 0.f;
+            for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
             for (int a = 0; a < kt; a += TS_UNROLL) {
                 float2 x[TS_UNROLL];
 #pragma unroll
@@ -1041,13 +1099,15 @@ __global__ void __launch_bounds__(256) k_ts_nn_df(int n, int k, int m, double al
                 for (int u = 0; u < TS_UNROLL; ++u) {
                     if (a + u >= kt) break;
 #pragma unroll
-                    for (int b = 0; b < MAXM; ++b)
-                        if (b < m) df_madd(sh[b], sl[b], x[u], Hs[(a + u) * MAXM + b]);
+                    for (int q = 0; q < MP; ++q)
+                        if (q < np) df_madd2(SH[q], SL[q], x[u], Hs[(a + u) * MP + q]);
                 }
             }
 #pragma unroll
-            for (int b = 0; b < MAXM; ++b)
-                if (b < m) acc[b] += (double)sh[b] + (double)sl[b];
+            for (int q = 0; q < MP; ++q) {
+                if (2 * q < m) acc[2 * q] += (double)SH[q].x + (double)SL[q].x;
+                if (2 * q + 1 < m && 2 * q + 1 < MAXM) acc[2 * q + 1] += (double)SH[q].y + (double)SL[q].y;
+            }
         }
     }
     if (r >= n) return;
@@ -1248,6 +1308,83 @@ __global__ void k_scale_cols_dev(int n, int m, double* __restrict__ X, long long
     const int c = (int)(idx / n);
     const long long r = idx % n;
     X[(size_t)c * ldx + r] *= f[c];
+}
+
+// ---------------------------------------------------------------------------
+// x-line preconditioner of convection-diffusion.  With the y (and z)
+// directions in sine modes, eps K + beta_x Gx (x) M_rest + s M is block
+// diagonal: mode (j, k) of the transformed directions carries the 1D matrix
+// mu_j mu_k T(m), T(m) = eps Kx + beta_x Gx + m Mx, m = s + eps (lam_j + lam_k)
+// (the y, z convection is left out).  T(m) is tridiagonal Toeplitz with
+// sub-diagonal a = -eps/h - beta/2 + m h/6, diagonal d = 2 eps/h + 4 m h/6 and
+// super-diagonal c = -eps/h + beta/2 + m h/6.  Its symmetric part is positive
+// definite, so the pivots of elimination without pivoting stay positive.
+// ---------------------------------------------------------------------------
+
+// Thomas factors per mode: IP[i] = 1 / (d - a CP[i-1]), CP[i] = c IP[i].
+__global__ void k_line_factor(int nx, int nmodes, int ny, int dim, double hx, double eps, double bx, double shift,
+                              const double* __restrict__ lam1, const double* __restrict__ lam2,
+                              double* __restrict__ CP64, double* __restrict__ IP64, float* __restrict__ CP32,
+                              float* __restrict__ IP32) {
+    const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode >= nmodes) return;
+    double mu = shift;
+    if (dim > 1) mu += eps * lam1[mode % ny];
+    if (dim > 2) mu += eps * lam2[mode / ny];
+    const double a = -eps / hx - 0.5 * bx + mu * hx / 6.0;
+    const double d = 2.0 * eps / hx + 4.0 * mu * hx / 6.0;
+    const double c = -eps / hx + 0.5 * bx + mu * hx / 6.0;
+    double cp = 0.0;
+    const size_t o = (size_t)mode * nx;
+    for (int i = 0; i < nx; ++i) {
+        const double ip = 1.0 / (d - a * cp);
+        cp = c * ip;
+        CP64[o + i] = cp;
+        IP64[o + i] = ip;
+        CP32[o + i] = (float)cp;
+        IP32[o + i] = (float)ip;
+    }
+}
+
+// One thread per (mode, column) row of nx entries: the right-hand side scaled
+// by coef c2_j c2_k (the normalisation of the transformed directions), then
+// the forward and backward Thomas sweeps.  dst may equal src.  Consecutive
+// threads walk consecutive rows, so each 32-byte sector serves several steps
+// from L1.
+template <typename T>
+__global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, const T* __restrict__ src,
+                             long long lds, T* dst, long long ldd, const T* __restrict__ CP,
+                             const T* __restrict__ IP, double hx, double eps, double bx, double shift,
+                             const double* __restrict__ lam1, const double* __restrict__ lam2,
+                             const double* __restrict__ c2y, const double* __restrict__ c2z, double coef) {
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (long long)nmodes * ncols) return;
+    const int col = (int)(row / nmodes), mode = (int)(row % nmodes);
+    double w = coef, mu = shift;
+    if (dim > 1) {
+        w *= c2y[mode % ny];
+        mu += eps * lam1[mode % ny];
+    }
+    if (dim > 2) {
+        w *= c2z[mode / ny];
+        mu += eps * lam2[mode / ny];
+    }
+    const T wt = (T)w;
+    const T a = (T)(-eps / hx - 0.5 * bx + mu * hx / 6.0);   // sub-diagonal of T(mu)
+    const T* x = src + (size_t)col * lds + (size_t)mode * nx;
+    T* y = dst + (size_t)col * ldd + (size_t)mode * nx;
+    const T* cp = CP + (size_t)mode * nx;
+    const T* ip = IP + (size_t)mode * nx;
+    T dprev = T(0);
+    for (int i = 0; i < nx; ++i) {
+        dprev = (wt * x[i] - a * dprev) * ip[i];
+        y[i] = dprev;
+    }
+    T xn = dprev;
+    for (int i = nx - 2; i >= 0; --i) {
+        xn = y[i] - cp[i] * xn;
+        y[i] = xn;
+    }
 }
 
 }  // namespace
@@ -1554,6 +1691,104 @@ int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const f
     return fd_apply_impl<float>(p, kind, shift, coef, X, ldx, ncols, W, ldw, tmp, s, Q, HG, "fd_gemm32");
 }
 
+bool st_line_usable(const st_problem* p) {
+    if (p->d.op != ST_CONVDIFF || p->dim < 1 || p->dim > 3 || !(p->d.eps > 0)) return false;
+    const double bx = std::fabs(p->d.beta[0]);
+    for (int d = 1; d < p->dim; ++d)
+        if (std::fabs(p->d.beta[d]) > bx) return false;
+    return true;
+}
+
+int st_line_factor(st_problem* p, double shift, cudaStream_t s) {
+    if (!st_line_usable(p)) return ST_ENOTSUP;
+    if (p->line_valid && p->line_shift == shift) return ST_OK;
+    const size_t nh = (size_t)p->n_h;
+    if (!p->line_cp64) {
+        ST_TRY(st_alloc(p, (void**)&p->line_cp64, sizeof(double) * nh));
+        ST_TRY(st_alloc(p, (void**)&p->line_ip64, sizeof(double) * nh));
+        ST_TRY(st_alloc(p, (void**)&p->line_cp32, sizeof(float) * nh));
+        ST_TRY(st_alloc(p, (void**)&p->line_ip32, sizeof(float) * nh));
+    }
+    const int nx = p->n[0];
+    const int ny = p->dim > 1 ? p->n[1] : 1;
+    const int nmodes = (int)(nh / nx);
+    k_line_factor<<<(nmodes + 127) / 128, 128, 0, s>>>(nx, nmodes, ny, p->dim, p->ax[0].h, p->d.eps, p->d.beta[0],
+                                                      shift, p->dim > 1 ? p->ax[1].lam : nullptr,
+                                                      p->dim > 2 ? p->ax[2].lam : nullptr, p->line_cp64,
+                                                      p->line_ip64, p->line_cp32, p->line_ip32);
+    ST_LAUNCH_CHECK();
+    p->line_shift = shift;
+    p->line_valid = true;
+    return ST_OK;
+}
+
+// y (and z) forward transforms, the x line solves, the backward transforms:
+// 2D X -> tmp -> (solve in place) -> W; 3D X -> tmp -> W -> (solve) -> tmp -> W;
+// 1D the solve alone, X -> W.
+template <typename T>
+static int line_apply_impl(st_problem* p, double coef, const T* X, int ldx, int ncols, T* W, int ldw, T* tmp,
+                           cudaStream_t s, const T* const (*HG)[4], const T* CP, const T* IP, const char* tag) {
+    if (!p->line_valid) return ST_EINVAL;
+    const int dim = p->dim, nx = p->n[0], ny = dim > 1 ? p->n[1] : 1;
+    const long long nh = p->n_h;
+    const int nmodes = (int)(nh / nx);
+    const double hx = p->ax[0].h, eps = p->d.eps, bx = p->d.beta[0];
+    FdEpi plain{};
+    plain.scale = 0;
+    plain.coef = 1.0;
+    auto transform = [&](int d, const T* src, long long lds, T* dst, long long ldd) -> int {
+        const long long J = (d == 1) ? nx : (long long)nx * ny;
+        const int nd = p->n[d];
+        const int outer = (int)(nh / (J * nd));
+        FdEpi ep = plain;
+        ep.left = 1;
+        ep.J = J;
+        Batch2 bt{outer, 0, 0, (long long)nd * J, lds, (long long)nd * J, ldd};
+        return launch_gemm_fold<T, 1>(nd, (int)J, src, J, HG[d], dst, J, outer * ncols, bt, ep, s, tag);
+    };
+    auto solve = [&](const T* src, long long lds, T* dst, long long ldd) -> int {
+        const long long rows = (long long)nmodes * ncols;
+        st_prof_begin(s, sizeof(T) == 8 ? "line64" : "line32", 4.0 * sizeof(T) * (double)nh * ncols,
+                      5.0 * (double)nh * ncols);
+        k_line_solve<T><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(
+            nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
+            dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
+            dim > 2 ? p->ax[2].c2 : nullptr, coef);
+        st_prof_end(s);
+        ST_LAUNCH_CHECK();
+        return ST_OK;
+    };
+    if (dim == 1) return solve(X, ldx, W, ldw);
+    if (dim == 2) {
+        ST_TRY(transform(1, X, ldx, tmp, nh));
+        ST_TRY(solve(tmp, nh, tmp, nh));
+        return transform(1, tmp, nh, W, ldw);
+    }
+    ST_TRY(transform(1, X, ldx, tmp, nh));
+    ST_TRY(transform(2, tmp, nh, W, ldw));
+    ST_TRY(solve(W, ldw, W, ldw));
+    ST_TRY(transform(1, W, ldw, tmp, nh));
+    return transform(2, tmp, nh, W, ldw);
+}
+
+int st_line_apply64(st_problem* p, double coef, const double* X, int ldx, int ncols, double* W, int ldw, double* tmp,
+                    cudaStream_t s) {
+    const double* HG[3][4];
+    for (int d = 0; d < 3; ++d)
+        for (int t = 0; t < 4; ++t) HG[d][t] = p->ax[d].fold64[t];
+    return line_apply_impl<double>(p, coef, X, ldx, ncols, W, ldw, tmp, s, HG, p->line_cp64, p->line_ip64,
+                                   "fd_gemm64");
+}
+
+int st_line_apply32(st_problem* p, double coef, const float* X, int ldx, int ncols, float* W, int ldw, float* tmp,
+                    cudaStream_t s) {
+    const float* HG[3][4];
+    for (int d = 0; d < 3; ++d)
+        for (int t = 0; t < 4; ++t) HG[d][t] = p->ax[d].fold32[t];
+    return line_apply_impl<float>(p, coef, X, ldx, ncols, W, ldw, tmp, s, HG, p->line_cp32, p->line_ip32,
+                                  "fd_gemm32");
+}
+
 size_t st_tsgemm_partial_elems(int n, int k, int m) {
     // the largest partial buffer any column chunk of at most kMaxCols needs
     int mm = m < kMaxCols ? m : kMaxCols;
@@ -1585,7 +1820,7 @@ template <int MAXM> struct LaunchTn {
 };
 template <int MAXM> struct LaunchTnDf {
     static void go(dim3 grid, size_t smem, cudaStream_t s, int n, int k, int m, int rows, const float2* V, int ldv,
-                   const float2* W, int ldw, double* part) {
+                   const float2* W, int ldw, float2* part) {
         static const bool set = [] {
             cudaFuncSetAttribute(k_ts_tn_df_partial<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
             return true;
@@ -1682,13 +1917,14 @@ int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2*
     }
     const int rows = ts_rows(n, k, m);
     const int nch = (n + rows - 1) / rows;
-    const size_t smem = sizeof(double) * (size_t)m * rows;
+    const size_t smem = sizeof(float4) * (size_t)((m + 1) / 2) * rows;   // column pairs, at most 64 KB
     dim3 grid(nch, (k + TS_CG - 1) / TS_CG);
     if (grid.y > 65535) return ST_EINVAL;
+    float2* part2 = reinterpret_cast<float2*>(partial);   // (hi, lo) pairs in the doubles' room
     st_prof_begin(s, "ts_tn_df", 8.0 * (double)n * (k + m) + 16.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
-    dispatch_m<LaunchTnDf>(m, grid, smem, s, n, k, m, rows, V, ldv, W, ldw, partial);
+    dispatch_m<LaunchTnDf>(m, grid, smem, s, n, k, m, rows, V, ldv, W, ldw, part2);
     ST_LAUNCH_CHECK();
-    k_ts_reduce<<<(k * m + 7) / 8, 256, 0, s>>>(nch, k, m, partial, H, ldh);
+    k_ts_reduce_df<<<(k * m + 7) / 8, 256, 0, s>>>(nch, k, m, part2, H, ldh);
     st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;

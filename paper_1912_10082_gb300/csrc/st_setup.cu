@@ -457,8 +457,9 @@ extern "C" int st_set_coefficients(st_problem* p, int op, double kappa, double e
     p->d.kappa = kap;
     p->d.eps = eps;
     for (int i = 0; i < 3; ++i) p->d.beta[i] = beta ? beta[i] : 0.0;
-    // the captured Crank-Nicolson graph holds the old coefficients
+    // the captured Crank-Nicolson graph and the line factors hold the old coefficients
     p->cn_stale = true;
+    p->line_valid = false;
     ST_TRY(assemble_tensor(p));
     set_spectrum(p);
     return read_box_stencil(p);

@@ -227,29 +227,29 @@ int mass_inverse(Ctx& c, int prec, const double* X, int ldx, int ncols, double* 
 
 // log of prod_j |s - s_j| / prod_i |s + theta_i| (products renormalised to avoid overflow).
 double shift_objective(double s, double b, const std::vector<double>& used, const std::vector<double>& ritz) {
-    double prod = 1.0;
-    long long ex = 0;
-    int cnt = 0;
-    for (double sj : used) {
-        prod *= std::fabs(s - sj) / b;
-        if (++cnt == 16) {
-            int e;
-            prod = std::frexp(prod, &e);
-            ex += e;
-            cnt = 0;
+    // numerator and denominator as separate products (multiplications only),
+    // renormalised every 16 factors to stay in range
+    const double ib = 1.0 / b;
+    auto logprod = [&](const std::vector<double>& v, double sign) {
+        double prod = 1.0;
+        long long ex = 0;
+        int cnt = 0;
+        for (double t : v) {
+            prod *= std::fabs(s + sign * t) * ib;
+            if (++cnt == 16) {
+                int e;
+                prod = std::frexp(prod, &e);
+                ex += e;
+                cnt = 0;
+            }
         }
-    }
-    for (double th : ritz) {
-        prod /= std::fabs(s + th) / b;
-        if (++cnt == 16) {
-            int e;
-            prod = std::frexp(prod, &e);
-            ex += e;
-            cnt = 0;
-        }
-    }
-    if (!(prod > 0.0)) return -1e300;
-    return std::log(prod) + (double)ex * std::log(2.0);
+        return prod > 0.0 ? std::log(prod) + (double)ex * std::log(2.0) : -1e300;
+    };
+    const double num = logprod(used, -1.0);
+    if (num <= -1e299) return -1e300;
+    const double den = logprod(ritz, 1.0);
+    if (den <= -1e299) return -1e300;
+    return num - den;
 }
 
 // Next shift by the adaptive rule: maximise prod_j |s - s_j| / prod_i |s + theta_i|
@@ -635,8 +635,10 @@ int check_gap(const std::vector<int>& hist_it, const std::vector<double>& hist_r
 }
 
 // Shifted solve (A + s M) W = M X for a nonsymmetric A (convection-diffusion):
-// flexible GMRES, right-preconditioned by the fast-diagonalisation solve of
-// the symmetric part eps K + s M.  The preconditioned directions T_j are kept,
+// flexible GMRES, right-preconditioned by the x-line solve of
+// eps K + beta_x Gx (x) M_rest + s M (y, z in sine modes, Thomas sweeps along x;
+// exact in 1D) when beta_x is the largest convection component, else by the
+// fast-diagonalisation solve of eps K + s M.  The preconditioned directions T_j are kept,
 // so W = T y has exactly the GMRES residual whatever the preconditioner's
 // precision: FP64 transforms, or FP32 ones in mixed precision.  The columns
 // run as independent GMRES processes advanced together (each kernel covers
@@ -672,10 +674,20 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
         ST_TRY(st_slot(p, S_W32, sizeof(float) * (size_t)n * mg, (void**)&w32));
         ST_TRY(st_slot(p, S_T32, sizeof(float) * (size_t)n * mg, (void**)&t32));
     }
+    // preconditioner: the x-line solve (x convection kept) when beta_x is the largest
+    // component, else the fast-diagonalisation solve of eps K + s M
+    const bool line = st_line_usable(p);
+    if (line) ST_TRY(st_line_factor(p, shift, c.s));
     auto precond = [&](const double* z, double* t, int m) -> int {
-        if (prec != ST_MIXED) return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, m, t, n, tmp, c.s);
+        if (prec != ST_MIXED) {
+            if (line) return st_line_apply64(p, 1.0, z, n, m, t, n, tmp, c.s);
+            return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, m, t, n, tmp, c.s);
+        }
         ST_TRY(st_convert_64_32(n, m, z, n, x32, n, c.s));
-        ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, m, w32, n, t32, c.s));
+        if (line)
+            ST_TRY(st_line_apply32(p, 1.0, x32, n, m, w32, n, t32, c.s));
+        else
+            ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, m, w32, n, t32, c.s));
         return st_convert_32_64_add(n, m, w32, n, t, n, 0.0, c.s);
     };
     ST_TRY(stage_reserve(p, pad32((size_t)mg * ldhd) + pad32((size_t)(J + 2) * mg) + 2 * pad32(mg)));
