@@ -1590,6 +1590,19 @@ int st_spmm_comb64(st_problem* p, double cm, double ca, const double* X, int ldx
 int st_cn_rhs_step(st_problem* p, const double* u, const double* F1, int ldf1, const double* F2, int ldf2, int l,
                    int ncols, double* out, cudaStream_t s) {
     int blocks = (p->n_h + 127) / 128;
+    if (u && use_box(p, 1)) {
+        // box grid: the load term first, then N u from the constant stencil added onto it
+        st_prof_begin(s, "cn_rhs_box", 8.0 * p->n_h * (3 + ncols), 2.0 * (p->dim == 2 ? 9 : 27) * p->n_h);
+        k_cn_rhs<<<blocks, 128, 0, s>>>(p->n_h, p->row_ptr, p->col, p->q64, nullptr, F1, ldf1, F2, ldf2, l, ncols,
+                                        out);
+        ST_LAUNCH_CHECK();
+        BoxPair<double> S;
+        for (int e = 0; e < 27; ++e) S.s[0][e] = S.s[1][e] = p->box_q64[e];
+        launch_stencil_box<double>(p, S, u, p->n_h, 1, 1.0, out, p->n_h, nullptr, 0, s);
+        st_prof_end(s);
+        ST_LAUNCH_CHECK();
+        return ST_OK;
+    }
     st_prof_begin(s, "cn_rhs", (double)p->nnz * 12.0 + 4.0 * (p->n_h + 1) + 8.0 * p->n_h * (2 + ncols),
                   2.0 * (double)p->nnz + 2.0 * p->n_h * ncols);
     k_cn_rhs<<<blocks, 128, 0, s>>>(p->n_h, p->row_ptr, p->col, p->q64, u, F1, ldf1, F2, ldf2, l, ncols, out);

@@ -105,7 +105,8 @@ int block_qr(Ctx& c, double* W, int ldw, int m, double ref2, double drop, std::v
     if (r == 0) return ST_OK;
     double* dR;
     std::vector<double> L = G;
-    bool full = (r == m) && dense::cholesky(m, L.data(), m) && w[0] > 1e-24 * lmax;
+    // CholQR2 only for well-conditioned blocks (its first step loses cond(W)^2 u)
+    bool full = (r == m) && w[0] > 1e-10 * lmax && dense::cholesky(m, L.data(), m);
     if (full) {
         // R1 = L^T; W <- W R1^{-1}; second pass
         std::vector<double> R1((size_t)m * m, 0.0);
@@ -133,33 +134,37 @@ int block_qr(Ctx& c, double* W, int ldw, int m, double ref2, double drop, std::v
         *r_out = m;
         return ST_OK;
     }
-    // rank-deficient: Q0 = W U_r diag(1/sqrt(w_r)), re-orthonormalise, R = Q^T W_in
+    // ill-conditioned or rank-deficient: classical Gram-Schmidt twice, one column at a
+    // time, each remainder's norm taken explicitly (not from a Gram matrix, whose small
+    // eigenvalues carry only the absolute rounding of the large ones).  Kept directions
+    // are packed into the first columns of W; R[:, j] holds column j's coordinates.
     double* copy;
     ST_TRY(st_slot(c.p, S_COPY, sizeof(double) * (size_t)c.n * m, (void**)&copy));
     ST_TRY(st_copy_cols64(c.n, m, W, ldw, copy, c.n, c.s));
-    std::vector<double> T((size_t)m * r);
-    for (int j = 0; j < r; ++j) {
-        int src = m - r + j;   // largest eigenvalues are last
-        double sc = 1.0 / std::sqrt(w[src]);
-        for (int i = 0; i < m; ++i) T[(size_t)j * m + i] = E[(size_t)src * m + i] * sc;
+    const double keep2 = drop * drop * std::max(lmax, ref2);
+    int kept = 0;
+    std::vector<double> h, h2;
+    for (int j = 0; j < m; ++j) {
+        double* wj = W + (size_t)kept * ldw;   // work column: the next free slot of W
+        ST_TRY(st_copy_cols64(c.n, 1, copy + (size_t)j * c.n, c.n, wj, ldw, c.s));
+        std::vector<double> coef(kept, 0.0);
+        for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+            h.assign(kept, 0.0);
+            ST_TRY(ts_tn_host(c, kept, 1, W, ldw, wj, ldw, h.data()));
+            ST_TRY(ts_nn_host(c, kept, 1, -1.0, W, ldw, h.data(), 1.0, wj, ldw));
+            for (int i = 0; i < kept; ++i) coef[i] += h[i];
+        }
+        h2.assign(1, 0.0);
+        ST_TRY(ts_tn_host(c, 1, 1, wj, ldw, wj, ldw, h2.data()));
+        for (int i = 0; i < kept; ++i) R[(size_t)j * m + i] = coef[i];
+        if (h2[0] > keep2) {
+            const double nrm = std::sqrt(h2[0]);
+            ST_TRY(st_axpby64(c.n, 1, 1.0 / nrm, wj, ldw, 0.0, wj, ldw, c.s));
+            R[(size_t)j * m + kept] = nrm;
+            ++kept;
+        }
     }
-    ST_TRY(ts_nn_host(c, m, r, 1.0, copy, c.n, T.data(), 0.0, W, ldw));
-    for (int pass = 0; pass < 2; ++pass) {
-        std::vector<double> G2((size_t)r * r);
-        ST_TRY(ts_tn_host(c, r, r, W, ldw, W, ldw, G2.data()));
-        if (!dense::cholesky(r, G2.data(), r)) return breakdown("block QR: Gram matrix of the kept directions not positive definite");
-        std::vector<double> R2((size_t)r * r, 0.0);
-        for (int j = 0; j < r; ++j)
-            for (int i = 0; i <= j; ++i) R2[(size_t)j * r + i] = G2[(size_t)i * r + j];
-        ST_TRY(st_slot(c.p, S_SMALL, sizeof(double) * r * r, (void**)&dR));
-        ST_TRY(write_dev(c, R2.data(), r, r, r, dR, r));
-        ST_TRY(st_trsm_right_upper(c.n, r, dR, r, W, ldw, c.s));
-    }
-    std::vector<double> Rq((size_t)r * m);
-    ST_TRY(ts_tn_host(c, r, m, W, ldw, copy, c.n, Rq.data()));
-    for (int j = 0; j < m; ++j)
-        for (int i = 0; i < r; ++i) R[(size_t)j * m + i] = Rq[(size_t)j * r + i];
-    *r_out = r;
+    *r_out = kept;
     return ST_OK;
 }
 
@@ -539,8 +544,11 @@ void qr_plan(const double* G, int m, double ref2, double drop, QrPlan& q) {
             ++q.rank;
         }
     q.severe = q.rank > 0 && wkept < 1e-12 * std::max(lmax, ref2);
+    // CholQR2 loses orthogonality like cond(W)^2 u in its first step: keep it to
+    // blocks with cond(W) < ~1e5 (Gram eigenvalue ratio 1e-10, also the accuracy of
+    // a double-float Gram matrix); the rest go to block_qr
     q.fast = false;
-    if (q.rank == m && w[0] > 1e-24 * lmax) {
+    if (q.rank == m && w[0] > 1e-10 * lmax) {
         std::vector<double> L(G, G + (size_t)m * m);
         if (dense::cholesky(m, L.data(), m)) {
             q.R1.assign((size_t)m * m, 0.0);
