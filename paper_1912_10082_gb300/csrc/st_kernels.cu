@@ -1352,8 +1352,8 @@ __global__ void k_line_factor(int nx, int nmodes, int ny, int dim, double hx, do
 // threads walk consecutive rows, so each 32-byte sector serves several steps
 // from L1.
 template <typename T>
-__global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, const T* __restrict__ src,
-                             long long lds, T* dst, long long ldd, const T* __restrict__ CP,
+__global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, const T* src, long long lds, T* dst,
+                             long long ldd, const T* __restrict__ CP,
                              const T* __restrict__ IP, double hx, double eps, double bx, double shift,
                              const double* __restrict__ lam1, const double* __restrict__ lam2,
                              const double* __restrict__ c2y, const double* __restrict__ c2z, double coef) {
@@ -1375,15 +1375,44 @@ __global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, con
     T* y = dst + (size_t)col * ldd + (size_t)mode * nx;
     const T* cp = CP + (size_t)mode * nx;
     const T* ip = IP + (size_t)mode * nx;
+    // The sweeps are chains of dependent FMAs; the operands of LB steps are loaded
+    // first so that memory latency is paid once per LB steps, not once per step.
+    constexpr int LB = 16;
     T dprev = T(0);
-    for (int i = 0; i < nx; ++i) {
-        dprev = (wt * x[i] - a * dprev) * ip[i];
-        y[i] = dprev;
+    for (int i0 = 0; i0 < nx; i0 += LB) {
+        T xv[LB], iv[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int i = i0 + u;
+            xv[u] = i < nx ? x[i] : T(0);
+            iv[u] = i < nx ? ip[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int i = i0 + u;
+            if (i < nx) {
+                dprev = (wt * xv[u] - a * dprev) * iv[u];
+                y[i] = dprev;
+            }
+        }
     }
     T xn = dprev;
-    for (int i = nx - 2; i >= 0; --i) {
-        xn = y[i] - cp[i] * xn;
-        y[i] = xn;
+    for (int i1 = nx - 2; i1 >= 0; i1 -= LB) {
+        T yv[LB], cv[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int i = i1 - u;
+            yv[u] = i >= 0 ? y[i] : T(0);
+            cv[u] = i >= 0 ? cp[i] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+            const int i = i1 - u;
+            if (i >= 0) {
+                xn = yv[u] - cv[u] * xn;
+                y[i] = xn;
+            }
+        }
     }
 }
 
