@@ -1351,7 +1351,7 @@ __global__ void k_line_factor(int nx, int nmodes, int ny, int dim, double hx, do
 // the forward and backward Thomas sweeps.  dst may equal src.  Consecutive
 // threads walk consecutive rows, so each 32-byte sector serves several steps
 // from L1.
-template <typename T>
+template <typename T, int LB>
 __global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, const T* src, long long lds, T* dst,
                              long long ldd, const T* __restrict__ CP,
                              const T* __restrict__ IP, double hx, double eps, double bx, double shift,
@@ -1377,7 +1377,6 @@ __global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, con
     const T* ip = IP + (size_t)mode * nx;
     // The sweeps are chains of dependent FMAs; the operands of LB steps are loaded
     // first so that memory latency is paid once per LB steps, not once per step.
-    constexpr int LB = 16;
     T dprev = T(0);
     for (int i0 = 0; i0 < nx; i0 += LB) {
         T xv[LB], iv[LB];
@@ -1792,7 +1791,15 @@ static int line_apply_impl(st_problem* p, double coef, const T* X, int ldx, int 
         const long long rows = (long long)nmodes * ncols;
         st_prof_begin(s, sizeof(T) == 8 ? "line64" : "line32", 4.0 * sizeof(T) * (double)nh * ncols,
                       5.0 * (double)nh * ncols);
-        k_line_solve<T><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(
+        // few rows (a 2D grid): every thread's sweep is latency-bound, so each batch
+        // of loads covers 64 steps; many rows: 16, and more threads per SM
+        if (rows < 8192)
+            k_line_solve<T, 64><<<(unsigned)((rows + 63) / 64), 64, 0, s>>>(
+                nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
+                dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
+                dim > 2 ? p->ax[2].c2 : nullptr, coef);
+        else
+        k_line_solve<T, 16><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(
             nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
             dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
             dim > 2 ? p->ax[2].c2 : nullptr, coef);
