@@ -166,9 +166,19 @@ int st_fd_apply32(st_problem* p, FdKind kind, double shift, double coef, const f
 size_t st_tsgemm_partial_elems(int n, int k, int m);
 // batched flexible GMRES (m independent Arnoldi processes, vectors interleaved)
 size_t st_gm_partial_elems(int n, int kk, int m);
-int st_gm_dots(int n, int kk, int m, const double* Z, double* part, double* H, int ldh, cudaStream_t s);
-int st_gm_update(int n, int nb, int m, double* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
+template <typename T>
+int st_gm_dots(int n, int kk, int m, const T* Z, double* part, double* H, int ldh, cudaStream_t s);
+template <typename T>
+int st_gm_update(int n, int nb, int m, T* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
                  long long ldhd, int jcol, int J, cudaStream_t s);
+int st_scale_cols_to32(int n, int m, const double* X, int ldx, const double* f, float* Y, int ldy, cudaStream_t s);
+struct GmSteps {   // Arnoldi steps that enter each column's solution (at most 16 columns)
+    int v[16];
+};
+int st_gm_accumulate32(int n, int m, const float* T, const double* y, int ldy, const GmSteps& ju, double* W, int ldw,
+                       cudaStream_t s);
+int st_spmm_comb32(st_problem* p, double cm, double ca, const float* X, int ldx, int ncols, float* Out, int ldo,
+                   cudaStream_t s);
 int st_scale_cols_dev(int n, int m, double* X, int ldx, const double* f, cudaStream_t s);
 int st_tsgemm_tn(int n, int k, int m, const double* V, int ldv, const double* W, int ldw,
                  double* H, int ldh, double* partial, cudaStream_t s);

@@ -1212,19 +1212,23 @@ __global__ void k_axpby(int n, int m, double a, const double* __restrict__ X, lo
 // for i < kk: the last vector is the one being orthogonalised, so i = kk - 1
 // is its squared norm.  The chunk of that vector is staged in shared memory;
 // a warp per basis vector, lanes over rows, a fixed butterfly.
-__global__ void __launch_bounds__(256) k_gm_dot_partial(int n, int kk, int m, int rows, const double* __restrict__ Z,
+// T = double, or float for the inner solve of iterative refinement: FP32
+// products summed per lane in FP32 (a few dozen terms), combined in FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gm_dot_partial(int n, int kk, int m, int rows, const T* __restrict__ Z,
                                                         double* __restrict__ part) {
-    extern __shared__ double us[];
+    extern __shared__ double us_raw[];
+    T* us = reinterpret_cast<T*>(us_raw);
     const int c = blockIdx.y;
     const long long r0 = (long long)blockIdx.x * rows;
     const int rn = (int)min((long long)rows, (long long)n - r0);
-    const double* u = Z + ((size_t)(kk - 1) * m + c) * n + r0;
+    const T* u = Z + ((size_t)(kk - 1) * m + c) * n + r0;
     for (int t = threadIdx.x; t < rn; t += blockDim.x) us[t] = u[t];
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int i = warp; i < kk; i += blockDim.x / 32) {
-        const double* z = Z + ((size_t)i * m + c) * n + r0;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const T* z = Z + ((size_t)i * m + c) * n + r0;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
         int t = lane;
         for (; t + 96 < rn; t += 128) {
             s0 += z[t] * us[t];
@@ -1233,7 +1237,7 @@ __global__ void __launch_bounds__(256) k_gm_dot_partial(int n, int kk, int m, in
             s3 += z[t + 96] * us[t + 96];
         }
         for (; t < rn; t += 32) s0 += z[t] * us[t];
-        double sum = (s0 + s1) + (s2 + s3);
+        double sum = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
         if (lane == 0) part[((size_t)blockIdx.x * m + c) * kk + i] = sum;
@@ -1260,8 +1264,8 @@ __global__ void k_gm_reduce(int nch, int kk, int m, const double* __restrict__ p
 // vector is divided by h (set to zero when h = 0) and CTA 0 writes column jcol
 // of each column's Hessenberg matrix, Hd[c ldhd + jcol (J + 1) + i] =
 // H1[i] + H[i] (i < nb) and h (i = nb).
-template <int MAXM>
-__global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, double* __restrict__ Z,
+template <typename T, int MAXM>
+__global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, T* __restrict__ Z,
                                                    const double* __restrict__ H, int ldh,
                                                    const double* __restrict__ H1, int ldh1, double* __restrict__ Hd,
                                                    long long ldhd, int jcol, int J) {
@@ -1285,20 +1289,20 @@ __global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, double*
     __syncthreads();
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    double acc[MAXM];
+    T acc[MAXM];
 #pragma unroll
-    for (int c = 0; c < MAXM; ++c) acc[c] = c < m ? Z[((size_t)nb * m + c) * n + r] : 0.0;
+    for (int c = 0; c < MAXM; ++c) acc[c] = c < m ? Z[((size_t)nb * m + c) * n + r] : T(0);
     for (int i = 0; i < nb; ++i) {
-        double z[MAXM];
+        T z[MAXM];
 #pragma unroll
-        for (int c = 0; c < MAXM; ++c) z[c] = c < m ? Z[((size_t)i * m + c) * n + r] : 0.0;
+        for (int c = 0; c < MAXM; ++c) z[c] = c < m ? Z[((size_t)i * m + c) * n + r] : T(0);
 #pragma unroll
         for (int c = 0; c < MAXM; ++c)
-            if (c < m) acc[c] -= z[c] * hs[c * (nb + 1) + i];   // hs holds m columns only
+            if (c < m) acc[c] -= z[c] * (T)hs[c * (nb + 1) + i];   // hs holds m columns only
     }
 #pragma unroll
     for (int c = 0; c < MAXM; ++c)
-        if (c < m) Z[((size_t)nb * m + c) * n + r] = H1 ? acc[c] * inv[c] : acc[c];
+        if (c < m) Z[((size_t)nb * m + c) * n + r] = H1 ? acc[c] * (T)inv[c] : acc[c];
 }
 
 // X[:,c] *= f[c] (device factors).
@@ -1308,6 +1312,30 @@ __global__ void k_scale_cols_dev(int n, int m, double* __restrict__ X, long long
     const int c = (int)(idx / n);
     const long long r = idx % n;
     X[(size_t)c * ldx + r] *= f[c];
+}
+
+// Y[:,c] (FP32) = f[c] X[:,c] (FP64): the scaled start vectors of an FP32 inner solve.
+__global__ void k_scale_cols_to32(int n, int m, const double* __restrict__ X, long long ldx,
+                                  const double* __restrict__ f, float* __restrict__ Y, long long ldy) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * m) return;
+    const int c = (int)(idx / n);
+    const long long r = idx % n;
+    Y[(size_t)c * ldy + r] = (float)(f[c] * X[(size_t)c * ldx + r]);
+}
+
+// W[:,c] += sum_{j < ju[c]} T_j[:,c] y[c][j] with the FP32 vectors of an inner
+// solve (interleaved, vector j of column c at T + (j m + c) n), FP64 sums.
+__global__ void k_gm_accumulate32(int n, int m, const float* __restrict__ T, const double* __restrict__ y, int ldy,
+                                  GmSteps ju, double* __restrict__ W, long long ldw) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int c = 0; c < m; ++c) {
+        double acc = W[(size_t)c * ldw + r];
+        const int jc = ju.v[c];
+        for (int j = 0; j < jc; ++j) acc += (double)T[((size_t)j * m + c) * n + r] * y[(size_t)c * ldy + j];
+        W[(size_t)c * ldw + r] = acc;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2077,12 +2105,14 @@ size_t st_gm_partial_elems(int n, int kk, int m) {
     return (size_t)((n + rows - 1) / rows) * (size_t)m * (size_t)kk;
 }
 
-int st_gm_dots(int n, int kk, int m, const double* Z, double* part, double* H, int ldh, cudaStream_t s) {
+template <typename T>
+int st_gm_dots(int n, int kk, int m, const T* Z, double* part, double* H, int ldh, cudaStream_t s) {
     if (n <= 0 || kk <= 0 || m <= 0 || m > kMaxCols) return ST_EINVAL;
     const int rows = gm_rows(n, m);
     const int nch = (n + rows - 1) / rows;
-    st_prof_begin(s, "gm_dot", 8.0 * (double)n * kk * m + 16.0 * (double)nch * kk * m, 2.0 * (double)n * kk * m);
-    k_gm_dot_partial<<<dim3(nch, m), 256, sizeof(double) * rows, s>>>(n, kk, m, rows, Z, part);
+    st_prof_begin(s, sizeof(T) == 8 ? "gm_dot" : "gm_dot32",
+                  (double)sizeof(T) * n * kk * m + 16.0 * (double)nch * kk * m, 2.0 * (double)n * kk * m);
+    k_gm_dot_partial<T><<<dim3(nch, m), 256, sizeof(T) * rows, s>>>(n, kk, m, rows, Z, part);
     ST_LAUNCH_CHECK();
     k_gm_reduce<<<(kk * m + 7) / 8, 256, 0, s>>>(nch, kk, m, part, H, ldh);
     st_prof_end(s);
@@ -2090,22 +2120,64 @@ int st_gm_dots(int n, int kk, int m, const double* Z, double* part, double* H, i
     return ST_OK;
 }
 
-int st_gm_update(int n, int nb, int m, double* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
+template int st_gm_dots<double>(int, int, int, const double*, double*, double*, int, cudaStream_t);
+template int st_gm_dots<float>(int, int, int, const float*, double*, double*, int, cudaStream_t);
+
+template <typename T>
+int st_gm_update(int n, int nb, int m, T* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
                  long long ldhd, int jcol, int J, cudaStream_t s) {
     if (n <= 0 || nb < 0 || m <= 0 || m > kMaxCols) return ST_EINVAL;
     const int blocks = (n + 255) / 256;
     const size_t smem = sizeof(double) * ((size_t)m * (nb + 1) + m);
-    st_prof_begin(s, "gm_update", 8.0 * (double)n * m * (nb + 2), 2.0 * (double)n * m * nb);
+    st_prof_begin(s, sizeof(T) == 8 ? "gm_update" : "gm_update32", (double)sizeof(T) * n * m * (nb + 2),
+                  2.0 * (double)n * m * nb);
     if (m <= 1)
-        k_gm_update<1><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+        k_gm_update<T, 1><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
     else if (m <= 2)
-        k_gm_update<2><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+        k_gm_update<T, 2><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
     else if (m <= 4)
-        k_gm_update<4><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+        k_gm_update<T, 4><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
     else if (m <= 8)
-        k_gm_update<8><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+        k_gm_update<T, 8><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
     else
-        k_gm_update<16><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+        k_gm_update<T, 16><<<blocks, 256, smem, s>>>(n, nb, m, Z, H, ldh, H1, ldh1, Hd, ldhd, jcol, J);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+template int st_gm_update<double>(int, int, int, double*, const double*, int, const double*, int, double*, long long,
+                                  int, int, cudaStream_t);
+template int st_gm_update<float>(int, int, int, float*, const double*, int, const double*, int, double*, long long,
+                                 int, int, cudaStream_t);
+
+int st_scale_cols_to32(int n, int m, const double* X, int ldx, const double* f, float* Y, int ldy, cudaStream_t s) {
+    if (n <= 0 || m <= 0) return ST_OK;
+    const long long tot = (long long)n * m;
+    k_scale_cols_to32<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, m, X, ldx, f, Y, ldy);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_gm_accumulate32(int n, int m, const float* T, const double* y, int ldy, const GmSteps& ju, double* W, int ldw,
+                       cudaStream_t s) {
+    if (n <= 0 || m <= 0) return ST_OK;
+    if (m > 16) return ST_EINVAL;
+    st_prof_begin(s, "gm_accumulate32", 4.0 * (double)n * m * 40 + 16.0 * (double)n * m, 2.0 * (double)n * m * 40);
+    k_gm_accumulate32<<<(n + 255) / 256, 256, 0, s>>>(n, m, T, y, ldy, ju, W, ldw);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+
+int st_spmm_comb32(st_problem* p, double cm, double ca, const float* X, int ldx, int ncols, float* Out, int ldo,
+                   cudaStream_t s) {
+    if (ncols <= 0) return ST_OK;
+    if (!use_box(p, ncols)) return ST_ENOTSUP;
+    BoxPair<float> S;
+    for (int e = 0; e < 27; ++e) S.s[0][e] = S.s[1][e] = (float)(cm * p->box_m64[e] + ca * p->box_a64[e]);
+    st_prof_begin(s, "spmm_comb32_box", 8.0 * (double)p->n_h * ncols, 2.0 * (p->dim == 2 ? 9 : 27) * (double)p->n_h * ncols);
+    launch_stencil_box<float>(p, S, X, ldx, ncols, 0.f, Out, ldo, nullptr, 0, s);
     st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "st_common.cuh"
@@ -646,36 +647,48 @@ int check_gap(const std::vector<int>& hist_it, const std::vector<double>& hist_r
 // flexible GMRES, right-preconditioned by the x-line solve of
 // eps K + beta_x Gx (x) M_rest + s M (y, z in sine modes, Thomas sweeps along x;
 // exact in 1D) when beta_x is the largest convection component, else by the
-// fast-diagonalisation solve of eps K + s M.  The preconditioned directions T_j are kept,
-// so W = T y has exactly the GMRES residual whatever the preconditioner's
-// precision: FP64 transforms, or FP32 ones in mixed precision.  The columns
-// run as independent GMRES processes advanced together (each kernel covers
-// the whole block, vectors interleaved): classical Gram-Schmidt twice, the
-// new vector normalised on the device from the second pass's Gram products,
-// so a step needs no synchronisation.  Every CHK steps the host fetches the
-// new Hessenberg columns, applies the Givens rotations of each column and
-// stops the cycle once every column satisfies ||b - (A + sM) w|| <= rtol ||b||
-// (a column that converged inside a CHK window uses only its own steps).
-// Restarts after J steps from the true residual.
-int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx,
-                         int ncols, double* W, int ldw, double rtol, int* iters_out) {
+// fast-diagonalisation solve of eps K + s M.  The preconditioned directions T_j
+// are kept, so W = T y has exactly the GMRES residual whatever the
+// preconditioner's precision.  The columns run as independent GMRES processes
+// advanced together (each kernel covers the whole block, vectors interleaved):
+// classical Gram-Schmidt twice, the new vector normalised on the device from
+// the second pass's Gram products, so a step needs no synchronisation.  Every
+// CHK steps the host fetches the new Hessenberg columns, applies the Givens
+// rotations of each column and stops the cycle once every column has reached
+// its target (a column that converged inside a CHK window uses only its own
+// steps).  Restarts after J steps from the true residual, in FP64.
+//
+// TB = double: the Krylov vectors in FP64, each cycle aims at
+// ||b - (A + sM) w|| <= rtol ||b||.  TB = float (mixed precision on large
+// grids): iterative refinement.  The Arnoldi process, the operator product
+// and the preconditioner run in FP32 on the FP64 true residual of the cycle
+// (half the bytes, and FP32 instead of 1/64-rate FP64 arithmetic); a cycle
+// aims at a 1e-5 reduction, its correction is added to w in FP64 and the next
+// cycle starts from the new FP64 residual, until rtol ||b|| is met.
+template <typename TB>
+int fgmres_impl(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx, int ncols,
+                double* W, int ldw, double rtol, int* iters_out) {
+    constexpr bool IR = std::is_same<TB, float>::value;
     st_problem* p = c.p;
     const int n = c.n;
     constexpr int J = 40, CYCLES = 12, CHK = 4, MAXG = 16;
+    constexpr double TAU = 1e-5;   // per-cycle reduction an FP32 inner solve aims at
     // columns per group: all of them (at most 16) unless the Krylov blocks would exceed 4 GB
-    const double per_col = 8.0 * n * (2.0 * J + 4.0);
+    const double per_col = (double)sizeof(TB) * n * (2.0 * J + 4.0);
     const int mg = std::max(1, std::min({ncols, MAXG, (int)std::max(1.0, 4e9 / per_col)}));
     const long long ldhd = (long long)J * (J + 1);
-    double *Z, *T, *B, *tmp, *Hc, *Hd, *part;
-    ST_TRY(st_slot(p, S_GZ, sizeof(double) * (size_t)n * (J + 1) * mg, (void**)&Z));
-    ST_TRY(st_slot(p, S_GT, sizeof(double) * (size_t)n * J * mg, (void**)&T));
+    TB *Z, *T;
+    double *B, *tmp, *Hc, *Hd, *part;
+    ST_TRY(st_slot(p, S_GZ, sizeof(TB) * (size_t)n * (J + 1) * mg, (void**)&Z));
+    ST_TRY(st_slot(p, S_GT, sizeof(TB) * (size_t)n * J * mg, (void**)&T));
     ST_TRY(st_slot(p, S_WH, sizeof(double) * (size_t)n * mg, (void**)&B));
-    ST_TRY(st_slot(p, S_TMP, sizeof(double) * (size_t)n * mg, (void**)&tmp));
+    ST_TRY(st_slot(p, S_TMP, sizeof(double) * (size_t)n * mg, (void**)&tmp));   // IR: the FP64 residual
     ST_TRY(st_slot(p, S_GH, sizeof(double) * (size_t)2 * (J + 2) * mg, (void**)&Hc));
     ST_TRY(st_slot(p, S_GHD, sizeof(double) * (size_t)ldhd * mg, (void**)&Hd));
     ST_TRY(st_slot(p, S_GPART, sizeof(double) * st_gm_partial_elems(n, J + 2, mg), (void**)&part));
     double* H1 = Hc;                          // first pass coefficients, ld J + 2
     double* H2 = Hc + (size_t)(J + 2) * mg;   // second pass (and the squared norm at i = j + 1)
+    double* R = IR ? tmp : nullptr;           // IR: FP64 residual of the cycle
     float *x32 = nullptr, *w32 = nullptr, *t32 = nullptr;
     if (prec == ST_MIXED) {
         ST_TRY(st_slot(p, S_X32, sizeof(float) * (size_t)n * mg, (void**)&x32));
@@ -686,19 +699,31 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
     // component, else the fast-diagonalisation solve of eps K + s M
     const bool line = st_line_usable(p);
     if (line) ST_TRY(st_line_factor(p, shift, c.s));
-    auto precond = [&](const double* z, double* t, int m) -> int {
-        if (prec != ST_MIXED) {
-            if (line) return st_line_apply64(p, 1.0, z, n, m, t, n, tmp, c.s);
-            return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, m, t, n, tmp, c.s);
+    auto precond = [&](const TB* z, TB* t, int m) -> int {
+        if constexpr (IR) {
+            if (line) return st_line_apply32(p, 1.0, z, n, m, t, n, t32, c.s);
+            return st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, z, n, m, t, n, t32, c.s);
+        } else {
+            if (prec != ST_MIXED) {
+                if (line) return st_line_apply64(p, 1.0, z, n, m, t, n, tmp, c.s);
+                return st_fd_apply64(p, FD_RESOLVENT, shift, 1.0, z, n, m, t, n, tmp, c.s);
+            }
+            ST_TRY(st_convert_64_32(n, m, z, n, x32, n, c.s));
+            if (line)
+                ST_TRY(st_line_apply32(p, 1.0, x32, n, m, w32, n, t32, c.s));
+            else
+                ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, m, w32, n, t32, c.s));
+            return st_convert_32_64_add(n, m, w32, n, t, n, 0.0, c.s);
         }
-        ST_TRY(st_convert_64_32(n, m, z, n, x32, n, c.s));
-        if (line)
-            ST_TRY(st_line_apply32(p, 1.0, x32, n, m, w32, n, t32, c.s));
-        else
-            ST_TRY(st_fd_apply32(p, FD_RESOLVENT, shift, 1.0, x32, n, m, w32, n, t32, c.s));
-        return st_convert_32_64_add(n, m, w32, n, t, n, 0.0, c.s);
     };
-    ST_TRY(stage_reserve(p, pad32((size_t)mg * ldhd) + pad32((size_t)(J + 2) * mg) + 2 * pad32(mg)));
+    auto op = [&](const TB* t, TB* u, int m) -> int {
+        if constexpr (IR)
+            return st_spmm_comb32(p, shift, 1.0, t, n, m, u, n, c.s);
+        else
+            return st_spmm_comb64(p, shift, 1.0, t, n, m, 0.0, u, n, c.s);
+    };
+    ST_TRY(stage_reserve(p, pad32((size_t)mg * ldhd) + pad32((size_t)(J + 2) * mg) + pad32((size_t)J * mg) +
+                                2 * pad32(mg)));
     Stage sg(c);
     int total = 0;
     struct ColState {
@@ -714,7 +739,7 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
         cl.sn.assign(J, 0.0);
         cl.g.assign(J + 1, 0.0);
     }
-    std::vector<double> f(mg), y(J);
+    std::vector<double> f(mg), y(J), ys((size_t)J * mg);
     for (int g0 = 0; g0 < ncols; g0 += mg) {
         const int m = std::min(mg, ncols - g0);
         double* Wg = W + (size_t)g0 * ldw;
@@ -724,11 +749,17 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
             ST_TRY(st_spmm_ma<double>(p, X + (size_t)g0 * ldx, ldx, m, B, n, (double*)nullptr, n, c.s));
         }
         for (int k = 0; k < m; ++k) ST_CUDA_TRY(cudaMemsetAsync(Wg + (size_t)k * ldw, 0, sizeof(double) * n, c.s));
-        ST_TRY(st_copy_cols64(n, m, B, n, Z, n, c.s));   // R = B
+        if constexpr (IR)
+            ST_TRY(st_copy_cols64(n, m, B, n, R, n, c.s));   // R = B
+        else
+            ST_TRY(st_copy_cols64(n, m, B, n, Z, n, c.s));   // R = B in vector 0
         for (int k = 0; k < m; ++k) cols[k].bnorm = -1.0;
         for (int cyc = 0; cyc < CYCLES; ++cyc) {
-            // residual norms of the block: the dots of vector 0 with itself
-            ST_TRY(st_gm_dots(n, 1, m, Z, part, H2, J + 2, c.s));
+            // residual norms of the block (FP64)
+            if constexpr (IR)
+                ST_TRY(st_gm_dots<double>(n, 1, m, R, part, H2, J + 2, c.s));
+            else
+                ST_TRY(st_gm_dots<double>(n, 1, m, Z, part, H2, J + 2, c.s));
             double* dn = sg.out(m);
             ST_CUDA_TRY(cudaMemcpy2DAsync(dn, sizeof(double), H2, sizeof(double) * (J + 2), sizeof(double), m,
                                           cudaMemcpyDeviceToDevice, c.s));
@@ -749,19 +780,22 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
             if (!any) break;
             double* df;
             ST_TRY(sg.in(f.data(), m, &df));
-            ST_TRY(st_scale_cols_dev(n, m, Z, n, df, c.s));
+            if constexpr (IR)
+                ST_TRY(st_scale_cols_to32(n, m, R, n, df, Z, n, c.s));
+            else
+                ST_TRY(st_scale_cols_dev(n, m, Z, n, df, c.s));
             int j = 0, checked = 0;
             bool all_conv = false;
             for (; j < J && !all_conv; ++j) {
-                double* Zj = Z + (size_t)j * m * n;
-                double* Tj = T + (size_t)j * m * n;
-                double* U = Z + (size_t)(j + 1) * m * n;
+                TB* Zj = Z + (size_t)j * m * n;
+                TB* Tj = T + (size_t)j * m * n;
+                TB* U = Z + (size_t)(j + 1) * m * n;
                 ST_TRY(precond(Zj, Tj, m));
-                ST_TRY(st_spmm_comb64(p, shift, 1.0, Tj, n, m, 0.0, U, n, c.s));
-                ST_TRY(st_gm_dots(n, j + 2, m, Z, part, H1, J + 2, c.s));
-                ST_TRY(st_gm_update(n, j + 1, m, Z, H1, J + 2, nullptr, 0, nullptr, 0, j, J, c.s));
-                ST_TRY(st_gm_dots(n, j + 2, m, Z, part, H2, J + 2, c.s));
-                ST_TRY(st_gm_update(n, j + 1, m, Z, H2, J + 2, H1, J + 2, Hd, ldhd, j, J, c.s));
+                ST_TRY(op(Tj, U, m));
+                ST_TRY(st_gm_dots<TB>(n, j + 2, m, Z, part, H1, J + 2, c.s));
+                ST_TRY(st_gm_update<TB>(n, j + 1, m, Z, H1, J + 2, nullptr, 0, nullptr, 0, j, J, c.s));
+                ST_TRY(st_gm_dots<TB>(n, j + 2, m, Z, part, H2, J + 2, c.s));
+                ST_TRY(st_gm_update<TB>(n, j + 1, m, Z, H2, J + 2, H1, J + 2, Hd, ldhd, j, J, c.s));
                 if ((j + 1) % CHK != 0 && j + 1 < J) continue;
                 // Hessenberg columns checked..j of every column of the block
                 const int nc = j + 1 - checked;
@@ -775,6 +809,7 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
                 for (int k = 0; k < m; ++k) {
                     ColState& cl = cols[k];
                     if (!cl.active || cl.conv) continue;
+                    const double target = IR ? std::max(rtol * cl.bnorm, TAU * cl.beta) : rtol * cl.bnorm;
                     const double* hk = sg.host_of(dh) + (size_t)k * ldhd;
                     for (int jj = checked; jj <= j && !cl.conv; ++jj) {
                         double* hc = &cl.H[(size_t)jj * (J + 1)];
@@ -794,7 +829,7 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
                         cl.g[jj] = cl.cs[jj] * cl.g[jj];
                         cl.used = jj + 1;
                         total++;
-                        cl.conv = std::fabs(cl.g[jj + 1]) <= rtol * cl.bnorm || hn == 0.0;
+                        cl.conv = std::fabs(cl.g[jj + 1]) <= target || hn == 0.0;
                     }
                     all_conv = all_conv && cl.conv;
                 }
@@ -802,30 +837,58 @@ int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ld
             }
             // y = R^{-1} g per column, w += T y over that column's own steps
             bool done = true;
+            GmSteps ju{};
+            std::fill(ys.begin(), ys.end(), 0.0);
             for (int k = 0; k < m; ++k) {
                 ColState& cl = cols[k];
                 if (!cl.active || cl.used == 0) continue;
-                const int ju = cl.used;
-                for (int i = ju - 1; i >= 0; --i) {
+                const int jn = cl.used;
+                for (int i = jn - 1; i >= 0; --i) {
                     double t0 = cl.g[i];
-                    for (int q = i + 1; q < ju; ++q) t0 -= cl.H[(size_t)q * (J + 1) + i] * y[q];
+                    for (int q = i + 1; q < jn; ++q) t0 -= cl.H[(size_t)q * (J + 1) + i] * y[q];
                     y[i] = t0 / cl.H[(size_t)i * (J + 1) + i];
                 }
-                double* dy;
-                ST_TRY(sg.in(y.data(), ju, &dy));
-                ST_TRY(st_tsgemm_nn(n, ju, 1, 1.0, T + (size_t)k * n, m * n, dy, ju, 1.0, Wg + (size_t)k * ldw, ldw,
-                                    c.s));
+                if constexpr (IR) {
+                    ju.v[k] = jn;
+                    for (int i = 0; i < jn; ++i) ys[(size_t)k * J + i] = y[i];
+                } else {
+                    double* dy;
+                    ST_TRY(sg.in(y.data(), jn, &dy));
+                    ST_TRY(st_tsgemm_nn(n, jn, 1, 1.0, T + (size_t)k * n, m * n, dy, jn, 1.0, Wg + (size_t)k * ldw,
+                                        ldw, c.s));
+                }
                 done = done && cl.conv;
+            }
+            if constexpr (IR) {
+                double* dys;
+                ST_TRY(sg.in(ys.data(), (size_t)J * m, &dys));
+                ST_TRY(st_gm_accumulate32(n, m, T, dys, J, ju, Wg, ldw, c.s));
+                done = false;   // the FP32 cycle met its own target; the next cycle checks the FP64 residual
             }
             ST_TRY(sg.fetch());   // the upload region is reused by the next cycle
             if (done) break;
-            // restart from the true residual R = B - (A + s M) W
-            ST_TRY(st_spmm_comb64(p, -shift, -1.0, Wg, ldw, m, 0.0, Z, n, c.s));
-            ST_TRY(st_axpby64(n, m, 1.0, B, n, 1.0, Z, n, c.s));
+            // restart from the true residual R = B - (A + s M) W (FP64)
+            double* Rd;
+            if constexpr (IR)
+                Rd = R;
+            else
+                Rd = Z;
+            ST_TRY(st_spmm_comb64(p, -shift, -1.0, Wg, ldw, m, 0.0, Rd, n, c.s));
+            ST_TRY(st_axpby64(n, m, 1.0, B, n, 1.0, Rd, n, c.s));
         }
     }
     if (iters_out) *iters_out += total;
     return ST_OK;
+}
+
+// FP32 iterative refinement for mixed precision where the work is bandwidth-
+// or FP64-bound (at least 2^17 grid points, box stencils for the FP32 product);
+// FP64 Krylov vectors otherwise.
+int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx,
+                         int ncols, double* W, int ldw, double rtol, int* iters_out) {
+    const bool ir = prec == ST_MIXED && c.n >= (1 << 17) && c.p->box_ok && (c.p->dim == 2 || c.p->dim == 3);
+    if (ir) return fgmres_impl<float>(c, prec, shift, X, ldx, MX, ldmx, ncols, W, ldw, rtol, iters_out);
+    return fgmres_impl<double>(c, prec, shift, X, ldx, MX, ldmx, ncols, W, ldw, rtol, iters_out);
 }
 
 // RKSM driver.  Each iteration synchronises twice: after phase A (shifted

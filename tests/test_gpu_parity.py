@@ -154,6 +154,42 @@ def test_shift_solve_convdiff_matches_sparse_lu(dim, n, eps, prec):
         assert relerr(out, ref) <= 1e-8, (s, relerr(out, ref))
 
 
+@pytest.mark.parametrize("dim,n", [(2, (384, 345)), (3, (60, 50, 45))])
+def test_shift_solve_convdiff_iterative_refinement(dim, n):
+    """Mixed precision on a grid of at least 2^17 points: FP32 inner FGMRES cycles refined on the FP64 residual."""
+    beta = (1.0, 0.5, 0.25)[:dim]
+    eps = 0.02
+    M, A = fem.tensor_operators(dim, n, op="convdiff", eps=eps, beta=beta)
+    assert M.shape[0] >= 1 << 17
+    X = np.random.default_rng(8).standard_normal((M.shape[0], 3))
+    for s in (0.5, 200.0):
+        with st.Problem(dim, n, 4, 1.0, op=st.ST_CONVDIFF, eps=eps, beta=beta) as prob:
+            out = host(prob.shift_solve(s, dev(X), precision=st.ST_MIXED))
+        B = M @ X
+        R = B - (A @ out + s * (M @ out))
+        for j in range(3):
+            res = np.linalg.norm(R[:, j]) / np.linalg.norm(B[:, j])
+            assert res <= 5e-12, (s, j, res)
+
+
+def test_solve_convdiff_large_grid_mixed_residual():
+    """RKSM with FP32-refined FGMRES resolvents: the oracle's exact residual of the returned (V, Y)."""
+    dim, n, nt, eps = 2, (384, 345), 16, 0.05
+    beta = (1.0, 0.5)
+    M, A = fem.tensor_operators(dim, n, op="convdiff", eps=eps, beta=beta)
+    D, C = timefe.time_matrices(nt, 1.0)
+    F1, F2 = workloads.gaussian_factors(M.shape[0], nt, 2, seed=19)
+    tol = 1e-9
+    with st.Problem(dim, n, nt, 1.0, op=st.ST_CONVDIFF, eps=eps, beta=beta, precision=st.ST_MIXED, tol=tol,
+                    maxit=300) as prob:
+        V, Y, stats, status = prob.solve(dev(F1), dev(F2))
+        Vh, Yh = host(V), host(Y)
+    assert status == st.ST_OK and stats["converged"] == 1
+    true_res = residual.relres_lowrank(M, A, D, C, Vh, Yh, F1, F2)
+    assert true_res <= 10 * tol
+    assert abs(stats["relres"] - true_res) <= 0.5 * true_res + 1e-11
+
+
 # ---------------------------------------------------------------- A10 Crank-Nicolson (K10)
 
 @pytest.mark.parametrize("dim,n,nt,p", [(1, 63, 64, 2), (2, 15, 40, 3), (3, 7, 12, 1)])
