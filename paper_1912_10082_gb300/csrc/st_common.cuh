@@ -51,6 +51,8 @@ struct FdAxis {
     float* Q32 = nullptr;
     double* lam = nullptr;  // eigenvalues of K phi = lam M phi, j = 1..n
     double* c2 = nullptr;   // 2 / ((n+1) mu_j), mu_j the M eigenvalue of sine mode j
+    float* lam32 = nullptr; // the same in FP32 (FP32 epilogues stay off the FP64 pipe)
+    float* c232 = nullptr;
     // folded half tables {H0, H1, G0, G1}: H_p[k][i'] = Q[k][2i'+p] (k, i' < K_p, K_0 = ceil(n/2),
     // K_1 = floor(n/2)), G_p = H_p^T
     double* fold64[4] = {};

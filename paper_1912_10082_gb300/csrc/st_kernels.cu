@@ -486,6 +486,8 @@ struct FdEpi {
     int dim, nx, ny, nz;
     const double *l0, *l1, *l2;   // eigenvalues per direction
     const double *c0, *c1, *c2;   // c2 factors per direction (resolvent of a general right-hand side)
+    const float *f0, *f1, *f2;    // FP32 copies of l0..l2 and of c0..c2, for FP32 products
+    const float *g0, *g1, *g2;
     int kind;           // FdKind
     double kappa, shift, coef;
 };
@@ -508,6 +510,28 @@ __device__ __forceinline__ double fd_omega(const FdEpi& ep, long long e) {
     if (ep.kind == FD_MASS_INVERSE) return w;
     if (ep.kind == FD_RESOLVENT) return w / (ep.kappa * lam + ep.shift);
     return 1.0 / (ep.kappa * lam + ep.shift);
+}
+
+// The same weight in FP32 from the FP32 tables (no FP64 instruction).
+__device__ __forceinline__ float fd_omega32(const FdEpi& ep, long long e) {
+    int x = (int)(e % ep.nx);
+    long long t = e / ep.nx;
+    int y = (int)(t % ep.ny);
+    int z = (int)(t / ep.ny);
+    float lam = ep.f0[x];
+    float w = ep.g0[x];
+    if (ep.dim > 1) {
+        lam += ep.f1[y];
+        w *= ep.g1[y];
+    }
+    if (ep.dim > 2) {
+        lam += ep.f2[z];
+        w *= ep.g2[z];
+    }
+    const float kap = (float)ep.kappa, sh = (float)ep.shift;
+    if (ep.kind == FD_MASS_INVERSE) return w;
+    if (ep.kind == FD_RESOLVENT) return w / (kap * lam + sh);
+    return 1.0f / (kap * lam + sh);
 }
 
 // Batch index z = blockIdx.z splits into (z2, z1) = (z / nb1, z % nb1); the
@@ -598,7 +622,9 @@ __global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __
                                                    const T* __restrict__ H0, const T* __restrict__ H1,
                                                    const T* __restrict__ G0, const T* __restrict__ G1,
                                                    T* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep) {
-    constexpr int BM = 16 * TM, BN = 16 * TM, BK = 16;
+    // FP32: the whole folded contraction of a 127-point direction (K <= 64) in one
+    // staged step (fewer barriers, more loads in flight); FP64: 16 at a time
+    constexpr int BM = 16 * TM, BN = 16 * TM, BK = sizeof(T) == 4 ? 64 : 16;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN];
     const int par = blockIdx.z & 1;
@@ -670,6 +696,7 @@ __global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __
         }
         __syncthreads();
     }
+    const float fcoef = (float)ep.coef;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         int gm = m0 + ty + 16 * i;
@@ -681,12 +708,19 @@ __global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __
             // output coordinates of the unfolded product
             long long om = SIDE == 0 ? gm : 2LL * gm + par;
             long long on = SIDE == 0 ? 2LL * gn + par : gn;
-            double f = ep.coef;
-            if (ep.scale) {
-                long long e = ep.left ? om * ep.J + on : on;
-                f *= fd_omega(ep, e);
+            if constexpr (sizeof(T) == 4) {
+                // FP32 epilogue: FP64 conversions and products here would run on the 1/64-rate pipe
+                float f = fcoef;
+                if (ep.scale) f *= fd_omega32(ep, ep.left ? om * ep.J + on : on);
+                C[(size_t)om * ldc + on] = f * acc[i][j];
+            } else {
+                double f = ep.coef;
+                if (ep.scale) {
+                    long long e = ep.left ? om * ep.J + on : on;
+                    f *= fd_omega(ep, e);
+                }
+                C[(size_t)om * ldc + on] = (T)(f * (double)acc[i][j]);
             }
-            C[(size_t)om * ldc + on] = (T)(f * (double)acc[i][j]);
         }
     }
 }
@@ -1237,10 +1271,12 @@ __global__ void __launch_bounds__(256) k_gm_dot_partial(int n, int kk, int m, in
             s3 += z[t + 96] * us[t + 96];
         }
         for (; t < rn; t += 32) s0 += z[t] * us[t];
-        double sum = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
+        // the lanes combine in T (FP64 adds on FP32 data would run on the 1/64-rate pipe);
+        // the chunk partials are summed in FP64 by k_gm_reduce
+        T sum = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-        if (lane == 0) part[((size_t)blockIdx.x * m + c) * kk + i] = sum;
+        if (lane == 0) part[((size_t)blockIdx.x * m + c) * kk + i] = (double)sum;
     }
 }
 
@@ -1269,8 +1305,9 @@ __global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, T* __re
                                                    const double* __restrict__ H, int ldh,
                                                    const double* __restrict__ H1, int ldh1, double* __restrict__ Hd,
                                                    long long ldhd, int jcol, int J) {
-    extern __shared__ double hs[];   // m x (nb + 1) coefficients, then m scale factors
+    extern __shared__ double hs[];   // m x (nb + 1) coefficients, then m scale factors, then the coefficients in T
     double* inv = hs + (size_t)m * (nb + 1);
+    T* ht = reinterpret_cast<T*>(inv + m);
     for (int t = threadIdx.x; t < m * (nb + 1); t += blockDim.x) hs[t] = H[(size_t)(t / (nb + 1)) * ldh + t % (nb + 1)];
     __syncthreads();
     if (H1 && threadIdx.x < m) {
@@ -1286,9 +1323,13 @@ __global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, T* __re
             col[nb] = h;
         }
     }
+    for (int t = threadIdx.x; t < m * (nb + 1); t += blockDim.x) ht[t] = (T)hs[t];
     __syncthreads();
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
+    T invt[MAXM];
+#pragma unroll
+    for (int c = 0; c < MAXM; ++c) invt[c] = (H1 && c < m) ? (T)inv[c] : T(1);
     T acc[MAXM];
 #pragma unroll
     for (int c = 0; c < MAXM; ++c) acc[c] = c < m ? Z[((size_t)nb * m + c) * n + r] : T(0);
@@ -1298,11 +1339,11 @@ __global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, T* __re
         for (int c = 0; c < MAXM; ++c) z[c] = c < m ? Z[((size_t)i * m + c) * n + r] : T(0);
 #pragma unroll
         for (int c = 0; c < MAXM; ++c)
-            if (c < m) acc[c] -= z[c] * (T)hs[c * (nb + 1) + i];   // hs holds m columns only
+            if (c < m) acc[c] -= z[c] * ht[c * (nb + 1) + i];   // ht holds m columns only
     }
 #pragma unroll
     for (int c = 0; c < MAXM; ++c)
-        if (c < m) Z[((size_t)nb * m + c) * n + r] = H1 ? acc[c] * (T)inv[c] : acc[c];
+        if (c < m) Z[((size_t)nb * m + c) * n + r] = H1 ? acc[c] * invt[c] : acc[c];
 }
 
 // X[:,c] *= f[c] (device factors).
@@ -1696,6 +1737,12 @@ static int fd_apply_impl(st_problem* p, FdKind kind, double shift, double coef, 
     sc.c0 = p->ax[0].c2;
     sc.c1 = dim > 1 ? p->ax[1].c2 : p->ax[0].c2;
     sc.c2 = dim > 2 ? p->ax[2].c2 : p->ax[0].c2;
+    sc.f0 = p->ax[0].lam32;
+    sc.f1 = dim > 1 ? p->ax[1].lam32 : p->ax[0].lam32;
+    sc.f2 = dim > 2 ? p->ax[2].lam32 : p->ax[0].lam32;
+    sc.g0 = p->ax[0].c232;
+    sc.g1 = dim > 1 ? p->ax[1].c232 : p->ax[0].c232;
+    sc.g2 = dim > 2 ? p->ax[2].c232 : p->ax[0].c232;
     sc.kind = kind;
     sc.kappa = p->fd_kappa;
     sc.shift = shift;
@@ -1819,9 +1866,10 @@ static int line_apply_impl(st_problem* p, double coef, const T* X, int ldx, int 
         const long long rows = (long long)nmodes * ncols;
         st_prof_begin(s, sizeof(T) == 8 ? "line64" : "line32", 4.0 * sizeof(T) * (double)nh * ncols,
                       5.0 * (double)nh * ncols);
-        // few rows (a 2D grid): every thread's sweep is latency-bound, so each batch
-        // of loads covers 64 steps; many rows: 16, and more threads per SM
-        if (rows < 8192)
+        // the sweeps are latency-bound (few warps per SM even on 127^3: one thread per row),
+        // so each batch of loads covers 64 steps; FP64 on many rows: 16, which keeps the
+        // registers below 128
+        if (rows < 8192 || sizeof(T) == 4)
             k_line_solve<T, 64><<<(unsigned)((rows + 63) / 64), 64, 0, s>>>(
                 nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
                 dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
@@ -2128,7 +2176,7 @@ int st_gm_update(int n, int nb, int m, T* Z, const double* H, int ldh, const dou
                  long long ldhd, int jcol, int J, cudaStream_t s) {
     if (n <= 0 || nb < 0 || m <= 0 || m > kMaxCols) return ST_EINVAL;
     const int blocks = (n + 255) / 256;
-    const size_t smem = sizeof(double) * ((size_t)m * (nb + 1) + m);
+    const size_t smem = sizeof(double) * ((size_t)m * (nb + 1) + m) + sizeof(T) * (size_t)m * (nb + 1);
     st_prof_begin(s, sizeof(T) == 8 ? "gm_update" : "gm_update32", (double)sizeof(T) * n * m * (nb + 2),
                   2.0 * (double)n * m * nb);
     if (m <= 1)

@@ -202,7 +202,8 @@ __global__ void k_assemble_tensor(int dim, int nx, int ny, int nz, Axis1D ax, Ax
 // M s_j = mu_j s_j with mu_j = h (4 + 2 cos(j pi/(n+1)))/6 and
 // K s_j = lam_j M s_j with lam_j = (6/h^2)(1 - cos)/(2 + cos).
 __global__ void k_fd_tables(int n, double h, double* __restrict__ Q64, float* __restrict__ Q32,
-                            double* __restrict__ lam, double* __restrict__ c2) {
+                            double* __restrict__ lam, double* __restrict__ c2, float* __restrict__ lam32,
+                            float* __restrict__ c232) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n * n) {
         int j = idx / n, i = idx % n;
@@ -218,6 +219,8 @@ __global__ void k_fd_tables(int n, double h, double* __restrict__ Q64, float* __
         lam[idx] = (6.0 / (h * h)) * (2.0 * s * s) / (2.0 + c);
         double mu = h * (4.0 + 2.0 * c) / 6.0;
         c2[idx] = 2.0 / ((n + 1) * mu);
+        lam32[idx] = (float)lam[idx];
+        c232[idx] = (float)c2[idx];
     }
 }
 
@@ -370,8 +373,10 @@ static int setup_tensor(st_problem* p) {
             ST_TRY(st_alloc(p, (void**)&ax.Q32, sizeof(float) * nn));
             ST_TRY(st_alloc(p, (void**)&ax.lam, sizeof(double) * ax.n));
             ST_TRY(st_alloc(p, (void**)&ax.c2, sizeof(double) * ax.n));
+            ST_TRY(st_alloc(p, (void**)&ax.lam32, sizeof(float) * ax.n));
+            ST_TRY(st_alloc(p, (void**)&ax.c232, sizeof(float) * ax.n));
             int nb = (int)((nn + 255) / 256);
-            k_fd_tables<<<nb, 256, 0, p->stream>>>(ax.n, ax.h, ax.Q64, ax.Q32, ax.lam, ax.c2);
+            k_fd_tables<<<nb, 256, 0, p->stream>>>(ax.n, ax.h, ax.Q64, ax.Q32, ax.lam, ax.c2, ax.lam32, ax.c232);
             ST_LAUNCH_CHECK();
             {
                 const size_t k0 = (size_t)(ax.n + 1) / 2, k1 = (size_t)ax.n / 2;
