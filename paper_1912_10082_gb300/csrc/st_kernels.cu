@@ -352,6 +352,76 @@ __global__ void __launch_bounds__(256) k_stencil_box(int nx, int ny, int nz, Box
         }
 }
 
+// FP32 variant of the constant-stencil product with the apply's shuffle scheme:
+// a lane loads one x of each of its (YB+2)(ZB+2) rows and takes x +- 1 from its
+// neighbours, a warp yields 30 outputs a row.  O = S * X (+ beta O).
+template <int DIM, int YB, int ZB>
+__global__ void __launch_bounds__(256) k_stencil_box_sh(int nx, int ny, int nz, BoxPair<float> S,
+                                                        const float* __restrict__ X, long long ldx, float beta,
+                                                        float* __restrict__ O, long long ldo) {
+    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
+    const int nxs = (nx + 29) / 30, nyb = (ny + 8 * YB - 1) / (8 * YB);
+    int b = blockIdx.x;
+    const int xs = b % nxs;
+    b /= nxs;
+    const int yb = b % nyb;
+    const int zb = b / nyb;
+    const int lane = threadIdx.x;
+    const int x = xs * 30 + lane - 1;
+    const int y0 = (yb * 8 + threadIdx.y) * YB;
+    const int z0 = zb * ZB;
+    if (y0 >= ny || (DIM == 3 && z0 >= nz)) return;   // uniform over the warp
+    const bool okx = x >= 0 && x < nx;
+    const bool emit = lane >= 1 && lane <= 30 && x < nx;
+    const long long nxy = (long long)nx * ny;
+    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
+    const float* u = X + (size_t)blockIdx.y * ldx;
+    float v[RY * RZ];
+#pragma unroll
+    for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < RY; ++iy) {
+            const bool ok = okx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny &&
+                            (DIM < 3 || (z0 + iz - 1 >= 0 && z0 + iz - 1 < nz));
+            const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx;
+            v[iz * RY + iy] = ok ? __ldg(u + base + off) : 0.f;
+        }
+    float t[YB * ZB];
+#pragma unroll
+    for (int o = 0; o < YB * ZB; ++o) t[o] = 0.f;
+#pragma unroll
+    for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < RY; ++iy) {
+            const float w0 = v[iz * RY + iy];
+            const float wm = __shfl_up_sync(0xffffffffu, w0, 1);
+            const float wp = __shfl_down_sync(0xffffffffu, w0, 1);
+#pragma unroll
+            for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+                for (int oy = 0; oy < YB; ++oy) {
+                    const int dz = DIM == 3 ? iz - 1 - oz : 0, dy = iy - 1 - oy;
+                    if (dz < -1 || dz > 1 || dy < -1 || dy > 1) continue;
+                    const int e = (dz + 1) * 9 + (dy + 1) * 3;
+                    const int o = oz * YB + oy;
+                    t[o] += S.s[0][e] * wm;
+                    t[o] += S.s[0][e + 1] * w0;
+                    t[o] += S.s[0][e + 2] * wp;
+                }
+        }
+    if (!emit) return;
+    float* out = O + (size_t)blockIdx.y * ldo;
+#pragma unroll
+    for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+        for (int oy = 0; oy < YB; ++oy) {
+            if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
+            const long long at = base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx;
+            const float r = t[oz * YB + oy];
+            out[at] = beta == 0.f ? r : r + beta * out[at];
+        }
+}
+
 // Generic CSR rows (any length): entries re-read from L1/L2 each step.
 template <typename T>
 __global__ void k_apply_generic(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
@@ -2225,7 +2295,15 @@ int st_spmm_comb32(st_problem* p, double cm, double ca, const float* X, int ldx,
     BoxPair<float> S;
     for (int e = 0; e < 27; ++e) S.s[0][e] = S.s[1][e] = (float)(cm * p->box_m64[e] + ca * p->box_a64[e]);
     st_prof_begin(s, "spmm_comb32_box", 8.0 * (double)p->n_h * ncols, 2.0 * (p->dim == 2 ? 9 : 27) * (double)p->n_h * ncols);
-    launch_stencil_box<float>(p, S, X, ldx, ncols, 0.f, Out, ldo, nullptr, 0, s);
+    // shuffle kernel: 4 y-rows (2D) or 4 x 2 (y, z) points a thread, 30 outputs a warp row
+    const int nx = p->n[0], ny = p->n[1], nz = p->dim == 3 ? p->n[2] : 1;
+    const int YB = 4, ZB = p->dim == 2 ? 1 : 2;
+    const long long blocks = (long long)((nx + 29) / 30) * ((ny + 8 * YB - 1) / (8 * YB)) * ((nz + ZB - 1) / ZB);
+    dim3 grid((unsigned)blocks, (unsigned)ncols);
+    if (p->dim == 2)
+        k_stencil_box_sh<2, 4, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, S, X, ldx, 0.f, Out, ldo);
+    else
+        k_stencil_box_sh<3, 4, 2><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, S, X, ldx, 0.f, Out, ldo);
     st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;
