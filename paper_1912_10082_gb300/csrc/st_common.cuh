@@ -173,6 +173,9 @@ int st_gm_dots(int n, int kk, int m, const T* Z, double* part, double* H, int ld
 template <typename T>
 int st_gm_update(int n, int nb, int m, T* Z, const double* H, int ldh, const double* H1, int ldh1, double* Hd,
                  long long ldhd, int jcol, int J, cudaStream_t s);
+template <typename T>
+int st_gm_update_dot(int n, int nb, int m, T* Z, const double* H1, int ldh1, double* part, double* H2, int ldh2,
+                     cudaStream_t s);
 int st_scale_cols_to32(int n, int m, const double* X, int ldx, const double* f, float* Y, int ldy, cudaStream_t s);
 struct GmSteps {   // Arnoldi steps that enter each column's solution (at most 16 columns)
     int v[16];

@@ -1416,6 +1416,69 @@ __global__ void __launch_bounds__(256) k_gm_update(int n, int nb, int m, T* __re
         if (c < m) Z[((size_t)nb * m + c) * n + r] = H1 ? acc[c] * invt[c] : acc[c];
 }
 
+// The first pass's update fused with the second pass's dot products, one CTA
+// per chunk of rows (the chunks of k_gm_dot_partial): the chunk's new vector
+// U = Z_nb - sum_i Z_i h1_i is written to Z and kept in shared memory, then the
+// partial dots Z_i . U (i < nb) and U . U are taken while the chunk's Z_i are
+// still in L2, so the second pass reads the basis from L2 instead of HBM.
+template <typename T, int MAXM>
+__global__ void __launch_bounds__(256) k_gm_update_dot(int n, int nb, int m, int rows, T* __restrict__ Z,
+                                                       const double* __restrict__ H, int ldh,
+                                                       double* __restrict__ part) {
+    extern __shared__ double sm_ud[];
+    double* hs = sm_ud;                                   // m x (nb + 1) first-pass coefficients
+    T* ht = reinterpret_cast<T*>(hs + (size_t)m * (nb + 1));
+    T* us = ht + (size_t)m * (nb + 1);                    // [m][rows] the chunk's new vectors
+    for (int t = threadIdx.x; t < m * (nb + 1); t += blockDim.x) {
+        hs[t] = H[(size_t)(t / (nb + 1)) * ldh + t % (nb + 1)];
+        ht[t] = (T)hs[t];
+    }
+    __syncthreads();
+    const long long r0 = (long long)blockIdx.x * rows;
+    const int rn = (int)min((long long)rows, (long long)n - r0);
+    for (int t = threadIdx.x; t < rn; t += blockDim.x) {
+        const long long r = r0 + t;
+        T acc[MAXM];
+#pragma unroll
+        for (int c = 0; c < MAXM; ++c) acc[c] = c < m ? Z[((size_t)nb * m + c) * n + r] : T(0);
+        for (int i = 0; i < nb; ++i) {
+            T z[MAXM];
+#pragma unroll
+            for (int c = 0; c < MAXM; ++c) z[c] = c < m ? Z[((size_t)i * m + c) * n + r] : T(0);
+#pragma unroll
+            for (int c = 0; c < MAXM; ++c)
+                if (c < m) acc[c] -= z[c] * ht[c * (nb + 1) + i];
+        }
+#pragma unroll
+        for (int c = 0; c < MAXM; ++c)
+            if (c < m) {
+                Z[((size_t)nb * m + c) * n + r] = acc[c];
+                us[(size_t)c * rows + t] = acc[c];
+            }
+    }
+    __syncthreads();
+    const int kk = nb + 1;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int q = warp; q < m * kk; q += blockDim.x / 32) {
+        const int c = q / kk, i = q % kk;
+        const T* u = us + (size_t)c * rows;
+        const T* z = i < nb ? Z + ((size_t)i * m + c) * n + r0 : u;
+        T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+        int t = lane;
+        for (; t + 96 < rn; t += 128) {
+            s0 += z[t] * u[t];
+            s1 += z[t + 32] * u[t + 32];
+            s2 += z[t + 64] * u[t + 64];
+            s3 += z[t + 96] * u[t + 96];
+        }
+        for (; t < rn; t += 32) s0 += z[t] * u[t];
+        T sum = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) part[((size_t)blockIdx.x * m + c) * kk + i] = (double)sum;
+    }
+}
+
 // X[:,c] *= f[c] (device factors).
 __global__ void k_scale_cols_dev(int n, int m, double* __restrict__ X, long long ldx, const double* __restrict__ f) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2218,9 +2281,18 @@ static int gm_rows(int n, int m) {
     return (int)std::min<long long>(4096, std::max<long long>(256, rows));
 }
 
+// Chunk rows of the fused update-and-dots kernel: as gm_rows, but the chunk's
+// new vectors (m x rows of T) must fit in 160 KB of shared memory.
+static int gm_rows_ud(int n, int m, size_t tsize) {
+    const int cap = (int)((160 * 1024) / ((size_t)m * tsize)) / 32 * 32;
+    return std::max(32, std::min(gm_rows(n, m), cap));
+}
+
 size_t st_gm_partial_elems(int n, int kk, int m) {
-    const int rows = gm_rows(n, m);
-    return (size_t)((n + rows - 1) / rows) * (size_t)m * (size_t)kk;
+    // the larger chunk count of the two partitions (the fused one at its FP64 worst case)
+    const int r1 = gm_rows(n, m), r2 = gm_rows_ud(n, m, sizeof(double));
+    const size_t nch = (size_t)std::max((n + r1 - 1) / r1, (n + r2 - 1) / r2);
+    return nch * (size_t)m * (size_t)kk;
 }
 
 template <typename T>
@@ -2263,6 +2335,48 @@ int st_gm_update(int n, int nb, int m, T* Z, const double* H, int ldh, const dou
     ST_LAUNCH_CHECK();
     return ST_OK;
 }
+
+template <typename T, int MAXM>
+static void launch_update_dot(int nch, size_t smem, cudaStream_t s, int n, int nb, int m, int rows, T* Z,
+                              const double* H, int ldh, double* part) {
+    static const bool set = [] {
+        cudaFuncSetAttribute(k_gm_update_dot<T, MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return true;
+    }();
+    (void)set;
+    k_gm_update_dot<T, MAXM><<<nch, 256, smem, s>>>(n, nb, m, rows, Z, H, ldh, part);
+}
+
+template <typename T>
+int st_gm_update_dot(int n, int nb, int m, T* Z, const double* H1, int ldh1, double* part, double* H2, int ldh2,
+                     cudaStream_t s) {
+    if (n <= 0 || nb < 0 || m <= 0 || m > kMaxCols) return ST_EINVAL;
+    const int rows = gm_rows_ud(n, m, sizeof(T));
+    const int nch = (n + rows - 1) / rows;
+    const int kk = nb + 1;
+    const size_t smem = sizeof(double) * (size_t)m * kk + sizeof(T) * ((size_t)m * kk + (size_t)m * rows);
+    if (smem > 200 * 1024) return ST_EINVAL;
+    st_prof_begin(s, sizeof(T) == 8 ? "gm_update_dot" : "gm_update_dot32",
+                  (double)sizeof(T) * n * m * (nb + 2) + 16.0 * (double)nch * kk * m, 4.0 * (double)n * m * kk);
+    if (m <= 1)
+        launch_update_dot<T, 1>(nch, smem, s, n, nb, m, rows, Z, H1, ldh1, part);
+    else if (m <= 2)
+        launch_update_dot<T, 2>(nch, smem, s, n, nb, m, rows, Z, H1, ldh1, part);
+    else if (m <= 4)
+        launch_update_dot<T, 4>(nch, smem, s, n, nb, m, rows, Z, H1, ldh1, part);
+    else if (m <= 8)
+        launch_update_dot<T, 8>(nch, smem, s, n, nb, m, rows, Z, H1, ldh1, part);
+    else
+        launch_update_dot<T, 16>(nch, smem, s, n, nb, m, rows, Z, H1, ldh1, part);
+    ST_LAUNCH_CHECK();
+    k_gm_reduce<<<(kk * m + 7) / 8, 256, 0, s>>>(nch, kk, m, part, H2, ldh2);
+    st_prof_end(s);
+    ST_LAUNCH_CHECK();
+    return ST_OK;
+}
+template int st_gm_update_dot<double>(int, int, int, double*, const double*, int, double*, double*, int,
+                                      cudaStream_t);
+template int st_gm_update_dot<float>(int, int, int, float*, const double*, int, double*, double*, int, cudaStream_t);
 
 template int st_gm_update<double>(int, int, int, double*, const double*, int, const double*, int, double*, long long,
                                   int, int, cudaStream_t);

@@ -793,8 +793,8 @@ int fgmres_impl(Ctx& c, int prec, double shift, const double* X, int ldx, const 
                 ST_TRY(precond(Zj, Tj, m));
                 ST_TRY(op(Tj, U, m));
                 ST_TRY(st_gm_dots<TB>(n, j + 2, m, Z, part, H1, J + 2, c.s));
-                ST_TRY(st_gm_update<TB>(n, j + 1, m, Z, H1, J + 2, nullptr, 0, nullptr, 0, j, J, c.s));
-                ST_TRY(st_gm_dots<TB>(n, j + 2, m, Z, part, H2, J + 2, c.s));
+                // first pass's update and second pass's dots in one sweep of the basis
+                ST_TRY(st_gm_update_dot<TB>(n, j + 1, m, Z, H1, J + 2, part, H2, J + 2, c.s));
                 ST_TRY(st_gm_update<TB>(n, j + 1, m, Z, H2, J + 2, H1, J + 2, Hd, ldhd, j, J, c.s));
                 if ((j + 1) % CHK != 0 && j + 1 < J) continue;
                 // Hessenberg columns checked..j of every column of the block
