@@ -1617,6 +1617,123 @@ __global__ void k_line_solve(int nx, int nmodes, int ny, int dim, int ncols, con
     }
 }
 
+// Line solves with a warp per row (partition method) for grids with few rows,
+// where one sequential thread per row leaves the GPU idle: lane k owns the
+// chunk [k L, (k+1) L) of the row (L = ceil(nx/32) <= 8).  Each lane solves
+// its chunk's Toeplitz block three times (the leading-block Thomas factors are
+// the first entries of the row's factors): y for its right-hand side, v and w
+// for the couplings -a and -c to the unknowns left and right of the chunk, so
+// x = y + v x_left + w x_right.  The chunks' first and last unknowns then
+// satisfy a two-term recurrence over the chunks, run by lane 0 in shared
+// memory, and every lane finishes its chunk.
+template <typename T>
+__global__ void __launch_bounds__(128) k_line_solve_warp(int nx, int nmodes, int ny, int dim, int ncols, const T* src,
+                                                         long long lds, T* dst, long long ldd,
+                                                         const T* __restrict__ CP, const T* __restrict__ IP,
+                                                         double hx, double eps, double bx, double shift,
+                                                         const double* __restrict__ lam1,
+                                                         const double* __restrict__ lam2,
+                                                         const double* __restrict__ c2y,
+                                                         const double* __restrict__ c2z, double coef) {
+    constexpr int LMAX = 8;
+    __shared__ T sh[4][32][6];   // per warp: y, v, w at the chunk ends
+    __shared__ T sx[4][33][2];   // per warp: the chunk's first and last unknowns
+    const int wib = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const long long row = (long long)blockIdx.x * 4 + wib;
+    if (row >= (long long)nmodes * ncols) return;   // uniform over the warp
+    const int col = (int)(row / nmodes), mode = (int)(row % nmodes);
+    double w = coef, mu = shift;
+    if (dim > 1) {
+        w *= c2y[mode % ny];
+        mu += eps * lam1[mode % ny];
+    }
+    if (dim > 2) {
+        w *= c2z[mode / ny];
+        mu += eps * lam2[mode / ny];
+    }
+    const T wt = (T)w;
+    const T a = (T)(-eps / hx - 0.5 * bx + mu * hx / 6.0);
+    const T cc = (T)(-eps / hx + 0.5 * bx + mu * hx / 6.0);
+    const int L = (nx + 31) / 32;
+    const int P = (nx + L - 1) / L;   // non-empty chunks
+    const int s0 = lane * L;
+    const int Lk = lane < P ? min(L, nx - s0) : 0;
+    const T* x = src + (size_t)col * lds + (size_t)mode * nx;
+    T* out = dst + (size_t)col * ldd + (size_t)mode * nx;
+    const T* cp = CP + (size_t)mode * nx;
+    const T* ip = IP + (size_t)mode * nx;
+    T b[LMAX], y[LMAX], v[LMAX], u[LMAX], cpl[LMAX], ipl[LMAX];
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) {
+        const bool in = i < Lk;
+        b[i] = in ? wt * x[s0 + i] : T(0);
+        cpl[i] = in ? cp[i] : T(0);
+        ipl[i] = in ? ip[i] : T(0);
+    }
+    // forward sweeps of the three right-hand sides (b, -a e_1, -c e_Lk)
+    T dy = T(0), dv = T(0), du = T(0);
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) {
+        if (i < Lk) {
+            dy = (b[i] - a * dy) * ipl[i];
+            dv = ((i == 0 ? -a : T(0)) - a * dv) * ipl[i];
+            du = ((i == Lk - 1 ? -cc : T(0)) - a * du) * ipl[i];
+            y[i] = dy;
+            v[i] = dv;
+            u[i] = du;
+        }
+    }
+#pragma unroll
+    for (int i = LMAX - 2; i >= 0; --i) {
+        if (i < Lk - 1) {
+            y[i] -= cpl[i] * y[i + 1];
+            v[i] -= cpl[i] * v[i + 1];
+            u[i] -= cpl[i] * u[i + 1];
+        }
+    }
+    if (lane < P) {
+        sh[wib][lane][0] = y[0];
+        sh[wib][lane][1] = y[Lk - 1 < 0 ? 0 : Lk - 1];
+        sh[wib][lane][2] = v[0];
+        sh[wib][lane][3] = v[Lk - 1 < 0 ? 0 : Lk - 1];
+        sh[wib][lane][4] = u[0];
+        sh[wib][lane][5] = u[Lk - 1 < 0 ? 0 : Lk - 1];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // g_{k-1} = al + be f_k; f_k = A_k + B_k f_{k+1}; g_k = al_k + be_k f_{k+1}
+        T al = T(0), be = T(0);
+        T A[32], B[32], AL[32], BE[32];
+        for (int k = 0; k < P; ++k) {
+            const T yf = sh[wib][k][0], yl = sh[wib][k][1], vf = sh[wib][k][2], vl = sh[wib][k][3];
+            const T wf = sh[wib][k][4], wl = sh[wib][k][5];
+            const T den = T(1) - vf * be;
+            A[k] = (yf + vf * al) / den;
+            B[k] = wf / den;
+            AL[k] = yl + vl * al + vl * be * A[k];
+            BE[k] = vl * be * B[k] + wl;
+            al = AL[k];
+            be = BE[k];
+        }
+        T fnext = T(0);   // the unknown right of the last chunk is the boundary
+        for (int k = P - 1; k >= 0; --k) {
+            const T f = A[k] + B[k] * fnext;
+            const T g = AL[k] + BE[k] * fnext;
+            sx[wib][k][0] = f;
+            sx[wib][k][1] = g;
+            fnext = f;
+        }
+    }
+    __syncwarp();
+    if (lane < P) {
+        const T xl = lane > 0 ? sx[wib][lane - 1][1] : T(0);
+        const T xr = lane + 1 < P ? sx[wib][lane + 1][0] : T(0);
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i)
+            if (i < Lk) out[s0 + i] = y[i] + v[i] * xl + u[i] * xr;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1999,6 +2116,17 @@ static int line_apply_impl(st_problem* p, double coef, const T* X, int ldx, int 
         const long long rows = (long long)nmodes * ncols;
         st_prof_begin(s, sizeof(T) == 8 ? "line64" : "line32", 4.0 * sizeof(T) * (double)nh * ncols,
                       5.0 * (double)nh * ncols);
+        // few rows (a 2D grid: N_y p) and short rows: a warp per row, partition method
+        // (2D 255^2: 58 -> 12 us a launch; on 63^3, 7938 rows, the thread per row is faster)
+        if (rows < 2048 && nx <= 256) {
+            k_line_solve_warp<T><<<(unsigned)((rows + 3) / 4), 128, 0, s>>>(
+                nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
+                dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
+                dim > 2 ? p->ax[2].c2 : nullptr, coef);
+            st_prof_end(s);
+            ST_LAUNCH_CHECK();
+            return ST_OK;
+        }
         // the sweeps are latency-bound (few warps per SM even on 127^3: one thread per row),
         // so each batch of loads covers 64 steps; FP64 on many rows: 16, which keeps the
         // registers below 128
