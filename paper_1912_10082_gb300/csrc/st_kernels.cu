@@ -2117,7 +2117,7 @@ static int line_apply_impl(st_problem* p, double coef, const T* X, int ldx, int 
         st_prof_begin(s, sizeof(T) == 8 ? "line64" : "line32", 4.0 * sizeof(T) * (double)nh * ncols,
                       5.0 * (double)nh * ncols);
         // few rows (a 2D grid: N_y p) and short rows: a warp per row, partition method
-        // (2D 255^2: 58 -> 12 us a launch; on 63^3, 7938 rows, the thread per row is faster)
+        // (2D 255^2: 58 -> 13 us a launch; on 63^3, 7938 rows, the thread per row is faster)
         if (rows < 2048 && nx <= 256) {
             k_line_solve_warp<T><<<(unsigned)((rows + 3) / 4), 128, 0, s>>>(
                 nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
