@@ -205,12 +205,16 @@ unsigned long st_shift_solve_noalloc_max(void);
  * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL.
  * Heat (ST_HEAT): the shifted solves are exact fast-diagonalisation
  * transforms.  Convection-diffusion (ST_CONVDIFF, A nonsymmetric): each
- * shifted solve is flexible GMRES right-preconditioned by the
- * fast-diagonalisation solve of eps K + s M, to 1e-3 tol relative (at least
+ * shifted solve is flexible GMRES (all columns advanced together)
+ * right-preconditioned by the x-line solve of eps K + beta_x Gx (x) M_rest
+ * + s M when |beta_x| is the largest component (else by the
+ * fast-diagonalisation solve of eps K + s M), to 1e-3 tol relative (at least
  * 1e-13); the projected matrices are not symmetrised and the projected time
  * recurrence uses LU.  ST_MIXED: FP32 transforms (refined to FP64 accuracy,
- * or inside FGMRES as the preconditioner) and basis products in double-float
- * arithmetic on the FP32 pipes (about 48 significant bits). */
+ * or inside FGMRES as the preconditioner), basis products in double-float
+ * arithmetic on the FP32 pipes (about 48 significant bits), and on
+ * convection-diffusion grids of at least 2^17 points FGMRES cycles in FP32
+ * refined on the FP64 residual. */
 int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
              st_solution* sol, st_stats* stats);
 
