@@ -886,7 +886,7 @@ int fgmres_impl(Ctx& c, int prec, double shift, const double* X, int ldx, const 
 // FP64 Krylov vectors otherwise.
 int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx,
                          int ncols, double* W, int ldw, double rtol, int* iters_out) {
-    const bool ir = prec == ST_MIXED && c.n >= (1 << 17) && c.p->box_ok && (c.p->dim == 2 || c.p->dim == 3);
+    const bool ir = prec == ST_MIXED && c.n >= (1 << 15) && c.p->box_ok && (c.p->dim == 2 || c.p->dim == 3);
     if (ir) return fgmres_impl<float>(c, prec, shift, X, ldx, MX, ldmx, ncols, W, ldw, rtol, iters_out);
     return fgmres_impl<double>(c, prec, shift, X, ldx, MX, ldmx, ncols, W, ldw, rtol, iters_out);
 }
