@@ -213,7 +213,7 @@ unsigned long st_shift_solve_noalloc_max(void);
  * recurrence uses LU.  ST_MIXED: FP32 transforms (refined to FP64 accuracy,
  * or inside FGMRES as the preconditioner), basis products in double-float
  * arithmetic on the FP32 pipes (about 48 significant bits), and on
- * convection-diffusion grids of at least 2^17 points FGMRES cycles in FP32
+ * convection-diffusion grids of at least 2^15 points FGMRES cycles in FP32
  * refined on the FP64 residual. */
 int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
              st_solution* sol, st_stats* stats);

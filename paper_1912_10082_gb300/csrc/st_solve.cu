@@ -882,7 +882,7 @@ int fgmres_impl(Ctx& c, int prec, double shift, const double* X, int ldx, const 
 }
 
 // FP32 iterative refinement for mixed precision where the work is bandwidth-
-// or FP64-bound (at least 2^17 grid points, box stencils for the FP32 product);
+// or FP64-bound (at least 2^15 grid points, box stencils for the FP32 product);
 // FP64 Krylov vectors otherwise.
 int shifted_solve_fgmres(Ctx& c, int prec, double shift, const double* X, int ldx, const double* MX, int ldmx,
                          int ncols, double* W, int ldw, double rtol, int* iters_out) {
