@@ -1,0 +1,86 @@
+// Host dense algebra of the solver (st_dense.cpp): results must not depend on
+// the number of host threads, and must solve what they claim to.  Built and
+// run by tests/test_host_algebra.py; prints one line per check and the
+// eigenvalues of a fixed matrix for comparison with numpy.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "st_common.cuh"
+
+namespace {
+
+std::vector<double> spd(int n, unsigned seed) {
+    std::mt19937 g(seed);
+    std::normal_distribution<double> nd;
+    std::vector<double> B((size_t)n * n), A((size_t)n * n);
+    for (auto& x : B) x = nd(g);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0;
+            for (int k = 0; k < n; ++k) s += B[(size_t)k * n + i] * B[(size_t)k * n + j];
+            A[(size_t)j * n + i] = s + (i == j ? n : 0.0);
+        }
+    return A;
+}
+
+// run f with the host treated as busy (one thread per call) or idle (up to 8)
+template <class F>
+void with_threads(bool one, F f) {
+    std::vector<hostpar::ActiveSolve*> hold;
+    if (one)
+        for (int q = 0; q < 4096; ++q) hold.push_back(new hostpar::ActiveSolve());
+    f();
+    for (auto* h : hold) delete h;
+}
+
+}  // namespace
+
+int main() {
+    int bad = 0;
+    for (int n : {7, 64, 301, 552}) {
+        const std::vector<double> A = spd(n, 3 + n);
+        std::vector<double> L1 = A, L8 = A, R1(A), R8(A), E1 = A, E8 = A, w1(n), w8(n);
+        bool ok1 = false, ok8 = false;
+        with_threads(true, [&] {
+            ok1 = dense::cholesky(n, L1.data(), n);
+            dense::chol_solve(n, L1.data(), n, R1.data(), n, n);
+            dense::sym_eigvals(n, E1.data(), n, w1.data());
+        });
+        with_threads(false, [&] {
+            ok8 = dense::cholesky(n, L8.data(), n);
+            dense::chol_solve(n, L8.data(), n, R8.data(), n, n);
+            dense::sym_eigvals(n, E8.data(), n, w8.data());
+        });
+        const bool same = ok1 && ok8 && !std::memcmp(L1.data(), L8.data(), sizeof(double) * L1.size()) &&
+                          !std::memcmp(R1.data(), R8.data(), sizeof(double) * R1.size()) &&
+                          !std::memcmp(w1.data(), w8.data(), sizeof(double) * n);
+        // L L^T = A and A X = A (X = I) up to rounding
+        double e1 = 0, e2 = 0, na = 0;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double s = 0;
+                for (int k = 0; k <= std::min(i, j); ++k) s += L8[(size_t)k * n + i] * L8[(size_t)k * n + j];
+                e1 = std::max(e1, std::fabs(s - A[(size_t)j * n + i]));
+                e2 = std::max(e2, std::fabs(R8[(size_t)j * n + i] - (i == j ? 1.0 : 0.0)));
+                na = std::max(na, std::fabs(A[(size_t)j * n + i]));
+            }
+        const bool acc = e1 <= 1e-12 * na * n && e2 <= 1e-10;
+        std::printf("n=%d threads=%d same=%d chol_err=%.2e solve_err=%.2e\n", n,
+                    hostpar::threads_for((double)n * n * n / 3.0), (int)same, e1 / na, e2);
+        bad += !(same && acc);
+    }
+    // eigenvalues of a fixed 40 x 40 matrix for the numpy comparison
+    const int m = 40;
+    std::vector<double> C = spd(m, 7), w(m);
+    std::printf("mat");
+    for (double x : C) std::printf(" %.17g", x);
+    std::printf("\n");
+    dense::sym_eigvals(m, C.data(), m, w.data());
+    std::printf("eig");
+    for (double x : w) std::printf(" %.17g", x);
+    std::printf("\n%s\n", bad ? "FAIL" : "PASS");
+    return bad;
+}
