@@ -872,6 +872,7 @@ int launch_gemm_rr(int M, int N, int K, const T* A, long long lda, const T* B, l
 // ---------------------------------------------------------------------------
 constexpr int TS_THREADS = 256;
 constexpr int TS_CG = 16;      // basis columns per CTA of H = V^T W
+constexpr int TS_CG_DF = 32;   // the same for the double-float product (half the restaging of W per basis column)
 constexpr int TS_UNROLL = 8;   // independent loads in flight per lane
 
 // Rows of one chunk of H = V^T W: enough chunks that chunks x column groups
@@ -1103,8 +1104,8 @@ __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, i
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     float2* out = part + (size_t)chunk * k * m;
-    for (int cc = warp; cc < TS_CG; cc += TS_THREADS / 32) {
-        const int a = blockIdx.y * TS_CG + cc;
+    for (int cc = warp; cc < TS_CG_DF; cc += TS_THREADS / 32) {
+        const int a = blockIdx.y * TS_CG_DF + cc;
         if (a >= k) break;
         const float2* v = V + (size_t)a * ldv + r0;
         float2 SH[MP], SL[MP];
@@ -2304,7 +2305,7 @@ int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2*
     const int rows = ts_rows(n, k, m);
     const int nch = (n + rows - 1) / rows;
     const size_t smem = sizeof(float4) * (size_t)((m + 1) / 2) * rows;   // column pairs, at most 64 KB
-    dim3 grid(nch, (k + TS_CG - 1) / TS_CG);
+    dim3 grid(nch, (k + TS_CG_DF - 1) / TS_CG_DF);
     if (grid.y > 65535) return ST_EINVAL;
     float2* part2 = reinterpret_cast<float2*>(partial);   // (hi, lo) pairs in the doubles' room
     st_prof_begin(s, "ts_tn_df", 8.0 * (double)n * (k + m) + 16.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
