@@ -1128,14 +1128,14 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         // ---- shift ----
         tp = Clock::now();
         // Ritz values cost O(k^3) on the host: refresh them while the basis is
-        // small, then whenever it has grown by an eighth (a quarter beyond 128
+        // small, then whenever it has grown by an eighth (a quarter beyond 64
         // columns) since the last refresh
         if (last_ritz_k < 0 || k <= 16 ||
-            k >= last_ritz_k + std::max(2, last_ritz_k / (last_ritz_k > 128 ? 4 : 8))) {
+            k >= last_ritz_k + std::max(2, last_ritz_k / (last_ritz_k > 64 ? 4 : 8))) {
             if (!ritz_values(k, Am.a.data(), Mm.a.data(), Mm.ld, ritz)) ritz.clear();
             last_ritz_k = k;
         }
-        double s = next_shift(a_int, b_int, shifts, ritz, 150);
+        double s = next_shift(a_int, b_int, shifts, ritz, 80);
         shifts.push_back(s);
         S.ms_phase[7] += ms_since(tp);
         ++it;
