@@ -283,6 +283,7 @@ def bench_batched(args, wl, rank, world, local):
     torch.cuda.synchronize()
     slots = args.slots
     dof = sum(r["n"] ** 2 * r["n_t"] for r in insts)
+    tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(2, r["n"]) for r in insts], wl["p"])
 
     def timed(prec, method, steps, warmup, data):
         res = None
@@ -344,6 +345,7 @@ def bench_batched(args, wl, rank, world, local):
         "config": {"workload": f"batched: {len(insts)} 2D heat instances, grid side from (63,127,255), n_t from "
                                f"(64,128,256,512), kappa 10^U(-1,1), rank-{wl['p']} Gaussian load, mixed precision",
                    "instances": len(insts), "dof": dof, "slots": slots, "tol": 1e-8,
+                   "autotune": {"shapes": tune[0], "seconds": tune[1]},
                    "l2": "inputs of the batch (%.0f MB) exceed L2" % (sum(r['F1'].nbytes for r in insts) / 1e6),
                    "parallelism": f"replicas{world}"},
         "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its)),
@@ -353,6 +355,26 @@ def bench_batched(args, wl, rank, world, local):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def autotune_grids(st, grids, max_cols, convdiff=False, precisions=None):
+    """Launch variants of the shifted solves picked by timing on this GPU, once per grid shape (untimed, before
+    the warm-up): 1..max_cols columns (RKSM blocks after rank compression, and the single columns of
+    Crank-Nicolson), FP64 and mixed precision unless told otherwise.  grids: (dim, n) pairs.  Returns
+    (shapes added, seconds)."""
+    precisions = precisions or (st.ST_FP64, st.ST_MIXED)
+    t0 = time.perf_counter()
+    added = 0
+    for dim, n in sorted(set(grids)):
+        kinds = [dict()]
+        if convdiff:   # x-line preconditioner shapes (|beta_x| largest)
+            kinds.append(dict(op=st.ST_CONVDIFF, eps=0.05, beta=(1.0, 0.5, 0.25)[:dim]))
+        for kw in kinds:
+            with st.Problem(dim, n, 4, 1.0, **kw) as tp:
+                for m in range(1, max_cols + 1):
+                    for prec in precisions:
+                        added += tp.autotune(1.0, m, precision=prec)
+    return added, time.perf_counter() - t0
 
 
 def bench_served(args, wl, rank, world, local):
@@ -369,6 +391,8 @@ def bench_served(args, wl, rank, world, local):
     gap = wl["mean_gap_s"] * args.gap_scale
     reqs = workloads.served_requests(count=count, seed=wl["seed"], mean_gap_s=gap, p=wl["p"])
     facs = [tuple(np.asfortranarray(x) for x in workloads.request_factors(r)) for r in reqs]
+    tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(r["dim"], r["n"]) for r in reqs], wl["p"],
+                                                            convdiff=True, precisions=(st.ST_MIXED,))
     lc = st.launch_count()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
@@ -403,7 +427,7 @@ def bench_served(args, wl, rank, world, local):
                                f"{1e3 * gap:.2f} ms, heat and convection-diffusion, 1D/2D/3D n 63..127^3, "
                                f"n_t 64..512, rank-{wl['p']} Gaussian loads, mixed precision, tol 1e-8",
                    "slots": args.slots, "gap_scale": args.gap_scale, "policy": args.policy,
-                   "parallelism": f"replicas{world}"},
+                   "autotune": {"shapes": tune[0], "seconds": tune[1]}, "parallelism": f"replicas{world}"},
         "latency": {"p50_s": out["p50_s"], "p99_s": out["p99_s"], "per_kind": per_kind},
         "served": {"measured": out["measured"], "ok": out["ok"], "not_converged": out["not_converged"],
                    "wall_s": wall, "failures": failures},
@@ -421,6 +445,8 @@ def main():
     ap.add_argument("--workload", default="heat2d")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch choices (no timing of launch variants before the warm-up)")
     ap.add_argument("--slots", type=int, default=16, help="executor slots of the batched and served workloads")
     ap.add_argument("--requests", type=int, default=0, help="served workload: number of requests (0: all)")
     ap.add_argument("--gap-scale", type=float, default=1.0, help="served workload: scale of the mean arrival gap")
@@ -474,6 +500,7 @@ def main():
         f1, f2 = make_inputs(st, prob, wl, torch)
     stream.synchronize()
     units = prob.n_h * prob.n_t
+    tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(wl["dim"], wl["n"])], f1.shape[1])
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -608,7 +635,8 @@ def main():
         "config": {"workload": f"{args.workload}: {wl['dim']}D heat, Q1 {wl['n']}^{wl['dim']} interior grid, "
                                f"n_t={wl['n_t']}, T={wl['T']}, {wl['rhs']} load",
                    "n_h": prob.n_h, "n_t": prob.n_t, "precision": "fp64" if prec == st.ST_FP64 else "mixed",
-                   "tol": 1e-8, "l2": "flushed between steps (256 MB read)", "parallelism": f"replicas{world}"},
+                   "tol": 1e-8, "l2": "flushed between steps (256 MB read)",
+                   "autotune": {"shapes": tune[0], "seconds": tune[1]}, "parallelism": f"replicas{world}"},
         "solver": {"status": last["status"], "iterations": s["iterations"], "basis_cols": s["basis_cols"],
                    "rank": s["rank"], "relres": s["relres"], "relres_certified": relres_cert,
                    "mu_mem": s["mu_mem"], "residual_checks": s["residual_checks"],

@@ -192,6 +192,37 @@ int st_shift_solve_noalloc(st_problem* p, double s, const double* X, int ldx, in
 /* st_shift_solve_noalloc_max -- capacity of that scratch array in doubles. */
 unsigned long st_shift_solve_noalloc_max(void);
 
+/* st_autotune -- pick, by timing on this GPU, the launch variants of the
+ * kernels behind the shifted solves of Section 4 for this problem's shapes
+ * (the paper has no counterpart: its solves ran on CPUs).  Tuned: the tile
+ * edge (16, 32 or 64) of the fast-diagonalisation mode products, and the
+ * x-line tridiagonal solve of the convection-diffusion preconditioner (a warp
+ * per row for rows of at most 256 points, or a thread per row loading 64 or
+ * 16 steps at a time).  Runs st_shift_solve once at shift s (same domain) on
+ * ncols (1..16) internal seeded columns in the given precision; the first
+ * launch of each shape missing from the table runs every valid variant on
+ * its own operands, four interleaved rounds of three launches timed with
+ * CUDA events on the handle's stream (the first round discarded), and keeps
+ * the fastest, unless it beats the built-in choice by 3% or less.  The
+ * choices are kept, process-wide, for every later launch of the same kernel
+ * shape on any handle and thread (a shape: precision, grid direction and
+ * length, columns per launch); RKSM solves with p columns after rank
+ * compression use the shapes of ncols = p.  All variants compute the same
+ * quantity; they may differ in rounding.  Allocates and frees 3 n_h ncols
+ * doubles of device memory (besides the handle workspace st_shift_solve
+ * may grow); synchronises; call it with the GPU otherwise
+ * idle, outside stream capture (a captured stream is never tuned).  *tuned
+ * (may be NULL): shapes added.  Errors: ST_EINVAL, ST_ENOTSUP (as
+ * st_shift_solve), ST_ENOMEM, ST_ECUDA. */
+int st_autotune(st_problem* p, double s, int ncols, int precision, int* tuned);
+
+/* st_autotune_reset -- forget every tuned choice; later launches take the
+ * built-in choices again.  Not to be called while solves run. */
+int st_autotune_reset(void);
+
+/* st_autotune_count -- number of kernel shapes with a tuned choice. */
+int st_autotune_count(void);
+
 /* st_solve -- rational Krylov Galerkin projection (RKSM) for (1) (Section 4):
  * compress F to a full-column-rank F1 (QR + SVD), grow an orthonormal basis
  * V of the rational Krylov space of the pencil (A, M) started from M^{-1} F1

@@ -35,7 +35,7 @@ ABI_SYMBOLS = (
     "st_error_string", "st_last_error", "st_launch_count", "st_profile_begin", "st_profile_end",
     "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
-    "st_executor_destroy", "st_executor_set_policy",
+    "st_executor_destroy", "st_executor_set_policy", "st_autotune", "st_autotune_reset", "st_autotune_count",
 )
 
 
@@ -120,6 +120,9 @@ def lib() -> C.CDLL:
         "st_launch_count": ([], C.c_ulonglong),
         "st_shift_solve_noalloc": ([vp, d, vp, i, i, vp, i], i),
         "st_shift_solve_noalloc_max": ([], C.c_ulong),
+        "st_autotune": ([vp, d, i, i, C.POINTER(i)], i),
+        "st_autotune_reset": ([], i),
+        "st_autotune_count": ([], i),
         "st_set_coefficients": ([vp, i, d, d, vp], i),
         "st_request_bytes": ([C.POINTER(StDesc), i], d),
         "st_executor_create": ([i, d, C.POINTER(vp)], i),
@@ -302,6 +305,12 @@ class Problem:
         _check(lib().st_shift_solve(self.h, float(s), px, lx, m, pw, lw, int(precision)), "st_shift_solve")
         return W
 
+    def autotune(self, s: float, ncols: int, precision: int = ST_FP64) -> int:
+        """Times the shifted solve's launch variants for this problem's shapes; returns the shapes added."""
+        n = C.c_int(0)
+        _check(lib().st_autotune(self.h, float(s), int(ncols), int(precision), C.byref(n)), "st_autotune")
+        return n.value
+
     def solve(self, F1, F2, U_dense=None, ok=(ST_OK,)):
         """Returns (V, Y, stats, status); V, Y are views of library-owned memory."""
         import torch
@@ -428,6 +437,16 @@ class Executor:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(lib().st_launch_count())
+
+
+def autotune_reset():
+    """Forget every tuned launch choice (later launches take the built-in choices)."""
+    _check(lib().st_autotune_reset(), "st_autotune_reset")
+
+
+def autotune_count() -> int:
+    """Number of kernel shapes with a tuned launch choice in this process."""
+    return int(lib().st_autotune_count())
 
 
 def profile_begin():

@@ -37,6 +37,25 @@ void st_capture_leave();
 void st_prof_begin(cudaStream_t s, const char* tag, double bytes, double flops);
 void st_prof_end(cudaStream_t s);
 
+// Launch-variant tuning (st_tune.h).  While a session is set on the calling
+// thread, a launcher whose shape is missing from the table times each valid
+// variant on the launch's own operands, records the pick and then launches it.
+struct StTuneSession {
+    void* scratch = nullptr;   // device bytes for saving the input of an in-place launch
+    size_t scratch_bytes = 0;
+    int tuned = 0;             // shapes this session added to the table
+};
+void st_tune_set_session(StTuneSession* sess);
+// The calling thread's session, or nullptr when none is set or s is being captured.
+StTuneSession* st_tune_session(cudaStream_t s);
+// Times n launch variants on stream s: run(c) launches variant c (valid[c]
+// only); prep, if given, runs before every launch outside the timed span (it
+// restores the input of an in-place launch).  Four rounds (the first a
+// warm-up) of three launches a variant, interleaved; ms[c] = the best round's
+// time, or -1 for an invalid variant.  Synchronises s.
+int st_tune_measure(cudaStream_t s, int n, const bool* valid, const std::function<void(int)>& run,
+                    const std::function<int()>& prep, double* ms);
+
 // One device allocation owned by a handle.
 struct DevArray {
     void* ptr = nullptr;

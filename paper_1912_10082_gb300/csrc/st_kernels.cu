@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "st_common.cuh"
+#include "st_tune.h"
 
 namespace {
 
@@ -801,29 +802,54 @@ int launch_gemm_fold(int n, int other, const T* X, long long ldx, const T* const
     if (n <= 0 || other <= 0 || batch <= 0) return ST_OK;
     const int K0 = (n + 1) / 2, K1 = n / 2;
     const int M = SIDE == 0 ? other : K0, N = SIDE == 0 ? K0 : other;
-    // tile choice as for the unfolded product, over both parities
-    int bm = 64;
+    // built-in tile choice: the fewest tile rows per SM over both parities
+    constexpr int kEdge[3] = {16, 32, 64};
+    int def = 2;
     double best = 1e300;
-    for (int e : {64, 32, 16}) {
+    for (int c = 2; c >= 0; --c) {
+        const int e = kEdge[c];
         long long tiles = (long long)((N + e - 1) / e) * ((M + e - 1) / e) * batch * 2;
         double eff = sizeof(T) == 8 ? 1.0 : (double)e / 64.0;
         double share = (double)((tiles + 151) / 152) * e * e / eff;
         if (share < 0.999 * best) {
             best = share;
-            bm = e;
+            def = c;
         }
     }
-    dim3 grid((N + bm - 1) / bm, (M + bm - 1) / bm, 2 * batch);
-    if (grid.y > 65535 || grid.z > 65535) return ST_EINVAL;
+    auto fits = [&](int c) {
+        const int e = kEdge[c];
+        return (M + e - 1) / e <= 65535 && 2LL * batch <= 65535;
+    };
+    auto go = [&](int c) {
+        const int e = kEdge[c];
+        dim3 grid((N + e - 1) / e, (M + e - 1) / e, 2 * batch);
+        if (e == 16)
+            k_gemm_fold<T, 1, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+        else if (e == 32)
+            k_gemm_fold<T, 2, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+        else
+            k_gemm_fold<T, 4, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+    };
+    const sttune::Key key{sttune::FOLD, (int)sizeof(T), SIDE, n, other, batch};
+    int c = sttune::table().get(key);
+    if (c < 0) {
+        if (StTuneSession* ts = st_tune_session(s)) {
+            // every variant writes all of C from X and the tables (no aliasing), so the
+            // candidates may run on the launch's own operands
+            bool valid[3] = {fits(0), fits(1), fits(2)};
+            double ms[3];
+            ST_TRY(st_tune_measure(s, 3, valid, go, nullptr, ms));
+            c = sttune::pick(ms, 3, def, 0.03);
+            sttune::table().put(key, c);
+            ++ts->tuned;
+        }
+    }
+    if (c < 0 || !fits(c)) c = def;
+    if (!fits(c)) return ST_EINVAL;
     double fma = (double)other * ((double)K0 * K0 + (double)K1 * K1) * batch;
     double bytes = (double)sizeof(T) * ((double)K0 * K0 + (double)K1 * K1 + 2.0 * (double)other * n * batch);
     st_prof_begin(s, tag, bytes, 2.0 * fma);
-    if (bm == 16)
-        k_gemm_fold<T, 1, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
-    else if (bm == 32)
-        k_gemm_fold<T, 2, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
-    else
-        k_gemm_fold<T, 4, SIDE><<<grid, 256, 0, s>>>(n, other, X, ldx, HG[0], HG[1], HG[2], HG[3], C, ldc, bt, ep);
+    go(c);
     st_prof_end(s);
     ST_LAUNCH_CHECK();
     return ST_OK;
@@ -1740,6 +1766,73 @@ __global__ void __launch_bounds__(128) k_line_solve_warp(int nx, int nmodes, int
 // ---------------------------------------------------------------------------
 // host wrappers
 // ---------------------------------------------------------------------------
+namespace {
+thread_local StTuneSession* t_tune = nullptr;
+}
+
+void st_tune_set_session(StTuneSession* sess) { t_tune = sess; }
+
+StTuneSession* st_tune_session(cudaStream_t s) {
+    if (!t_tune) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();   // the query's error must not surface at a later launch check
+        return nullptr;
+    }
+    return cs == cudaStreamCaptureStatusNone ? t_tune : nullptr;
+}
+
+int st_tune_measure(cudaStream_t s, int n, const bool* valid, const std::function<void(int)>& run,
+                    const std::function<int()>& prep, double* ms) {
+    constexpr int kRounds = 4, kReps = 3;
+    std::vector<cudaEvent_t> ev((size_t)2 * kRounds * n * kReps, nullptr);
+    int rc = ST_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            rc = ST_ECUDA;
+        }
+    for (int r = 0; r < kRounds && rc == ST_OK; ++r)
+        for (int c = 0; c < n && rc == ST_OK; ++c) {
+            if (!valid[c]) continue;
+            for (int q = 0; q < kReps && rc == ST_OK; ++q) {
+                if (prep) rc = prep();
+                if (rc != ST_OK) break;
+                const size_t i = 2 * (((size_t)r * n + c) * kReps + q);
+                cudaEventRecord(ev[i], s);
+                run(c);
+                st_count_launch();
+                if (cudaGetLastError() != cudaSuccess) rc = ST_ECUDA;
+                cudaEventRecord(ev[i + 1], s);
+            }
+        }
+    if (rc == ST_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = ST_ECUDA;
+    std::vector<double> t((size_t)kRounds * n, -1.0);
+    for (int r = 0; r < kRounds && rc == ST_OK; ++r)
+        for (int c = 0; c < n; ++c) {
+            if (!valid[c]) continue;
+            double sum = 0.0;
+            for (int q = 0; q < kReps; ++q) {
+                const size_t i = 2 * (((size_t)r * n + c) * kReps + q);
+                float e = 0.f;
+                if (cudaEventElapsedTime(&e, ev[i], ev[i + 1]) != cudaSuccess) {
+                    rc = ST_ECUDA;
+                    break;
+                }
+                sum += e;
+            }
+            t[(size_t)r * n + c] = sum;
+        }
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc != ST_OK) {
+        st_note_msg("autotune: a timed launch failed");
+        return rc;
+    }
+    sttune::reduce_rounds(t.data(), kRounds, n, ms);
+    return ST_OK;
+}
+
 template <typename T>
 int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, cudaStream_t s) {
     const T* pv;
@@ -2115,32 +2208,62 @@ static int line_apply_impl(st_problem* p, double coef, const T* X, int ldx, int 
     };
     auto solve = [&](const T* src, long long lds, T* dst, long long ldd) -> int {
         const long long rows = (long long)nmodes * ncols;
+        const double* l1 = dim > 1 ? p->ax[1].lam : nullptr;
+        const double* l2 = dim > 2 ? p->ax[2].lam : nullptr;
+        const double* g1 = dim > 1 ? p->ax[1].c2 : nullptr;
+        const double* g2 = dim > 2 ? p->ax[2].c2 : nullptr;
+        // variants: 0 a warp per row (partition method, rows of at most 256 points);
+        // 1 a thread per row, loads in batches of 64 steps; 2 the same with 16 steps
+        // (fewer registers on many rows)
+        auto go = [&](int c) {
+            if (c == 0)
+                k_line_solve_warp<T><<<(unsigned)((rows + 3) / 4), 128, 0, s>>>(
+                    nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift, l1, l2, g1,
+                    g2, coef);
+            else if (c == 1)
+                k_line_solve<T, 64><<<(unsigned)((rows + 63) / 64), 64, 0, s>>>(
+                    nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift, l1, l2, g1,
+                    g2, coef);
+            else
+                k_line_solve<T, 16><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(
+                    nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift, l1, l2, g1,
+                    g2, coef);
+        };
+        // built-in choice: few rows (a 2D grid: N_y p) and short rows take a warp per row
+        // (2D 255^2: 58 -> 13 us a launch; on 63^3, 7938 rows, the thread per row is
+        // faster); the sweeps are latency-bound, so each batch of loads covers 64 steps,
+        // except FP64 on many rows: 16, which keeps the registers below 128
+        const int def = (rows < 2048 && nx <= 256) ? 0 : ((rows < 8192 || sizeof(T) == 4) ? 1 : 2);
+        const sttune::Key key{sttune::LINE, (int)sizeof(T), nx, (int)std::min<long long>(rows, 1LL << 30), dim, 0};
+        int c = sttune::table().get(key);
+        const size_t col_bytes = sizeof(T) * (size_t)nh;
+        const bool in_place = (const void*)src == (const void*)dst;
+        StTuneSession* ts = c < 0 ? st_tune_session(s) : nullptr;
+        if (ts && (!in_place || ts->scratch_bytes >= col_bytes * ncols)) {
+            // an in-place solve is timed on a saved copy of its input, restored before
+            // every launch and once more before the launch that counts
+            std::function<int()> restore;
+            if (in_place) {
+                ST_CUDA_TRY(cudaMemcpy2DAsync(ts->scratch, col_bytes, src, sizeof(T) * lds, col_bytes, ncols,
+                                              cudaMemcpyDeviceToDevice, s));
+                restore = [&]() -> int {
+                    ST_CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(T) * ldd, ts->scratch, col_bytes, col_bytes, ncols,
+                                                  cudaMemcpyDeviceToDevice, s));
+                    return ST_OK;
+                };
+            }
+            bool valid[3] = {nx <= 256, true, true};
+            double ms[3];
+            ST_TRY(st_tune_measure(s, 3, valid, go, restore, ms));
+            c = sttune::pick(ms, 3, def, 0.03);
+            sttune::table().put(key, c);
+            ++ts->tuned;
+            if (in_place) ST_TRY(restore());
+        }
+        if (c < 0 || (c == 0 && nx > 256)) c = def;
         st_prof_begin(s, sizeof(T) == 8 ? "line64" : "line32", 4.0 * sizeof(T) * (double)nh * ncols,
                       5.0 * (double)nh * ncols);
-        // few rows (a 2D grid: N_y p) and short rows: a warp per row, partition method
-        // (2D 255^2: 58 -> 13 us a launch; on 63^3, 7938 rows, the thread per row is faster)
-        if (rows < 2048 && nx <= 256) {
-            k_line_solve_warp<T><<<(unsigned)((rows + 3) / 4), 128, 0, s>>>(
-                nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
-                dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
-                dim > 2 ? p->ax[2].c2 : nullptr, coef);
-            st_prof_end(s);
-            ST_LAUNCH_CHECK();
-            return ST_OK;
-        }
-        // the sweeps are latency-bound (few warps per SM even on 127^3: one thread per row),
-        // so each batch of loads covers 64 steps; FP64 on many rows: 16, which keeps the
-        // registers below 128
-        if (rows < 8192 || sizeof(T) == 4)
-            k_line_solve<T, 64><<<(unsigned)((rows + 63) / 64), 64, 0, s>>>(
-                nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
-                dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
-                dim > 2 ? p->ax[2].c2 : nullptr, coef);
-        else
-        k_line_solve<T, 16><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(
-            nx, nmodes, ny, dim, ncols, src, lds, dst, ldd, CP, IP, hx, eps, bx, p->line_shift,
-            dim > 1 ? p->ax[1].lam : nullptr, dim > 2 ? p->ax[2].lam : nullptr, dim > 1 ? p->ax[1].c2 : nullptr,
-            dim > 2 ? p->ax[2].c2 : nullptr, coef);
+        go(c);
         st_prof_end(s);
         ST_LAUNCH_CHECK();
         return ST_OK;

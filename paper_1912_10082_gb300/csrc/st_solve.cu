@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "st_common.cuh"
+#include "st_tune.h"
 
 int st_slot(st_problem* p, int id, size_t bytes, void** out) {
     if (id < 0 || id >= 32) return ST_EINVAL;
@@ -1518,6 +1519,56 @@ extern "C" int st_shift_solve(st_problem* p, double s, const double* X, int ldx,
     }
     return ST_OK;
 }
+
+extern "C" int st_autotune(st_problem* p, double s, int ncols, int precision, int* tuned) {
+    if (tuned) *tuned = 0;
+    if (!p || ncols < 1 || ncols > 16) return ST_EINVAL;
+    if (precision != ST_FP64 && precision != ST_MIXED) return ST_EINVAL;
+    if (!p->tensor_heat && !(p->dim >= 1 && p->d.op == ST_CONVDIFF)) return ST_ENOTSUP;
+    if (!(s > -p->lam_min)) return ST_EINVAL;
+    const size_t n = (size_t)p->n_h, bytes = sizeof(double) * n * (size_t)ncols;
+    // seeded values in [-1, 1) from an integer hash: the solve must do real work (a
+    // zero right-hand side would stop FGMRES before its first preconditioner call)
+    std::vector<double> h(n * (size_t)ncols);
+    for (size_t e = 0; e < h.size(); ++e) {
+        uint32_t x = (uint32_t)e * 2654435761u + 0x9e3779b9u;
+        x ^= x >> 15;
+        x *= 0x85ebca6bu;
+        x ^= x >> 13;
+        h[e] = (double)(x >> 8) / 8388608.0 - 1.0;
+    }
+    double *X = nullptr, *W = nullptr;
+    void* scratch = nullptr;
+    int rc = ST_OK;
+    if (cudaMalloc(&X, bytes) != cudaSuccess || cudaMalloc(&W, bytes) != cudaSuccess ||
+        cudaMalloc(&scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();   // a failed allocation must not surface at a later launch check
+        st_note_msg("st_autotune: device allocation failed");
+        rc = ST_ENOMEM;
+    }
+    if (rc == ST_OK && cudaMemcpy(X, h.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) rc = ST_ECUDA;
+    if (rc == ST_OK) {
+        StTuneSession sess;
+        sess.scratch = scratch;
+        sess.scratch_bytes = bytes;
+        st_tune_set_session(&sess);
+        rc = st_shift_solve(p, s, X, (int)n, ncols, W, (int)n, precision);
+        st_tune_set_session(nullptr);
+        if (cudaStreamSynchronize(p->stream) != cudaSuccess && rc == ST_OK) rc = ST_ECUDA;
+        if (tuned) *tuned = sess.tuned;
+    }
+    cudaFree(X);
+    cudaFree(W);
+    cudaFree(scratch);
+    return rc;
+}
+
+extern "C" int st_autotune_reset(void) {
+    sttune::table().clear();
+    return ST_OK;
+}
+
+extern "C" int st_autotune_count(void) { return sttune::table().size(); }
 
 extern "C" int st_residual(st_problem* p, const double* U, int ldu, const double* F1, int ldf1, const double* F2,
                            int ldf2, int ncols, double* relres) {
