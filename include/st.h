@@ -223,6 +223,26 @@ int st_autotune_reset(void);
 /* st_autotune_count -- number of kernel shapes with a tuned choice. */
 int st_autotune_count(void);
 
+/* st_autotune_save -- write every tuned choice to a text file at path
+ * ("st-autotune 1", "device <device_tag>", then one sorted line per shape),
+ * so that a later process on the same kind of GPU can skip the timing.
+ * device_tag: caller-chosen identity of the GPU (name, SM count, compute
+ * capability...), non-empty, at most 199 characters, no line breaks.  Host
+ * only; no CUDA call.  Errors: ST_EINVAL (NULL or bad tag, file not writable;
+ * text in st_last_error). */
+int st_autotune_save(const char* path, const char* device_tag);
+
+/* st_autotune_load -- add the choices of a file written by st_autotune_save
+ * to the table (replacing those of the same shapes) when its device tag
+ * equals device_tag; otherwise load nothing and return ST_OK with
+ * *loaded = 0.  Entries of unknown kernel families, element sizes or variant
+ * indices are skipped; every loaded choice is still checked against the
+ * shape of each launch before use (a variant that cannot run the shape is
+ * replaced by the built-in choice).  *loaded (may be NULL): entries added.
+ * Host only; no CUDA call.  Errors: ST_EINVAL (NULL or bad tag, unreadable
+ * file, bad header, a malformed line: then nothing is loaded). */
+int st_autotune_load(const char* path, const char* device_tag, int* loaded);
+
 /* st_solve -- rational Krylov Galerkin projection (RKSM) for (1) (Section 4):
  * compress F to a full-column-rank F1 (QR + SVD), grow an orthonormal basis
  * V of the rational Krylov space of the pencil (A, M) started from M^{-1} F1

@@ -36,6 +36,7 @@ ABI_SYMBOLS = (
     "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
     "st_executor_destroy", "st_executor_set_policy", "st_autotune", "st_autotune_reset", "st_autotune_count",
+    "st_autotune_save", "st_autotune_load",
 )
 
 
@@ -123,6 +124,8 @@ def lib() -> C.CDLL:
         "st_autotune": ([vp, d, i, i, C.POINTER(i)], i),
         "st_autotune_reset": ([], i),
         "st_autotune_count": ([], i),
+        "st_autotune_save": ([C.c_char_p, C.c_char_p], i),
+        "st_autotune_load": ([C.c_char_p, C.c_char_p, C.POINTER(i)], i),
         "st_set_coefficients": ([vp, i, d, d, vp], i),
         "st_request_bytes": ([C.POINTER(StDesc), i], d),
         "st_executor_create": ([i, d, C.POINTER(vp)], i),
@@ -447,6 +450,27 @@ def autotune_reset():
 def autotune_count() -> int:
     """Number of kernel shapes with a tuned launch choice in this process."""
     return int(lib().st_autotune_count())
+
+
+def device_tag(device=None) -> str:
+    """Identity of a CUDA device for the tuning cache: name, compute capability and SM count."""
+    import torch
+    pr = torch.cuda.get_device_properties(torch.cuda.current_device() if device is None else device)
+    return f"{pr.name} sm_{pr.major}{pr.minor} {pr.multi_processor_count}SM"
+
+
+def autotune_save(path, tag: str | None = None):
+    """Write the tuned launch choices to a file (tag: device identity; default: the current CUDA device's)."""
+    tag = device_tag() if tag is None else tag
+    _check(lib().st_autotune_save(str(path).encode(), tag.encode()), "st_autotune_save")
+
+
+def autotune_load(path, tag: str | None = None) -> int:
+    """Add the choices of a tuning cache written for the same device tag; returns the entries added."""
+    tag = device_tag() if tag is None else tag
+    n = C.c_int(0)
+    _check(lib().st_autotune_load(str(path).encode(), tag.encode(), C.byref(n)), "st_autotune_load")
+    return n.value
 
 
 def profile_begin():

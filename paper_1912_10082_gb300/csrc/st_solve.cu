@@ -5,6 +5,8 @@
 // projections).  Host work (Grace cores): the k x k projected problems, the
 // adaptive shifts and the time recurrence of the projected equation.
 #include <algorithm>
+#include <array>
+#include <cstdio>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -1569,6 +1571,83 @@ extern "C" int st_autotune_reset(void) {
 }
 
 extern "C" int st_autotune_count(void) { return sttune::table().size(); }
+
+// Tuning cache file (text): "st-autotune 1", "device <tag>", then one line
+// "family tsize a b c d choice" per entry, sorted.
+namespace {
+bool valid_tag(const char* tag) {
+    if (!tag || !*tag) return false;
+    size_t n = 0;
+    for (const char* c = tag; *c; ++c, ++n)
+        if (*c == '\n' || *c == '\r') return false;
+    return n < 200;
+}
+}  // namespace
+
+extern "C" int st_autotune_save(const char* path, const char* device_tag) {
+    if (!path || !valid_tag(device_tag)) return ST_EINVAL;
+    std::vector<std::array<int, 7>> rows;
+    sttune::table().for_each([&](const sttune::Key& k, int v) {
+        rows.push_back({k.family, k.tsize, k.a, k.b, k.c, k.d, v});
+    });
+    std::sort(rows.begin(), rows.end());
+    FILE* f = std::fopen(path, "w");
+    if (!f) {
+        st_note_msg("st_autotune_save: cannot open the file for writing");
+        return ST_EINVAL;
+    }
+    bool ok = std::fprintf(f, "st-autotune 1\ndevice %s\n", device_tag) > 0;
+    for (const auto& r : rows)
+        ok = ok && std::fprintf(f, "%d %d %d %d %d %d %d\n", r[0], r[1], r[2], r[3], r[4], r[5], r[6]) > 0;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) st_note_msg("st_autotune_save: write failed");
+    return ok ? ST_OK : ST_EINVAL;
+}
+
+extern "C" int st_autotune_load(const char* path, const char* device_tag, int* loaded) {
+    if (loaded) *loaded = 0;
+    if (!path || !valid_tag(device_tag)) return ST_EINVAL;
+    FILE* f = std::fopen(path, "r");
+    if (!f) {
+        st_note_msg("st_autotune_load: cannot open the file");
+        return ST_EINVAL;
+    }
+    char line[512];
+    auto next = [&]() -> bool {
+        if (!std::fgets(line, sizeof(line), f)) return false;
+        size_t n = std::strlen(line);
+        while (n > 0 && (line[n - 1] == '\n' || line[n - 1] == '\r')) line[--n] = '\0';
+        return true;
+    };
+    int rc = ST_OK;
+    std::vector<std::pair<sttune::Key, int>> rows;
+    if (!next() || std::strcmp(line, "st-autotune 1") != 0 || !next() || std::strncmp(line, "device ", 7) != 0) {
+        st_note_msg("st_autotune_load: not a tuning cache (header)");
+        rc = ST_EINVAL;
+    } else if (std::strcmp(line + 7, device_tag) != 0) {
+        st_note_msg("st_autotune_load: the cache was written for another device; nothing loaded");
+    } else {
+        while (next()) {
+            if (line[0] == '\0') continue;
+            int v[7];
+            char extra;
+            if (std::sscanf(line, "%d %d %d %d %d %d %d %c", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                            &extra) != 7) {
+                st_note_msg("st_autotune_load: malformed entry; nothing loaded");
+                rc = ST_EINVAL;
+                break;
+            }
+            const sttune::Key k{v[0], v[1], v[2], v[3], v[4], v[5]};
+            if (sttune::plausible(k, v[6])) rows.push_back({k, v[6]});
+        }
+    }
+    std::fclose(f);
+    if (rc != ST_OK) return rc;
+    // a loaded choice is still checked against its launch's shape before use
+    for (const auto& r : rows) sttune::table().put(r.first, r.second);
+    if (loaded) *loaded = (int)rows.size();
+    return ST_OK;
+}
 
 extern "C" int st_residual(st_problem* p, const double* U, int ldu, const double* F1, int ldf1, const double* F2,
                            int ldf2, int ncols, double* relres) {

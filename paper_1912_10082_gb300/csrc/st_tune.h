@@ -59,12 +59,26 @@ public:
         n_.store(0, std::memory_order_release);
     }
     int size() const { return n_.load(std::memory_order_acquire); }
+    // Calls f(key, choice) for every entry, under the lock (f must not use the table).
+    template <class F>
+    void for_each(F f) const {
+        std::lock_guard<std::mutex> g(mu_);
+        for (const auto& kv : m_) f(kv.first, kv.second);
+    }
 
 private:
     mutable std::mutex mu_;
     std::unordered_map<Key, int, KeyHash> m_;
     std::atomic<int> n_{0};
 };
+
+// Whether a stored entry can describe a launch of this library: a known
+// family, element size 4 or 8, a variant index below the family's count.
+inline bool plausible(const Key& k, int choice) {
+    if (k.family != FOLD && k.family != LINE) return false;
+    if (k.tsize != 4 && k.tsize != 8) return false;
+    return choice >= 0 && choice < 3;
+}
 
 inline Table& table() {
     static Table t;

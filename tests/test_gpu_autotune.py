@@ -158,6 +158,25 @@ def test_tuned_choices_inside_a_captured_cn_graph():
     assert relerr(out, ref) <= 1e-12
 
 
+def test_tuning_cache_round_trip(tmp_path):
+    """Choices tuned on this GPU, saved, forgotten and loaded again drive the same (bitwise equal) heat solve."""
+    dim, n, s = 2, (45, 38), 40.0
+    M, A = fem.tensor_operators(dim, n)
+    X = np.random.default_rng(26).standard_normal((M.shape[0], 2))
+    ref = np.linalg.solve((A + s * M).toarray(), M @ X)
+    path = tmp_path / "tune.txt"
+    with st.Problem(dim, n, 4, 1.0) as prob:
+        added = prob.autotune(s, 2)
+        tuned = host(prob.shift_solve(s, dev(X)))
+        st.autotune_save(path)
+        st.autotune_reset()
+        assert st.autotune_load(path, "another device") == 0 and st.autotune_count() == 0
+        assert st.autotune_load(path) == added and st.autotune_count() == added
+        loaded = host(prob.shift_solve(s, dev(X)))
+    assert relerr(tuned, ref) <= 1e-12
+    assert np.array_equal(tuned, loaded)
+
+
 def test_autotune_rejects_bad_arguments():
     L = st.lib()
     with st.Problem(2, 9, 4, 1.0) as prob:
