@@ -18,13 +18,18 @@ rhs       manufactured loads with exact integrals; trapezoidal loads (Section 3)
 cn        Crank-Nicolson time stepping (Section 3 remark, Section 5)
 residual  relative residual norms of dense and low-rank iterates (Section 4)
 rksm      rational Krylov Galerkin projection (RKSM) reference (Section 4)
+lrfgmres  low-rank flexible GMRES preconditioned by RKSM, the comparison solver
+          of Section 5, Example 1 (Table 1)
 
 Pins (tests marked ``not gpu``): closed-form 1D generalised eigenpairs, Gauss
 quadrature of every matrix entry from the basis functions, an exact rational
 solve of a tiny system, Crank-Nicolson equivalence, the manufactured closed form,
-second-order convergence, and the Galerkin invariants of the RKSM reference.
+second-order convergence, and the Galerkin invariants of the RKSM reference;
+for LR-FGMRES+RKSM the Eckart-Young truncation error, GMRES's minimal residual
+over the explicit Krylov space, one step with an exact preconditioner and the
+direct solution.
 Parity unpinned: the RKSM iteration counts and shift sequence (the paper only
 says the shifts are chosen adaptively); the converged solution is pinned.
 """
 
-from . import fem, timefe, kron, rhs, cn, residual, rksm  # noqa: F401
+from . import fem, timefe, kron, rhs, cn, residual, rksm, lrfgmres  # noqa: F401
