@@ -304,7 +304,9 @@ int st_set_coefficients(st_problem* p, int op, double kappa, double eps, const d
 /* st_error_string -- static text for a status code. */
 const char* st_error_string(int status);
 
-/* st_last_error -- text of the last CUDA failure seen by this thread. */
+/* st_last_error -- text of the last failure recorded on the calling thread:
+ * a CUDA error (call, file, line) or a message of a call that returned an
+ * error status (sizes, files, solver state).  Per thread; never cleared. */
 const char* st_last_error(void);
 
 /* ---- many independent solves on one GPU: batched and served workloads ----
