@@ -133,8 +133,45 @@ def make_inputs(st, prob, wl, torch):
     return f1, f2
 
 
-def roofline_of(prof, hbm_gbs):
-    """Dominant kernel of a profiled region and its roofline position."""
+FAMILY_TAGS = {(1, 8): "fd_gemm64", (1, 4): "fd_gemm32", (2, 8): "line64", (2, 4): "line32"}
+VARIANTS = {1: ("tile16", "tile32", "tile64"), 2: ("warp_per_row", "thread_64_steps", "thread_16_steps")}
+
+
+def tuned_choices(st):
+    """The process's tuned launch choices as (family, element size, a, b, c, d, variant) rows, read back through
+    the library's cache writer (host only); None if that fails."""
+    import os
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".txt")
+    os.close(fd)
+    try:
+        st.autotune_save(path, "bench")
+        lines = Path(path).read_text().splitlines()[2:]
+        return [tuple(int(x) for x in ln.split()) for ln in lines if ln.strip()]
+    except Exception:
+        return None
+    finally:
+        os.unlink(path)
+
+
+def choice_summary(rows):
+    """{kernel tag: {variant name: shapes}} of tuned choice rows."""
+    if rows is None:
+        return None
+    out = {}
+    for fam, tsize, *_, v in rows:
+        tag = FAMILY_TAGS.get((fam, tsize), f"family{fam}_{tsize}")
+        name = VARIANTS.get(fam, ())[v] if 0 <= v < len(VARIANTS.get(fam, ())) else str(v)
+        out.setdefault(tag, {}).setdefault(name, 0)
+        out[tag][name] += 1
+    return out
+
+
+def roofline_of(prof, hbm_gbs, choices=None):
+    """Dominant kernel of a profiled region and its roofline position.  ``traffic`` (DRAM bytes per launch from
+    one ncu capture, profiles/traffic.json) is reported only while every tuned shape of that kernel runs the
+    launch variant the capture measured (``choices``: the summary of choice_summary, None when nothing was
+    tuned)."""
     if not prof:
         return None
     tag, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -157,7 +194,9 @@ def roofline_of(prof, hbm_gbs):
     traffic_file = ROOT / "profiles" / "traffic.json"
     if traffic_file.exists():
         tr = json.loads(traffic_file.read_text()).get(tag)
-        if tr and tr.get("valid_for") == out["kernel"]:
+        tuned = (choices or {}).get(tag, {})
+        same_variant = all(name == tr.get("variant") for name in tuned) if tr else False
+        if tr and tr.get("valid_for") == out["kernel"] and same_variant:
             out["traffic"] = tr.get("bytes_per_launch")
     return out
 
@@ -284,6 +323,7 @@ def bench_batched(args, wl, rank, world, local):
     slots = args.slots
     dof = sum(r["n"] ** 2 * r["n_t"] for r in insts)
     tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(2, r["n"]) for r in insts], wl["p"])
+    choices = choice_summary(tuned_choices(st)) if tune[0] else None
 
     def timed(prec, method, steps, warmup, data):
         res = None
@@ -345,7 +385,7 @@ def bench_batched(args, wl, rank, world, local):
         "config": {"workload": f"batched: {len(insts)} 2D heat instances, grid side from (63,127,255), n_t from "
                                f"(64,128,256,512), kappa 10^U(-1,1), rank-{wl['p']} Gaussian load, mixed precision",
                    "instances": len(insts), "dof": dof, "slots": slots, "tol": 1e-8,
-                   "autotune": {"shapes": tune[0], "seconds": tune[1]},
+                   "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
                    "l2": "inputs of the batch (%.0f MB) exceed L2" % (sum(r['F1'].nbytes for r in insts) / 1e6),
                    "parallelism": f"replicas{world}"},
         "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its)),
@@ -393,6 +433,7 @@ def bench_served(args, wl, rank, world, local):
     facs = [tuple(np.asfortranarray(x) for x in workloads.request_factors(r)) for r in reqs]
     tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(r["dim"], r["n"]) for r in reqs], wl["p"],
                                                             convdiff=True, precisions=(st.ST_MIXED,))
+    choices = choice_summary(tuned_choices(st)) if tune[0] else None
     lc = st.launch_count()
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
@@ -427,7 +468,8 @@ def bench_served(args, wl, rank, world, local):
                                f"{1e3 * gap:.2f} ms, heat and convection-diffusion, 1D/2D/3D n 63..127^3, "
                                f"n_t 64..512, rank-{wl['p']} Gaussian loads, mixed precision, tol 1e-8",
                    "slots": args.slots, "gap_scale": args.gap_scale, "policy": args.policy,
-                   "autotune": {"shapes": tune[0], "seconds": tune[1]}, "parallelism": f"replicas{world}"},
+                   "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
+                   "parallelism": f"replicas{world}"},
         "latency": {"p50_s": out["p50_s"], "p99_s": out["p99_s"], "per_kind": per_kind},
         "served": {"measured": out["measured"], "ok": out["ok"], "not_converged": out["not_converged"],
                    "wall_s": wall, "failures": failures},
@@ -501,6 +543,7 @@ def main():
     stream.synchronize()
     units = prob.n_h * prob.n_t
     tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(wl["dim"], wl["n"])], f1.shape[1])
+    choices = choice_summary(tuned_choices(st)) if tune[0] else None
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -550,7 +593,7 @@ def main():
         step()
     torch.cuda.synchronize()
     prof = st.profile_end()
-    roof = roofline_of(prof, pk["hbm_gbs"])
+    roof = roofline_of(prof, pk["hbm_gbs"], choices)
     if roof:
         roof["peak_source"] = pk["src"] if roof["unit"] == "GB/s" else "derived"
 
@@ -636,7 +679,8 @@ def main():
                                f"n_t={wl['n_t']}, T={wl['T']}, {wl['rhs']} load",
                    "n_h": prob.n_h, "n_t": prob.n_t, "precision": "fp64" if prec == st.ST_FP64 else "mixed",
                    "tol": 1e-8, "l2": "flushed between steps (256 MB read)",
-                   "autotune": {"shapes": tune[0], "seconds": tune[1]}, "parallelism": f"replicas{world}"},
+                   "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
+                   "parallelism": f"replicas{world}"},
         "solver": {"status": last["status"], "iterations": s["iterations"], "basis_cols": s["basis_cols"],
                    "rank": s["rank"], "relres": s["relres"], "relres_certified": relres_cert,
                    "mu_mem": s["mu_mem"], "residual_checks": s["residual_checks"],
