@@ -322,7 +322,7 @@ def bench_batched(args, wl, rank, world, local):
     torch.cuda.synchronize()
     slots = args.slots
     dof = sum(r["n"] ** 2 * r["n_t"] for r in insts)
-    tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(2, r["n"]) for r in insts], wl["p"])
+    tune = (0, 0.0) if args.autotune == "off" else autotune_grids(st, [(2, r["n"]) for r in insts], wl["p"])
     choices = choice_summary(tuned_choices(st)) if tune[0] else None
 
     def timed(prec, method, steps, warmup, data):
@@ -431,7 +431,7 @@ def bench_served(args, wl, rank, world, local):
     gap = wl["mean_gap_s"] * args.gap_scale
     reqs = workloads.served_requests(count=count, seed=wl["seed"], mean_gap_s=gap, p=wl["p"])
     facs = [tuple(np.asfortranarray(x) for x in workloads.request_factors(r)) for r in reqs]
-    tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(r["dim"], r["n"]) for r in reqs], wl["p"],
+    tune = (0, 0.0) if args.autotune == "off" else autotune_grids(st, [(r["dim"], r["n"]) for r in reqs], wl["p"],
                                                             convdiff=True, precisions=(st.ST_MIXED,))
     choices = choice_summary(tuned_choices(st)) if tune[0] else None
     lc = st.launch_count()
@@ -487,8 +487,10 @@ def main():
     ap.add_argument("--workload", default="heat2d")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the built-in launch choices (no timing of launch variants before the warm-up)")
+    ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
+                    help="time the shifted solves' launch variants before the warm-up and keep the fastest (auto: on "
+                         "for the batched and served workloads, off for single problems, which keep the launch "
+                         "variants the ncu traffic figures were captured on)")
     ap.add_argument("--slots", type=int, default=16, help="executor slots of the batched and served workloads")
     ap.add_argument("--requests", type=int, default=0, help="served workload: number of requests (0: all)")
     ap.add_argument("--gap-scale", type=float, default=1.0, help="served workload: scale of the mean arrival gap")
@@ -542,7 +544,7 @@ def main():
         f1, f2 = make_inputs(st, prob, wl, torch)
     stream.synchronize()
     units = prob.n_h * prob.n_t
-    tune = (0, 0.0) if args.no_autotune else autotune_grids(st, [(wl["dim"], wl["n"])], f1.shape[1])
+    tune = autotune_grids(st, [(wl["dim"], wl["n"])], f1.shape[1]) if args.autotune == "on" else (0, 0.0)
     choices = choice_summary(tuned_choices(st)) if tune[0] else None
 
     def timed(fn, steps, warmup):
