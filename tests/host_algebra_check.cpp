@@ -72,6 +72,52 @@ int main() {
                     hostpar::threads_for((double)n * n * n / 3.0), (int)same, e1 / na, e2);
         bad += !(same && acc);
     }
+    // one-sided Jacobi SVD (rank compression of F): graded singular values 1 .. 1e-14 between random
+    // orthogonal factors (Householder QR of Gaussian matrices), tall and square
+    for (int shape = 0; shape < 2; ++shape) {
+        const int sm = shape == 0 ? 15 : 12, sn = 12;
+        std::mt19937 g(11 + shape);
+        std::normal_distribution<double> nd;
+        std::vector<double> Gu((size_t)sm * sn), Gv((size_t)sn * sn), Ru((size_t)sn * sn), Rv((size_t)sn * sn);
+        for (auto& x : Gu) x = nd(g);
+        for (auto& x : Gv) x = nd(g);
+        dense::thin_qr(sm, sn, Gu.data(), sm, Ru.data(), sn);
+        dense::thin_qr(sn, sn, Gv.data(), sn, Rv.data(), sn);
+        std::vector<double> sig(sn), B((size_t)sm * sn, 0.0);
+        for (int k = 0; k < sn; ++k) sig[k] = std::pow(10.0, -14.0 * k / (sn - 1));
+        for (int c = 0; c < sn; ++c)
+            for (int r = 0; r < sm; ++r) {
+                double acc = 0;
+                for (int k = 0; k < sn; ++k) acc += Gu[(size_t)k * sm + r] * sig[k] * Gv[(size_t)k * sn + c];
+                B[(size_t)c * sm + r] = acc;
+            }
+        std::vector<double> U((size_t)sm * sn), sv(sn), Vt((size_t)sn * sn);
+        dense::svd_small(sm, sn, B.data(), sm, U.data(), sv.data(), Vt.data());
+        // reconstruction, orthogonality of V, orthonormality of U's columns with sigma above 1e-8
+        double rec = 0, orv = 0, oru = 0;
+        for (int c = 0; c < sn; ++c)
+            for (int r = 0; r < sm; ++r) {
+                double acc = 0;
+                for (int k = 0; k < sn; ++k) acc += U[(size_t)k * sm + r] * sv[k] * Vt[(size_t)c * sn + k];
+                rec = std::max(rec, std::fabs(acc - B[(size_t)c * sm + r]));
+            }
+        for (int a = 0; a < sn; ++a)
+            for (int b = 0; b < sn; ++b) {
+                double vv = 0, uu = 0;
+                for (int k = 0; k < sn; ++k) vv += Vt[(size_t)k * sn + a] * Vt[(size_t)k * sn + b];
+                for (int r = 0; r < sm; ++r) uu += U[(size_t)a * sm + r] * U[(size_t)b * sm + r];
+                orv = std::max(orv, std::fabs(vv - (a == b ? 1.0 : 0.0)));
+                if (sv[a] > 1e-8 && sv[b] > 1e-8) oru = std::max(oru, std::fabs(uu - (a == b ? 1.0 : 0.0)));
+            }
+        const bool ok = rec <= 1e-14 && orv <= 1e-13 && oru <= 1e-7;
+        std::printf("svd %dx%d rec=%.2e orthV=%.2e orthU=%.2e %s\n", sm, sn, rec, orv, oru, ok ? "ok" : "BAD");
+        bad += !ok;
+        std::printf("svdmat%d %d %d", shape, sm, sn);
+        for (double x : B) std::printf(" %.17g", x);
+        std::printf("\nsvdval%d", shape);
+        for (double x : sv) std::printf(" %.17g", x);
+        std::printf("\n");
+    }
     // eigenvalues of a fixed 40 x 40 matrix for the numpy comparison
     const int m = 40;
     std::vector<double> C = spd(m, 7), w(m);

@@ -47,3 +47,21 @@ def test_eigenvalues_match_numpy(run_check):
     ref = np.linalg.eigvalsh(C)
     assert np.all(np.diff(got) >= 0)
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_jacobi_svd_matches_numpy(run_check, shape):
+    """The one-sided Jacobi SVD behind the rank compression of F: graded singular values 1 .. 1e-14 (tall 15 x 12
+    and square 12 x 12) agree with LAPACK's to rounding of the largest."""
+    lines = run_check.stdout.splitlines()
+    head = [ln for ln in lines if ln.startswith(f"svdmat{shape} ")][0].split()
+    m, n = int(head[1]), int(head[2])
+    B = np.array([float(x) for x in head[3:]]).reshape(n, m).T
+    got = np.array([float(x) for x in [ln for ln in lines if ln.startswith(f"svdval{shape}")][0].split()[1:]])
+    ref = np.linalg.svd(B, compute_uv=False)
+    assert np.all(np.diff(got) <= 0)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * ref[0]
+    # the graded values themselves, well above rounding: 1, 10^(-14/11), ...
+    exact = 10.0 ** (-14.0 * np.arange(n) / (n - 1))
+    big = exact > 1e-10
+    assert np.max(np.abs(got[big] - exact[big]) / exact[big]) <= 1e-5
