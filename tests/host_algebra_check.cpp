@@ -72,6 +72,114 @@ int main() {
                     hostpar::threads_for((double)n * n * n / 3.0), (int)same, e1 / na, e2);
         bad += !(same && acc);
     }
+    // LU with partial pivoting (the convection-diffusion projected recurrence): A X = B and A^T X = B
+    for (int n : {7, 64, 301}) {
+        std::mt19937 g(100 + n);
+        std::normal_distribution<double> nd;
+        std::vector<double> A((size_t)n * n), B((size_t)n * 3);
+        for (auto& x : A) x = nd(g);
+        for (auto& x : B) x = nd(g);
+        std::vector<double> F = A, X = B, Xt = B;
+        std::vector<int> piv(n);
+        const bool ok = dense::lu(n, F.data(), n, piv.data());
+        dense::lu_solve(n, F.data(), n, piv.data(), X.data(), n, 3);
+        const bool okt = dense::lu_solve_transpose(n, F.data(), n, piv.data(), Xt.data(), n, 3);
+        double r = 0, rt = 0, na = 0, nx = 0, nxt = 0;
+        for (int c = 0; c < 3; ++c)
+            for (int i = 0; i < n; ++i) {
+                double s1 = 0, s2 = 0;
+                for (int k = 0; k < n; ++k) {
+                    s1 += A[(size_t)k * n + i] * X[(size_t)c * n + k];
+                    s2 += A[(size_t)i * n + k] * Xt[(size_t)c * n + k];
+                }
+                r = std::max(r, std::fabs(s1 - B[(size_t)c * n + i]));
+                rt = std::max(rt, std::fabs(s2 - B[(size_t)c * n + i]));
+                nx = std::max(nx, std::fabs(X[(size_t)c * n + i]));
+                nxt = std::max(nxt, std::fabs(Xt[(size_t)c * n + i]));
+            }
+        for (double x : A) na = std::max(na, std::fabs(x));
+        const bool acc = ok && okt && r <= 1e-13 * n * na * nx && rt <= 1e-13 * n * na * nxt;
+        std::printf("lu n=%d resid=%.2e resid_T=%.2e %s\n", n, r / (na * nx), rt / (na * nxt), acc ? "ok" : "BAD");
+        bad += !acc;
+    }
+    {
+        // a zero column: no pivot, reported
+        const int n = 5;
+        std::vector<double> A((size_t)n * n, 1.0);
+        for (int i = 0; i < n; ++i) A[(size_t)2 * n + i] = 0.0;
+        std::vector<int> piv(n);
+        const bool singular = !dense::lu(n, A.data(), n, piv.data());
+        std::printf("lu singular reported=%d\n", (int)singular);
+        bad += !singular;
+    }
+    // forward substitution on a thread team: bitwise independent of the team, L X = B
+    {
+        const int n = 400, nr = 24;
+        const std::vector<double> S = spd(n, 21);
+        std::vector<double> L = S;
+        dense::cholesky(n, L.data(), n);
+        std::mt19937 g(5);
+        std::normal_distribution<double> nd;
+        std::vector<double> B((size_t)n * nr);
+        for (auto& x : B) x = nd(g);
+        std::vector<double> X1 = B, X8 = B;
+        with_threads(true, [&] { dense::lower_solve(n, L.data(), n, X1.data(), n, nr); });
+        with_threads(false, [&] { dense::lower_solve(n, L.data(), n, X8.data(), n, nr); });
+        double r = 0;
+        for (int c = 0; c < nr; ++c)
+            for (int i = 0; i < n; ++i) {
+                double acc = 0;
+                for (int k = 0; k <= i; ++k) acc += L[(size_t)k * n + i] * X8[(size_t)c * n + k];
+                r = std::max(r, std::fabs(acc - B[(size_t)c * n + i]));
+            }
+        const bool same = !std::memcmp(X1.data(), X8.data(), sizeof(double) * X1.size());
+        std::printf("lower_solve same=%d resid=%.2e\n", (int)same, r);
+        bad += !(same && r <= 1e-11);
+    }
+    // Householder thin QR and symmetric eigenvectors
+    {
+        const int m = 50, n = 12;
+        std::mt19937 g(9);
+        std::normal_distribution<double> nd;
+        std::vector<double> A((size_t)m * n), Q, R((size_t)n * n);
+        for (auto& x : A) x = nd(g);
+        Q = A;
+        dense::thin_qr(m, n, Q.data(), m, R.data(), n);
+        double orth = 0, rec = 0, low = 0;
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                double qq = 0;
+                for (int r = 0; r < m; ++r) qq += Q[(size_t)a * m + r] * Q[(size_t)b * m + r];
+                orth = std::max(orth, std::fabs(qq - (a == b ? 1.0 : 0.0)));
+                if (a > b) low = std::max(low, std::fabs(R[(size_t)b * n + a]));
+            }
+        for (int c = 0; c < n; ++c)
+            for (int r = 0; r < m; ++r) {
+                double acc = 0;
+                for (int k = 0; k <= c; ++k) acc += Q[(size_t)k * m + r] * R[(size_t)c * n + k];
+                rec = std::max(rec, std::fabs(acc - A[(size_t)c * m + r]));
+            }
+        const int ne = 40;
+        const std::vector<double> S = spd(ne, 13);
+        std::vector<double> Z = S, w(ne);
+        dense::sym_eig(ne, Z.data(), ne, w.data());
+        double er = 0, eo = 0, ns = 0;
+        for (double x : S) ns = std::max(ns, std::fabs(x));
+        for (int c = 0; c < ne; ++c)
+            for (int r = 0; r < ne; ++r) {
+                double az = 0, zz = 0;
+                for (int k = 0; k < ne; ++k) {
+                    az += S[(size_t)k * ne + r] * Z[(size_t)c * ne + k];
+                    zz += Z[(size_t)r * ne + k] * Z[(size_t)c * ne + k];
+                }
+                er = std::max(er, std::fabs(az - w[c] * Z[(size_t)c * ne + r]));
+                eo = std::max(eo, std::fabs(zz - (r == c ? 1.0 : 0.0)));
+            }
+        const bool ok = orth <= 1e-14 && rec <= 1e-13 && low == 0.0 && er <= 1e-13 * ns * ne && eo <= 1e-13;
+        std::printf("thin_qr orth=%.2e rec=%.2e lower=%.1e sym_eig resid=%.2e orth=%.2e %s\n", orth, rec, low,
+                    er / ns, eo, ok ? "ok" : "BAD");
+        bad += !ok;
+    }
     // one-sided Jacobi SVD (rank compression of F): graded singular values 1 .. 1e-14 between random
     // orthogonal factors (Householder QR of Gaussian matrices), tall and square
     for (int shape = 0; shape < 2; ++shape) {

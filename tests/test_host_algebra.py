@@ -3,8 +3,10 @@
 The projected problems (Cholesky, multi-right-hand-side solves, the symmetric eigenvalues behind the adaptive
 shifts) run on a host thread team whose size depends on how many solves share the host.  Each parallel loop gives
 every output element to one thread in the serial summation order, so a solve's numbers must not depend on the
-team size: the check program compares one thread with the full team bitwise, checks L L^T = A and A A^{-1} = I, and
-prints the eigenvalues of a fixed matrix, compared here with numpy's.
+team size: the check program compares one thread with the full team bitwise (Cholesky, its solve, the eigenvalues,
+forward substitution), checks L L^T = A and A A^{-1} = I, the LU solves A X = B and A^T X = B (and that a singular
+matrix is reported), the Householder QR and the eigenvectors, and prints the eigenvalues of a fixed matrix and the
+singular values of two graded matrices, compared here with numpy's.
 """
 
 import shutil
