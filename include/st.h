@@ -355,11 +355,15 @@ typedef struct st_result {
     char message[160];       /* on failure, the worker's st_last_error text ("" on success) */
 } st_result;
 
-/* st_request_bytes -- admission estimate of a request's device footprint:
- * operators, tables, a basis V and M V of min(max_basis, p (min(maxit,80)+1))
- * columns, the N_h-sized work blocks and Y; for convection-diffusion also
- * the flexible GMRES blocks (84 N_h doubles per column, at most 16 columns
- * and 4 GB).  0 for invalid descriptors. */
+/* st_request_bytes -- admission estimate of a request's device footprint
+ * in bytes: the CSR operators (P, N, M, A in FP64 and FP32), the
+ * fast-diagonalisation tables, a basis of k = min(max_basis + 16,
+ * p (min(maxit, m) + 1)) columns with m = 80 for heat and 200 for
+ * convection-diffusion, stored as V and M V (plus the float-pair copy of V
+ * under ST_MIXED), 12 p N_h-sized work columns and Y (k x N_t); for
+ * convection-diffusion also the flexible GMRES blocks (84 N_h doubles per
+ * column, at most 16 columns and 4 GB).  Host only.  0 for invalid
+ * descriptors (NULL, dim outside 1..3, p < 1). */
 double st_request_bytes(const st_desc* d, int p);
 
 /* st_executor_create -- start `slots` (1..256) worker threads on the current
