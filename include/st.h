@@ -253,7 +253,8 @@ int st_autotune_load(const char* path, const char* device_tag, int* loaded);
  * F1: n_h x p (ld ldf1), F2: n_t x p (ld ldf2), double, host OR device.
  * 1 <= p <= 16.  Output in *sol (V, Y owned by the handle; U_dense filled if
  * given).  stats may be NULL.  Synchronises.  Returns ST_OK, ST_ENOTCONV
- * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL.
+ * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL
+ * (also for a NaN or Inf in F1 or F2, or an F1 whose Gram matrix overflows).
  * Heat (ST_HEAT): the shifted solves are exact fast-diagonalisation
  * transforms.  Convection-diffusion (ST_CONVDIFF, A nonsymmetric): each
  * shifted solve is flexible GMRES (all columns advanced together)

@@ -942,6 +942,18 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     } else {
         for (int j = 0; j < p0; ++j) std::memcpy(&F2h[(size_t)j * nt], F2 + (size_t)j * ldf2, sizeof(double) * nt);
     }
+    {
+        // a NaN or Inf in F1 (seen through its Gram matrix) or F2 would make the kept rank 0
+        // and the call return U = 0 as converged: refuse it instead
+        const double* g = sg.host_of(dGF);
+        bool finite = true;
+        for (size_t i = 0; i < (size_t)p0 * p0; ++i) finite = finite && std::isfinite(g[i]);
+        for (double v : F2h) finite = finite && std::isfinite(v);
+        if (!finite) {
+            st_note_msg("st_solve: F1 or F2 holds a NaN or Inf (or F1^T F1 overflows)");
+            return ST_EINVAL;
+        }
+    }
     // F1 = Q1 R1 from F1^T F1 = E diag(w) E^T: Q1 = F1 E_r w_r^{-1/2}, R1 = w_r^{1/2} E_r^T
     // over the kept directions.  One Gram product loses orthogonality like
     // eps cond(F1)^2, so a condition number above 1e4 takes the CholQR2 route.

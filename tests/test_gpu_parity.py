@@ -305,6 +305,23 @@ def test_solve_not_converged_returns_best_iterate():
     assert status == st.ST_ENOTCONV and stats["converged"] == 0 and stats["iterations"] == 2
 
 
+def test_solve_refuses_non_finite_loads():
+    """A NaN in F1 (device) or an Inf in F2 (host) is refused with ST_EINVAL and a message, never solved as F = 0;
+    the handle then solves a finite load."""
+    F1, F2 = workloads.gaussian_factors(15 * 15, 16, 2, seed=30)
+    F1n = F1.copy()
+    F1n[7, 1] = np.nan
+    F2i = np.asfortranarray(F2.copy())
+    F2i[3, 0] = np.inf
+    with st.Problem(2, 15, 16, 1.0) as prob:
+        for a, b in ((dev(F1n), dev(F2)), (dev(F1), F2i)):
+            with pytest.raises(st.StError) as e:
+                prob.solve(a, b)
+            assert e.value.status == st.ST_EINVAL and "NaN or Inf" in str(e.value)
+        V, Y, stats, status = prob.solve(dev(F1), dev(F2))
+    assert status == st.ST_OK and stats["converged"] == 1 and stats["basis_cols"] > 0
+
+
 # ---------------------------------------------------------------- residual entry points
 
 def test_residual_entry_points_match_oracle():
