@@ -1,0 +1,145 @@
+// Low-rank flexible GMRES (LR-FGMRES), the comparison solver of Section 5,
+// Example 1 (Table 1): GMRES on B vec(U) = vec(F) for the matrix form
+// L(U) = M U D_t^T + A U C_t^T (Section 4) with every Krylov vector held as
+// low-rank factors, right-preconditioned by a nonlinear map (a fixed number
+// of RKSM steps), hence the flexible variant.
+//
+// This header is the method's host driver only: the Arnoldi process over
+// vectors that a Backend stores and combines, the Hessenberg least squares by
+// Givens rotations, the stopping rule and the memory count.  Where the
+// factors live (host or device), how sums are truncated and what the
+// preconditioner is belong to the Backend.  Host-only C++ (no CUDA).
+//
+// Steps, with X_0 = 0 and no restart: V_1 = F / beta (beta = ||F||_F);
+// step j: Z_j = P(V_j), W = L(Z_j), classical Gram-Schmidt of W against
+// V_1..V_j run twice, h_{j+1,j} = ||W||_F, V_{j+1} = W / h_{j+1,j}; the
+// Givens-reduced least-squares residual |g_{j+1}| / beta is the estimate the
+// iteration stops on (<= tol, or an exact breakdown h_{j+1,j} = 0); then
+// X = sum_i Z_i y_i with R y = g.  mu_mem counts the stored columns of
+// V_1..V_{m+1} and Z_1..Z_m.
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+namespace lrgmres {
+
+// Storage and arithmetic of the low-rank vectors, addressed by integer ids
+// that the driver chooses (0 .. 2 maxit + 4).  Every call returns 0 or a
+// negative status, which the driver passes on.
+struct Backend {
+    virtual ~Backend() = default;
+    virtual int inner(int a, int b, double* out) = 0;                   // trace(X_a^T X_b)
+    virtual int combine(int dst, const double* c, const int* src, int n) = 0;   // X_dst = trunc(sum c_i X_src_i); dst not in src
+    virtual int apply(int dst, int src) = 0;                            // X_dst = trunc(L(X_src))
+    virtual int precondition(int dst, int src) = 0;                     // X_dst = P(X_src)
+    virtual int rank(int id) const = 0;                                 // columns of X_id's factors
+};
+
+struct Options {
+    double tol = 1e-8;
+    int maxit = 50;
+};
+
+struct Result {
+    int iterations = 0;
+    bool converged = false;
+    int mu_mem = 0;
+    std::vector<double> history;   // relative residual estimates, history[0] = 1
+};
+
+// Ids used by run(): the right-hand side at rhs, the solution written to x;
+// V_j at vbase + j, Z_j at zbase + j, two scratch ids for W.
+inline int run(Backend& b, int rhs, int x, const Options& o, Result* res) {
+    const int maxit = o.maxit > 0 ? o.maxit : 1;
+    const int vbase = 2, zbase = vbase + maxit + 1, w0 = zbase + maxit, w1 = w0 + 1;
+    if (rhs == x || (rhs >= vbase && rhs <= w1) || (x >= vbase && x <= w1)) return -1;
+    Result r;
+    double bb = 0.0;
+    int st = b.inner(rhs, rhs, &bb);
+    if (st) return st;
+    const double beta = std::sqrt(bb > 0.0 ? bb : 0.0);
+    r.history.push_back(1.0);
+    if (!(beta > 0.0)) {
+        if (!(bb == 0.0)) return -1;   // NaN
+        st = b.combine(x, nullptr, nullptr, 0);
+        if (st) return st;
+        r.converged = true;
+        r.history.back() = 0.0;
+        *res = r;
+        return 0;
+    }
+    const double inv = 1.0 / beta;
+    if ((st = b.combine(vbase, &inv, &rhs, 1))) return st;
+    // H (maxit + 1) x maxit column-major; Givens rotations; g the rotated beta e_1
+    std::vector<double> H((size_t)(maxit + 1) * maxit, 0.0), cs(maxit, 0.0), sn(maxit, 0.0), g(maxit + 1, 0.0);
+    g[0] = beta;
+    auto h = [&](int i, int j) -> double& { return H[(size_t)j * (maxit + 1) + i]; };
+    int m = 0, wcur = w0;
+    for (int j = 0; j < maxit; ++j) {
+        if ((st = b.precondition(zbase + j, vbase + j))) return st;
+        if ((st = b.apply(wcur, zbase + j))) return st;
+        std::vector<double> coef(j + 2);
+        std::vector<int> src(j + 2);
+        for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+            coef[0] = 1.0;
+            src[0] = wcur;
+            for (int i = 0; i <= j; ++i) {
+                double hij = 0.0;
+                if ((st = b.inner(vbase + i, wcur, &hij))) return st;
+                h(i, j) += hij;
+                coef[i + 1] = -hij;
+                src[i + 1] = vbase + i;
+            }
+            const int wnext = wcur == w0 ? w1 : w0;
+            if ((st = b.combine(wnext, coef.data(), src.data(), j + 2))) return st;
+            wcur = wnext;
+        }
+        double ww = 0.0;
+        if ((st = b.inner(wcur, wcur, &ww))) return st;
+        const double hn = std::sqrt(ww > 0.0 ? ww : 0.0);
+        h(j + 1, j) = hn;
+        // apply the earlier rotations to column j, then zero its subdiagonal
+        for (int i = 0; i < j; ++i) {
+            const double a = h(i, j), c = h(i + 1, j);
+            h(i, j) = cs[i] * a + sn[i] * c;
+            h(i + 1, j) = -sn[i] * a + cs[i] * c;
+        }
+        const double a = h(j, j), c = h(j + 1, j);
+        const double rr = std::hypot(a, c);
+        cs[j] = rr > 0.0 ? a / rr : 1.0;
+        sn[j] = rr > 0.0 ? c / rr : 0.0;
+        h(j, j) = rr;
+        h(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        const double est = std::fabs(g[j + 1]) / beta;
+        r.history.push_back(est);
+        m = j + 1;
+        if (est <= o.tol || hn == 0.0) {
+            r.converged = est <= o.tol || hn == 0.0;
+            break;
+        }
+        if (j + 1 < maxit) {
+            const double ih = 1.0 / hn;
+            if ((st = b.combine(vbase + j + 1, &ih, &wcur, 1))) return st;
+        }
+    }
+    // R y = g (upper triangular, m x m)
+    std::vector<double> y(m, 0.0);
+    for (int i = m - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int k = i + 1; k < m; ++k) s -= h(i, k) * y[k];
+        y[i] = h(i, i) != 0.0 ? s / h(i, i) : 0.0;
+    }
+    std::vector<int> zs(m);
+    for (int i = 0; i < m; ++i) zs[i] = zbase + i;
+    if ((st = b.combine(x, y.data(), zs.data(), m))) return st;
+    r.iterations = m;
+    r.mu_mem = b.rank(wcur);
+    for (int i = 0; i < m; ++i) r.mu_mem += b.rank(vbase + i) + b.rank(zbase + i);
+    *res = r;
+    return 0;
+}
+
+}  // namespace lrgmres
