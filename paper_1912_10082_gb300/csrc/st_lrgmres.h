@@ -36,6 +36,61 @@ struct Backend {
     virtual int rank(int id) const = 0;                                 // columns of X_id's factors
 };
 
+// Host half of the truncation of X = P Q^T (reading of the oracle's step 2):
+// given R_P (r x r, upper) from a QR P = Q_P R_P computed where P lives, and
+// Q (n_t x r) on the host, factor Q = Q_Q R_Q with q = min(r, n_t) columns
+// (Householder when r <= n_t; otherwise Q_Q = I and R_Q = Q, n_t x r), take
+// the SVD R_P R_Q^T = U S V^T (r x q) and keep the k singular
+// values above trunc * largest.  Outputs: Cp (r x k, ld r) with
+// P' = Q_P Cp = Q_P U_k S_k, and Qn (n_t x k, ld n_t) = Q_Q V_k, so that
+// P' Qn^T is the truncation of X.  svd(m, n, A, lda, U, s, Vt) is a one-sided
+// SVD of an m x n matrix, m >= n (the library's dense::svd_small);
+// qr(m, n, A, lda, R, ldr) a thin QR with A <- Q (dense::thin_qr).
+template <class Svd, class Qr>
+inline int truncate_core(int r, const double* RP, int ldrp, int nt, const double* Q, int ldq, double trunc, Svd svd,
+                         Qr qr, std::vector<double>* Cp, std::vector<double>* Qn, int* k) {
+    *k = 0;
+    Cp->clear();
+    Qn->clear();
+    if (r == 0 || nt == 0) return 0;
+    const int q = r <= nt ? r : nt;
+    std::vector<double> QQ((size_t)nt * q, 0.0), RQ((size_t)q * r, 0.0);   // Q = QQ RQ, RQ q x r (ld q)
+    if (r <= nt) {
+        for (int c = 0; c < r; ++c)
+            for (int i = 0; i < nt; ++i) QQ[(size_t)c * nt + i] = Q[(size_t)c * ldq + i];
+        qr(nt, r, QQ.data(), nt, RQ.data(), q);
+    } else {
+        for (int i = 0; i < nt; ++i) QQ[(size_t)i * nt + i] = 1.0;
+        for (int c = 0; c < r; ++c)
+            for (int i = 0; i < nt; ++i) RQ[(size_t)c * q + i] = Q[(size_t)c * ldq + i];
+    }
+    // core K = R_P R_Q^T (r x q)
+    std::vector<double> K((size_t)r * q, 0.0);
+    for (int j = 0; j < q; ++j)
+        for (int i = 0; i < r; ++i) {
+            double acc = 0.0;
+            for (int t = 0; t < r; ++t) acc += RP[(size_t)t * ldrp + i] * RQ[(size_t)t * q + j];
+            K[(size_t)j * r + i] = acc;
+        }
+    std::vector<double> U((size_t)r * q), sv(q), Vt((size_t)q * q);
+    svd(r, q, K.data(), r, U.data(), sv.data(), Vt.data());
+    int kk = 0;
+    if (sv[0] > 0.0)
+        for (int i = 0; i < q; ++i) kk += sv[i] > trunc * sv[0];
+    Cp->assign((size_t)r * kk, 0.0);
+    Qn->assign((size_t)nt * kk, 0.0);
+    for (int c = 0; c < kk; ++c) {
+        for (int i = 0; i < r; ++i) (*Cp)[(size_t)c * r + i] = U[(size_t)c * r + i] * sv[c];
+        for (int i = 0; i < nt; ++i) {
+            double acc = 0.0;
+            for (int t = 0; t < q; ++t) acc += QQ[(size_t)t * nt + i] * Vt[(size_t)t * q + c];
+            (*Qn)[(size_t)c * nt + i] = acc;
+        }
+    }
+    *k = kk;
+    return 0;
+}
+
 struct Options {
     double tol = 1e-8;
     int maxit = 50;

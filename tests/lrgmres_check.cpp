@@ -6,6 +6,7 @@
 // and the dense solution for comparison with the oracle.
 //
 // usage: lrgmres_check <file> <identity|exact> <maxit> <tol> <trunc>
+//        lrgmres_check <file> truncate <trunc>   (file: "n_h n_t r", P, Q; prints k and P' Q'^T)
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -160,7 +161,38 @@ std::vector<double> read(FILE* f, size_t n) {
 
 }  // namespace
 
+// The host half of the truncation (lrgmres::truncate_core), with R_P from a
+// Householder QR of P standing in for the device block QR.
+int truncate_mode(const char* path, double trunc) {
+    FILE* f = std::fopen(path, "r");
+    if (!f) return 2;
+    int nh, nt, r;
+    if (std::fscanf(f, "%d %d %d", &nh, &nt, &r) != 3) return 2;
+    auto P = read(f, (size_t)nh * r), Q = read(f, (size_t)nt * r);
+    std::fclose(f);
+    std::vector<double> QP = P, RP((size_t)r * r);
+    dense::thin_qr(nh, r, QP.data(), nh, RP.data(), r);
+    std::vector<double> Cp, Qn;
+    int k = 0;
+    const int st = lrgmres::truncate_core(r, RP.data(), r, nt, Q.data(), nt, trunc, dense::svd_small,
+                                          dense::thin_qr, &Cp, &Qn, &k);
+    std::printf("status %d\nk %d\nX", st, k);
+    for (int l = 0; l < nt; ++l)
+        for (int i = 0; i < nh; ++i) {
+            double acc = 0.0;
+            for (int c = 0; c < k; ++c) {
+                double pc = 0.0;
+                for (int t = 0; t < r; ++t) pc += QP[(size_t)t * nh + i] * Cp[(size_t)c * r + t];
+                acc += pc * Qn[(size_t)c * nt + l];
+            }
+            std::printf(" %.17g", acc);
+        }
+    std::printf("\n");
+    return st == 0 ? 0 : 1;
+}
+
 int main(int argc, char** argv) {
+    if (argc == 4 && std::string(argv[2]) == "truncate") return truncate_mode(argv[1], std::atof(argv[3]));
     if (argc != 6) return 2;
     FILE* f = std::fopen(argv[1], "r");
     if (!f) return 2;

@@ -98,3 +98,30 @@ def test_zero_load_returns_zero(exe, tmp_path):
     M, A, D, C, F1, F2 = problem(1, 5, 4, 1, 7)
     got = run(exe, tmp_path, (M, A, D, C, 0.0 * F1, F2), "identity", 5, 1e-8, 1e-14)
     assert got["converged"] and got["its"] == 0 and np.all(got["X"] == 0.0)
+
+
+@pytest.mark.parametrize("nh,nt,r,rank", [(30, 12, 6, 3), (30, 5, 8, 3), (9, 40, 7, 7)])
+def test_truncation_core_matches_the_oracle(exe, tmp_path, nh, nt, r, rank):
+    """The host half of the device backend's truncation (R_P from a QR of P, then the QR of Q or Q_Q = I when
+    r > n_t, the core SVD) against the oracle's truncation and the Eckart-Young error."""
+    rng = np.random.default_rng(nh + nt + r)
+    s = 10.0 ** -np.arange(rank, dtype=float) * 3.0
+    s[-1] = 1e-13 if rank > 1 else s[-1]                       # one value below trunc * largest
+    U, _ = np.linalg.qr(rng.standard_normal((nh, rank)))
+    V, _ = np.linalg.qr(rng.standard_normal((nt, rank)))
+    G = rng.standard_normal((rank, r))                          # r redundant columns of the same product
+    P = (U * s) @ G
+    Q = V @ np.linalg.pinv(G).T
+    X = P @ Q.T
+    path = tmp_path / "trunc.txt"
+    path.write_text(f"{nh} {nt} {r}\n" + " ".join(repr(float(x)) for x in P.reshape(-1, order="F")) + "\n"
+                    + " ".join(repr(float(x)) for x in Q.reshape(-1, order="F")) + "\n")
+    out = subprocess.run([str(exe), str(path), "truncate", "1e-12"], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    rec = {ln.split()[0]: ln.split()[1:] for ln in out.stdout.splitlines()}
+    k = int(rec["k"][0])
+    Xt = np.array([float(x) for x in rec["X"]]).reshape(nh, nt, order="F")
+    Pr, Qr = lrfgmres.lr_truncate(P, Q, 1e-12)
+    assert k == Pr.shape[1] == (rank - 1 if rank > 1 else 1)
+    assert np.linalg.norm(Xt - Pr @ Qr.T) <= 1e-13 * np.linalg.norm(X)
+    assert abs(np.linalg.norm(X - Xt) - (s[-1] if rank > 1 else 0.0)) <= 1e-14 * s[0]
