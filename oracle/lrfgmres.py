@@ -27,6 +27,9 @@ to a companion paper.  Readings taken here, in the order the method runs:
     factor pair, V_1..V_{m+1} and Z_1..Z_m.  The numerical rank of U counts singular values above 1e-8
     of the largest, as for RKSM.
 
+Scope: the heat equation (A symmetric), as in Example 1; the RKSM preconditioner takes its shifts from the
+symmetric pencil (A, M).  A nonsymmetric A is refused unless ``precondition=False``.
+
 Pins (tests/test_oracle_lrfgmres.py): the truncation against the Eckart-Young error of a matrix with known
 singular values; without a preconditioner, the residual norms against brute-force least squares over the
 explicit Krylov space of B; with RKSM run to convergence as the preconditioner, one step; the converged
@@ -87,6 +90,8 @@ def lr_fgmres(M, A, D, C, F1, F2, tol: float = 1e-8, maxit: int = 50, precond_it
                  mu_mem=0, rank=0, relres=0.0)
     if beta == 0.0:
         return empty
+    if precondition and abs(A - A.T).max() > 1e-12 * abs(A).max():
+        raise NotImplementedError("the RKSM preconditioner of this oracle needs a symmetric A (heat)")
     if precondition and interval is None:
         interval = _rksm.pencil_interval(M, A)
 

@@ -152,3 +152,16 @@ def test_planted_gram_schmidt_mistake_fails_the_krylov_pin(monkeypatch):
     monkeypatch.setattr(lrfgmres, "lr_inner", lambda X, Y: good(X, Y) if X is Y else -good(X, Y))
     with pytest.raises(AssertionError):
         test_unpreconditioned_residuals_are_minimal_over_the_krylov_space()
+
+
+def test_nonsymmetric_operator_needs_no_preconditioner():
+    """The oracle's RKSM preconditioner is for the heat equation; a convection-diffusion operator is refused with
+    it and solved without it."""
+    M, A = fem.tensor_operators(1, 9, op="convdiff", eps=0.1, beta=(1.0,))
+    D, C = timefe.time_matrices(6, 1.0)
+    F1, F2 = workloads.gaussian_factors(9, 6, 1, seed=8)
+    with pytest.raises(NotImplementedError):
+        lrfgmres.lr_fgmres(M, A, D, C, F1, F2)
+    out = lrfgmres.lr_fgmres(M, A, D, C, F1, F2, tol=1e-10, maxit=54, precondition=False)
+    assert out["converged"]
+    assert relerr(out["P"] @ out["Q"].T, kron.solve_sparse(M, A, D, C, F1 @ F2.T)) <= 1e-7
