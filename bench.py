@@ -201,6 +201,22 @@ def roofline_of(prof, hbm_gbs, choices=None):
     return out
 
 
+def workload_desc(name, wl, args=None):
+    """config.workload of both arms: the workload's name and what it is."""
+    if wl.get("kind") == "batched":
+        return (f"batched: {wl['count']} 2D heat instances, grid side from (63,127,255), n_t from "
+                f"(64,128,256,512), kappa 10^U(-1,1), rank-{wl['p']} Gaussian load, mixed precision")
+    if wl.get("kind") == "served":
+        count = (getattr(args, "requests", 0) or wl["count"])
+        warm = min(wl["warmup"], count // 10)
+        gap = wl["mean_gap_s"] * (getattr(args, "gap_scale", 1.0) or 1.0)
+        return (f"served: Poisson stream of {count} requests (first {warm} warm-up), mean gap "
+                f"{1e3 * gap:.2f} ms, heat and convection-diffusion, 1D/2D/3D n 63..127^3, "
+                f"n_t 64..512, rank-{wl['p']} Gaussian loads, mixed precision, tol 1e-8")
+    return (f"{name}: {wl['dim']}D heat, Q1 {wl['n']}^{wl['dim']} interior grid, "
+            f"n_t={wl['n_t']}, T={wl['T']}, {wl['rhs']} load")
+
+
 def run_reference_many(args, wl, world, rank):
     """The oracle on a bounded sample of a batched or served workload: exact direct solves
     (block forward substitution of the assembled system) of its instances in order, each step
@@ -246,7 +262,7 @@ def run_reference_many(args, wl, world, rank):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"]},
+            "config": {"workload": workload_desc(wl["name"], wl, args)},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -288,7 +304,7 @@ def run_reference(args, wl, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "n_h": int(M.shape[0]), "n_t": nt},
+            "config": {"workload": workload_desc(wl["name"], wl, args), "n_h": int(M.shape[0]), "n_t": nt},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
@@ -382,8 +398,7 @@ def bench_batched(args, wl, rank, world, local):
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"batched: {len(insts)} 2D heat instances, grid side from (63,127,255), n_t from "
-                               f"(64,128,256,512), kappa 10^U(-1,1), rank-{wl['p']} Gaussian load, mixed precision",
+        "config": {"workload": workload_desc(wl["name"], wl, args),
                    "instances": len(insts), "dof": dof, "slots": slots, "tol": 1e-8,
                    "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
                    "l2": "inputs of the batch (%.0f MB) exceed L2" % (sum(r['F1'].nbytes for r in insts) / 1e6),
@@ -464,9 +479,7 @@ def bench_served(args, wl, rank, world, local):
         "metric": METRIC, "value": out["dof_per_s"] * world, "unit": "DoF/s", "n_gpus": world, "steps": 1,
         "warmup": warm, "ms_per_step": 1e3 * out["makespan_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"served: Poisson stream of {count} requests (first {warm} warm-up), mean gap "
-                               f"{1e3 * gap:.2f} ms, heat and convection-diffusion, 1D/2D/3D n 63..127^3, "
-                               f"n_t 64..512, rank-{wl['p']} Gaussian loads, mixed precision, tol 1e-8",
+        "config": {"workload": workload_desc(wl["name"], wl, args),
                    "slots": args.slots, "gap_scale": args.gap_scale, "policy": args.policy,
                    "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
                    "parallelism": f"replicas{world}"},
@@ -677,8 +690,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == st.ST_FP64 else "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {wl['dim']}D heat, Q1 {wl['n']}^{wl['dim']} interior grid, "
-                               f"n_t={wl['n_t']}, T={wl['T']}, {wl['rhs']} load",
+        "config": {"workload": workload_desc(args.workload, wl, args),
                    "n_h": prob.n_h, "n_t": prob.n_t, "precision": "fp64" if prec == st.ST_FP64 else "mixed",
                    "tol": 1e-8, "l2": "flushed between steps (256 MB read)",
                    "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
