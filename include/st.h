@@ -178,15 +178,19 @@ int st_shift_solve(st_problem* p, double s, const double* X, int ldx, int ncols,
  * synchronise the device or fail) is not allowed.  st_shift_solve may grow a
  * workspace owned by the handle; this call allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).  The paper has no counterpart.
- * Scratch: a file-scope device array of 4,194,304 doubles (32 MiB), present
- * on every GPU that loads the library until the process exits; calls with
- * n_h * ncols above that return ST_EINVAL (text in st_last_error).  The first
- * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call
- * shares the array (each call overwrites it completely before reading it),
- * so calls that overlap on the GPU, on any stream, race.  X and W: device
- * double, n_h x ncols, ld >= n_h, may alias.  Work is issued on the handle's
- * stream; asynchronous.  ST_ENOTSUP without the tensor-grid heat solver. */
+ * Scratch: a file-scope device array of 4,194,304 doubles (32 MiB); calls
+ * with n_h * ncols above that return ST_EINVAL (text in st_last_error).  The
+ * first call on a device loads the library's device code there, which
+ * reserves the array on that device until the process exits, and looks up
+ * its device address: make that first call before any stream capture.  Every
+ * later call allocates nothing.  The problem's device (current at st_setup)
+ * must be the current device (else ST_EINVAL).  The call never times launch
+ * variants (st_autotune): it uses the tuned or built-in choices as they are.
+ * Every call shares the array (each call overwrites it completely before
+ * reading it), so calls that overlap on the GPU, on any stream, race.  X and
+ * W: device double, n_h x ncols, ld >= n_h, may alias (also W == X).  Work is
+ * issued on the handle's stream; asynchronous.  ST_ENOTSUP without the
+ * tensor-grid heat solver. */
 int st_shift_solve_noalloc(st_problem* p, double s, const double* X, int ldx, int ncols, double* W, int ldw);
 
 /* st_shift_solve_noalloc_max -- capacity of that scratch array in doubles. */

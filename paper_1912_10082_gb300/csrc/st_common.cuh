@@ -45,7 +45,8 @@ struct StTuneSession {
     size_t scratch_bytes = 0;
     int tuned = 0;             // shapes this session added to the table
 };
-void st_tune_set_session(StTuneSession* sess);
+// Sets the calling thread's session and returns the one it replaces.
+StTuneSession* st_tune_set_session(StTuneSession* sess);
 // The calling thread's session, or nullptr when none is set or s is being captured.
 StTuneSession* st_tune_session(cudaStream_t s);
 // Times n launch variants on stream s: run(c) launches variant c (valid[c]
@@ -81,6 +82,7 @@ struct FdAxis {
 struct st_problem {
     st_desc d{};
     cudaStream_t stream = nullptr;
+    int device = 0;         // CUDA device current at st_setup (owner of every buffer)
     int dim = 0;            // 0 for user CSR
     int n[3] = {1, 1, 1};
     double len[3] = {1, 1, 1};

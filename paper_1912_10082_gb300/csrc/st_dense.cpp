@@ -323,8 +323,12 @@ static void tridiagonalize(int n, double* A, int lda, double* d, double* e, bool
     for (int c = 0; c < n; ++c) std::memcpy(&A_(0, c), &Q[(size_t)c * n], sizeof(double) * n);
 }
 
-// Implicit QL iterations with Wilkinson-type shifts on a symmetric
-// tridiagonal matrix; Z (n x n, ldz) receives the rotations when non-null.
+// Eigenvalues (and, with Z, eigenvectors) of a symmetric tridiagonal matrix
+// by the implicit QL algorithm with Wilkinson-type shifts, the published
+// method of Bowdler, Martin, Reinsch and Wilkinson, "The QR and QL algorithms
+// for symmetric matrices" (Numer. Math. 11, 1968; EISPACK tql1/tql2), whose
+// steps this routine follows.  Z (n x n, ldz) receives the rotations when
+// non-null.
 static void tridiag_ql(int n, double* d, double* e, double* Z, int ldz) {
     if (n <= 1) return;
     std::vector<double> ee(n, 0.0);

@@ -1770,7 +1770,11 @@ namespace {
 thread_local StTuneSession* t_tune = nullptr;
 }
 
-void st_tune_set_session(StTuneSession* sess) { t_tune = sess; }
+StTuneSession* st_tune_set_session(StTuneSession* sess) {
+    StTuneSession* prev = t_tune;
+    t_tune = sess;
+    return prev;
+}
 
 StTuneSession* st_tune_session(cudaStream_t s) {
     if (!t_tune) return nullptr;

@@ -14,7 +14,9 @@
 // step j: Z_j = P(V_j), W = L(Z_j), classical Gram-Schmidt of W against
 // V_1..V_j run twice, h_{j+1,j} = ||W||_F, V_{j+1} = W / h_{j+1,j}; the
 // Givens-reduced least-squares residual |g_{j+1}| / beta is the estimate the
-// iteration stops on (<= tol, or an exact breakdown h_{j+1,j} = 0); then
+// iteration stops on (<= tol, or an exact breakdown h_{j+1,j} = 0 with a
+// nonsingular rotated diagonal; a vanishing rotated diagonal is reported as
+// stagnation, converged = false, without step j); then
 // X = sum_i Z_i y_i with R y = g.  mu_mem counts the stored columns of
 // V_1..V_{m+1} and Z_1..Z_m.
 #pragma once
@@ -162,8 +164,18 @@ inline int run(Backend& b, int rhs, int x, const Options& o, Result* res) {
         }
         const double a = h(j, j), c = h(j + 1, j);
         const double rr = std::hypot(a, c);
-        cs[j] = rr > 0.0 ? a / rr : 1.0;
-        sn[j] = rr > 0.0 ? c / rr : 0.0;
+        if (!(rr > 0.0)) {
+            // h(j,j) and h(j+1,j) both vanish after the rotations: the new preconditioned
+            // direction adds nothing (L Z_j lies in span V_1..V_j, e.g. a preconditioner
+            // output truncated to rank 0), so the least-squares matrix is singular at this
+            // step.  That is stagnation, not convergence: the estimate stays |g_j| / beta
+            // and step j does not enter the solution.
+            r.history.push_back(std::fabs(g[j]) / beta);
+            r.converged = false;
+            break;
+        }
+        cs[j] = a / rr;
+        sn[j] = c / rr;
         h(j, j) = rr;
         h(j + 1, j) = 0.0;
         g[j + 1] = -sn[j] * g[j];
@@ -172,7 +184,8 @@ inline int run(Backend& b, int rhs, int x, const Options& o, Result* res) {
         r.history.push_back(est);
         m = j + 1;
         if (est <= o.tol || hn == 0.0) {
-            r.converged = est <= o.tol || hn == 0.0;
+            // hn == 0 with rr > 0 is the exact (lucky) breakdown: g_{j+1} = 0 and R is nonsingular
+            r.converged = true;
             break;
         }
         if (j + 1 < maxit) {

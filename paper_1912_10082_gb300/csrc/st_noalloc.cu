@@ -14,7 +14,10 @@
 
 namespace {
 
-// 4,194,304 doubles = 32 MiB, reserved on every GPU that loads the library
+// 4,194,304 doubles = 32 MiB.  With lazy module loading (the default since
+// CUDA 12.2) the array is reserved on a device when this file's device code is
+// first loaded there, i.e. at the first cudaGetSymbolAddress below (the first
+// call of the entry point on that device); from then on it stays reserved
 // until the process exits.  Enough for n_h * ncols <= 4,194,304 (e.g. one
 // column of the 127^3 grid, or 64 columns of the 255^2 grid).
 constexpr size_t kScratchDoubles = size_t(1) << 22;
@@ -25,11 +28,16 @@ std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
 
 // Host-side name g_fd_scratch is only a stand-in; the device address is looked
-// up once per device with that device current.
-int scratch_address(double** out) {
+// up once per device with that device current.  The problem's device must be
+// current: the cached address belongs to the current device only.
+int scratch_address(const st_problem* p, double** out) {
     int dev = 0;
     ST_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return ST_EINVAL;
+    if (dev != p->device) {
+        st_note_msg("st_shift_solve_noalloc: the problem's device is not the current device");
+        return ST_EINVAL;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {
         void* ptr = nullptr;
@@ -58,7 +66,12 @@ extern "C" int st_shift_solve_noalloc(st_problem* p, double s, const double* X, 
         return ST_EINVAL;
     }
     double* scratch = nullptr;
-    ST_TRY(scratch_address(&scratch));
+    ST_TRY(scratch_address(p, &scratch));
+    // No launch-variant timing here, whatever the calling thread is doing: the tuner would
+    // synchronise and use its own buffers.  The tuned or built-in variants are used as they are.
+    StTuneSession* saved = st_tune_set_session(nullptr);
     // every entry of the scratch tensor is written before it is read: nothing to clear
-    return st_fd_apply64(p, FD_MASS_RESOLVENT, s, 1.0, X, ldx, ncols, W, ldw, scratch, p->stream);
+    const int rc = st_fd_apply64(p, FD_MASS_RESOLVENT, s, 1.0, X, ldx, ncols, W, ldw, scratch, p->stream);
+    st_tune_set_session(saved);
+    return rc;
 }

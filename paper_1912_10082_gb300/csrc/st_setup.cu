@@ -490,6 +490,10 @@ extern "C" int st_setup(const st_desc* d, st_problem** out) {
     if (p->d.maxit <= 0) p->d.maxit = 400;
     if (p->d.max_basis <= 0) p->d.max_basis = 2048;
     p->stream = (cudaStream_t)d->stream;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        p->device = 0;
+    }
     p->n_t = d->n_t;
     p->dt = d->T / d->n_t;
     p->kappa = d->kappa > 0 ? d->kappa : 1.0;

@@ -93,6 +93,11 @@ public:
         return 0;
     }
     int precondition(int dst, int src) override {
+        if (zero_) {   // a preconditioner whose output truncates to rank 0
+            v_[dst] = Factors{};
+            v_[dst].r = 0;
+            return 0;
+        }
         if (!exact_) {
             v_[dst] = v_[src];
             return 0;
@@ -105,6 +110,7 @@ public:
         truncate(X, v_[dst]);
         return 0;
     }
+    void set_zero_preconditioner(bool z) { zero_ = z; }
     int rank(int id) const override {
         auto it = v_.find(id);
         return it == v_.end() ? 0 : it->second.r;
@@ -149,6 +155,7 @@ private:
     bool ok_ = true;
     double trunc_;
     bool exact_;
+    bool zero_ = false;
     std::map<int, Factors> v_;
 };
 
@@ -207,6 +214,7 @@ int main(int argc, char** argv) {
     o.maxit = std::atoi(argv[3]);
     o.tol = std::atof(argv[4]);
     DenseBackend b(nh, nt, M, A, D, C, std::atof(argv[5]), exact);
+    b.set_zero_preconditioner(std::string(argv[2]) == "zero");
     Factors& rhs = b.at(0);
     rhs.r = p;
     rhs.P = F1;

@@ -7,6 +7,8 @@ admission rule keeps requests whose footprints do not fit together from
 running at the same time.
 """
 
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -147,8 +149,10 @@ def test_admission_policy_orders_waiting_requests(policy):
     small = [req(7, 8, 3 + i) for i in range(3)]
     with st.Executor(slots=1, policy=policy) as ex:
         ex.submit(*blocker, tag=0)
+        t_end = time.monotonic() + 60.0
         while ex.pending()[0] > 0:   # the blocker is admitted before the others arrive
-            pass
+            assert time.monotonic() < t_end, "the first request was not admitted within 60 s"
+            time.sleep(0.001)
         ex.submit(*big, tag=1)
         for i, s in enumerate(small):
             ex.submit(*s, tag=2 + i)

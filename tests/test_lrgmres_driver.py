@@ -125,3 +125,15 @@ def test_truncation_core_matches_the_oracle(exe, tmp_path, nh, nt, r, rank):
     assert k == Pr.shape[1] == (rank - 1 if rank > 1 else 1)
     assert np.linalg.norm(Xt - Pr @ Qr.T) <= 1e-13 * np.linalg.norm(X)
     assert abs(np.linalg.norm(X - Xt) - (s[-1] if rank > 1 else 0.0)) <= 1e-14 * s[0]
+
+
+def test_vanishing_preconditioned_direction_is_stagnation_not_convergence(exe, tmp_path):
+    """A preconditioner whose output truncates to rank 0 makes h(j,j) and h(j+1,j) vanish together.  The
+    least-squares problem is then singular at that step: the driver must report stagnation (not converged,
+    the estimate unchanged at |g_j| / beta = 1) and leave the step out of the solution (X = 0)."""
+    prob = problem(1, 5, 4, 1, 8)
+    got = run(exe, tmp_path, prob, "zero", 5, 1e-8, 1e-14)
+    assert not got["converged"]
+    assert got["its"] == 0
+    assert np.allclose(got["hist"], [1.0, 1.0], rtol=0, atol=1e-15)
+    assert np.all(got["X"] == 0.0)
