@@ -1,12 +1,16 @@
 """Benchmark: space-time DoF/s of the space-time Petrov-Galerkin heat solve on GB300.
 
-One step = one rational Krylov Galerkin solve (st_solve: rank compression,
-shifted solves, block Gram-Schmidt, projection, projected Sylvester solve,
-residual check, low-rank output) of the named workload, with the load factors
-resident in HBM.  The default workload is the 2D heat problem on a 255 x 255
-Q1 grid with 256 time intervals and the manufactured load (plain FP64 solve),
-compared on the same GPU with the mixed-precision solve and with Crank-Nicolson
-time stepping.  Prints one JSON line (rank 0).
+Default workload (``batched``): 256 independent 2D heat problems (grid side from
+{63, 127, 255}, n_t from {64, ..., 512}, kappa 10^U(-1,1), rank-2 Gaussian loads),
+solved to a relative residual of 1e-8 in mixed precision by st_solve_batch: the
+rational Krylov Galerkin method (paper Section 4) for every problem, in lock step,
+every device step one grouped launch over the problems still iterating.  One step
+= one solve of the whole batch with the load factors resident in HBM.  Compared on
+the same GPU with the FP64 batch, batched Crank-Nicolson, the thread-per-slot
+executor, and single heat2d_gauss / heat3d solves.  Prints one JSON line (rank 0).
+
+Other workloads: ``--workload heat2d|heat2d_gauss|heat3d|heat3d_small`` (one
+st_solve per step), ``served`` (a Poisson request stream through the executor).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                        [--impl ours|reference]
@@ -318,97 +322,182 @@ def cpu_baseline(wl):
     return line["cpu_baseline"]
 
 
+def single_comparators(st, torch, names, stream):
+    """Single-problem workloads on the same GPU (one warm-up and one timed solve each): mixed and FP64 RKSM
+    and FP64 Crank-Nicolson, DoF/s each."""
+    import workloads
+    out = {}
+    for name in names:
+        wl = workloads.WORKLOADS[name]
+        entry = {}
+        for prec, tag in ((st.ST_MIXED, "mixed_rksm"), (st.ST_FP64, "fp64_rksm")):
+            with st.Problem(wl["dim"], wl["n"], wl["n_t"], wl["T"], kappa=wl.get("kappa", 1.0), precision=prec,
+                            tol=1e-8, maxit=400, stream=stream) as prob:
+                with torch.cuda.stream(stream):
+                    f1, f2 = make_inputs(st, prob, wl, torch)
+                stream.synchronize()
+                ms = []
+                for it in range(2):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    V, Y, stats, status = prob.solve(f1, f2)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                entry[tag] = {"value": prob.n_h * prob.n_t / (ms[-1] * 1e-3), "ms": ms[-1],
+                              "iterations": stats["iterations"], "relres": stats["relres"]}
+                if prec == st.ST_FP64:
+                    U = st.empty_colmajor(prob.n_h, prob.n_t)
+                    ms = []
+                    for it in range(2):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        prob.timestep_cn(f1, f2, U)
+                        e1.record(stream)
+                        e1.synchronize()
+                        ms.append(e0.elapsed_time(e1))
+                    entry["cn_fp64"] = {"value": prob.n_h * prob.n_t / (ms[-1] * 1e-3), "ms": ms[-1]}
+                    del U
+        out[name] = entry
+        print(f"[bench] {name}: " + ", ".join(f"{k} {v['ms']:.1f} ms" for k, v in entry.items()), file=sys.stderr,
+              flush=True)
+    return out
+
+
 def bench_batched(args, wl, rank, world, local):
-    """Batched workload: many 2D instances of mixed sizes solved at once through the executor."""
+    """Batched workload: 256 2D heat instances of mixed sizes solved at once by st_solve_batch (lock-step RKSM,
+    every device step one grouped launch over the instances still iterating)."""
     import torch
     import paper_1912_10082_gb300 as st
     from paper_1912_10082_gb300 import serve
     import workloads
 
     torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    pk = peaks()
     insts = workloads.batched_instances(count=wl["count"], seed=wl["seed"], p=wl["p"])
-    dev = []
-    for r in insts:
-        d = dict(r)
-        for key in ("F1", "F2"):
-            t = st.empty_colmajor(*r[key].shape)
-            t.copy_(torch.from_numpy(r[key]))
-            d[key] = t
-        dev.append(d)
-    torch.cuda.synchronize()
-    slots = args.slots
     dof = sum(r["n"] ** 2 * r["n_t"] for r in insts)
-    tune = (0, 0.0) if args.autotune == "off" else autotune_grids(st, [(2, r["n"]) for r in insts], wl["p"])
-    choices = choice_summary(tuned_choices(st)) if tune[0] else None
+    stream = torch.cuda.Stream()
+    F1d = [st.colmajor(torch.from_numpy(r["F1"]).cuda()) for r in insts]
+    F2d = [st.colmajor(torch.from_numpy(r["F2"]).cuda()) for r in insts]
+    torch.cuda.synchronize()
 
-    def timed(prec, method, steps, warmup, data):
-        res = None
+    def problems(prec):
+        return [st.Problem(2, r["n"], r["n_t"], 1.0, r["kappa"], precision=prec, tol=1e-8, maxit=400, stream=stream)
+                for r in insts]
+
+    def timed(probs, F1s, F2s, steps, warmup):
         for _ in range(warmup):
-            serve.run_batch(data, precision=prec, slots=slots, method=method)
+            st.solve_batch(probs, F1s, F2s, stream=stream)
         torch.cuda.synchronize()
-        ms, lc = [], st.launch_count()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        ms, lc, res, bs = [], st.launch_count(), None, None
         for _ in range(steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = serve.run_batch(data, precision=prec, slots=slots, method=method)
-            torch.cuda.synchronize()
-            ms.append(1e3 * (time.perf_counter() - t0))
-        return ms, res, st.launch_count() - lc
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res, bs = st.solve_batch(probs, F1s, F2s, stream=stream)   # synchronises before returning
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        launches = st.launch_count() - lc
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        return ms, res, bs, launches
 
+    mixed = problems(st.ST_MIXED)
     with ClockSampler(local) as clk:
-        ms, res, launches = timed(st.ST_MIXED, st.ST_METHOD_RKSM, args.steps, args.warmup, dev)
-    print(f"[bench] batched mixed RKSM: {ms} ms per batch", file=sys.stderr, flush=True)
-    ms_step = statistics.mean(ms)
-    value = world * dof / (ms_step * 1e-3)
-    bad = [r for r in res["results"] if r["status"] != st.ST_OK]
-    its = [r["stats"]["iterations"] for r in res["results"]]
-    # where the slots' time went (host clock between synchronisation points, summed over instances)
-    names = ["compress", "shift_solve_cgs", "block_qr", "products", "projected_solve", "residual", "output",
-             "shifts"]
-    phase_s = {nm: sum(r["stats"]["ms_phase"][i] for r in res["results"]) * 1e-3 for i, nm in enumerate(names)}
-    busy_s = sum(r["t_end"] - r["t_start"] for r in res["results"])
-    comps = {}
-    ms64, _, _ = timed(st.ST_FP64, st.ST_METHOD_RKSM, 1, 0, dev)
-    comps["fp64_rksm_batched"] = {"value": dof / (ms64[0] * 1e-3), "ms_per_step": ms64[0]}
-    mscn, _, _ = timed(st.ST_FP64, st.ST_METHOD_CN, 1, 0, dev)
-    comps["cn_fp64_batched"] = {"value": dof / (mscn[0] * 1e-3), "ms_per_step": mscn[0]}
-    print(f"[bench] batched fp64 RKSM {ms64[0]:.1f} ms, CN {mscn[0]:.1f} ms", file=sys.stderr, flush=True)
-    # one instance at a time on one stream (no batching), mixed precision
-    t0 = time.perf_counter()
-    serve.run_batch(dev[:32], precision=st.ST_MIXED, slots=1)
-    el = time.perf_counter() - t0
-    comps["mixed_rksm_one_at_a_time_first32"] = {
-        "value": sum(r["n"] ** 2 * r["n_t"] for r in insts[:32]) / el, "ms_per_step": 1e3 * el}
-    # end to end: host factors staged inside every solve; results = per-instance statistics
-    host = [dict(r) for r in insts]
-    for r in host:
-        for key in ("F1", "F2"):
+        ms, res, bs, launches = timed(mixed, F1d, F2d, args.steps, args.warmup)
+    tot_ms = max_over_ranks(sum(ms), pg, device="cuda")
+    ms_step = tot_ms / args.steps
+    value = job_throughput(dof, world, args.steps, tot_ms)
+    print(f"[bench] batched mixed RKSM (grouped): {ms} ms per batch", file=sys.stderr, flush=True)
+    bad = [i for i, r in enumerate(res) if r[3] != st.ST_OK]
+    its = [r[2]["iterations"] for r in res]
+    relres = [r[2]["relres"] for r in res]
+    # per-kernel profile of one more batch solve (separate pass after the timed region)
+    st.profile_begin()
+    st.solve_batch(mixed, F1d, F2d, stream=stream)
+    torch.cuda.synchronize()
+    prof = st.profile_end()
+    roof = roofline_of(prof, pk["hbm_gbs"])
+    if roof:
+        roof["peak_source"] = pk["src"] if roof["unit"] == "GB/s" else "derived"
+    # certification: the FP64 residual of a sample of the solutions, from their factors (independent formula)
+    cert = []
+    for i in range(0, len(insts), 32):
+        V, Y = res[i][0], res[i][1]
+        cert.append(mixed[i].residual_lowrank(V, Y, F1d[i], F2d[i]))
+    # end to end through the public API with host buffers: the loads staged from pinned host memory inside the
+    # call, the per-instance statistics returned to the host
+    F1h, F2h = [], []
+    for r in insts:
+        for key, lst in (("F1", F1h), ("F2", F2h)):
             t = torch.empty((r[key].shape[1], r[key].shape[0]), dtype=torch.float64).pin_memory().t()
             t.copy_(torch.from_numpy(r[key]))
-            r[key] = t
-    mse, rese, _ = timed(st.ST_MIXED, st.ST_METHOD_RKSM, 1, 0, host)
-    h2d = sum((r["F1"].size + r["F2"].size) * 8 for r in insts)
-    from paper_1912_10082_gb300 import StResult
+            lst.append(t)
+    mse, _, _, _ = timed(mixed, F1h, F2h, 1, 1)
     import ctypes
+    h2d = sum((r["F1"].size + r["F2"].size) * 8 for r in insts)
     e2e = {"value": world * dof / (mse[0] * 1e-3), "unit": "DoF/s", "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(len(insts) * ctypes.sizeof(StResult))}
+           "d2h_bytes_per_step": int(len(insts) * (ctypes.sizeof(st.StStats) + ctypes.sizeof(ctypes.c_int)))}
+    for p in mixed:
+        p.close()
+    comps = {}
+    fp64 = problems(st.ST_FP64)
+    ms64, res64, bs64, _ = timed(fp64, F1d, F2d, 1, 1)
+    comps["fp64_rksm_batched"] = {"value": dof / (ms64[0] * 1e-3), "ms_per_step": ms64[0],
+                                  "failed": sum(r[3] != st.ST_OK for r in res64), "rounds": bs64["rounds"]}
+    for p in fp64:
+        p.close()
+    dev = [dict(r, F1=F1d[i], F2=F2d[i]) for i, r in enumerate(insts)]
+    t0 = time.perf_counter()
+    serve.run_batch(dev, precision=st.ST_FP64, slots=args.slots, method=st.ST_METHOD_CN)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    comps["cn_fp64_batched"] = {"value": dof / el, "ms_per_step": 1e3 * el,
+                                "how": f"executor, {args.slots} slots, one CUDA graph per instance"}
+    t0 = time.perf_counter()
+    serve.run_batch(dev, precision=st.ST_MIXED, slots=args.slots, method=st.ST_METHOD_RKSM)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    comps["mixed_rksm_executor"] = {"value": dof / el, "ms_per_step": 1e3 * el,
+                                    "how": f"executor, {args.slots} slots, single-problem launches per stream"}
+    print(f"[bench] batched fp64 {ms64[0]:.1f} ms, CN {comps['cn_fp64_batched']['ms_per_step']:.1f} ms, "
+          f"executor mixed {comps['mixed_rksm_executor']['ms_per_step']:.1f} ms", file=sys.stderr, flush=True)
+    if not args.no_singles:
+        comps["single_problems"] = single_comparators(st, torch, ("heat2d_gauss", "heat3d"), stream)
     if rank != 0:
         return 0
+    cb = None if args.no_cpu_baseline else cpu_baseline(wl)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": workload_desc(wl["name"], wl, args),
-                   "instances": len(insts), "dof": dof, "slots": slots, "tol": 1e-8,
-                   "autotune": {"shapes": tune[0], "seconds": tune[1], "choices": choices},
-                   "l2": "inputs of the batch (%.0f MB) exceed L2" % (sum(r['F1'].nbytes for r in insts) / 1e6),
+                   "instances": len(insts), "dof": dof, "tol": 1e-8, "method": "st_solve_batch (lock-step RKSM)",
+                   "l2": "inputs and bases of the batch (several GB) exceed L2",
                    "parallelism": f"replicas{world}"},
         "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its)),
-                   "slot_busy_s": busy_s, "phase_s": phase_s},
-        "cpu_baseline": None, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
+                   "relres_max": float(max(relres)), "relres_certified_sample_max": float(max(cert)),
+                   "rounds": bs["rounds"], "grouped_launches": bs["grouped_launches"],
+                   "phase_ms": bs["ms_phase"]},
+        "roofline": roof, "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()},
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
         "comparators": comps,
     }
     print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
     return 0
 
 
@@ -495,11 +584,13 @@ def bench_served(args, wl, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="heat2d")
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 8 for batched, else 20)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 3 for batched, else 5)""")
+    ap.add_argument("--workload", default="batched")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-singles", action="store_true",
+                    help="batched workload: skip the single-problem comparators (heat2d_gauss, heat3d)")
     ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
                     help="time the shifted solves' launch variants before the warm-up and keep the fastest (auto: on "
                          "for the batched and served workloads, off for single problems, which keep the launch "
@@ -510,6 +601,11 @@ def main():
     ap.add_argument("--policy", default="hrrn", choices=["fifo", "hrrn"],
                     help="served workload: admission order of the executor")
     args = ap.parse_args()
+    many = args.workload in ("batched", "served")
+    if args.steps is None:
+        args.steps = 8 if many else 20
+    if args.warmup is None:
+        args.warmup = 3 if many else 5
     args.warmup = max(3, args.warmup)
 
     import workloads

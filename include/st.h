@@ -274,6 +274,53 @@ int st_autotune_load(const char* path, const char* device_tag, int* loaded);
 int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
              st_solution* sol, st_stats* stats);
 
+/* Statistics of one st_solve_batch call. */
+typedef struct st_batch_stats {
+    int instances;          /* problems in the call */
+    int grouped;            /* problems solved on the grouped lock-step path */
+    int rounds;             /* lock-step iterations (the most iterations of a grouped problem) */
+    int grouped_launches;   /* grouped kernel launches issued */
+    int groups;             /* lock-step groups run concurrently, each on its own stream */
+    double ms_total;        /* wall time of the call (host clock) */
+    double ms_phase[8];     /* wall time: 0 rank compression, 1 shifted solves and block Gram-Schmidt
+                               (and the start blocks), 2 block QR decisions on the host (with the
+                               per-problem fallbacks), 3 block QR on the device and products of the
+                               new blocks, 4 projected solves, 5 residual checks, 6 output, 7 shifts */
+} st_batch_stats;
+
+/* st_solve_batch -- st_solve for `count` independent problems at once
+ * (Section 4's method for each; the paper solves one problem at a time).
+ * The problems advance in lock step, one rational Krylov iteration per
+ * round: every device step of a round (the shifted solves, block
+ * Gram-Schmidt, block QR and products of the new blocks, the residual
+ * checks) is ONE launch of a grouped kernel over all problems still
+ * iterating, and each round synchronises with the host once per phase for
+ * the whole group; the small host problems of a round (rank decisions,
+ * shifts, projected solves) run on a pool of host threads.  The problems
+ * run as `groups` such lock-step groups (<= 0: min(4, count / 32), at least
+ * 1; problems dealt by decreasing size) on streams and host threads of their
+ * own, so one group's host work overlaps the others' device work; `stream`
+ * waits for all of them.  Each problem
+ * takes exactly the steps and decisions st_solve takes on it, and the
+ * grouped kernels run the per-problem kernels' tiles, so problems[i]'s
+ * result does not depend on the other problems of the call.
+ * problems: distinct handles of the current device.  The grouped path
+ * covers box heat problems of dimension 2 or 3 with at least 3 points a
+ * side; the others (dimension 1, user matrices, convection-diffusion) are
+ * solved one after another by st_solve's driver on the same stream.
+ * F1[i] (n_h x ncols[i], ld ldf1[i]) and F2[i] (n_t x ncols[i], ld ldf2[i]):
+ * host or device, 1 <= ncols[i] <= 16.  Outputs per problem (arrays of
+ * count entries): sols (may be NULL; as st_solve, V and Y owned by the
+ * handle, U_dense filled if given), stats (may be NULL), status (required:
+ * st_solve's return value for that problem).  Work runs on `stream` (NULL:
+ * default stream); each handle's own stream is restored on return.  Returns
+ * ST_OK when the call ran (see status[]), ST_EINVAL for bad arguments, or
+ * ST_ENOMEM / ST_ECUDA when a failure stopped the whole call.  bstats may be
+ * NULL.  Synchronises. */
+int st_solve_batch(int count, st_problem* const* problems, const double* const* F1, const int* ldf1,
+                   const double* const* F2, const int* ldf2, const int* ncols, st_solution* sols,
+                   st_stats* stats, int* status, void* stream, int groups, st_batch_stats* bstats);
+
 /* st_residual -- relres = ||F - M U D_t^T - A U C_t^T||_F / ||F1 F2^T||_F in
  * FP64 for a dense U (device double, ld >= n_h) (Section 5 stopping
  * quantity).  F1, F2 host or device.  relres: host.  Synchronises. */

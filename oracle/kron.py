@@ -99,6 +99,37 @@ def forward_substitution_cg(M, A, D, C, F1: np.ndarray, F2: np.ndarray, steps: i
     return U
 
 
+class _NormalOperator:
+    """x -> B^T B x for the normal equations of a nonsymmetric block."""
+
+    def __init__(self, B):
+        self.B = B
+        self.BT = B.T.tocsr()
+
+    def __matmul__(self, x):
+        return self.BT @ (self.B @ x)
+
+
+def forward_substitution_normal_cg(M, A, D, C, F1: np.ndarray, F2: np.ndarray, steps: int, rtol: float = 1e-15):
+    """forward_substitution_cg for a nonsymmetric operator (convection-diffusion): each diagonal block
+    B_l = D[l,l] M + C[l,l] A is nonsingular but not symmetric, so the block equation B_l u = r is solved as
+    the normal equations B_l^T B_l u = B_l^T r by the same textbook conjugate gradients (CGNR, Hestenes and
+    Stiefel 1952, Section 10).  The first ``steps`` columns only, as forward_substitution_cg."""
+    n_h = M.shape[0]
+    U = np.zeros((n_h, steps))
+    prev = None
+    for l in range(steps):
+        Bl = (D[l, l] * M + C[l, l] * A).tocsr()
+        rhs = F1 @ F2[l]
+        if l > 0:
+            rhs = rhs - (D[l, l - 1] * (M @ prev) + C[l, l - 1] * (A @ prev))
+        Nl = _NormalOperator(Bl)
+        x = _cg(Nl, Nl.BT @ rhs, rtol, 50 * n_h)
+        U[:, l] = x
+        prev = x
+    return U
+
+
 def _cg(B, b: np.ndarray, rtol: float, maxiter: int) -> np.ndarray:
     """Textbook conjugate gradients (Hestenes-Stiefel) from x = 0, stopping at ||r|| <= rtol ||b||."""
     x = np.zeros_like(b)

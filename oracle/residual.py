@@ -31,3 +31,25 @@ def relres_lowrank(M, A, D, C, V: np.ndarray, Y: np.ndarray, F1: np.ndarray,
     L = np.hstack([F1, M @ V, A @ V])
     Z = np.hstack([F2, -(D @ Y.T), -(C @ Y.T)])
     return lowrank_fro(L, Z) / lowrank_fro(F1, F2)
+
+
+def relres_lowrank_by_columns(M, A, D, C, V: np.ndarray, Y: np.ndarray, F1: np.ndarray, F2: np.ndarray,
+                              chunk: int = 64) -> float:
+    """The dense residual's relative Frobenius norm for U = V Y, without holding U or R whole.
+
+    R = F1 F2^T - M V (Y D^T) - A V (Y C^T) (paper Section 4's matrix equation) is formed a block of
+    ``chunk`` time columns at a time and its squared norm summed; the load's norm comes from F1, F2
+    the same way.  This is relres_dense written out block by block, for solutions too large to form.
+    """
+    YD = Y @ D.T
+    YC = Y @ C.T
+    num = 0.0
+    den = 0.0
+    n_t = Y.shape[1]
+    for c0 in range(0, n_t, chunk):
+        c1 = min(n_t, c0 + chunk)
+        F = F1 @ F2[c0:c1].T
+        R = F - (M @ (V @ YD[:, c0:c1]) + A @ (V @ YC[:, c0:c1]))
+        num += float(np.sum(R * R))
+        den += float(np.sum(F * F))
+    return float(np.sqrt(num / den))

@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
     "st_executor_destroy", "st_executor_set_policy", "st_autotune", "st_autotune_reset", "st_autotune_count",
-    "st_autotune_save", "st_autotune_load",
+    "st_autotune_save", "st_autotune_load", "st_solve_batch",
 )
 
 
@@ -83,6 +83,19 @@ class StResult(C.Structure):
         d = {name: getattr(self, name) for name, _ in self._fields_ if name not in ("stats", "message")}
         d["stats"] = self.stats.as_dict()
         d["message"] = self.message.decode(errors="replace")
+        return d
+
+
+class StBatchStats(C.Structure):
+    _fields_ = [("instances", C.c_int), ("grouped", C.c_int), ("rounds", C.c_int), ("grouped_launches", C.c_int),
+                ("groups", C.c_int), ("ms_total", C.c_double), ("ms_phase", C.c_double * 8)]
+
+    PHASES = ("compress", "shift_solve_cgs", "block_qr_host", "qr_products", "projected_solve", "residual",
+              "output", "shifts")
+
+    def as_dict(self):
+        d = {name: getattr(self, name) for name, _ in self._fields_ if name != "ms_phase"}
+        d["ms_phase"] = dict(zip(self.PHASES, list(self.ms_phase)))
         return d
 
 
@@ -137,6 +150,9 @@ def lib() -> C.CDLL:
         "st_executor_destroy": ([vp], i),
         "st_profile_begin": ([], i),
         "st_profile_end": ([C.POINTER(StKernelTime), i, C.POINTER(i)], i),
+        "st_solve_batch": ([i, C.POINTER(vp), C.POINTER(vp), C.POINTER(i), C.POINTER(vp), C.POINTER(i),
+                            C.POINTER(i), C.POINTER(StSolution), C.POINTER(StStats), C.POINTER(i), vp, i,
+                            C.POINTER(StBatchStats)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -360,6 +376,52 @@ class Problem:
         pu, lu, _, _ = _ptr_ld(U)
         _check(lib().st_timestep_cn(self.h, p1, l1, p2, l2, m, pu, lu), "st_timestep_cn")
         return U
+
+
+def solve_batch(problems, F1s, F2s, U_dense=None, stream=None, groups=0):
+    """st_solve_batch: solve every problem of the list at once (lock-step RKSM, grouped launches).
+
+    ``problems``: distinct Problem objects; ``F1s[i]``, ``F2s[i]``: column-major load factors (host numpy or
+    device torch).  ``U_dense`` (optional list, entries may be None) receives dense solutions.  Returns
+    (results, batch_stats): results[i] = (V, Y, stats, status) as Problem.solve, V and Y views of the
+    problem's own memory; batch_stats a dict of st_batch_stats.  ``groups``: lock-step groups run
+    concurrently (0: the library's choice).
+    """
+    import torch
+    n = len(problems)
+    hs = (C.c_void_p * n)(*[p.h.value if isinstance(p.h, C.c_void_p) else p.h for p in problems])
+    f1p = (C.c_void_p * n)()
+    f2p = (C.c_void_p * n)()
+    l1 = (C.c_int * n)()
+    l2 = (C.c_int * n)()
+    nc = (C.c_int * n)()
+    for i in range(n):
+        p1, ld1, _, m = _ptr_ld(F1s[i])
+        p2, ld2, _, _ = _ptr_ld(F2s[i])
+        f1p[i], f2p[i], l1[i], l2[i], nc[i] = p1, p2, ld1, ld2, m
+    sols = (StSolution * n)()
+    if U_dense is not None:
+        for i, U in enumerate(U_dense):
+            if U is not None:
+                pu, lu, _, _ = _ptr_ld(U)
+                sols[i].U_dense, sols[i].ldu = pu, lu
+    stats = (StStats * n)()
+    status = (C.c_int * n)()
+    bs = StBatchStats()
+    sv = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().st_solve_batch(n, hs, f1p, l1, f2p, l2, nc, sols, stats, status, sv, int(groups), C.byref(bs)),
+           "st_solve_batch")
+    out = []
+    for i, prob in enumerate(problems):
+        k = sols[i].k
+        if k > 0 and sols[i].V:
+            V = torch.as_tensor(_DevView(sols[i].V, prob.n_h, k, prob.n_h), device="cuda")
+            Y = torch.as_tensor(_DevView(sols[i].Y, k, prob.n_t, k), device="cuda")
+        else:
+            V = torch.zeros((prob.n_h, 0), dtype=torch.float64, device="cuda")
+            Y = torch.zeros((0, prob.n_t), dtype=torch.float64, device="cuda")
+        out.append((V, Y, stats[i].as_dict(), int(status[i])))
+    return out, bs.as_dict()
 
 
 def request_bytes(desc: StDesc, p: int) -> float:

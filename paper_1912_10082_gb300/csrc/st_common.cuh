@@ -2,7 +2,10 @@
 #pragma once
 
 #include <atomic>
+#include <condition_variable>
 #include <functional>
+#include <mutex>
+#include <thread>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -171,6 +174,44 @@ int st_cn_rhs_step(st_problem* p, const double* u, const double* F1, int ldf1, c
 enum FdKind { FD_MASS_RESOLVENT = 0, FD_RESOLVENT = 1, FD_MASS_INVERSE = 2 };
 int st_fd_apply64(st_problem* p, FdKind kind, double shift, double coef, const double* X, int ldx,
                   int ncols, double* W, int ldw, double* tmp, cudaStream_t s);
+// Constant box stencils of two spatial operators (27 values each, (dz, dy, dx)
+// order, zeros beyond the grid's dimension), passed to the box-stencil kernels.
+template <typename T>
+struct BoxPair {
+    T s[2][27];
+};
+
+// 1D factors of a box problem's M and A (the sum-factorised apply): per
+// direction d the mass stencil (m1, m0, m1) and the operator stencil
+// (am, a0, ap) on the offsets (-1, 0, +1); hdt = dt / 2.
+struct SfStencil {
+    float m0[3], m1[3];
+    float am[3], a0[3], ap[3];
+    float hdt;
+};
+
+// Epilogue of a fast-diagonalisation mode product: a constant factor and,
+// for the middle product, the spectral weight of the output entry.
+struct FdEpi {
+    int scale;          // 0: C = coef * acc; 1: C = coef * omega(e) * acc
+    int left;           // 1: linear index e = m * J + j (batch = one vector column); 0: e = m
+    long long J;
+    int dim, nx, ny, nz;
+    const double *l0, *l1, *l2;   // eigenvalues per direction
+    const double *c0, *c1, *c2;   // c2 factors per direction (resolvent of a general right-hand side)
+    const float *f0, *f1, *f2;    // FP32 copies of l0..l2 and of c0..c2, for FP32 products
+    const float *g0, *g1, *g2;
+    int kind;           // FdKind
+    double kappa, shift, coef;
+};
+
+// Batch index z = blockIdx.z splits into (z2, z1) = (z / nb1, z % nb1); the
+// operand offsets are z1 * s*1 + z2 * s*2.
+struct Batch2 {
+    int nb1;
+    long long sA1, sA2, sB1, sB2, sC1, sC2;
+};
+
 // x-line preconditioner (convection-diffusion with |beta_x| the largest
 // component): W = coef (eps K + beta_x Gx (x) M_rest + s M)^{-1} X, exact in
 // 1D; y (and z) by sine transforms, x by Thomas sweeps with the factors of
@@ -253,6 +294,37 @@ class Barrier {
     int n;
 };
 void run(int T, const std::function<void(int, Barrier&)>& body);   // body(t, barrier), t = 0 on the caller
+// While a ThreadBudget lives on a thread, threads_for() returns at most n
+// there: work already spread over a Pool's threads starts thread teams of at
+// most its share of the cores (n = 1: none).
+struct ThreadBudget {
+    explicit ThreadBudget(int n);
+    ~ThreadBudget();
+    int prev;
+};
+// Persistent worker threads for loops over independent items (the instances
+// of a batched solve).  run(n, f) calls f(i) for every i in [0, n) on the
+// workers and the caller, each item on one thread, and returns when all are
+// done.  Each item runs under a ThreadBudget of max(1, threads / n), so a few
+// large items still use the cores.  Not reentrant.
+class Pool {
+   public:
+    explicit Pool(int threads);   // total threads including the caller, >= 1
+    ~Pool();
+    void run(int n, const std::function<void(int)>& f);
+    int threads() const { return (int)workers_.size() + 1; }
+
+   private:
+    void work();
+    std::vector<std::thread> workers_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int)>* job_ = nullptr;
+    std::atomic<int> next_{0};
+    int n_ = 0, busy_ = 0;
+    unsigned gen_ = 0;
+    bool stop_ = false;
+};
 }  // namespace hostpar
 
 namespace dense {

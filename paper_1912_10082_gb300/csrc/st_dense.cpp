@@ -22,10 +22,17 @@ static std::atomic<int> g_active{0};
 ActiveSolve::ActiveSolve() { g_active.fetch_add(1); }
 ActiveSolve::~ActiveSolve() { g_active.fetch_sub(1); }
 
+namespace {
+thread_local int t_budget = 0;   // 0: no budget set on this thread
+}
+
+ThreadBudget::ThreadBudget(int n) : prev(t_budget) { t_budget = std::max(1, n); }
+ThreadBudget::~ThreadBudget() { t_budget = prev; }
+
 int threads_for(double flops) {
     static const int hw = std::max(1, (int)std::thread::hardware_concurrency());
     if (flops < 4e6) return 1;
-    const int share = std::max(1, hw / std::max(1, g_active.load()));
+    const int share = t_budget > 0 ? t_budget : std::max(1, hw / std::max(1, g_active.load()));
     return std::max(1, std::min({8, share, (int)(flops / 2e6)}));
 }
 
@@ -53,6 +60,69 @@ void run(int T, const std::function<void(int, Barrier&)>& body) {
     for (int t = 1; t < T; ++t) th.emplace_back([&body, &b, t] { body(t, b); });
     body(0, b);
     for (auto& x : th) x.join();
+}
+
+Pool::Pool(int threads) {
+    for (int t = 1; t < threads; ++t) workers_.emplace_back([this] { work(); });
+}
+
+Pool::~Pool() {
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        stop_ = true;
+        ++gen_;
+    }
+    cv_.notify_all();
+    for (auto& w : workers_) w.join();
+}
+
+void Pool::work() {
+    unsigned seen = 0;
+    while (true) {
+        const std::function<void(int)>* job;
+        int n;
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            cv_.wait(lk, [&] { return gen_ != seen; });
+            seen = gen_;
+            if (stop_) return;
+            job = job_;
+            n = n_;
+            ++busy_;   // before taking an item: run() waits for busy_ == 0
+        }
+        {
+            ThreadBudget budget(std::max(1, threads() / std::max(1, n)));
+            for (int i = next_.fetch_add(1); job && i < n; i = next_.fetch_add(1)) (*job)(i);
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            --busy_;
+        }
+        done_cv_.notify_all();
+    }
+}
+
+void Pool::run(int n, const std::function<void(int)>& f) {
+    if (n <= 0) return;
+    ThreadBudget budget(std::max(1, threads() / n));
+    if (workers_.empty() || n == 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    {
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [&] { return busy_ == 0; });   // no worker is still inside an earlier job
+        job_ = &f;
+        n_ = n;
+        next_.store(0);
+        ++gen_;
+    }
+    cv_.notify_all();
+    for (int i = next_.fetch_add(1); i < n; i = next_.fetch_add(1)) f(i);
+    // every item has been taken; wait for the workers still running theirs
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return busy_ == 0; });
+    job_ = nullptr;
 }
 
 }  // namespace hostpar

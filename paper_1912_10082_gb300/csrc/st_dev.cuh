@@ -1,0 +1,627 @@
+// Device-side building blocks shared by the single-problem kernels
+// (st_kernels.cu) and the grouped kernels of the batched solve
+// (st_group.cu): the fast-diagonalisation epilogue, the tall-skinny and
+// double-float product bodies, the box-stencil product, the block QR helpers
+// and the elementwise column operations.  Each body computes one CTA's share
+// of a launch from explicit block coordinates, so a single-problem kernel
+// (coordinates from blockIdx) and a grouped kernel (coordinates of a tile of
+// one instance of a batch) run the same arithmetic in the same order.
+#pragma once
+
+#include "st_common.cuh"
+
+namespace {
+
+constexpr int kMaxCols = 16;   // widest block handled by the tall-skinny and SpMM kernels
+
+
+
+__device__ __forceinline__ double fd_omega(const FdEpi& ep, long long e) {
+    int x = (int)(e % ep.nx);
+    long long t = e / ep.nx;
+    int y = (int)(t % ep.ny);
+    int z = (int)(t / ep.ny);
+    double lam = ep.l0[x];
+    double w = ep.c0[x];
+    if (ep.dim > 1) {
+        lam += ep.l1[y];
+        w *= ep.c1[y];
+    }
+    if (ep.dim > 2) {
+        lam += ep.l2[z];
+        w *= ep.c2[z];
+    }
+    if (ep.kind == FD_MASS_INVERSE) return w;
+    if (ep.kind == FD_RESOLVENT) return w / (ep.kappa * lam + ep.shift);
+    return 1.0 / (ep.kappa * lam + ep.shift);
+}
+
+// The same weight in FP32 from the FP32 tables (no FP64 instruction).
+__device__ __forceinline__ float fd_omega32(const FdEpi& ep, long long e) {
+    int x = (int)(e % ep.nx);
+    long long t = e / ep.nx;
+    int y = (int)(t % ep.ny);
+    int z = (int)(t / ep.ny);
+    float lam = ep.f0[x];
+    float w = ep.g0[x];
+    if (ep.dim > 1) {
+        lam += ep.f1[y];
+        w *= ep.g1[y];
+    }
+    if (ep.dim > 2) {
+        lam += ep.f2[z];
+        w *= ep.g2[z];
+    }
+    const float kap = (float)ep.kappa, sh = (float)ep.shift;
+    if (ep.kind == FD_MASS_INVERSE) return w;
+    if (ep.kind == FD_RESOLVENT) return w / (kap * lam + sh);
+    return 1.0f / (kap * lam + sh);
+}
+
+
+constexpr int TS_THREADS = 256;
+constexpr int TS_CG = 16;      // basis columns per CTA of H = V^T W
+constexpr int TS_CG_DF = 32;   // the same for the double-float product (half the restaging of W per basis column)
+constexpr int TS_UNROLL = 8;   // independent loads in flight per lane
+
+// Rows of one chunk of H = V^T W: enough chunks that chunks x column groups
+// fill the GPU about four CTAs deep (a few basis columns need many short
+// chunks to keep enough loads in flight), at least 128 rows, and a staged
+// chunk of W of rows x m <= 8192 doubles.
+__host__ __device__ inline int ts_rows(int n, int k, int m) {
+    const int maxr = m <= 8 ? 1024 : 512;
+    const long long groups = (k + 15) / 16;
+    const long long want = 4 * 152;
+    long long nch = (want + groups - 1) / groups;
+    long long r = (n + nch - 1) / nch;
+    r = ((r + 31) / 32) * 32;
+    return (int)(r < 128 ? 128 : (r > maxr ? maxr : r));
+}
+
+// ---------------------------------------------------------------------------
+// Double-float tall-skinny products.  FP64 runs at 1/64 of the FP32 rate on
+// this chip, so the basis products of the mixed-precision solve use
+// double-float arithmetic on the FP32 pipes instead (Dekker, "A floating-point
+// technique for extending the available precision", 1971; Knuth, TAOCP
+// vol. 2, 4.2.2, two-sum): a value is hi + lo with two floats, a product
+// a*b = p + e with e = fma(a, b, -p) exact, and a running sum keeps its
+// rounding error by two-sum.  Every 32 terms the pair is folded into an FP64
+// accumulator.  The result carries about 48 significant bits, with no FP64
+// instruction in the inner loops.  All FP32 operations are explicitly rounded
+// intrinsics so that the compiler cannot contract them.  The basis is kept as
+// (hi, lo) pairs (float2, 8 bytes per entry: the same traffic as FP64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return make_float2(hi, lo);
+}
+
+// (sh, sl) += (oh, ol) for two double-float partial sums (two-sum on the heads).
+__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
+    float s = __fadd_rn(sh, oh);
+    float z = __fsub_rn(s, sh);
+    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(oh, z));
+    sl = __fadd_rn(sl, __fadd_rn(t, ol));
+    sh = s;
+}
+
+// Two double-float multiply-adds at once, (SH, SL)[c] += a * b_c for the two
+// columns c of a pair, with the packed FP32 instructions of sm_100+ (each lane
+// of a packed operation rounds exactly as the scalar one): the product
+// p = a.hi b.hi with its exact error fma(a.hi, b.hi, -p) plus the two cross
+// terms, then a two-sum of p onto the running head.
+// b = (b0.hi, b1.hi, b0.lo, b1.lo).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void df_madd2(float2& SH, float2& SL, float2 a, float4 b) {
+    const float2 Ax = make_float2(a.x, a.x), Ay = make_float2(a.y, a.y);
+    const float2 Bx = make_float2(b.x, b.y), By = make_float2(b.z, b.w);
+    const float2 P = __fmul2_rn(Ax, Bx);
+    float2 E = __ffma2_rn(Ax, Bx, neg2(P));
+    E = __ffma2_rn(Ax, By, E);
+    E = __ffma2_rn(Ay, Bx, E);
+    const float2 S = __fadd2_rn(SH, P);
+    const float2 Z = __fadd2_rn(S, neg2(SH));
+    const float2 T = __fadd2_rn(__fadd2_rn(SH, neg2(__fadd2_rn(S, neg2(Z)))), __fadd2_rn(P, neg2(Z)));
+    SL = __fadd2_rn(SL, __fadd2_rn(T, E));
+    SH = S;
+}
+
+template <typename T, int TM, int SIDE>
+__device__ __forceinline__ void gemm_fold_body(int n, int other, const T* __restrict__ X, long long ldx,
+                                                   const T* __restrict__ H0, const T* __restrict__ H1,
+                                                   const T* __restrict__ G0, const T* __restrict__ G1,
+                                                   T* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep, int bx, int by, int bz) {
+    // FP32: the whole folded contraction of a 127-point direction (K <= 64) in one
+    // staged step (fewer barriers, more loads in flight); FP64: 16 at a time
+    constexpr int BM = 16 * TM, BN = 16 * TM, BK = sizeof(T) == 4 ? 64 : 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN];
+    const int par = bz & 1;
+    const int zb = bz >> 1;
+    const int z1 = zb % bt.nb1, z2 = zb / bt.nb1;
+    const int K = par ? n / 2 : (n + 1) / 2;   // folded length = outputs of this parity
+    const int mid = (n & 1) ? (n - 1) / 2 : -1;
+    const T sgn = par ? T(-1) : T(1);
+    const int M = SIDE == 0 ? other : K;
+    const int N = SIDE == 0 ? K : other;
+    const int m0 = by * BM, n0 = bx * BN;
+    if (m0 >= M || n0 >= N) return;   // the odd parity has one output fewer for odd n
+    if (SIDE == 0) {
+        X += (size_t)z1 * bt.sA1 + (size_t)z2 * bt.sA2;
+    } else {
+        X += (size_t)z1 * bt.sB1 + (size_t)z2 * bt.sB2;
+    }
+    C += (size_t)z1 * bt.sC1 + (size_t)z2 * bt.sC2;
+    const T* Hp = par ? H1 : H0;   // K x K' (k-major), SIDE 0 right operand
+    const T* Gp = par ? G1 : G0;   // K' x K (output-major), SIDE 1 left operand
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    T acc[TM][TM];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += 256) {
+            int mm = idx / BK, kk = idx % BK;
+            int gm = m0 + mm, gk = k0 + kk;
+            T v = T(0);
+            if (gm < M && gk < K) {
+                if (SIDE == 0) {
+                    const T* row = X + (size_t)gm * ldx;
+                    v = gk == mid ? row[gk] : row[gk] + sgn * row[n - 1 - gk];
+                } else {
+                    v = Gp[(size_t)gm * K + gk];
+                }
+            }
+            As[kk][mm] = v;
+        }
+        for (int idx = tid; idx < BK * BN; idx += 256) {
+            int kk = idx / BN, nn = idx % BN;
+            int gk = k0 + kk, gn = n0 + nn;
+            T v = T(0);
+            if (gk < K && gn < N) {
+                if (SIDE == 0) {
+                    v = Hp[(size_t)gk * K + gn];
+                } else {
+                    v = gk == mid ? X[(size_t)gk * ldx + gn]
+                                  : X[(size_t)gk * ldx + gn] + sgn * X[(size_t)(n - 1 - gk) * ldx + gn];
+                }
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], bb[TM];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TM; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TM; ++j) acc[i][j] += a[i] * bb[j];
+        }
+        __syncthreads();
+    }
+    const float fcoef = (float)ep.coef;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+            int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            // output coordinates of the unfolded product
+            long long om = SIDE == 0 ? gm : 2LL * gm + par;
+            long long on = SIDE == 0 ? 2LL * gn + par : gn;
+            if constexpr (sizeof(T) == 4) {
+                // FP32 epilogue: FP64 conversions and products here would run on the 1/64-rate pipe
+                float f = fcoef;
+                if (ep.scale) f *= fd_omega32(ep, ep.left ? om * ep.J + on : on);
+                C[(size_t)om * ldc + on] = f * acc[i][j];
+            } else {
+                double f = ep.coef;
+                if (ep.scale) {
+                    long long e = ep.left ? om * ep.J + on : on;
+                    f *= fd_omega(ep, e);
+                }
+                C[(size_t)om * ldc + on] = (T)(f * (double)acc[i][j]);
+            }
+        }
+    }
+}
+
+template <typename T, int DIM, int YB, int ZB>
+__device__ __forceinline__ void stencil_box_body(int nx, int ny, int nz, BoxPair<T> S, const T* __restrict__ X,
+                                                     long long ldx, T beta, T* __restrict__ O1, long long ld1,
+                                                     T* __restrict__ O2, long long ld2, int bx, int by) {
+    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
+    constexpr int NV = RY * RZ * 3;
+    const int nxs = (nx + 31) / 32, nyb = (ny + 8 * YB - 1) / (8 * YB);
+    int b = bx;
+    const int xs = b % nxs;
+    b /= nxs;
+    const int yb = b % nyb;
+    const int zb = b / nyb;
+    const int x = xs * 32 + threadIdx.x;
+    const int y0 = (yb * 8 + threadIdx.y) * YB;
+    const int z0 = zb * ZB;
+    if (x >= nx || y0 >= ny || (DIM == 3 && z0 >= nz)) return;
+    const long long nxy = (long long)nx * ny;
+    const int c = by;
+    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
+    const T* u = X + (size_t)c * ldx + base;
+    T v[NV];
+#pragma unroll
+    for (int iz = 0; iz < RZ; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < RY; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < 3; ++ix) {
+                const bool ok = x + ix - 1 >= 0 && x + ix - 1 < nx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny &&
+                                (DIM < 3 || (z0 + iz - 1 >= 0 && z0 + iz - 1 < nz));
+                const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx + ix - 1;
+                v[(iz * RY + iy) * 3 + ix] = ok ? u[off] : T(0);
+            }
+#pragma unroll
+    for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
+#pragma unroll
+        for (int oy = 0; oy < YB; ++oy) {
+            if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
+            T t1 = T(0), t2 = T(0);
+#pragma unroll
+            for (int e = 0; e < 27; ++e) {
+                const int dz = e / 9 - 1, dy = (e / 3) % 3 - 1, dx = e % 3 - 1;
+                if (DIM < 3 && dz != 0) continue;
+                const T w = v[((DIM == 3 ? oz + 1 + dz : 0) * RY + oy + 1 + dy) * 3 + dx + 1];
+                t1 += S.s[0][e] * w;
+                if (O2) t2 += S.s[1][e] * w;
+            }
+            const long long at = base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx;
+            T* o1 = O1 + (size_t)c * ld1 + at;
+            *o1 = beta == T(0) ? t1 : t1 + beta * *o1;
+            if (O2) O2[(size_t)c * ld2 + at] = t2;
+        }
+}
+
+template <int MAXM>
+__device__ __forceinline__ void ts_tn_partial_body(int n, int k, int m, int rows,
+                                                              const double* __restrict__ V, long long ldv,
+                                                              const double* __restrict__ W, long long ldw,
+                                                              double* __restrict__ part, double* Ws, int bx, int by) {
+    const int chunk = bx;
+    const int r0 = chunk * rows;
+    const int nr = min(rows, n - r0);
+    for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
+        int b = idx / rows, rr = idx % rows;
+        Ws[idx] = rr < nr ? W[(size_t)b * ldw + r0 + rr] : 0.0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double* out = part + (size_t)chunk * k * m;
+    for (int cc = warp; cc < TS_CG; cc += TS_THREADS / 32) {
+        const int a = by * TS_CG + cc;
+        if (a >= k) break;
+        const double* v = V + (size_t)a * ldv + r0;
+        double acc[MAXM];
+#pragma unroll
+        for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
+        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
+            double x[TS_UNROLL];
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = base + 32 * u;
+                x[u] = rr < nr ? v[rr] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = min(base + 32 * u, rows - 1);
+#pragma unroll
+                for (int b = 0; b < MAXM; ++b)
+                    if (b < m) acc[b] += x[u] * Ws[b * rows + rr];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < MAXM; ++b) {
+            if (b >= m) break;
+            double t = acc[b];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+            if (lane == 0) out[(size_t)a * m + b] = t;
+        }
+    }
+}
+
+__device__ __forceinline__ void ts_reduce_body(int nchunks, int k, int m, const double* __restrict__ part, double* __restrict__ H,
+                            long long ldh, int bx) {
+    int idx = bx * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x % 32;
+    if (idx >= k * m) return;
+    double s = 0.0;
+    for (int c = lane; c < nchunks; c += 32) s += part[(size_t)c * k * m + idx];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        int a = idx / m, b = idx % m;
+        H[(size_t)b * ldh + a] = s;
+    }
+}
+
+template <int MAXM>
+__device__ __forceinline__ void ts_nn_body(int n, int k, int m, double alpha, const double* __restrict__ V,
+                                               long long ldv, const double* __restrict__ H, long long ldh,
+                                               double beta, double* __restrict__ W, long long ldw, int bx) {
+    constexpr int KT = 128;
+    __shared__ double Hs[KT * MAXM];
+    int r = bx * blockDim.x + threadIdx.x;
+    double acc[MAXM];
+#pragma unroll
+    for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
+    for (int a0 = 0; a0 < k; a0 += KT) {
+        int kt = min(KT, k - a0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kt * m; idx += blockDim.x) {
+            int a = idx / m, b = idx % m;
+            Hs[a * MAXM + b] = H[(size_t)b * ldh + a0 + a];
+        }
+        __syncthreads();
+        if (r < n) {
+            for (int a = 0; a < kt; a += TS_UNROLL) {
+                double x[TS_UNROLL];
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u) x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : 0.0;
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u) {
+                    if (a + u >= kt) break;
+#pragma unroll
+                    for (int b = 0; b < MAXM; ++b)
+                        if (b < m) acc[b] += x[u] * Hs[(a + u) * MAXM + b];
+                }
+            }
+        }
+    }
+    if (r >= n) return;
+#pragma unroll
+    for (int b = 0; b < MAXM; ++b) {
+        if (b >= m) break;
+        double* w = W + (size_t)b * ldw + r;
+        // explicit rounding: one product, then the other fused into the sum, so every kernel
+        // that inlines this body rounds the same way
+        *w = beta == 0.0 ? __dmul_rn(alpha, acc[b]) : __fma_rn(alpha, acc[b], __dmul_rn(beta, *w));
+    }
+}
+
+__device__ __forceinline__ void to_df_body(int n, int m, const double* __restrict__ X, long long ldx, float2* __restrict__ Y,
+                        long long ldy, int bx) {
+    long long idx = bx * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * m) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    Y[(size_t)j * ldy + i] = df_split(X[(size_t)j * ldx + i]);
+}
+
+template <int MAXM>
+__device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int rows,
+                                                                 const float2* __restrict__ V, long long ldv,
+                                                                 const float2* __restrict__ W, long long ldw,
+                                                                 float2* __restrict__ part, double* sm, int bx, int by) {
+    constexpr int MP = (MAXM + 1) / 2;
+    float4* Ws = reinterpret_cast<float4*>(sm);   // [pairs][rows]
+    const int chunk = bx;
+    const int r0 = chunk * rows;
+    const int nr = min(rows, n - r0);
+    const int np = (m + 1) / 2;
+    for (int idx = threadIdx.x; idx < np * rows; idx += TS_THREADS) {
+        const int q = idx / rows, rr = idx % rows;
+        float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
+        if (rr < nr) {
+            w0 = W[(size_t)(2 * q) * ldw + r0 + rr];
+            if (2 * q + 1 < m) w1 = W[(size_t)(2 * q + 1) * ldw + r0 + rr];
+        }
+        Ws[idx] = make_float4(w0.x, w1.x, w0.y, w1.y);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    float2* out = part + (size_t)chunk * k * m;
+    for (int cc = warp; cc < TS_CG_DF; cc += TS_THREADS / 32) {
+        const int a = by * TS_CG_DF + cc;
+        if (a >= k) break;
+        const float2* v = V + (size_t)a * ldv + r0;
+        float2 SH[MP], SL[MP];
+#pragma unroll
+        for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
+        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
+            float2 x[TS_UNROLL];
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = base + 32 * u;
+                x[u] = rr < nr ? v[rr] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < TS_UNROLL; ++u) {
+                int rr = min(base + 32 * u, rows - 1);
+#pragma unroll
+                for (int q = 0; q < MP; ++q)
+                    if (q < np) df_madd2(SH[q], SL[q], x[u], Ws[q * rows + rr]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MP; ++q) {
+            if (q >= np) break;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int b = 2 * q + h2;
+                if (b >= m) break;
+                float h = h2 ? SH[q].y : SH[q].x, l = h2 ? SL[q].y : SL[q].x;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    float oh = __shfl_xor_sync(0xffffffffu, h, off);
+                    float ol = __shfl_xor_sync(0xffffffffu, l, off);
+                    df_add(h, l, oh, ol);
+                }
+                if (lane == 0) out[(size_t)a * m + b] = make_float2(h, l);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void ts_reduce_df_body(int nchunks, int k, int m, const float2* __restrict__ part, double* __restrict__ H,
+                               long long ldh, int bx) {
+    int idx = bx * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x % 32;
+    if (idx >= k * m) return;
+    double s = 0.0;
+    for (int c = lane; c < nchunks; c += 32) {
+        const float2 hl = part[(size_t)c * k * m + idx];
+        s += (double)hl.x + (double)hl.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        int a = idx / m, b = idx % m;
+        H[(size_t)b * ldh + a] = s;
+    }
+}
+
+template <int MAXM>
+__device__ __forceinline__ void ts_nn_df_body(int n, int k, int m, double alpha, const float2* __restrict__ V,
+                                                  long long ldv, const double* __restrict__ H, long long ldh,
+                                                  double beta, double* __restrict__ W, long long ldw, int bx) {
+    constexpr int KT = 128, MP = (MAXM + 1) / 2;
+    __shared__ float4 Hs[KT * MP];
+    const int np = (m + 1) / 2;
+    int r = bx * blockDim.x + threadIdx.x;
+    double acc[MAXM];
+#pragma unroll
+    for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
+    for (int a0 = 0; a0 < k; a0 += KT) {
+        int kt = min(KT, k - a0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kt * np; idx += blockDim.x) {
+            const int a = idx / np, q = idx % np;
+            const float2 h0 = df_split(H[(size_t)(2 * q) * ldh + a0 + a]);
+            const float2 h1 = 2 * q + 1 < m ? df_split(H[(size_t)(2 * q + 1) * ldh + a0 + a]) : make_float2(0.f, 0.f);
+            Hs[a * MP + q] = make_float4(h0.x, h1.x, h0.y, h1.y);
+        }
+        __syncthreads();
+        if (r < n) {
+            float2 SH[MP], SL[MP];
+#pragma unroll
+            for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
+            for (int a = 0; a < kt; a += TS_UNROLL) {
+                float2 x[TS_UNROLL];
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u)
+                    x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < TS_UNROLL; ++u) {
+                    if (a + u >= kt) break;
+#pragma unroll
+                    for (int q = 0; q < MP; ++q)
+                        if (q < np) df_madd2(SH[q], SL[q], x[u], Hs[(a + u) * MP + q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MP; ++q) {
+                if (2 * q < m) acc[2 * q] += (double)SH[q].x + (double)SL[q].x;
+                if (2 * q + 1 < m && 2 * q + 1 < MAXM) acc[2 * q + 1] += (double)SH[q].y + (double)SL[q].y;
+            }
+        }
+    }
+    if (r >= n) return;
+#pragma unroll
+    for (int b = 0; b < MAXM; ++b) {
+        if (b >= m) break;
+        double* w = W + (size_t)b * ldw + r;
+        // explicit rounding: one product, then the other fused into the sum, so every kernel
+        // that inlines this body rounds the same way
+        *w = beta == 0.0 ? __dmul_rn(alpha, acc[b]) : __fma_rn(alpha, acc[b], __dmul_rn(beta, *w));
+    }
+}
+
+__device__ __forceinline__ void trsm_right_upper_body(int n, int m, const double* __restrict__ R, long long ldr, double* __restrict__ W,
+                                   long long ldw, int bx) {
+    __shared__ double Rs[kMaxCols * kMaxCols];
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Rs[idx] = R[(size_t)(idx / m) * ldr + idx % m];
+    __syncthreads();
+    int r = bx * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double x[kMaxCols];
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) x[j] = j < m ? W[(size_t)j * ldw + r] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) {
+        if (j >= m) break;
+        double s = x[j];
+#pragma unroll
+        for (int i = 0; i < kMaxCols; ++i)
+            if (i < j) s -= x[i] * Rs[j * m + i];   // R[i][j] stored column-major: Rs[j*m + i]
+        x[j] = s / Rs[j * m + j];
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j)
+        if (j < m) W[(size_t)j * ldw + r] = x[j];
+}
+
+__device__ __forceinline__ void chol_small_body(int m, const double* __restrict__ G, long long ldg, double* __restrict__ R,
+                             long long ldr, double* __restrict__ flag) {
+    __shared__ double a[kMaxCols][kMaxCols + 1];
+    int t = threadIdx.x;
+    for (int idx = t; idx < m * m; idx += 32) a[idx % m][idx / m] = G[(size_t)(idx / m) * ldg + idx % m];
+    __syncwarp();
+    bool bad = false;
+    for (int j = 0; j < m; ++j) {
+        double d = a[j][j];   // the same shared value in every lane: uniform branch
+        if (!(d > 0.0)) {
+            bad = true;
+            break;
+        }
+        double rj = sqrt(d);
+        __syncwarp();
+        if (t > j && t < m) a[t][j] /= rj;
+        if (t == j) a[j][j] = rj;
+        __syncwarp();
+        if (t > j && t < m) {
+            double aij = a[t][j];
+            for (int l = j + 1; l <= t; ++l) a[t][l] -= aij * a[l][j];
+        }
+        __syncwarp();
+    }
+    for (int idx = t; idx < m * m; idx += 32) {
+        int i = idx % m, j = idx / m;   // R(i, j) = L(j, i) for i <= j
+        double v = bad ? (i == j ? 1.0 : 0.0) : (i <= j ? a[j][i] : 0.0);
+        R[(size_t)j * ldr + i] = v;
+    }
+    if (t == 0) *flag = bad ? 1.0 : 0.0;
+}
+
+template <typename S, typename D>
+__device__ __forceinline__ void copy_cols_body(int n, int m, const S* __restrict__ X, long long ldx, D* __restrict__ Y, long long ldy,
+                            double beta, int bx) {
+    long long idx = bx * (long long)blockDim.x + threadIdx.x;
+    long long tot = (long long)n * m;
+    if (idx >= tot) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    D v = (D)X[(size_t)j * ldx + i];
+    D* y = Y + (size_t)j * ldy + i;
+    if constexpr (sizeof(D) == 8)
+        *y = beta == 0.0 ? v : (D)__fma_rn(beta, (double)(*y), (double)v);   // fused: the same in every kernel
+    else
+        *y = beta == 0.0 ? v : (D)__dmul_rn(beta, (double)(*y)) + v;
+}
+
+__device__ __forceinline__ void axpby_body(int n, int m, double a, const double* __restrict__ X, long long ldx, double b,
+                        double* __restrict__ Y, long long ldy, int bx) {
+    long long idx = bx * (long long)blockDim.x + threadIdx.x;
+    long long tot = (long long)n * m;
+    if (idx >= tot) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    double* y = Y + (size_t)j * ldy + i;
+    // explicit rounding (b y rounded, a x fused into the sum): the same in every kernel inlining this body
+    *y = __fma_rn(a, X[(size_t)j * ldx + i], b == 0.0 ? 0.0 : __dmul_rn(b, *y));
+}
+
+}  // namespace

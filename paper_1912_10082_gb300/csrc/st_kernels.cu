@@ -4,11 +4,11 @@
 #include <cmath>
 
 #include "st_common.cuh"
+#include "st_dev.cuh"
 #include "st_tune.h"
 
 namespace {
 
-constexpr int kMaxCols = 16;   // widest block handled by the tall-skinny and SpMM kernels
 
 // ---------------------------------------------------------------------------
 // Fused space-time apply (Section 4, vec identity): column l of
@@ -290,67 +290,120 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 1) k_apply_box_sh(int nx, 
     }
 }
 
-// Spatial products with a constant box stencil: O1[:,c] = S1 * X[:,c] (+ beta
-// O1[:,c]) and, when O2 is given, O2[:,c] = S2 * X[:,c] from the same loads.
-// Same thread layout and register blocking as the apply (a warp spans 32
-// consecutive x; a thread owns YB x ZB points), one column per blockIdx.y.
-// Only the vectors move: the stencil travels in the kernel parameters.
-template <typename T>
-struct BoxPair {
-    T s[2][27];
-};
-
-template <typename T, int DIM, int YB, int ZB>
-__global__ void __launch_bounds__(256) k_stencil_box(int nx, int ny, int nz, BoxPair<T> S, const T* __restrict__ X,
-                                                     long long ldx, T beta, T* __restrict__ O1, long long ld1,
-                                                     T* __restrict__ O2, long long ld2) {
-    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
-    constexpr int NV = RY * RZ * 3;
+// ---------------------------------------------------------------------------
+// Sum-factorised FP32 apply on a 3D box grid.  On a uniform box the Q1 mass
+// and operator matrices are Kronecker products of 3-point 1D stencils,
+// M = m_z (x) m_y (x) m_x and A = a_z (x) m_y (x) m_x + m_z (x) a_y (x) m_x +
+// m_z (x) m_y (x) a_x (heat: a_d = kappa k_d; convection-diffusion:
+// a_d = eps k_d + beta_d g_d), so with c = dt/2
+//     P u = m_z S1 + c (m_z S2 + a_z S1),   N u = m_z S1 - c (m_z S2 + a_z S1),
+//     S1 = (m_y (x) m_x) u,   S2 = (a_y (x) m_x + m_y (x) a_x) u,
+// three passes of 3-point stencils (x, then y, then z) instead of the
+// 27-point sums for P and N: about 20 operations an output instead of 54 FMA.
+// A warp spans 32 consecutive x (the two edge lanes load their outer
+// neighbour), a thread owns YB rows in y and walks ZB planes in z with a
+// window of S1, S2 over three planes, then the next time column, carrying
+// N u_{l-1} for its YB x ZB outputs.  Dirichlet neighbours are zeros at every
+// stage, which is the tensor product of the interior 1D matrices.
+// ---------------------------------------------------------------------------
+template <int YB, int ZB>
+__global__ void __launch_bounds__(256, 2) k_apply_sf3(int nx, int ny, int nz, int n_t, int steps, SfStencil f,
+                                                     const float* __restrict__ U, long long ldu, float* __restrict__ Y,
+                                                     long long ldy) {
     const int nxs = (nx + 31) / 32, nyb = (ny + 8 * YB - 1) / (8 * YB);
     int b = blockIdx.x;
     const int xs = b % nxs;
     b /= nxs;
     const int yb = b % nyb;
     const int zb = b / nyb;
-    const int x = xs * 32 + threadIdx.x;
+    const int lane = threadIdx.x;
+    const int x = xs * 32 + lane;
     const int y0 = (yb * 8 + threadIdx.y) * YB;
     const int z0 = zb * ZB;
-    if (x >= nx || y0 >= ny || (DIM == 3 && z0 >= nz)) return;
-    const long long nxy = (long long)nx * ny;
-    const int c = blockIdx.y;
-    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
-    const T* u = X + (size_t)c * ldx + base;
-    T v[NV];
+    if (y0 >= ny) return;   // uniform over the warp: the shuffles see all lanes
+    const bool okx = x < nx;
+    const int xe = lane == 0 ? x - 1 : x + 1;   // the outer neighbour an edge lane loads itself
+    const bool edge = (lane == 0 || lane == 31) && xe >= 0 && xe < nx;
+    bool oky[YB + 2];
 #pragma unroll
-    for (int iz = 0; iz < RZ; ++iz)
+    for (int r = 0; r < YB + 2; ++r) oky[r] = y0 + r - 1 >= 0 && y0 + r - 1 < ny;
+    const int l0 = blockIdx.y * steps;
+    const int l1 = min(n_t, l0 + steps);
+    float pn[ZB][YB];
 #pragma unroll
-        for (int iy = 0; iy < RY; ++iy)
+    for (int j = 0; j < ZB; ++j)
 #pragma unroll
-            for (int ix = 0; ix < 3; ++ix) {
-                const bool ok = x + ix - 1 >= 0 && x + ix - 1 < nx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny &&
-                                (DIM < 3 || (z0 + iz - 1 >= 0 && z0 + iz - 1 < nz));
-                const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx + ix - 1;
-                v[(iz * RY + iy) * 3 + ix] = ok ? u[off] : T(0);
+        for (int o = 0; o < YB; ++o) pn[j][o] = 0.f;
+#pragma unroll 1
+    for (int c = l0 > 0 ? l0 - 1 : 0; c < l1; ++c) {
+        const float* u = U + (long long)c * ldu;
+        float s1a[YB], s2a[YB], s1b[YB], s2b[YB];   // S1, S2 of planes zz - 2 (a) and zz - 1 (b)
+#pragma unroll
+        for (int j = 0; j < ZB + 2; ++j) {
+            const int zz = z0 - 1 + j;
+            const bool okz = zz >= 0 && zz < nz;
+            float xm[YB + 2], xa[YB + 2];
+#pragma unroll
+            for (int r = 0; r < YB + 2; ++r) {
+                const long long row = ((long long)zz * ny + (y0 + r - 1)) * nx;
+                const bool ok = okz && oky[r];
+                const float v = ok && okx ? __ldg(u + row + x) : 0.f;
+                const float ve = ok && edge ? __ldg(u + row + xe) : 0.f;
+                float wm = __shfl_up_sync(0xffffffffu, v, 1);
+                float wp = __shfl_down_sync(0xffffffffu, v, 1);
+                if (lane == 0) wm = ve;
+                if (lane == 31) wp = ve;
+                xm[r] = fmaf(f.m1[0], wm + wp, f.m0[0] * v);
+                xa[r] = fmaf(f.ap[0], wp, fmaf(f.am[0], wm, f.a0[0] * v));
+            }
+            float s1c[YB], s2c[YB];
+#pragma unroll
+            for (int o = 0; o < YB; ++o) {
+                const int r = o + 1;
+                s1c[o] = fmaf(f.m1[1], xm[r - 1] + xm[r + 1], f.m0[1] * xm[r]);
+                const float yam = fmaf(f.ap[1], xm[r + 1], fmaf(f.am[1], xm[r - 1], f.a0[1] * xm[r]));
+                const float yma = fmaf(f.m1[1], xa[r - 1] + xa[r + 1], f.m0[1] * xa[r]);
+                s2c[o] = yam + yma;
+            }
+            if (j >= 2) {
+                const int zo = zz - 1;   // the plane at the window's centre
+                if (zo < nz) {
+#pragma unroll
+                    for (int o = 0; o < YB; ++o) {
+                        const float mz1 = fmaf(f.m1[2], s1a[o] + s1c[o], f.m0[2] * s1b[o]);
+                        const float mz2 = fmaf(f.m1[2], s2a[o] + s2c[o], f.m0[2] * s2b[o]);
+                        const float az1 = fmaf(f.ap[2], s1c[o], fmaf(f.am[2], s1a[o], f.a0[2] * s1b[o]));
+                        const float t = mz2 + az1;
+                        const float P = fmaf(f.hdt, t, mz1);
+                        const float N = fmaf(-f.hdt, t, mz1);
+                        if (c >= l0 && okx && y0 + o < ny)
+                            Y[(long long)c * ldy + ((long long)zo * ny + y0 + o) * nx + x] = P - pn[j - 2][o];
+                        pn[j - 2][o] = N;
+                    }
+                }
             }
 #pragma unroll
-    for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
-#pragma unroll
-        for (int oy = 0; oy < YB; ++oy) {
-            if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
-            T t1 = T(0), t2 = T(0);
-#pragma unroll
-            for (int e = 0; e < 27; ++e) {
-                const int dz = e / 9 - 1, dy = (e / 3) % 3 - 1, dx = e % 3 - 1;
-                if (DIM < 3 && dz != 0) continue;
-                const T w = v[((DIM == 3 ? oz + 1 + dz : 0) * RY + oy + 1 + dy) * 3 + dx + 1];
-                t1 += S.s[0][e] * w;
-                if (O2) t2 += S.s[1][e] * w;
+            for (int o = 0; o < YB; ++o) {
+                s1a[o] = s1b[o];
+                s2a[o] = s2b[o];
+                s1b[o] = s1c[o];
+                s2b[o] = s2c[o];
             }
-            const long long at = base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx;
-            T* o1 = O1 + (size_t)c * ld1 + at;
-            *o1 = beta == T(0) ? t1 : t1 + beta * *o1;
-            if (O2) O2[(size_t)c * ld2 + at] = t2;
         }
+    }
+}
+
+// Spatial products with a constant box stencil: O1[:,c] = S1 * X[:,c] (+ beta
+// O1[:,c]) and, when O2 is given, O2[:,c] = S2 * X[:,c] from the same loads.
+// Same thread layout and register blocking as the apply (a warp spans 32
+// consecutive x; a thread owns YB x ZB points), one column per blockIdx.y.
+// Only the vectors move: the stencil travels in the kernel parameters.
+
+template <typename T, int DIM, int YB, int ZB>
+__global__ void __launch_bounds__(256) k_stencil_box(int nx, int ny, int nz, BoxPair<T> S, const T* __restrict__ X,
+                                                     long long ldx, T beta, T* __restrict__ O1, long long ld1,
+                                                     T* __restrict__ O2, long long ld2) {
+    stencil_box_body<T, DIM, YB, ZB>(nx, ny, nz, S, X, ldx, beta, O1, ld1, O2, ld2, blockIdx.x, blockIdx.y);
 }
 
 // FP32 variant of the constant-stencil product with the apply's shuffle scheme:
@@ -550,67 +603,6 @@ __global__ void k_cn_rhs(int n_h, const int* __restrict__ row_ptr, const int* __
 // that scales by a constant and optionally by the spectral weight of the
 // output entry.  64 x 64 tiles, 256 threads, 4 x 4 outputs per thread.
 // ---------------------------------------------------------------------------
-struct FdEpi {
-    int scale;          // 0: C = coef * acc; 1: C = coef * omega(e) * acc
-    int left;           // 1: linear index e = m * J + j (batch = one vector column); 0: e = m
-    long long J;
-    int dim, nx, ny, nz;
-    const double *l0, *l1, *l2;   // eigenvalues per direction
-    const double *c0, *c1, *c2;   // c2 factors per direction (resolvent of a general right-hand side)
-    const float *f0, *f1, *f2;    // FP32 copies of l0..l2 and of c0..c2, for FP32 products
-    const float *g0, *g1, *g2;
-    int kind;           // FdKind
-    double kappa, shift, coef;
-};
-
-__device__ __forceinline__ double fd_omega(const FdEpi& ep, long long e) {
-    int x = (int)(e % ep.nx);
-    long long t = e / ep.nx;
-    int y = (int)(t % ep.ny);
-    int z = (int)(t / ep.ny);
-    double lam = ep.l0[x];
-    double w = ep.c0[x];
-    if (ep.dim > 1) {
-        lam += ep.l1[y];
-        w *= ep.c1[y];
-    }
-    if (ep.dim > 2) {
-        lam += ep.l2[z];
-        w *= ep.c2[z];
-    }
-    if (ep.kind == FD_MASS_INVERSE) return w;
-    if (ep.kind == FD_RESOLVENT) return w / (ep.kappa * lam + ep.shift);
-    return 1.0 / (ep.kappa * lam + ep.shift);
-}
-
-// The same weight in FP32 from the FP32 tables (no FP64 instruction).
-__device__ __forceinline__ float fd_omega32(const FdEpi& ep, long long e) {
-    int x = (int)(e % ep.nx);
-    long long t = e / ep.nx;
-    int y = (int)(t % ep.ny);
-    int z = (int)(t / ep.ny);
-    float lam = ep.f0[x];
-    float w = ep.g0[x];
-    if (ep.dim > 1) {
-        lam += ep.f1[y];
-        w *= ep.g1[y];
-    }
-    if (ep.dim > 2) {
-        lam += ep.f2[z];
-        w *= ep.g2[z];
-    }
-    const float kap = (float)ep.kappa, sh = (float)ep.shift;
-    if (ep.kind == FD_MASS_INVERSE) return w;
-    if (ep.kind == FD_RESOLVENT) return w / (kap * lam + sh);
-    return 1.0f / (kap * lam + sh);
-}
-
-// Batch index z = blockIdx.z splits into (z2, z1) = (z / nb1, z % nb1); the
-// operand offsets are z1 * s*1 + z2 * s*2.
-struct Batch2 {
-    int nb1;
-    long long sA1, sA2, sB1, sB2, sC1, sC2;
-};
 
 template <typename T, int TM>
 __global__ void __launch_bounds__(256) k_gemm_rr(int M, int N, int K, const T* __restrict__ A, long long lda,
@@ -693,107 +685,7 @@ __global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __
                                                    const T* __restrict__ H0, const T* __restrict__ H1,
                                                    const T* __restrict__ G0, const T* __restrict__ G1,
                                                    T* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep) {
-    // FP32: the whole folded contraction of a 127-point direction (K <= 64) in one
-    // staged step (fewer barriers, more loads in flight); FP64: 16 at a time
-    constexpr int BM = 16 * TM, BN = 16 * TM, BK = sizeof(T) == 4 ? 64 : 16;
-    __shared__ T As[BK][BM + 1];
-    __shared__ T Bs[BK][BN];
-    const int par = blockIdx.z & 1;
-    const int zb = blockIdx.z >> 1;
-    const int z1 = zb % bt.nb1, z2 = zb / bt.nb1;
-    const int K = par ? n / 2 : (n + 1) / 2;   // folded length = outputs of this parity
-    const int mid = (n & 1) ? (n - 1) / 2 : -1;
-    const T sgn = par ? T(-1) : T(1);
-    const int M = SIDE == 0 ? other : K;
-    const int N = SIDE == 0 ? K : other;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    if (m0 >= M || n0 >= N) return;   // the odd parity has one output fewer for odd n
-    if (SIDE == 0) {
-        X += (size_t)z1 * bt.sA1 + (size_t)z2 * bt.sA2;
-    } else {
-        X += (size_t)z1 * bt.sB1 + (size_t)z2 * bt.sB2;
-    }
-    C += (size_t)z1 * bt.sC1 + (size_t)z2 * bt.sC2;
-    const T* Hp = par ? H1 : H0;   // K x K' (k-major), SIDE 0 right operand
-    const T* Gp = par ? G1 : G0;   // K' x K (output-major), SIDE 1 left operand
-    const int tid = threadIdx.x;
-    const int tx = tid % 16, ty = tid / 16;
-    T acc[TM][TM];
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TM; ++j) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int idx = tid; idx < BM * BK; idx += 256) {
-            int mm = idx / BK, kk = idx % BK;
-            int gm = m0 + mm, gk = k0 + kk;
-            T v = T(0);
-            if (gm < M && gk < K) {
-                if (SIDE == 0) {
-                    const T* row = X + (size_t)gm * ldx;
-                    v = gk == mid ? row[gk] : row[gk] + sgn * row[n - 1 - gk];
-                } else {
-                    v = Gp[(size_t)gm * K + gk];
-                }
-            }
-            As[kk][mm] = v;
-        }
-        for (int idx = tid; idx < BK * BN; idx += 256) {
-            int kk = idx / BN, nn = idx % BN;
-            int gk = k0 + kk, gn = n0 + nn;
-            T v = T(0);
-            if (gk < K && gn < N) {
-                if (SIDE == 0) {
-                    v = Hp[(size_t)gk * K + gn];
-                } else {
-                    v = gk == mid ? X[(size_t)gk * ldx + gn]
-                                  : X[(size_t)gk * ldx + gn] + sgn * X[(size_t)(n - 1 - gk) * ldx + gn];
-                }
-            }
-            Bs[kk][nn] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            T a[TM], bb[TM];
-#pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < TM; ++j) bb[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < TM; ++i)
-#pragma unroll
-                for (int j = 0; j < TM; ++j) acc[i][j] += a[i] * bb[j];
-        }
-        __syncthreads();
-    }
-    const float fcoef = (float)ep.coef;
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-        int gm = m0 + ty + 16 * i;
-        if (gm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < TM; ++j) {
-            int gn = n0 + tx + 16 * j;
-            if (gn >= N) continue;
-            // output coordinates of the unfolded product
-            long long om = SIDE == 0 ? gm : 2LL * gm + par;
-            long long on = SIDE == 0 ? 2LL * gn + par : gn;
-            if constexpr (sizeof(T) == 4) {
-                // FP32 epilogue: FP64 conversions and products here would run on the 1/64-rate pipe
-                float f = fcoef;
-                if (ep.scale) f *= fd_omega32(ep, ep.left ? om * ep.J + on : on);
-                C[(size_t)om * ldc + on] = f * acc[i][j];
-            } else {
-                double f = ep.coef;
-                if (ep.scale) {
-                    long long e = ep.left ? om * ep.J + on : on;
-                    f *= fd_omega(ep, e);
-                }
-                C[(size_t)om * ldc + on] = (T)(f * (double)acc[i][j]);
-            }
-        }
-    }
+    gemm_fold_body<T, TM, SIDE>(n, other, X, ldx, H0, H1, G0, G1, C, ldc, bt, ep, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T, int SIDE>
@@ -896,24 +788,6 @@ int launch_gemm_rr(int M, int N, int K, const T* A, long long lda, const T* B, l
 // H = V^T W: each CTA reduces a chunk of rows into a k x m partial, a second
 // kernel sums the partials in chunk order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int TS_THREADS = 256;
-constexpr int TS_CG = 16;      // basis columns per CTA of H = V^T W
-constexpr int TS_CG_DF = 32;   // the same for the double-float product (half the restaging of W per basis column)
-constexpr int TS_UNROLL = 8;   // independent loads in flight per lane
-
-// Rows of one chunk of H = V^T W: enough chunks that chunks x column groups
-// fill the GPU about four CTAs deep (a few basis columns need many short
-// chunks to keep enough loads in flight), at least 128 rows, and a staged
-// chunk of W of rows x m <= 8192 doubles.
-__host__ __device__ inline int ts_rows(int n, int k, int m) {
-    const int maxr = m <= 8 ? 1024 : 512;
-    const long long groups = (k + 15) / 16;
-    const long long want = 4 * 152;
-    long long nch = (want + groups - 1) / groups;
-    long long r = (n + nch - 1) / nch;
-    r = ((r + 31) / 32) * 32;
-    return (int)(r < 128 ? 128 : (r > maxr ? maxr : r));
-}
 
 // Partial products of H = V^T W over one chunk of rows and a group of TS_CG
 // basis columns.  Each warp takes a column at a time; its lanes stride over
@@ -926,65 +800,15 @@ __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_partial(int n, int k, int 
                                                               const double* __restrict__ V, long long ldv,
                                                               const double* __restrict__ W, long long ldw,
                                                               double* __restrict__ part) {
-    extern __shared__ double Ws[];   // [m][rows]
-    const int chunk = blockIdx.x;
-    const int r0 = chunk * rows;
-    const int nr = min(rows, n - r0);
-    for (int idx = threadIdx.x; idx < m * rows; idx += TS_THREADS) {
-        int b = idx / rows, rr = idx % rows;
-        Ws[idx] = rr < nr ? W[(size_t)b * ldw + r0 + rr] : 0.0;
-    }
-    __syncthreads();
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    double* out = part + (size_t)chunk * k * m;
-    for (int cc = warp; cc < TS_CG; cc += TS_THREADS / 32) {
-        const int a = blockIdx.y * TS_CG + cc;
-        if (a >= k) break;
-        const double* v = V + (size_t)a * ldv + r0;
-        double acc[MAXM];
-#pragma unroll
-        for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
-        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
-            double x[TS_UNROLL];
-#pragma unroll
-            for (int u = 0; u < TS_UNROLL; ++u) {
-                int rr = base + 32 * u;
-                x[u] = rr < nr ? v[rr] : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < TS_UNROLL; ++u) {
-                int rr = min(base + 32 * u, rows - 1);
-#pragma unroll
-                for (int b = 0; b < MAXM; ++b)
-                    if (b < m) acc[b] += x[u] * Ws[b * rows + rr];
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < MAXM; ++b) {
-            if (b >= m) break;
-            double t = acc[b];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-            if (lane == 0) out[(size_t)a * m + b] = t;
-        }
-    }
+    extern __shared__ double Ws[];
+    ts_tn_partial_body<MAXM>(n, k, m, rows, V, ldv, W, ldw, part, Ws, blockIdx.x, blockIdx.y);
 }
 
 // One warp per output entry: lanes take every 32nd chunk, then a fixed
 // butterfly sums the lanes, so the result does not depend on scheduling.
 __global__ void k_ts_reduce(int nchunks, int k, int m, const double* __restrict__ part, double* __restrict__ H,
                             long long ldh) {
-    int idx = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    int lane = threadIdx.x % 32;
-    if (idx >= k * m) return;
-    double s = 0.0;
-    for (int c = lane; c < nchunks; c += 32) s += part[(size_t)c * k * m + idx];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        int a = idx / m, b = idx % m;
-        H[(size_t)b * ldh + a] = s;
-    }
+    ts_reduce_body(nchunks, k, m, part, H, ldh, blockIdx.x);
 }
 
 // W = beta W + alpha V H, one thread per row, H staged through shared memory;
@@ -993,111 +817,9 @@ template <int MAXM>
 __global__ void __launch_bounds__(256) k_ts_nn(int n, int k, int m, double alpha, const double* __restrict__ V,
                                                long long ldv, const double* __restrict__ H, long long ldh,
                                                double beta, double* __restrict__ W, long long ldw) {
-    constexpr int KT = 128;
-    __shared__ double Hs[KT * MAXM];
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[MAXM];
-#pragma unroll
-    for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
-    for (int a0 = 0; a0 < k; a0 += KT) {
-        int kt = min(KT, k - a0);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < kt * m; idx += blockDim.x) {
-            int a = idx / m, b = idx % m;
-            Hs[a * MAXM + b] = H[(size_t)b * ldh + a0 + a];
-        }
-        __syncthreads();
-        if (r < n) {
-            for (int a = 0; a < kt; a += TS_UNROLL) {
-                double x[TS_UNROLL];
-#pragma unroll
-                for (int u = 0; u < TS_UNROLL; ++u) x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : 0.0;
-#pragma unroll
-                for (int u = 0; u < TS_UNROLL; ++u) {
-                    if (a + u >= kt) break;
-#pragma unroll
-                    for (int b = 0; b < MAXM; ++b)
-                        if (b < m) acc[b] += x[u] * Hs[(a + u) * MAXM + b];
-                }
-            }
-        }
-    }
-    if (r >= n) return;
-#pragma unroll
-    for (int b = 0; b < MAXM; ++b) {
-        if (b >= m) break;
-        double* w = W + (size_t)b * ldw + r;
-        *w = beta == 0.0 ? alpha * acc[b] : beta * (*w) + alpha * acc[b];
-    }
+    ts_nn_body<MAXM>(n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw, blockIdx.x);
 }
 
-// ---------------------------------------------------------------------------
-// Double-float tall-skinny products.  FP64 runs at 1/64 of the FP32 rate on
-// this chip, so the basis products of the mixed-precision solve use
-// double-float arithmetic on the FP32 pipes instead (Dekker, "A floating-point
-// technique for extending the available precision", 1971; Knuth, TAOCP
-// vol. 2, 4.2.2, two-sum): a value is hi + lo with two floats, a product
-// a*b = p + e with e = fma(a, b, -p) exact, and a running sum keeps its
-// rounding error by two-sum.  Every 32 terms the pair is folded into an FP64
-// accumulator.  The result carries about 48 significant bits, with no FP64
-// instruction in the inner loops.  All FP32 operations are explicitly rounded
-// intrinsics so that the compiler cannot contract them.  The basis is kept as
-// (hi, lo) pairs (float2, 8 bytes per entry: the same traffic as FP64).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 df_split(double v) {
-    float hi = __double2float_rn(v);
-    float lo = __double2float_rn(v - (double)hi);
-    return make_float2(hi, lo);
-}
-
-// (sh, sl) += a * b for double-floats a, b.
-__device__ __forceinline__ void df_madd(float& sh, float& sl, float2 a, float2 b) {
-    float p = __fmul_rn(a.x, b.x);
-    float e = __fmaf_rn(a.x, b.x, -p);
-    e = __fmaf_rn(a.x, b.y, e);
-    e = __fmaf_rn(a.y, b.x, e);
-    float s = __fadd_rn(sh, p);
-    float z = __fsub_rn(s, sh);
-    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
-    sl = __fadd_rn(sl, __fadd_rn(t, e));
-    sh = s;
-}
-
-__global__ void k_to_df(int n, int m, const double* __restrict__ X, long long ldx, float2* __restrict__ Y,
-                        long long ldy) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)n * m) return;
-    int j = (int)(idx / n), i = (int)(idx % n);
-    Y[(size_t)j * ldy + i] = df_split(X[(size_t)j * ldx + i]);
-}
-
-// (sh, sl) += (oh, ol) for two double-float partial sums (two-sum on the heads).
-__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
-    float s = __fadd_rn(sh, oh);
-    float z = __fsub_rn(s, sh);
-    float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(oh, z));
-    sl = __fadd_rn(sl, __fadd_rn(t, ol));
-    sh = s;
-}
-
-// Two double-float multiply-adds at once, (SH, SL)[c] += a * b_c for the two
-// columns c of a pair, with the packed FP32 instructions of sm_100+ (each lane
-// of a packed operation rounds exactly as the scalar one, so the results are
-// those of df_madd).  b = (b0.hi, b1.hi, b0.lo, b1.lo).
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ void df_madd2(float2& SH, float2& SL, float2 a, float4 b) {
-    const float2 Ax = make_float2(a.x, a.x), Ay = make_float2(a.y, a.y);
-    const float2 Bx = make_float2(b.x, b.y), By = make_float2(b.z, b.w);
-    const float2 P = __fmul2_rn(Ax, Bx);
-    float2 E = __ffma2_rn(Ax, Bx, neg2(P));
-    E = __ffma2_rn(Ax, By, E);
-    E = __ffma2_rn(Ay, Bx, E);
-    const float2 S = __fadd2_rn(SH, P);
-    const float2 Z = __fadd2_rn(S, neg2(SH));
-    const float2 T = __fadd2_rn(__fadd2_rn(SH, neg2(__fadd2_rn(S, neg2(Z)))), __fadd2_rn(P, neg2(Z)));
-    SL = __fadd2_rn(SL, __fadd2_rn(T, E));
-    SH = S;
-}
 
 // Partial H = V^T W as k_ts_tn_partial, with V and W both in double-float
 // (W split once by the caller, not once per CTA: the split costs FP64).  W's
@@ -1106,90 +828,25 @@ __device__ __forceinline__ void df_madd2(float2& SH, float2& SL, float2 a, float
 // combined by a double-float butterfly and stored as (hi, lo) float pairs: no
 // FP64 instruction runs here (FP64 is 1/64 of FP32); k_ts_reduce_df folds
 // them.
+__global__ void k_to_df(int n, int m, const double* __restrict__ X, long long ldx, float2* __restrict__ Y,
+                        long long ldy) {
+    to_df_body(n, m, X, ldx, Y, ldy, blockIdx.x);
+}
+
 template <int MAXM>
 __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, int m, int rows,
                                                                  const float2* __restrict__ V, long long ldv,
                                                                  const float2* __restrict__ W, long long ldw,
                                                                  float2* __restrict__ part) {
-    constexpr int MP = (MAXM + 1) / 2;
     extern __shared__ double sm[];
-    float4* Ws = reinterpret_cast<float4*>(sm);   // [pairs][rows]
-    const int chunk = blockIdx.x;
-    const int r0 = chunk * rows;
-    const int nr = min(rows, n - r0);
-    const int np = (m + 1) / 2;
-    for (int idx = threadIdx.x; idx < np * rows; idx += TS_THREADS) {
-        const int q = idx / rows, rr = idx % rows;
-        float2 w0 = make_float2(0.f, 0.f), w1 = make_float2(0.f, 0.f);
-        if (rr < nr) {
-            w0 = W[(size_t)(2 * q) * ldw + r0 + rr];
-            if (2 * q + 1 < m) w1 = W[(size_t)(2 * q + 1) * ldw + r0 + rr];
-        }
-        Ws[idx] = make_float4(w0.x, w1.x, w0.y, w1.y);
-    }
-    __syncthreads();
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    float2* out = part + (size_t)chunk * k * m;
-    for (int cc = warp; cc < TS_CG_DF; cc += TS_THREADS / 32) {
-        const int a = blockIdx.y * TS_CG_DF + cc;
-        if (a >= k) break;
-        const float2* v = V + (size_t)a * ldv + r0;
-        float2 SH[MP], SL[MP];
-#pragma unroll
-        for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
-        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
-            float2 x[TS_UNROLL];
-#pragma unroll
-            for (int u = 0; u < TS_UNROLL; ++u) {
-                int rr = base + 32 * u;
-                x[u] = rr < nr ? v[rr] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < TS_UNROLL; ++u) {
-                int rr = min(base + 32 * u, rows - 1);
-#pragma unroll
-                for (int q = 0; q < MP; ++q)
-                    if (q < np) df_madd2(SH[q], SL[q], x[u], Ws[q * rows + rr]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < MP; ++q) {
-            if (q >= np) break;
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int b = 2 * q + h2;
-                if (b >= m) break;
-                float h = h2 ? SH[q].y : SH[q].x, l = h2 ? SL[q].y : SL[q].x;
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    float oh = __shfl_xor_sync(0xffffffffu, h, off);
-                    float ol = __shfl_xor_sync(0xffffffffu, l, off);
-                    df_add(h, l, oh, ol);
-                }
-                if (lane == 0) out[(size_t)a * m + b] = make_float2(h, l);
-            }
-        }
-    }
+    ts_tn_df_partial_body<MAXM>(n, k, m, rows, V, ldv, W, ldw, part, sm, blockIdx.x, blockIdx.y);
 }
 
 // H = sum over chunks of the (hi, lo) partials, each folded to FP64 first:
 // a warp per output, fixed order (as k_ts_reduce).
 __global__ void k_ts_reduce_df(int nchunks, int k, int m, const float2* __restrict__ part, double* __restrict__ H,
                                long long ldh) {
-    int idx = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    int lane = threadIdx.x % 32;
-    if (idx >= k * m) return;
-    double s = 0.0;
-    for (int c = lane; c < nchunks; c += 32) {
-        const float2 hl = part[(size_t)c * k * m + idx];
-        s += (double)hl.x + (double)hl.y;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        int a = idx / m, b = idx % m;
-        H[(size_t)b * ldh + a] = s;
-    }
+    ts_reduce_df_body(nchunks, k, m, part, H, ldh, blockIdx.x);
 }
 
 // W = beta W + alpha V H with V in double-float, one thread per row; H is
@@ -1200,78 +857,12 @@ template <int MAXM>
 __global__ void __launch_bounds__(256) k_ts_nn_df(int n, int k, int m, double alpha, const float2* __restrict__ V,
                                                   long long ldv, const double* __restrict__ H, long long ldh,
                                                   double beta, double* __restrict__ W, long long ldw) {
-    constexpr int KT = 128, MP = (MAXM + 1) / 2;
-    __shared__ float4 Hs[KT * MP];
-    const int np = (m + 1) / 2;
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[MAXM];
-#pragma unroll
-    for (int b = 0; b < MAXM; ++b) acc[b] = 0.0;
-    for (int a0 = 0; a0 < k; a0 += KT) {
-        int kt = min(KT, k - a0);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < kt * np; idx += blockDim.x) {
-            const int a = idx / np, q = idx % np;
-            const float2 h0 = df_split(H[(size_t)(2 * q) * ldh + a0 + a]);
-            const float2 h1 = 2 * q + 1 < m ? df_split(H[(size_t)(2 * q + 1) * ldh + a0 + a]) : make_float2(0.f, 0.f);
-            Hs[a * MP + q] = make_float4(h0.x, h1.x, h0.y, h1.y);
-        }
-        __syncthreads();
-        if (r < n) {
-            float2 SH[MP], SL[MP];
-#pragma unroll
-            for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
-            for (int a = 0; a < kt; a += TS_UNROLL) {
-                float2 x[TS_UNROLL];
-#pragma unroll
-                for (int u = 0; u < TS_UNROLL; ++u)
-                    x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : make_float2(0.f, 0.f);
-#pragma unroll
-                for (int u = 0; u < TS_UNROLL; ++u) {
-                    if (a + u >= kt) break;
-#pragma unroll
-                    for (int q = 0; q < MP; ++q)
-                        if (q < np) df_madd2(SH[q], SL[q], x[u], Hs[(a + u) * MP + q]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < MP; ++q) {
-                if (2 * q < m) acc[2 * q] += (double)SH[q].x + (double)SL[q].x;
-                if (2 * q + 1 < m && 2 * q + 1 < MAXM) acc[2 * q + 1] += (double)SH[q].y + (double)SL[q].y;
-            }
-        }
-    }
-    if (r >= n) return;
-#pragma unroll
-    for (int b = 0; b < MAXM; ++b) {
-        if (b >= m) break;
-        double* w = W + (size_t)b * ldw + r;
-        *w = beta == 0.0 ? alpha * acc[b] : beta * (*w) + alpha * acc[b];
-    }
+    ts_nn_df_body<MAXM>(n, k, m, alpha, V, ldv, H, ldh, beta, W, ldw, blockIdx.x);
 }
 
 __global__ void k_trsm_right_upper(int n, int m, const double* __restrict__ R, long long ldr, double* __restrict__ W,
                                    long long ldw) {
-    __shared__ double Rs[kMaxCols * kMaxCols];
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Rs[idx] = R[(size_t)(idx / m) * ldr + idx % m];
-    __syncthreads();
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double x[kMaxCols];
-#pragma unroll
-    for (int j = 0; j < kMaxCols; ++j) x[j] = j < m ? W[(size_t)j * ldw + r] : 0.0;
-#pragma unroll
-    for (int j = 0; j < kMaxCols; ++j) {
-        if (j >= m) break;
-        double s = x[j];
-#pragma unroll
-        for (int i = 0; i < kMaxCols; ++i)
-            if (i < j) s -= x[i] * Rs[j * m + i];   // R[i][j] stored column-major: Rs[j*m + i]
-        x[j] = s / Rs[j * m + j];
-    }
-#pragma unroll
-    for (int j = 0; j < kMaxCols; ++j)
-        if (j < m) W[(size_t)j * ldw + r] = x[j];
+    trsm_right_upper_body(n, m, R, ldr, W, ldw, blockIdx.x);
 }
 
 // Cholesky factor of a small SPD matrix by one warp, lane i owning row i of
@@ -1279,56 +870,18 @@ __global__ void k_trsm_right_upper(int n, int m, const double* __restrict__ R, l
 // lane updates its row of the trailing block.
 __global__ void k_chol_small(int m, const double* __restrict__ G, long long ldg, double* __restrict__ R,
                              long long ldr, double* __restrict__ flag) {
-    __shared__ double a[kMaxCols][kMaxCols + 1];
-    int t = threadIdx.x;
-    for (int idx = t; idx < m * m; idx += 32) a[idx % m][idx / m] = G[(size_t)(idx / m) * ldg + idx % m];
-    __syncwarp();
-    bool bad = false;
-    for (int j = 0; j < m; ++j) {
-        double d = a[j][j];   // the same shared value in every lane: uniform branch
-        if (!(d > 0.0)) {
-            bad = true;
-            break;
-        }
-        double rj = sqrt(d);
-        __syncwarp();
-        if (t > j && t < m) a[t][j] /= rj;
-        if (t == j) a[j][j] = rj;
-        __syncwarp();
-        if (t > j && t < m) {
-            double aij = a[t][j];
-            for (int l = j + 1; l <= t; ++l) a[t][l] -= aij * a[l][j];
-        }
-        __syncwarp();
-    }
-    for (int idx = t; idx < m * m; idx += 32) {
-        int i = idx % m, j = idx / m;   // R(i, j) = L(j, i) for i <= j
-        double v = bad ? (i == j ? 1.0 : 0.0) : (i <= j ? a[j][i] : 0.0);
-        R[(size_t)j * ldr + i] = v;
-    }
-    if (t == 0) *flag = bad ? 1.0 : 0.0;
+    chol_small_body(m, G, ldg, R, ldr, flag);
 }
 
 template <typename S, typename D>
 __global__ void k_copy_cols(int n, int m, const S* __restrict__ X, long long ldx, D* __restrict__ Y, long long ldy,
                             double beta) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long tot = (long long)n * m;
-    if (idx >= tot) return;
-    int j = (int)(idx / n), i = (int)(idx % n);
-    D v = (D)X[(size_t)j * ldx + i];
-    D* y = Y + (size_t)j * ldy + i;
-    *y = beta == 0.0 ? v : (D)(beta * (double)(*y)) + v;
+    copy_cols_body<S, D>(n, m, X, ldx, Y, ldy, beta, blockIdx.x);
 }
 
 __global__ void k_axpby(int n, int m, double a, const double* __restrict__ X, long long ldx, double b,
                         double* __restrict__ Y, long long ldy) {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long tot = (long long)n * m;
-    if (idx >= tot) return;
-    int j = (int)(idx / n), i = (int)(idx % n);
-    double* y = Y + (size_t)j * ldy + i;
-    *y = (b == 0.0 ? 0.0 : b * (*y)) + a * X[(size_t)j * ldx + i];
+    axpby_body(n, m, a, X, ldx, b, Y, ldy, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1837,6 +1390,33 @@ int st_tune_measure(cudaStream_t s, int n, const bool* valid, const std::functio
     return ST_OK;
 }
 
+// 1D factors of the box problem's M and A (see k_apply_sf3): mass h/6 (1, 4, 1),
+// stiffness (-1, 2, -1)/h, convection beta_d/2 (-1, 0, 1), as the assembly uses them.
+static SfStencil sf_stencil(const st_problem* p) {
+    SfStencil f{};
+    for (int d = 0; d < 3; ++d) {
+        const double h = p->len[d] / (p->n[d] + 1);
+        const double k0 = 2.0 / h, k1 = -1.0 / h;
+        double am, a0, ap;
+        if (p->d.op == ST_CONVDIFF) {
+            const double e = p->d.eps, b = p->d.beta[d];
+            am = e * k1 - 0.5 * b;
+            a0 = e * k0;
+            ap = e * k1 + 0.5 * b;
+        } else {
+            am = ap = p->kappa * k1;
+            a0 = p->kappa * k0;
+        }
+        f.m0[d] = (float)(4.0 * h / 6.0);
+        f.m1[d] = (float)(h / 6.0);
+        f.am[d] = (float)am;
+        f.a0[d] = (float)a0;
+        f.ap[d] = (float)ap;
+    }
+    f.hdt = (float)(0.5 * p->dt);
+    return f;
+}
+
 template <typename T>
 int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, cudaStream_t s) {
     const T* pv;
@@ -1870,10 +1450,18 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
         st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32", ts * 2.0 * (double)p->n_h * n_t,
                       4.0 * (double)p->max_row_nnz * p->n_h * n_t);
         if constexpr (sizeof(T) == 4) {
-            if (p->dim == 2)
+            if (p->dim == 2) {
                 k_apply_box_sh<T, 2, 4, 1, 8, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
-            else
-                k_apply_box_sh<T, 3, 4, 2, 8, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+            } else {
+                // sum-factorised: 32 x-points, 8 x 2 rows in y, 8 planes in z a CTA; 16 time columns
+                constexpr int YB3 = 2, ZB3 = 8, ST3 = 16;
+                const long long b3 = (long long)((nx + 31) / 32) * ((ny + 8 * YB3 - 1) / (8 * YB3)) *
+                                     ((nz + ZB3 - 1) / ZB3);
+                const dim3 g3((unsigned)b3, (unsigned)((n_t + ST3 - 1) / ST3));
+                if (b3 > 0x7fffffffLL || g3.y > 65535) return ST_EINVAL;
+                k_apply_sf3<YB3, ZB3><<<g3, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, ST3, sf_stencil(p),
+                                                                 (const float*)U, ldu, (float*)Y, ldy);
+            }
         } else {
             if (p->dim == 2)
                 k_apply_box<T, 2, 4, 1, 8><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);

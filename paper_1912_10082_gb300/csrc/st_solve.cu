@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "st_common.cuh"
+#include "st_rksm.h"
 #include "st_tune.h"
 
 int st_slot(st_problem* p, int id, size_t bytes, void** out) {
@@ -30,17 +31,9 @@ int st_slot(st_problem* p, int id, size_t bytes, void** out) {
     return ST_OK;
 }
 
-namespace {
+namespace rksm {
 
-using Clock = std::chrono::steady_clock;
-inline double ms_since(Clock::time_point t0) {
-    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
-}
 
-enum SlotId {
-    S_F1D = 0, S_F1C, S_MAQ, S_WH, S_WH2, S_TMP, S_X32, S_W32, S_T32, S_SMALL, S_PART, S_COPY, S_MV,
-    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT, S_WDF, S_GH, S_GHD, S_GPART
-};
 
 // Records why the Krylov process broke down (text of st_last_error).
 int breakdown(const char* why) {
@@ -48,11 +41,6 @@ int breakdown(const char* why) {
     return ST_EBREAKDOWN;
 }
 
-struct Ctx {
-    st_problem* p;
-    cudaStream_t s;
-    int n;
-};
 
 int read_dev(Ctx& c, const double* d, int ld, int rows, int cols, double* h, int ldh) {
     if (rows == 0 || cols == 0) return ST_OK;
@@ -322,7 +310,7 @@ bool ritz_values(int k, const double* Am, const double* Mm, int ld, std::vector<
 // With P = Mm + dt/2 Am factored once, S = P^{-1}(Mm - dt/2 Am) and
 // G = P^{-1} Gm are formed first, so each step costs one k x k product.
 bool projected_solve(int k, int n_t, double dt, const double* Mm, const double* Am, int ld, const double* Gm,
-                     int ldg, int r, const double* F2c, std::vector<double>& Y, bool sym = true) {
+                     int ldg, int r, const double* F2c, std::vector<double>& Y, bool sym) {
     std::vector<double> P((size_t)k * k), S((size_t)k * k), G((size_t)k * r);
     for (int j = 0; j < k; ++j)
         for (int i = 0; i < k; ++i) {
@@ -406,20 +394,6 @@ int ensure_basis(st_problem* p, Ctx& c, int need_cols, int keep_cols, double** M
     return ST_OK;
 }
 
-struct HostSym {
-    std::vector<double> a;
-    int ld = 0;
-    void grow(int need) {
-        if (need <= ld) return;
-        int nl = std::max(need, 2 * ld + 16);
-        std::vector<double> b((size_t)nl * nl, 0.0);
-        for (int j = 0; j < ld; ++j)
-            for (int i = 0; i < ld; ++i) b[(size_t)j * nl + i] = a[(size_t)j * ld + i];
-        a.swap(b);
-        ld = nl;
-    }
-    double& operator()(int i, int j) { return a[(size_t)j * ld + i]; }
-};
 
 // ---- staging of the small results of one synchronisation point ----
 // The device buffer sm_dev holds a download region [0, cap) that collects the
@@ -447,7 +421,6 @@ int stage_reserve(st_problem* p, size_t need) {
     return ST_OK;
 }
 
-inline size_t pad32(size_t m) { return (m + 31) & ~size_t(31); }
 
 struct Stage {
     Ctx& c;
@@ -528,12 +501,6 @@ int basis_nn_sub(Ctx& c, bool df, int k, int m, const double* H, int ldh, double
 // has full rank and a Cholesky factor, the first CholQR factor R1 = L^T.
 // The rank counts the eigenvalues above drop^2 max(lambda_max, ref2), the
 // rule of block_qr, which handles every block that is not of full rank.
-struct QrPlan {
-    int rank = 0;
-    bool fast = false;
-    bool severe = false;      // a kept direction lost more than 6 digits to Gram-Schmidt
-    std::vector<double> R1;   // m x m upper, ld m
-};
 
 void qr_plan(const double* G, int m, double ref2, double drop, QrPlan& q) {
     std::vector<double> E(G, G + (size_t)m * m), w(m);
@@ -1495,7 +1462,9 @@ __global__ void k_dense_resid(int n, int nt, const double* __restrict__ F1, long
     }
 }
 
-}  // namespace
+}  // namespace rksm
+
+using namespace rksm;
 
 extern "C" int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
                         st_solution* sol, st_stats* stats) {

@@ -327,6 +327,29 @@ def test_lowrank_residual_equals_dense_residual():
     assert abs(a - b) <= 1e-13 * b
 
 
+@pytest.mark.parametrize("chunk", [1, 4, 9, 64])
+def test_blockwise_residual_equals_dense_residual(chunk):
+    """The block-by-block residual (for solutions too large to form) is the dense residual, for any block
+    size; near the exact solution it resolves a relative residual at rounding level."""
+    M, A = fem.tensor_operators(2, 6, kappa=0.8)
+    D, C = timefe.time_matrices(9, 1.0)
+    rng = np.random.default_rng(6)
+    V = rng.standard_normal((36, 4))
+    Y = rng.standard_normal((4, 9))
+    F1, F2 = rng.standard_normal((36, 2)), rng.standard_normal((9, 2))
+    a = residual.relres_lowrank_by_columns(M, A, D, C, V, Y, F1, F2, chunk=chunk)
+    b = residual.relres_dense(M, A, D, C, V @ Y, F1 @ F2.T)
+    assert abs(a - b) <= 1e-13 * b
+    U = kron.solve_sparse(M, A, D, C, F1 @ F2.T)
+    Uv, s_, Ut = np.linalg.svd(U, full_matrices=False)
+    Vx, Yx = Uv * s_, Ut
+    exact = residual.relres_lowrank_by_columns(M, A, D, C, Vx, Yx, F1, F2, chunk=chunk)
+    assert exact <= 1e-13
+    Yp = Yx + 1e-9 * rng.standard_normal(Yx.shape)
+    pert = residual.relres_lowrank_by_columns(M, A, D, C, Vx, Yp, F1, F2, chunk=chunk)
+    assert abs(pert - residual.relres_dense(M, A, D, C, Vx @ Yp, F1 @ F2.T)) <= 1e-6 * pert
+
+
 # ---------------------------------------------------------------- RKSM reference
 
 
@@ -448,3 +471,14 @@ def test_cg_forward_substitution_equals_direct_elimination():
     U = kron.forward_substitution(M, A, D, C, F1 @ F2.T)
     Uc = kron.forward_substitution_cg(M, A, D, C, F1, F2, 3, rtol=1e-14)
     assert np.linalg.norm(Uc - U[:, :3]) <= 1e-12 * np.linalg.norm(U[:, :3])
+
+
+def test_normal_equations_forward_substitution_matches_direct_elimination():
+    """CG on the normal equations of each nonsymmetric block gives the direct elimination's first columns."""
+    M, A = fem.tensor_operators(2, (9, 7), op="convdiff", eps=0.05, beta=(1.0, 0.5))
+    D, C = timefe.time_matrices(6, 1.0)
+    F1, F2 = workloads.gaussian_factors(M.shape[0], 6, 2, seed=4)
+    assert abs(A - A.T).max() > 1e-3                      # the operator really is nonsymmetric
+    U = kron.forward_substitution(M, A, D, C, F1 @ F2.T)
+    Un = kron.forward_substitution_normal_cg(M, A, D, C, F1, F2, 3)
+    assert np.linalg.norm(Un - U[:, :3]) <= 1e-11 * np.linalg.norm(U[:, :3])
