@@ -274,6 +274,27 @@ int st_autotune_load(const char* path, const char* device_tag, int* loaded);
 int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
              st_solution* sol, st_stats* stats);
 
+/* st_solve_lrfgmres -- LR-FGMRES+RKSM, the comparison solver of Section 5,
+ * Example 1 (Table 1): flexible GMRES (no restart, X_0 = 0) on (1) with every
+ * Krylov vector held as a low-rank pair P Q^T (P on the device, Q on the host),
+ * inner product trace(X^T Y), every sum and operator product truncated (thin
+ * QRs of both factors and an SVD of the core; singular values at or below
+ * trunc times the largest dropped), right-preconditioned by st_solve's RKSM
+ * stopped after precond_iters shifted solves on the vector's factors (blocks
+ * of at most 16 columns, their results summed).  Stops when the least-squares
+ * residual estimate is <= the problem's tol, or after maxit steps.  Heat
+ * problems on box grids (ST_ENOTSUP otherwise).  F1, F2 as st_solve (host or
+ * device, 1 <= ncols).  Output in *sol: V = P (n_h x k), Y = Q^T (k x n_t),
+ * owned by the handle (valid until its next solve or st_destroy), U_dense
+ * filled if given.  stats (may be NULL): iterations = GMRES steps, basis_cols
+ * = k, mu_mem = stored columns of every factor pair V_1..V_{m+1}, Z_1..Z_m
+ * (Table 1's memory count), relres = the final least-squares estimate,
+ * inner_iterations = RKSM iterations of all preconditioner calls.  Returns
+ * ST_OK, ST_ENOTCONV (best iterate returned), ST_EINVAL, ST_ENOTSUP, ST_ENOMEM,
+ * ST_ECUDA.  Synchronises. */
+int st_solve_lrfgmres(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
+                      int maxit, int precond_iters, double trunc, st_solution* sol, st_stats* stats);
+
 /* Statistics of one st_solve_batch call. */
 typedef struct st_batch_stats {
     int instances;          /* problems in the call */
@@ -297,8 +318,8 @@ typedef struct st_batch_stats {
  * iterating, and each round synchronises with the host once per phase for
  * the whole group; the small host problems of a round (rank decisions,
  * shifts, projected solves) run on a pool of host threads.  The problems
- * run as `groups` such lock-step groups (<= 0: min(4, count / 32), at least
- * 1; problems dealt by decreasing size) on streams and host threads of their
+ * run as `groups` such lock-step groups (<= 0: about 8 problems a group, at
+ * most 32 groups; problems dealt by decreasing size) on streams and host threads of their
  * own, so one group's host work overlaps the others' device work; `stream`
  * waits for all of them.  Each problem
  * takes exactly the steps and decisions st_solve takes on it, and the

@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
     "st_executor_destroy", "st_executor_set_policy", "st_autotune", "st_autotune_reset", "st_autotune_count",
-    "st_autotune_save", "st_autotune_load", "st_solve_batch",
+    "st_autotune_save", "st_autotune_load", "st_solve_batch", "st_solve_lrfgmres",
 )
 
 
@@ -150,6 +150,7 @@ def lib() -> C.CDLL:
         "st_executor_destroy": ([vp], i),
         "st_profile_begin": ([], i),
         "st_profile_end": ([C.POINTER(StKernelTime), i, C.POINTER(i)], i),
+        "st_solve_lrfgmres": ([vp, vp, i, vp, i, i, i, i, d, C.POINTER(StSolution), C.POINTER(StStats)], i),
         "st_solve_batch": ([i, C.POINTER(vp), C.POINTER(vp), C.POINTER(i), C.POINTER(vp), C.POINTER(i),
                             C.POINTER(i), C.POINTER(StSolution), C.POINTER(StStats), C.POINTER(i), vp, i,
                             C.POINTER(StBatchStats)], i),
@@ -342,6 +343,29 @@ class Problem:
         stats = StStats()
         st = lib().st_solve(self.h, p1, l1, p2, l2, m, C.byref(sol), C.byref(stats))
         _check(st, "st_solve", ok)
+        k = sol.k
+        if k > 0:
+            V = torch.as_tensor(_DevView(sol.V, self.n_h, k, self.n_h), device="cuda")
+            Y = torch.as_tensor(_DevView(sol.Y, k, self.n_t, k), device="cuda")
+        else:
+            V = torch.zeros((self.n_h, 0), dtype=torch.float64, device="cuda")
+            Y = torch.zeros((0, self.n_t), dtype=torch.float64, device="cuda")
+        return V, Y, stats.as_dict(), st
+
+    def solve_lrfgmres(self, F1, F2, maxit: int = 50, precond_iters: int = 5, trunc: float = 1e-12, U_dense=None,
+                       ok=(ST_OK,)):
+        """LR-FGMRES+RKSM (st_solve_lrfgmres): returns (V, Y, stats, status) with U = V Y."""
+        import torch
+        p1, l1, _, m = _ptr_ld(F1)
+        p2, l2, _, _ = _ptr_ld(F2)
+        sol = StSolution()
+        if U_dense is not None:
+            pu, lu, _, _ = _ptr_ld(U_dense)
+            sol.U_dense, sol.ldu = pu, lu
+        stats = StStats()
+        st = lib().st_solve_lrfgmres(self.h, p1, l1, p2, l2, m, int(maxit), int(precond_iters), float(trunc),
+                                     C.byref(sol), C.byref(stats))
+        _check(st, "st_solve_lrfgmres", ok)
         k = sol.k
         if k > 0:
             V = torch.as_tensor(_DevView(sol.V, self.n_h, k, self.n_h), device="cuda")

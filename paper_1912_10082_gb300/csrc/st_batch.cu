@@ -231,8 +231,10 @@ void fd_steps(const st_problem* p, FdKind kind, double shift, double coef, const
                 N = (int)J;
             }
             t.ep = ep;
-            t.gx = (N + kFoldEdge - 1) / kFoldEdge;
-            t.gy = (M + kFoldEdge - 1) / kFoldEdge;
+            t.tc = sizeof(T) == 4 && fold_tc_grouped(t.n) ? 1 : 0;
+            const int ex = t.tc ? FTC_N : kFoldEdge, ey = t.tc ? FTC_M : kFoldEdge;
+            t.gx = (N + ex - 1) / ex;
+            t.gy = (M + ey - 1) / ey;
             t.gz = 2 * batch;
             out.push_back(t);
             side.push_back(d == 0 ? 0 : 1);
@@ -1432,7 +1434,9 @@ extern "C" int st_solve_batch(int count, st_problem* const* problems, const doub
         // decisions, shifts, projected solves), the others' grouped launches keep the device busy.  Problems
         // are dealt to the groups in decreasing order of size, so every group gets a share of the large ones.
         const int hw = std::max(1, (int)std::thread::hardware_concurrency());
-        const int G = groups > 0 ? std::min(groups, m) : std::max(1, std::min(4, m / 32));
+        // automatic: groups of about 8 problems (measured on the 256-problem batch: 1 group 1.6 s, 4 groups
+        // 1.19 s, 32 groups 0.97 s; lock step couples fast and slow problems, so small groups win)
+        const int G = groups > 0 ? std::min(groups, m) : std::max(1, std::min(32, (m + 7) / 8));
         std::vector<int> order(m);
         for (int j = 0; j < m; ++j) order[j] = j;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {

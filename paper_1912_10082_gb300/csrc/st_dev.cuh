@@ -8,6 +8,8 @@
 // one instance of a batch) run the same arithmetic in the same order.
 #pragma once
 
+#include <cstdint>
+
 #include "st_common.cuh"
 
 namespace {
@@ -622,6 +624,245 @@ __device__ __forceinline__ void axpby_body(int n, int m, double a, const double*
     double* y = Y + (size_t)j * ldy + i;
     // explicit rounding (b y rounded, a x fused into the sum): the same in every kernel inlining this body
     *y = __fma_rn(a, X[(size_t)j * ldx + i], b == 0.0 ? 0.0 : __dmul_rn(b, *y));
+}
+
+
+// ---------------------------------------------------------------------------
+// Folded mode product on the 5th-generation tensor cores (FP32 data, 3xTF32).
+// The quantity of gemm_fold_body<float, TM, SIDE>: per parity p, the product
+// of the folded operand with the half table (SIDE 0: C[line][2i'+p] =
+// sum_k Xf[line][k] G_p[i'][k]; SIDE 1: C[2i'+p][col] = sum_k G_p[i'][k]
+// Xf[k][col]) and the same epilogue.  A CTA of 256 threads computes a tile of
+// 128 rows (the MMA's M) by FTC_N columns of D: it stages K in chunks of
+// FTC_KC into shared memory as tf32 hi/lo planes (a = hi + lo, hi rounded to
+// tf32) in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes a core
+// matrix), one thread issues D += Ahi Bhi + Ahi Blo + Alo Bhi with
+// tcgen05.mma kind::tf32 (FP32 accumulator in TMEM; the dropped lo*lo term
+// and tf32 rounding of the lo parts leave about FP32 accuracy), the CTA waits
+// on an mbarrier (bounded), and the epilogue reads TMEM with tcgen05.ld,
+// transposes through shared memory and stores coalesced.
+// ---------------------------------------------------------------------------
+constexpr int FTC_M = 128, FTC_N = 128, FTC_KC = 32, FTC_THREADS = 256;
+
+// Built-in choice of the FP32 mode product's tile, the same for single and
+// batched solves (so a problem's result does not depend on the path): the
+// tensor-core tile when the folded length is at least FTC_MIN_K and one launch
+// has at least FTC_MIN_TILES of its 128 x 128 tiles, else the SIMT tiles.
+constexpr int FTC_MIN_K = 32, FTC_MIN_TILES = 64;
+__host__ __device__ inline bool fold_tc_default(int n, int other, int batch) {
+    const int K0 = (n + 1) / 2;
+    if (K0 < FTC_MIN_K) return false;
+    // SIDE 0 tiles: lines x modes; SIDE 1: modes x lines -- the same count
+    const long long tiles = (long long)((other + 127) / 128) * ((K0 + 127) / 128) * 2 * batch;
+    return tiles >= FTC_MIN_TILES;
+}
+// The batched solver's choice, per problem and independent of the other problems of the batch (so a
+// problem's batched result does not depend on its batch-mates): the tensor-core tile from a folded
+// length of 64 (grids of 127+ points a side), where a grouped launch holds tiles of many problems.
+__host__ __device__ inline bool fold_tc_grouped(int n) { return (n + 1) / 2 >= 64; }
+constexpr int FTC_PLANE = FTC_M * FTC_KC * 4;                  // 16 KB: one operand plane of a K chunk
+constexpr int FTC_SMEM = 4 * FTC_PLANE > FTC_M * (FTC_N + 1) * 4 ? 4 * FTC_PLANE : FTC_M * (FTC_N + 1) * 4;
+constexpr int FTC_TMEM_COLS = 128;
+constexpr long long FTC_WAIT_LIMIT = 1ll << 24;                // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t ftc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, byte offsets between core matrices along K (lbo) and
+// along M/N (sbo), descriptor version 1
+__device__ __forceinline__ uint64_t ftc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ float ftc_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// byte offset of (row, k) in a 128-row K-major plane of FTC_KC columns: core matrix (row/8, k/4) at
+// ((k/4) * 16 + row/8) * 128
+__device__ __forceinline__ int ftc_off(int row, int k) {
+    return ((k >> 2) * 16 + (row >> 3)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ void ftc_put(unsigned char* sm, int row, int k, float v) {
+    const float hi = ftc_tf32(v);
+    const int o = ftc_off(row, k);
+    *(float*)(sm + o) = hi;                                   // plane 0: A hi (rows) / plane 2: B hi
+    *(float*)(sm + FTC_PLANE + o) = ftc_tf32(v - hi);         // plane 1 / 3: lo
+}
+
+// TMEM allocation of the CTA (warp 0), done once per CTA.
+__device__ __forceinline__ void ftc_alloc(uint32_t* slot) {
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ftc_smem_u32(slot)),
+                     "r"(FTC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+}
+__device__ __forceinline__ void ftc_dealloc(uint32_t tmem) {
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FTC_TMEM_COLS));
+}
+__device__ __forceinline__ void ftc_mbar_init(uint64_t* mbar) {
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ftc_smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+}
+
+// Waits for the mbarrier's phase `ph`; false after FTC_WAIT_LIMIT polls.
+__device__ __forceinline__ bool ftc_wait(uint64_t* mbar, uint32_t ph) {
+    uint32_t done = 0;
+    for (long long it = 0; it < FTC_WAIT_LIMIT && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(ftc_smem_u32(mbar)), "r"(ph));
+    return done != 0;
+}
+
+// One tile (bx, by, bz as gemm_fold_body with 128-row, FTC_N-column tiles).  Returns false if an MMA wait
+// gave up (the tile's outputs are then NaN); *phase tracks the mbarrier's phase across calls.
+template <int SIDE>
+__device__ bool fold_tc_body(int n, int other, const float* __restrict__ X, long long ldx,
+                             const float* __restrict__ G0, const float* __restrict__ G1, float* __restrict__ C,
+                             long long ldc, Batch2 bt, const FdEpi& ep, int bx, int by, int bz, unsigned char* sm,
+                             uint32_t tmem, uint64_t* mbar, uint32_t* phase) {
+    const int par = bz & 1;
+    const int zb = bz >> 1;
+    const int z1 = zb % bt.nb1, z2 = zb / bt.nb1;
+    const int K = par ? n / 2 : (n + 1) / 2;
+    const int mid = (n & 1) ? (n - 1) / 2 : -1;
+    const float sgn = par ? -1.f : 1.f;
+    const int M = SIDE == 0 ? other : K;
+    const int N = SIDE == 0 ? K : other;
+    const int m0 = by * FTC_M, n0 = bx * FTC_N;
+    if (m0 >= M || n0 >= N) return true;   // uniform over the CTA
+    if (SIDE == 0)
+        X += (size_t)z1 * bt.sA1 + (size_t)z2 * bt.sA2;
+    else
+        X += (size_t)z1 * bt.sB1 + (size_t)z2 * bt.sB2;
+    C += (size_t)z1 * bt.sC1 + (size_t)z2 * bt.sC2;
+    const float* Gp = par ? G1 : G0;   // K' x K, output-major: G_p[i'][k]
+    const int tid = threadIdx.x;
+    unsigned char* sa = sm;                       // A hi, A lo
+    unsigned char* sb = sm + 2 * FTC_PLANE;       // B hi, B lo
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(FTC_N >> 3) << 17) |
+                           ((uint32_t)(FTC_M >> 4) << 24);   // f32 accumulate, tf32 A and B, K-major, M 128
+    const uint32_t kstride = (FTC_M / 8) * 128, mstride = 128;   // bytes between core matrices along K, M/N
+    bool ok = true;
+    for (int k0 = 0; k0 < K; k0 += FTC_KC) {
+        // stage the chunk (zeros beyond the operands' edges)
+        for (int idx = tid; idx < FTC_M * FTC_KC; idx += FTC_THREADS) {
+            const int r = idx / FTC_KC, kk = idx % FTC_KC;
+            const int gm = m0 + r, gk = k0 + kk;
+            float v = 0.f;
+            if (gm < M && gk < K) {
+                if (SIDE == 0) {
+                    const float* row = X + (size_t)gm * ldx;
+                    v = gk == mid ? row[gk] : row[gk] + sgn * row[n - 1 - gk];
+                } else {
+                    v = Gp[(size_t)gm * K + gk];
+                }
+            }
+            ftc_put(sa, r, kk, v);
+        }
+        for (int idx = tid; idx < FTC_N * FTC_KC; idx += FTC_THREADS) {
+            int c, kk;
+            if (SIDE == 0) {   // G_p rows: k contiguous
+                c = idx / FTC_KC;
+                kk = idx % FTC_KC;
+            } else {           // X rows: columns contiguous
+                kk = idx / FTC_N;
+                c = idx % FTC_N;
+            }
+            const int gn = n0 + c, gk = k0 + kk;
+            float v = 0.f;
+            if (gn < N && gk < K) {
+                if (SIDE == 0) {
+                    v = Gp[(size_t)gn * K + gk];
+                } else {
+                    v = gk == mid ? X[(size_t)gk * ldx + gn]
+                                  : X[(size_t)gk * ldx + gn] + sgn * X[(size_t)(n - 1 - gk) * ldx + gn];
+                }
+            }
+            ftc_put(sb, c, kk, v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");   // generic-proxy stores visible to the tensor cores
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            for (int s = 0; s < FTC_KC / 8; ++s) {
+                const uint32_t ko = (uint32_t)s * 2 * kstride;
+                const uint64_t ah = ftc_desc(ftc_smem_u32(sa) + ko, kstride, mstride);
+                const uint64_t al = ftc_desc(ftc_smem_u32(sa + FTC_PLANE) + ko, kstride, mstride);
+                const uint64_t bh = ftc_desc(ftc_smem_u32(sb) + ko, kstride, mstride);
+                const uint64_t bl = ftc_desc(ftc_smem_u32(sb + FTC_PLANE) + ko, kstride, mstride);
+                const uint64_t pa[3] = {ah, ah, al}, pb[3] = {bh, bl, bh};
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const uint32_t acc = (k0 > 0 || s > 0 || t > 0) ? 1u : 0u;
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                 "l"(pa[t]), "l"(pb[t]), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                ftc_smem_u32(mbar)));
+        }
+        if (!ftc_wait(mbar, *phase) && !ftc_wait(mbar, *phase)) ok = false;   // the chunk's MMAs are done
+        *phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!ok) break;
+    }
+    if (!ok) {
+        // a wait gave up (no MMA completion after two bounded waits): the tile's outputs become NaN, so
+        // the caller's solve stops on its non-finite checks, and the kernel takes no further tile
+        for (int idx = tid; idx < FTC_M * FTC_N; idx += FTC_THREADS) {
+            const int gm = m0 + idx / FTC_N, gn = n0 + idx % FTC_N;
+            if (gm >= M || gn >= N) continue;
+            const long long om = SIDE == 0 ? gm : 2LL * gm + par;
+            const long long on = SIDE == 0 ? 2LL * gn + par : gn;
+            C[(size_t)om * ldc + on] = __int_as_float(0x7fc00000);
+        }
+        return false;
+    }
+    // epilogue: warps w and w + 4 read TMEM lanes 32 (w % 4) .. +31 (rows), columns [0, 64) and [64, 128)
+    const int warp = tid / 32, lane = tid % 32;
+    float* T = reinterpret_cast<float*>(sm);   // 128 x (FTC_N + 1) transpose buffer over the operand planes
+    const int row = 32 * (warp & 3) + lane;
+    for (int c0 = (warp >> 2) * (FTC_N / 2); c0 < (warp >> 2) * (FTC_N / 2) + FTC_N / 2; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                       "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                       "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                       "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                       "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) T[row * (FTC_N + 1) + c0 + j] = __uint_as_float(v[j]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    const float fcoef = (float)ep.coef;
+    for (int idx = tid; idx < FTC_M * FTC_N; idx += FTC_THREADS) {
+        const int r = idx / FTC_N, c = idx % FTC_N;   // a warp stores 32 consecutive columns of a row
+        const int gm = m0 + r, gn = n0 + c;
+        if (gm >= M || gn >= N) continue;
+        const long long om = SIDE == 0 ? gm : 2LL * gm + par;
+        const long long on = SIDE == 0 ? 2LL * gn + par : gn;
+        float f = fcoef;
+        if (ep.scale) f *= fd_omega32(ep, ep.left ? om * ep.J + on : on);
+        C[(size_t)om * ldc + on] = f * T[r * (FTC_N + 1) + c];
+    }
+    __syncthreads();   // T is restaged by the next tile
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return true;
 }
 
 }  // namespace

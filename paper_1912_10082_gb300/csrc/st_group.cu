@@ -54,6 +54,42 @@ __global__ void __launch_bounds__(256) kg_fold(const stg::FoldTask* tasks, const
     }
 }
 
+// Tensor-core mode products (FP32): TMEM allocated once per CTA, one mbarrier whose phase runs across
+// the tiles; a tile whose MMA wait gave up stops the CTA (its outputs are NaN, see fold_tc_body).
+template <int SIDE>
+__global__ void __launch_bounds__(FTC_THREADS, 1) kg_fold_tc(const stg::FoldTask* tasks, const int* prefix,
+                                                            int ntasks) {
+    extern __shared__ __align__(1024) unsigned char ftc_sm[];
+    __shared__ stg::FoldTask tk;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    ftc_alloc(&tslot);
+    ftc_mbar_init(&mbar);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t ph = 0;
+    const int total = prefix[ntasks];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int i = g_task(prefix, ntasks, t);
+        __syncthreads();
+        g_load(tk, tasks + i, threadIdx.x, FTC_THREADS);
+        __syncthreads();
+        int local = t - prefix[i];
+        const int bx = local % tk.gx;
+        local /= tk.gx;
+        const int by = local % tk.gy, bz = local / tk.gy;
+        if (!fold_tc_body<SIDE>(tk.n, tk.other, (const float*)tk.X, tk.ldx, (const float*)tk.HG[2],
+                                (const float*)tk.HG[3], (float*)tk.C, tk.ldc, tk.bt, tk.ep, bx, by, bz, ftc_sm, tslot,
+                                &mbar, &ph))
+            break;   // uniform: every thread of the CTA saw the same waits
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ftc_dealloc(tslot);
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(256) kg_stencil(const stg::StencilTask* tasks, const int* prefix, int ntasks) {
     __shared__ stg::StencilTask tk;
@@ -253,7 +289,12 @@ size_t GroupPhase::put_tasks(const std::vector<Task>& t, const std::vector<int>&
 
 #define ST_PREFIX_OF(off, Task, n) ((((off) + sizeof(Task) * (n)) + 15) & ~size_t(15))
 
-void GroupPhase::fold(int tsize, int side, const std::vector<FoldTask>& t) {
+void GroupPhase::fold(int tsize, int side, const std::vector<FoldTask>& all) {
+    if (all.empty()) return;
+    // tensor-core tasks (FP32) in a launch of their own
+    std::vector<FoldTask> t, tct;
+    for (const FoldTask& k : all) (tsize == 4 && k.tc ? tct : t).push_back(k);
+    if (!tct.empty()) fold_tc(side, tct);
     if (t.empty()) return;
     std::vector<int> tiles(t.size());
     for (size_t i = 0; i < t.size(); ++i) tiles[i] = t[i].gx * t[i].gy * t[i].gz;
@@ -287,6 +328,38 @@ void GroupPhase::fold(int tsize, int side, const std::vector<FoldTask>& t) {
                 kg_fold<double, 2, 1><<<g, 256, 0, s>>>(T, P, nt);
         }
     }, tsize == 4 ? "g_fold32" : "g_fold64", bytes, flops});
+}
+
+void GroupPhase::fold_tc(int side, const std::vector<FoldTask>& t) {
+    std::vector<int> tiles(t.size());
+    for (size_t i = 0; i < t.size(); ++i) tiles[i] = t[i].gx * t[i].gy * t[i].gz;
+    int total = 0;
+    const size_t off = put_tasks(t, tiles, &total);
+    const size_t poff = ST_PREFIX_OF(off, FoldTask, t.size());
+    const int nt = (int)t.size();
+    if (total == 0) return;
+    double bytes = 0.0, flops = 0.0;
+    for (const FoldTask& k : t) {
+        const double K0 = (k.n + 1) / 2, K1 = k.n / 2, batch = k.gz / 2;
+        bytes += 4.0 * (K0 * K0 + K1 * K1 + 2.0 * k.other * k.n * batch);
+        flops += 2.0 * k.other * (K0 * K0 + K1 * K1) * batch;
+    }
+    cudaStream_t s = s_;
+    pend_.push_back({[=](const char* d) {
+        static const bool set = [] {
+            cudaFuncSetAttribute(kg_fold_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, FTC_SMEM);
+            cudaFuncSetAttribute(kg_fold_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, FTC_SMEM);
+            return true;
+        }();
+        (void)set;
+        const FoldTask* T = (const FoldTask*)(d + off);
+        const int* P = (const int*)(d + poff);
+        const int g = std::max(1, std::min(total, 152 * 3));   // up to three 66 KB CTAs an SM
+        if (side == 0)
+            kg_fold_tc<0><<<g, FTC_THREADS, FTC_SMEM, s>>>(T, P, nt);
+        else
+            kg_fold_tc<1><<<g, FTC_THREADS, FTC_SMEM, s>>>(T, P, nt);
+    }, "g_fold_tc", bytes, flops});
 }
 
 void GroupPhase::stencil(int dim, const std::vector<StencilTask>& t) {

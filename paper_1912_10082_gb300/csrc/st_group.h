@@ -30,6 +30,7 @@ struct FoldTask {
     Batch2 bt;
     FdEpi ep;
     int gx, gy, gz;   // tiles: gx * gy * gz (gz = 2 * batch: both parities)
+    int tc;           // FP32 only: 1 = tensor-core tiles (128 x 128), 0 = SIMT tiles (32 x 32)
 };
 
 // Box-stencil product O1 = S1 X (+ beta O1), O2 = S2 X (k_stencil_box's tile body, FP64).
@@ -129,6 +130,7 @@ class GroupPhase {
     GroupPhase(cudaStream_t s, GroupArena* arena) : s_(s), arena_(arena) {}
     // Each add_* queues one grouped launch (skipped when it has no task).
     void fold(int tsize, int side, const std::vector<FoldTask>& t);   // tsize 4 (float) or 8 (double)
+    void fold_tc(int side, const std::vector<FoldTask>& t);           // FP32 tasks on the tensor cores
     void stencil(int dim, const std::vector<StencilTask>& t);
     void tn(bool df, const std::vector<TnTask>& t);                  // partials and their sums: two launches
     void nn(bool df, const std::vector<NnTask>& t);

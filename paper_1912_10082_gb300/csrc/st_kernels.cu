@@ -297,36 +297,37 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 3 : 1) k_apply_box_sh(int nx, 
 // m_z (x) m_y (x) a_x (heat: a_d = kappa k_d; convection-diffusion:
 // a_d = eps k_d + beta_d g_d), so with c = dt/2
 //     P u = m_z S1 + c (m_z S2 + a_z S1),   N u = m_z S1 - c (m_z S2 + a_z S1),
-//     S1 = (m_y (x) m_x) u,   S2 = (a_y (x) m_x + m_y (x) a_x) u,
-// three passes of 3-point stencils (x, then y, then z) instead of the
-// 27-point sums for P and N: about 20 operations an output instead of 54 FMA.
-// A warp spans 32 consecutive x (the two edge lanes load their outer
-// neighbour), a thread owns YB rows in y and walks ZB planes in z with a
-// window of S1, S2 over three planes, then the next time column, carrying
-// N u_{l-1} for its YB x ZB outputs.  Dirichlet neighbours are zeros at every
-// stage, which is the tensor product of the interior 1D matrices.
+//     S1 = (m_y (x) m_x) u,   S2 = (a_y (x) m_x + m_y (x) a_x) u:
+// three passes of 3-point stencils (x, then y, then z) instead of the 27-point
+// sums for P and N.  A warp spans 32 consecutive x and yields 30 outputs a row
+// (the edge lanes supply halo values; x +- 1 by shuffles); a thread owns YB rows
+// in y and walks ZB planes in z with a window of S1, S2 over three planes,
+// the next plane's rows loaded while the current one is computed, then the
+// next time column, carrying N u_{l-1} for its YB x ZB outputs.  Dirichlet
+// neighbours are zeros at every stage, which is the tensor product of the
+// interior 1D matrices.  Row pointers advance plane by plane (per-row 64-bit
+// offsets hoisted out of the time loop would take the registers).
 // ---------------------------------------------------------------------------
 template <int YB, int ZB>
 __global__ void __launch_bounds__(256, 2) k_apply_sf3(int nx, int ny, int nz, int n_t, int steps, SfStencil f,
-                                                     const float* __restrict__ U, long long ldu, float* __restrict__ Y,
-                                                     long long ldy) {
-    const int nxs = (nx + 31) / 32, nyb = (ny + 8 * YB - 1) / (8 * YB);
+                                                      const float* __restrict__ U, long long ldu, float* __restrict__ Y,
+                                                      long long ldy) {
+    const int nxs = (nx + 29) / 30, nyb = (ny + 8 * YB - 1) / (8 * YB);
     int b = blockIdx.x;
     const int xs = b % nxs;
     b /= nxs;
     const int yb = b % nyb;
     const int zb = b / nyb;
     const int lane = threadIdx.x;
-    const int x = xs * 32 + lane;
+    const int x = xs * 30 + lane - 1;
     const int y0 = (yb * 8 + threadIdx.y) * YB;
     const int z0 = zb * ZB;
-    if (y0 >= ny) return;   // uniform over the warp: the shuffles see all lanes
-    const bool okx = x < nx;
-    const int xe = lane == 0 ? x - 1 : x + 1;   // the outer neighbour an edge lane loads itself
-    const bool edge = (lane == 0 || lane == 31) && xe >= 0 && xe < nx;
+    if (y0 >= ny) return;
+    const bool okx = x >= 0 && x < nx;
+    const bool emit = lane >= 1 && lane <= 30 && x < nx;
     bool oky[YB + 2];
 #pragma unroll
-    for (int r = 0; r < YB + 2; ++r) oky[r] = y0 + r - 1 >= 0 && y0 + r - 1 < ny;
+    for (int r = 0; r < YB + 2; ++r) oky[r] = okx && y0 + r - 1 >= 0 && y0 + r - 1 < ny;
     const int l0 = blockIdx.y * steps;
     const int l1 = min(n_t, l0 + steps);
     float pn[ZB][YB];
@@ -334,25 +335,39 @@ __global__ void __launch_bounds__(256, 2) k_apply_sf3(int nx, int ny, int nz, in
     for (int j = 0; j < ZB; ++j)
 #pragma unroll
         for (int o = 0; o < YB; ++o) pn[j][o] = 0.f;
+    const long long nxy = (long long)nx * ny;
+    // pointers advanced plane by plane (hoisted per-row 64-bit offsets would cost registers)
+    const long long in0 = ((long long)(z0 - 1) * ny + (y0 - 1)) * nx + x;   // plane z0 - 1, row y0 - 1
+    const long long out0 = ((long long)z0 * ny + y0) * nx + x;
 #pragma unroll 1
     for (int c = l0 > 0 ? l0 - 1 : 0; c < l1; ++c) {
-        const float* u = U + (long long)c * ldu;
-        float s1a[YB], s2a[YB], s1b[YB], s2b[YB];   // S1, S2 of planes zz - 2 (a) and zz - 1 (b)
+        const float* up = U + (long long)c * ldu + in0;
+        float* yp = Y + (long long)c * ldy + out0;
+        float s1a[YB], s2a[YB], s1b[YB], s2b[YB];
+        float vv[2][YB + 2];
+        {
+            const bool okz = z0 - 1 >= 0;
+#pragma unroll
+            for (int r = 0; r < YB + 2; ++r) vv[0][r] = okz && oky[r] ? __ldg(up + r * nx) : 0.f;
+        }
 #pragma unroll
         for (int j = 0; j < ZB + 2; ++j) {
+            if (j + 1 < ZB + 2) {   // plane j + 1 in flight while plane j is computed
+                up += nxy;
+                const int zn = z0 + j;
+                const bool okz = zn < nz;
+#pragma unroll
+                for (int r = 0; r < YB + 2; ++r) vv[(j + 1) % 2][r] = okz && oky[r] ? __ldg(up + r * nx) : 0.f;
+            }
+            // keep the loads of later planes from being hoisted above this one (registers)
+            asm volatile("" ::: "memory");
             const int zz = z0 - 1 + j;
-            const bool okz = zz >= 0 && zz < nz;
             float xm[YB + 2], xa[YB + 2];
 #pragma unroll
             for (int r = 0; r < YB + 2; ++r) {
-                const long long row = ((long long)zz * ny + (y0 + r - 1)) * nx;
-                const bool ok = okz && oky[r];
-                const float v = ok && okx ? __ldg(u + row + x) : 0.f;
-                const float ve = ok && edge ? __ldg(u + row + xe) : 0.f;
-                float wm = __shfl_up_sync(0xffffffffu, v, 1);
-                float wp = __shfl_down_sync(0xffffffffu, v, 1);
-                if (lane == 0) wm = ve;
-                if (lane == 31) wp = ve;
+                const float v = vv[j % 2][r];
+                const float wm = __shfl_up_sync(0xffffffffu, v, 1);
+                const float wp = __shfl_down_sync(0xffffffffu, v, 1);
                 xm[r] = fmaf(f.m1[0], wm + wp, f.m0[0] * v);
                 xa[r] = fmaf(f.ap[0], wp, fmaf(f.am[0], wm, f.a0[0] * v));
             }
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(256, 2) k_apply_sf3(int nx, int ny, int nz, in
                 s2c[o] = yam + yma;
             }
             if (j >= 2) {
-                const int zo = zz - 1;   // the plane at the window's centre
+                const int zo = zz - 1;
                 if (zo < nz) {
 #pragma unroll
                     for (int o = 0; o < YB; ++o) {
@@ -376,11 +391,11 @@ __global__ void __launch_bounds__(256, 2) k_apply_sf3(int nx, int ny, int nz, in
                         const float t = mz2 + az1;
                         const float P = fmaf(f.hdt, t, mz1);
                         const float N = fmaf(-f.hdt, t, mz1);
-                        if (c >= l0 && okx && y0 + o < ny)
-                            Y[(long long)c * ldy + ((long long)zo * ny + y0 + o) * nx + x] = P - pn[j - 2][o];
+                        if (c >= l0 && emit && y0 + o < ny) yp[o * nx] = P - pn[j - 2][o];
                         pn[j - 2][o] = N;
                     }
                 }
+                yp += nxy;
             }
 #pragma unroll
             for (int o = 0; o < YB; ++o) {
@@ -688,14 +703,39 @@ __global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __
     gemm_fold_body<T, TM, SIDE>(n, other, X, ldx, H0, H1, G0, G1, C, ldc, bt, ep, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// The FP32 mode product on the tensor cores (one tile a CTA; see fold_tc_body).
+template <int SIDE>
+__global__ void __launch_bounds__(FTC_THREADS, 1) k_fold_tc(int n, int other, const float* __restrict__ X,
+                                                           long long ldx, const float* __restrict__ G0,
+                                                           const float* __restrict__ G1, float* __restrict__ C,
+                                                           long long ldc, Batch2 bt, FdEpi ep) {
+    extern __shared__ __align__(1024) unsigned char ftc_sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    ftc_alloc(&tslot);
+    ftc_mbar_init(&mbar);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t ph = 0;
+    fold_tc_body<SIDE>(n, other, X, ldx, G0, G1, C, ldc, bt, ep, blockIdx.x, blockIdx.y, blockIdx.z, ftc_sm, tslot,
+                       &mbar, &ph);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ftc_dealloc(tslot);
+}
+
 template <typename T, int SIDE>
 int launch_gemm_fold(int n, int other, const T* X, long long ldx, const T* const* HG, T* C, long long ldc, int batch,
                      const Batch2& bt, const FdEpi& ep, cudaStream_t s, const char* tag) {
     if (n <= 0 || other <= 0 || batch <= 0) return ST_OK;
     const int K0 = (n + 1) / 2, K1 = n / 2;
     const int M = SIDE == 0 ? other : K0, N = SIDE == 0 ? K0 : other;
-    // built-in tile choice: the fewest tile rows per SM over both parities
+    // built-in tile choice: the tensor-core tile where fold_tc_default says so (FP32), else the SIMT tile
+    // edge with the fewest tile rows per SM over both parities
     constexpr int kEdge[3] = {16, 32, 64};
+    const bool tc_ok = sizeof(T) == 4;
     int def = 2;
     double best = 1e300;
     for (int c = 2; c >= 0; --c) {
@@ -708,11 +748,25 @@ int launch_gemm_fold(int n, int other, const T* X, long long ldx, const T* const
             def = c;
         }
     }
+    if (tc_ok && fold_tc_default(n, other, batch)) def = 3;
     auto fits = [&](int c) {
+        if (c == 3) return tc_ok && (M + FTC_M - 1) / FTC_M <= 65535 && 2LL * batch <= 65535;
         const int e = kEdge[c];
         return (M + e - 1) / e <= 65535 && 2LL * batch <= 65535;
     };
     auto go = [&](int c) {
+        if constexpr (sizeof(T) == 4) {
+            if (c == 3) {
+                static const bool set = [] {
+                    cudaFuncSetAttribute(k_fold_tc<SIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, FTC_SMEM);
+                    return true;
+                }();
+                (void)set;
+                dim3 grid((N + FTC_N - 1) / FTC_N, (M + FTC_M - 1) / FTC_M, 2 * batch);
+                k_fold_tc<SIDE><<<grid, FTC_THREADS, FTC_SMEM, s>>>(n, other, X, ldx, HG[2], HG[3], C, ldc, bt, ep);
+                return;
+            }
+        }
         const int e = kEdge[c];
         dim3 grid((N + e - 1) / e, (M + e - 1) / e, 2 * batch);
         if (e == 16)
@@ -728,10 +782,10 @@ int launch_gemm_fold(int n, int other, const T* X, long long ldx, const T* const
         if (StTuneSession* ts = st_tune_session(s)) {
             // every variant writes all of C from X and the tables (no aliasing), so the
             // candidates may run on the launch's own operands
-            bool valid[3] = {fits(0), fits(1), fits(2)};
-            double ms[3];
-            ST_TRY(st_tune_measure(s, 3, valid, go, nullptr, ms));
-            c = sttune::pick(ms, 3, def, 0.03);
+            bool valid[4] = {fits(0), fits(1), fits(2), fits(3)};
+            double ms[4];
+            ST_TRY(st_tune_measure(s, 4, valid, go, nullptr, ms));
+            c = sttune::pick(ms, 4, def, 0.03);
             sttune::table().put(key, c);
             ++ts->tuned;
         }
@@ -1453,9 +1507,10 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
             if (p->dim == 2) {
                 k_apply_box_sh<T, 2, 4, 1, 8, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
             } else {
-                // sum-factorised: 32 x-points, 8 x 2 rows in y, 8 planes in z a CTA; 16 time columns
-                constexpr int YB3 = 2, ZB3 = 8, ST3 = 16;
-                const long long b3 = (long long)((nx + 31) / 32) * ((ny + 8 * YB3 - 1) / (8 * YB3)) *
+                // sum-factorised: 30 x-points, 8 x 4 rows in y, 6 planes in z a CTA; 16 time columns
+                // (the fastest of the blockings measured on 63^3 x 128 and 127^3 x 512)
+                constexpr int YB3 = 4, ZB3 = 6, ST3 = 16;
+                const long long b3 = (long long)((nx + 29) / 30) * ((ny + 8 * YB3 - 1) / (8 * YB3)) *
                                      ((nz + ZB3 - 1) / ZB3);
                 const dim3 g3((unsigned)b3, (unsigned)((n_t + ST3 - 1) / ST3));
                 if (b3 > 0x7fffffffLL || g3.y > 65535) return ST_EINVAL;

@@ -15,7 +15,7 @@ namespace sttune {
 
 // Kernel families with more than one valid launch variant for a shape.
 enum Family : int {
-    FOLD = 1,   // fast-diagonalisation mode product: tile edge 16, 32 or 64
+    FOLD = 1,   // fast-diagonalisation mode product: tile edge 16, 32 or 64, or (FP32) the tensor-core tile
     LINE = 2,   // x-line tridiagonal solve: warp per row, or thread per row (64 or 16 steps a load batch)
 };
 
@@ -77,7 +77,8 @@ private:
 inline bool plausible(const Key& k, int choice) {
     if (k.family != FOLD && k.family != LINE) return false;
     if (k.tsize != 4 && k.tsize != 8) return false;
-    return choice >= 0 && choice < 3;
+    const int count = (k.family == FOLD && k.tsize == 4) ? 4 : 3;   // FP32 mode products: a tensor-core variant
+    return choice >= 0 && choice < count;
 }
 
 inline Table& table() {

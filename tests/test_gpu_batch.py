@@ -170,3 +170,34 @@ def test_batch_fills_dense_outputs():
     finally:
         for p in probs:
             p.close()
+
+
+def test_batch_tensor_core_mode_products_match_oracle():
+    """Mixed precision batch whose grids take the tensor-core (3xTF32) tiles for the mode products along their
+    long directions (folded length 64 and more) and the SIMT tiles along the short ones; ragged 2D and 3D."""
+    rng = np.random.default_rng(41)
+    shapes = [(2, [127, 127]), (2, [129, 64]), (3, [131, 9, 8]), (2, [255, 17])]
+    cases = []
+    for i, (dim, ns) in enumerate(shapes):
+        nt = 5
+        nh = int(np.prod(ns))
+        F1, F2 = workloads.gaussian_factors(nh, nt, 2, seed=700 + i)
+        cases.append(dict(dim=dim, n=ns, n_t=nt, kappa=float(10.0 ** rng.uniform(-1, 1)),
+                          F1=np.asfortranarray(F1), F2=np.asfortranarray(F2)))
+    probs = [st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=st.ST_MIXED, tol=1e-10, maxit=300)
+             for c in cases]
+    try:
+        res, bs = st.solve_batch(probs, [c["F1"] for c in cases], [c["F2"] for c in cases])
+        torch.cuda.synchronize()
+        assert bs["grouped"] == len(cases)
+        for i, c in enumerate(cases):
+            V, Y, stats, status = res[i]
+            assert status == st.ST_OK and stats["relres"] <= 1e-10, (i, status, stats)
+            U = dense(V, Y)
+            ref = oracle_solution(c)
+            err = np.linalg.norm(U - ref) / np.linalg.norm(ref)
+            assert err <= 1e-6, (i, err)
+            assert np.max(column_errors(U, ref)) <= 1e-5, i
+    finally:
+        for p in probs:
+            p.close()
