@@ -424,10 +424,14 @@ def bench_batched(args, wl, rank, world, local):
     bad = [i for i, r in enumerate(res) if r[3] != st.ST_OK]
     its = [r[2]["iterations"] for r in res]
     relres = [r[2]["relres"] for r in res]
-    # per-kernel profile of one more batch solve (separate pass after the timed region)
+    # per-kernel profile of one more batch solve (separate pass after the timed region), as one lock-step group:
+    # its launches run one after another on one stream, so each launch's event time is its own (with concurrent
+    # groups an event pair also spans other groups' kernels); the same kernels, tiles and work as the timed solve
     st.profile_begin()
-    st.solve_batch(mixed, F1d, F2d, stream=stream)
+    t0 = time.perf_counter()
+    _, bs1 = st.solve_batch(mixed, F1d, F2d, stream=stream, groups=1)
     torch.cuda.synchronize()
+    wall1 = 1e3 * (time.perf_counter() - t0)
     prof = st.profile_end()
     roof = roofline_of(prof, pk["hbm_gbs"])
     if roof:
@@ -489,8 +493,12 @@ def bench_batched(args, wl, rank, world, local):
                    "parallelism": f"replicas{world}"},
         "solver": {"failed": len(bad), "iterations_p50": float(np.median(its)), "iterations_max": int(max(its)),
                    "relres_max": float(max(relres)), "relres_certified_sample_max": float(max(cert)),
-                   "rounds": bs["rounds"], "grouped_launches": bs["grouped_launches"],
-                   "phase_ms": bs["ms_phase"]},
+                   "rounds": bs["rounds"], "grouped_launches": bs["grouped_launches"], "groups": bs["groups"],
+                   "instance_iterations": int(sum(its)),
+                   "launches_per_instance_iteration": launches / args.steps / max(1, sum(its)),
+                   "phase_ms_summed_over_groups": bs["ms_phase"],
+                   "one_group_profile": {"wall_ms": wall1, "phase_ms": bs1["ms_phase"],
+                                         "phase_share": {k: v / wall1 for k, v in bs1["ms_phase"].items()}}},
         "roofline": roof, "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()},
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
         "comparators": comps,

@@ -146,10 +146,6 @@ struct BI {
 
 constexpr int kNmaq = 2;   // [M q, A q] (heat: A symmetric)
 
-// Tile grid edge of the grouped mode products (every edge sums the folded index
-// in the same order, so it does not change a result).
-constexpr int kFoldEdge = 32;
-
 // The 2 dim mode products of one fast-diagonalisation transform
 // W = coef Q(x) diag(omega) Q(x) X (the launches of st_fd_apply64/32), in order,
 // with the side (0: x direction, 1: y, z) of each.
@@ -231,8 +227,11 @@ void fd_steps(const st_problem* p, FdKind kind, double shift, double coef, const
                 N = (int)J;
             }
             t.ep = ep;
-            t.tc = sizeof(T) == 4 && fold_tc_grouped(t.n) ? 1 : 0;
-            const int ex = t.tc ? FTC_N : kFoldEdge, ey = t.tc ? FTC_M : kFoldEdge;
+            // the single-problem launch's tile choice (so a problem's result does not depend on the path)
+            t.tc = sizeof(T) == 4 && fold_tc_default(t.n, t.other, batch) ? 1 : 0;
+            // FP32 SIMT: the 64 x 64 vector-read tile where both output extents fill it
+            t.tm = sizeof(T) == 4 && std::min(M, N) >= 64 ? 4 : 2;
+            const int ex = t.tc ? FTC_N : 16 * t.tm, ey = t.tc ? FTC_M : 16 * t.tm;
             t.gx = (N + ex - 1) / ex;
             t.gy = (M + ey - 1) / ey;
             t.gz = 2 * batch;
@@ -970,7 +969,7 @@ int solve_batch_impl(int count, st_problem* const* probs, const double* const* F
         L.issue(pa);
         for (int pass = 0; pass < 2; ++pass) {
             pa.elem(tdf[pass]);
-            pa.tn(true, tn_df[pass]);
+            pa.tn(true, tn_df[pass], pass == 0);   // first pass: FP32 on the leading parts
             pa.tn(false, tn_64[pass]);
             pa.nn(true, nn_df[pass]);
             pa.nn(false, nn_64[pass]);

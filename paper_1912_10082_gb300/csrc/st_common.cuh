@@ -255,8 +255,9 @@ int st_tsgemm_nn(int n, int k, int m, double alpha, const double* V, int ldv, co
 // Double-float variants for a basis V stored as (hi, lo) float pairs: FP64-accurate
 // to about 48 bits, computed on the FP32 pipes.
 int st_to_df(int n, int m, const double* X, int ldx, float2* Y, int ldy, cudaStream_t s);
+// hi_only: the FP32 product of the leading parts (first pass of the block Gram-Schmidt).
 int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2* W, int ldw,
-                    double* H, int ldh, double* partial, cudaStream_t s);
+                    double* H, int ldh, double* partial, cudaStream_t s, bool hi_only = false);
 int st_tsgemm_nn_df(int n, int k, int m, double alpha, const float2* V, int ldv, const double* H, int ldh,
                     double beta, double* W, int ldw, cudaStream_t s);
 // W = W * R^{-1} for upper triangular R (m x m, device), in place

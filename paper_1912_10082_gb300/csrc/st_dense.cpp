@@ -245,11 +245,23 @@ void lower_solve(int n, const double* L, int ldl, double* B, int ldb, int nrhs) 
 }
 
 bool lu(int n, double* A, int lda, int* piv) {
+    // lower bandwidth: rows below it are zero in every column (the block upper Hessenberg matrices of
+    // the rational Arnoldi relation have a band of one block).  Partial pivoting picks the pivot within
+    // the band and the multipliers stay in it, so restricting the row loops to the band computes the
+    // same factors in O(n^2 bw) instead of O(n^3)
+    int bw = 0;
+    for (int j = 0; j < n; ++j)
+        for (int i = n - 1; i > j + bw; --i)
+            if (A_(i, j) != 0.0) {
+                bw = i - j;
+                break;
+            }
     bool ok = true;
     for (int j = 0; j < n; ++j) {
+        const int iend = std::min(n, j + bw + 1);
         int pr = j;
         double mx = std::fabs(A_(j, j));
-        for (int i = j + 1; i < n; ++i)
+        for (int i = j + 1; i < iend; ++i)
             if (std::fabs(A_(i, j)) > mx) {
                 mx = std::fabs(A_(i, j));
                 pr = i;
@@ -262,13 +274,13 @@ bool lu(int n, double* A, int lda, int* piv) {
             ok = false;
             continue;
         }
-        for (int i = j + 1; i < n; ++i) A_(i, j) /= d;
+        for (int i = j + 1; i < iend; ++i) A_(i, j) /= d;
         for (int c = j + 1; c < n; ++c) {
             double t = A_(j, c);
             if (t == 0.0) continue;
             double* colc = A + (size_t)c * lda;
             const double* colj = A + (size_t)j * lda;
-            for (int i = j + 1; i < n; ++i) colc[i] -= colj[i] * t;
+            for (int i = j + 1; i < iend; ++i) colc[i] -= colj[i] * t;
         }
     }
     return ok;
@@ -485,10 +497,13 @@ void sym_eig(int n, double* A, int lda, double* w) {
     sort_eig(n, w, A, lda);
 }
 
-// Householder QR of an m x n matrix (m >= n): A <- Q (m x n), R (n x n).
+// Householder QR of an m x n matrix: A <- Q (m x n), R (n x n), A = Q R.  For m < n (more columns
+// than rows) the reflectors stop at column m: Q's first m columns are orthonormal and the rest zero,
+// R's rows from m on are zero (R upper trapezoidal in its first m rows).
 int thin_qr(int m, int n, double* A, int lda, double* R, int ldr) {
+    const int kq = std::min(m, n);
     std::vector<double> taus(n, 0.0);
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < kq; ++j) {
         double* x = &A_(j, j);
         int len = m - j;
         double alpha = 0.0;
@@ -516,14 +531,14 @@ int thin_qr(int m, int n, double* A, int lda, double* R, int ldr) {
         }
     }
     for (int c = 0; c < n; ++c)
-        for (int r = 0; r < n; ++r) R[(size_t)c * ldr + r] = r <= c ? A_(r, c) : 0.0;
+        for (int r = 0; r < n; ++r) R[(size_t)c * ldr + r] = r <= c && r < m ? A_(r, c) : 0.0;
     // form Q in place, backwards
     std::vector<double> Q((size_t)m * n, 0.0);
-    for (int i = 0; i < n; ++i) Q[(size_t)i * m + i] = 1.0;
-    for (int j = n - 1; j >= 0; --j) {
+    for (int i = 0; i < kq; ++i) Q[(size_t)i * m + i] = 1.0;
+    for (int j = kq - 1; j >= 0; --j) {
         if (taus[j] == 0.0) continue;
         int len = m - j;
-        for (int c = j; c < n; ++c) {
+        for (int c = j; c < kq; ++c) {
             double* y = &Q[(size_t)c * m + j];
             double s = y[0];
             for (int i = 1; i < len; ++i) s += A_(j + i, j) * y[i];

@@ -129,6 +129,14 @@ __device__ __forceinline__ void df_madd2(float2& SH, float2& SL, float2 a, float
     SH = S;
 }
 
+// One step of a mode product's sum, rounded once (the same in every tile shape).
+__device__ __forceinline__ float fold_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fold_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T, int TM, int SIDE>
+__device__ __forceinline__ void fold_epilogue(T (&acc)[TM][TM], int M, int N, int m0, int n0, int tx, int ty,
+                                              int par, T* __restrict__ C, long long ldc, const FdEpi& ep);
+
 template <typename T, int TM, int SIDE>
 __device__ __forceinline__ void gemm_fold_body(int n, int other, const T* __restrict__ X, long long ldx,
                                                    const T* __restrict__ H0, const T* __restrict__ H1,
@@ -204,10 +212,101 @@ __device__ __forceinline__ void gemm_fold_body(int n, int other, const T* __rest
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TM; ++j) acc[i][j] += a[i] * bb[j];
+                for (int j = 0; j < TM; ++j) acc[i][j] = fold_fma(a[i], bb[j], acc[i][j]);
         }
         __syncthreads();
     }
+    fold_epilogue<T, TM, SIDE>(acc, M, N, m0, n0, tx, ty, par, C, ldc, ep);
+}
+
+// FP32 tile of 64 x 64 outputs, 4 x 4 a thread, with vector shared-memory reads: the staged operands sit
+// in shared memory with the rows (columns) a thread owns -- ty, ty + 16, ty + 32, ty + 48 -- next to each
+// other, so one 16-byte read feeds four outputs (two reads for sixteen FMAs, where the scalar 4 x 4 tile
+// issues eight).  Every output is the same FMA chain over the folded index in the same order as in
+// gemm_fold_body, so the two tiles give the same bits.
+template <int SIDE>
+__device__ __forceinline__ void fold32_v4_body(int n, int other, const float* __restrict__ X, long long ldx,
+                                               const float* __restrict__ H0, const float* __restrict__ H1,
+                                               const float* __restrict__ G0, const float* __restrict__ G1,
+                                               float* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep, int bx,
+                                               int by, int bz) {
+    constexpr int BM = 64, BN = 64, BK = 64, LD = 68;   // row stride: 16-byte aligned, staging stores 4-way at most
+    __shared__ __align__(16) float As[BK][LD];
+    __shared__ __align__(16) float Bs[BK][LD];
+    const int par = bz & 1;
+    const int zb = bz >> 1;
+    const int z1 = zb % bt.nb1, z2 = zb / bt.nb1;
+    const int K = par ? n / 2 : (n + 1) / 2;
+    const int mid = (n & 1) ? (n - 1) / 2 : -1;
+    const float sgn = par ? -1.0f : 1.0f;
+    const int M = SIDE == 0 ? other : K;
+    const int N = SIDE == 0 ? K : other;
+    const int m0 = by * BM, n0 = bx * BN;
+    if (m0 >= M || n0 >= N) return;
+    if (SIDE == 0) {
+        X += (size_t)z1 * bt.sA1 + (size_t)z2 * bt.sA2;
+    } else {
+        X += (size_t)z1 * bt.sB1 + (size_t)z2 * bt.sB2;
+    }
+    C += (size_t)z1 * bt.sC1 + (size_t)z2 * bt.sC2;
+    const float* Hp = par ? H1 : H0;
+    const float* Gp = par ? G1 : G0;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    auto pos = [](int r) { return (r & 15) * 4 + (r >> 4); };   // row r of the tile -> its staged slot
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int idx = tid; idx < BM * BK; idx += 256) {
+            const int mm = idx / BK, kk = idx % BK;
+            const int gm = m0 + mm, gk = k0 + kk;
+            float v = 0.0f;
+            if (gm < M && gk < K) {
+                if (SIDE == 0) {
+                    const float* row = X + (size_t)gm * ldx;
+                    v = gk == mid ? row[gk] : row[gk] + sgn * row[n - 1 - gk];
+                } else {
+                    v = Gp[(size_t)gm * K + gk];
+                }
+            }
+            As[kk][pos(mm)] = v;
+        }
+        for (int idx = tid; idx < BK * BN; idx += 256) {
+            const int kk = idx / BN, nn = idx % BN;
+            const int gk = k0 + kk, gn = n0 + nn;
+            float v = 0.0f;
+            if (gk < K && gn < N) {
+                if (SIDE == 0) {
+                    v = Hp[(size_t)gk * K + gn];
+                } else {
+                    v = gk == mid ? X[(size_t)gk * ldx + gn]
+                                  : X[(size_t)gk * ldx + gn] + sgn * X[(size_t)(n - 1 - gk) * ldx + gn];
+                }
+            }
+            Bs[kk][pos(nn)] = v;
+        }
+        __syncthreads();
+        const int kt = min(BK, K - k0);   // beyond it both operands are zero: the chain stops where K does
+        for (int kk = 0; kk < kt; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[kk][4 * ty]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][4 * tx]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    fold_epilogue<float, 4, SIDE>(acc, M, N, m0, n0, tx, ty, par, C, ldc, ep);
+}
+
+template <typename T, int TM, int SIDE>
+__device__ __forceinline__ void fold_epilogue(T (&acc)[TM][TM], int M, int N, int m0, int n0, int tx, int ty,
+                                              int par, T* __restrict__ C, long long ldc, const FdEpi& ep) {
     const float fcoef = (float)ep.coef;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -235,6 +334,18 @@ __device__ __forceinline__ void gemm_fold_body(int n, int other, const T* __rest
             }
         }
     }
+}
+
+// The mode product's tile body: the vector-read FP32 tile for 4 x 4 outputs a thread, else gemm_fold_body.
+template <typename T, int TM, int SIDE>
+__device__ __forceinline__ void fold_tile(int n, int other, const T* __restrict__ X, long long ldx,
+                                          const T* __restrict__ H0, const T* __restrict__ H1,
+                                          const T* __restrict__ G0, const T* __restrict__ G1, T* __restrict__ C,
+                                          long long ldc, Batch2 bt, FdEpi ep, int bx, int by, int bz) {
+    if constexpr (sizeof(T) == 4 && TM == 4)
+        fold32_v4_body<SIDE>(n, other, X, ldx, H0, H1, G0, G1, C, ldc, bt, ep, bx, by, bz);
+    else
+        gemm_fold_body<T, TM, SIDE>(n, other, X, ldx, H0, H1, G0, G1, C, ldc, bt, ep, bx, by, bz);
 }
 
 template <typename T, int DIM, int YB, int ZB>
@@ -405,7 +516,10 @@ __device__ __forceinline__ void to_df_body(int n, int m, const double* __restric
     Y[(size_t)j * ldy + i] = df_split(X[(size_t)j * ldx + i]);
 }
 
-template <int MAXM>
+// HI = true: the FP32 product of the leading parts only (V.hi^T W.hi, FP32 sums per lane, the lanes' sums
+// combined by two-sum): the first pass of the mixed-precision block Gram-Schmidt, whose coefficients only
+// need FP32 accuracy because the double-float second pass removes what the first one leaves.
+template <int MAXM, bool HI = false>
 __device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int rows,
                                                                  const float2* __restrict__ V, long long ldv,
                                                                  const float2* __restrict__ W, long long ldw,
@@ -446,8 +560,14 @@ __device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int r
             for (int u = 0; u < TS_UNROLL; ++u) {
                 int rr = min(base + 32 * u, rows - 1);
 #pragma unroll
-                for (int q = 0; q < MP; ++q)
-                    if (q < np) df_madd2(SH[q], SL[q], x[u], Ws[q * rows + rr]);
+                for (int q = 0; q < MP; ++q) {
+                    if (q >= np) continue;
+                    const float4 b = Ws[q * rows + rr];
+                    if constexpr (HI)
+                        SH[q] = __ffma2_rn(make_float2(x[u].x, x[u].x), make_float2(b.x, b.y), SH[q]);
+                    else
+                        df_madd2(SH[q], SL[q], x[u], b);
+                }
             }
         }
 #pragma unroll
@@ -645,10 +765,14 @@ __device__ __forceinline__ void axpby_body(int n, int m, double a, const double*
 constexpr int FTC_M = 128, FTC_N = 128, FTC_KC = 32, FTC_THREADS = 256;
 
 // Built-in choice of the FP32 mode product's tile, the same for single and
-// batched solves (so a problem's result does not depend on the path): the
-// tensor-core tile when the folded length is at least FTC_MIN_K and one launch
-// has at least FTC_MIN_TILES of its 128 x 128 tiles, else the SIMT tiles.
-constexpr int FTC_MIN_K = 32, FTC_MIN_TILES = 64;
+// batched solves (so a problem's result does not depend on the path; in a
+// batch of 2-column problems, grouping the tiles of many problems was measured
+// no faster on the tensor cores, so the choice stays per problem): the tensor-core tile when
+// the folded length fills the tile's 128 modes (FTC_MIN_K; at 64 modes, grids
+// of 127 points a side, half of each MMA is padding and the SIMT tiles were
+// faster in the 127^3 solve) and one launch has at least FTC_MIN_TILES of its
+// 128 x 128 tiles, else the SIMT tiles.
+constexpr int FTC_MIN_K = 128, FTC_MIN_TILES = 64;
 __host__ __device__ inline bool fold_tc_default(int n, int other, int batch) {
     const int K0 = (n + 1) / 2;
     if (K0 < FTC_MIN_K) return false;
@@ -656,10 +780,6 @@ __host__ __device__ inline bool fold_tc_default(int n, int other, int batch) {
     const long long tiles = (long long)((other + 127) / 128) * ((K0 + 127) / 128) * 2 * batch;
     return tiles >= FTC_MIN_TILES;
 }
-// The batched solver's choice, per problem and independent of the other problems of the batch (so a
-// problem's batched result does not depend on its batch-mates): the tensor-core tile from a folded
-// length of 64 (grids of 127+ points a side), where a grouped launch holds tiles of many problems.
-__host__ __device__ inline bool fold_tc_grouped(int n) { return (n + 1) / 2 >= 64; }
 constexpr int FTC_PLANE = FTC_M * FTC_KC * 4;                  // 16 KB: one operand plane of a K chunk
 constexpr int FTC_SMEM = 4 * FTC_PLANE > FTC_M * (FTC_N + 1) * 4 ? 4 * FTC_PLANE : FTC_M * (FTC_N + 1) * 4;
 constexpr int FTC_TMEM_COLS = 128;

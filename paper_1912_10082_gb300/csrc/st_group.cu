@@ -36,7 +36,7 @@ __device__ __forceinline__ void g_load(Task& dst, const Task* src, int tid, int 
 }
 
 template <typename T, int TM, int SIDE>
-__global__ void __launch_bounds__(256) kg_fold(const stg::FoldTask* tasks, const int* prefix, int ntasks) {
+__global__ void __launch_bounds__(256, 3) kg_fold(const stg::FoldTask* tasks, const int* prefix, int ntasks) {
     __shared__ stg::FoldTask tk;
     const int total = prefix[ntasks];
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) kg_fold(const stg::FoldTask* tasks, const
         const int bx = local % tk.gx;
         local /= tk.gx;
         const int by = local % tk.gy, bz = local / tk.gy;
-        gemm_fold_body<T, TM, SIDE>(tk.n, tk.other, (const T*)tk.X, tk.ldx, (const T*)tk.HG[0], (const T*)tk.HG[1],
+        fold_tile<T, TM, SIDE>(tk.n, tk.other, (const T*)tk.X, tk.ldx, (const T*)tk.HG[0], (const T*)tk.HG[1],
                                     (const T*)tk.HG[2], (const T*)tk.HG[3], (T*)tk.C, tk.ldc, tk.bt, tk.ep, bx, by,
                                     bz);
     }
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) kg_stencil(const stg::StencilTask* tasks,
     }
 }
 
-template <int MAXM, bool DF>
+template <int MAXM, bool DF, bool HI = false>
 __global__ void __launch_bounds__(TS_THREADS) kg_tn_partial(const stg::TnTask* tasks, const int* prefix, int ntasks) {
     extern __shared__ double smem[];
     __shared__ stg::TnTask tk;
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(TS_THREADS) kg_tn_partial(const stg::TnTask* t
         const int local = t - prefix[i];
         const int bx = local % tk.nch, by = local / tk.nch;
         if constexpr (DF)
-            ts_tn_df_partial_body<MAXM>(tk.n, tk.k, tk.m, tk.rows, (const float2*)tk.V, tk.ldv, (const float2*)tk.W,
+            ts_tn_df_partial_body<MAXM, HI>(tk.n, tk.k, tk.m, tk.rows, (const float2*)tk.V, tk.ldv, (const float2*)tk.W,
                                         tk.ldw, (float2*)tk.part, smem, bx, by);
         else
             ts_tn_partial_body<MAXM>(tk.n, tk.k, tk.m, tk.rows, (const double*)tk.V, tk.ldv, (const double*)tk.W,
@@ -292,10 +292,14 @@ size_t GroupPhase::put_tasks(const std::vector<Task>& t, const std::vector<int>&
 void GroupPhase::fold(int tsize, int side, const std::vector<FoldTask>& all) {
     if (all.empty()) return;
     // tensor-core tasks (FP32) in a launch of their own
-    std::vector<FoldTask> t, tct;
-    for (const FoldTask& k : all) (tsize == 4 && k.tc ? tct : t).push_back(k);
+    std::vector<FoldTask> t2, t4, tct;
+    for (const FoldTask& k : all) (tsize == 4 && k.tc ? tct : (tsize == 4 && k.tm == 4 ? t4 : t2)).push_back(k);
     if (!tct.empty()) fold_tc(side, tct);
-    if (t.empty()) return;
+    if (!t4.empty()) fold_simt(tsize, side, 4, t4);
+    if (!t2.empty()) fold_simt(tsize, side, 2, t2);
+}
+
+void GroupPhase::fold_simt(int tsize, int side, int tm, const std::vector<FoldTask>& t) {
     std::vector<int> tiles(t.size());
     for (size_t i = 0; i < t.size(); ++i) tiles[i] = t[i].gx * t[i].gy * t[i].gz;
     int total = 0;
@@ -314,9 +318,14 @@ void GroupPhase::fold(int tsize, int side, const std::vector<FoldTask>& all) {
         const FoldTask* T = (const FoldTask*)(d + off);
         const int* P = (const int*)(d + poff);
         const int g = grid_for(total);
-        // edge-32 tiles (2 x 2 outputs a thread): every tile edge sums the folded index in the
-        // same order, so the edge does not change a result
-        if (tsize == 4) {
+        // every tile shape sums the folded index in the same order with the same rounding, so the
+        // shape does not change a result
+        if (tsize == 4 && tm == 4) {
+            if (side == 0)
+                kg_fold<float, 4, 0><<<g, 256, 0, s>>>(T, P, nt);
+            else
+                kg_fold<float, 4, 1><<<g, 256, 0, s>>>(T, P, nt);
+        } else if (tsize == 4) {
             if (side == 0)
                 kg_fold<float, 2, 0><<<g, 256, 0, s>>>(T, P, nt);
             else
@@ -389,7 +398,8 @@ void GroupPhase::stencil(int dim, const std::vector<StencilTask>& t) {
     }, "g_stencil64", bytes, flops});
 }
 
-void GroupPhase::tn(bool df, const std::vector<TnTask>& t) {
+void GroupPhase::tn(bool df, const std::vector<TnTask>& t, bool hi) {
+    hi = hi && df;
     if (t.empty()) return;
     const int cg = df ? TS_CG_DF : TS_CG;
     std::vector<int> tiles(t.size()), rtiles(t.size());
@@ -421,18 +431,20 @@ void GroupPhase::tn(bool df, const std::vector<TnTask>& t) {
             const int* P = (const int*)(d + poff);
             with_maxm(maxm, [&](auto mm) {
                 constexpr int MM = decltype(mm)::value;
-                auto kern = df ? kg_tn_partial<MM, true> : kg_tn_partial<MM, false>;
-                static bool set = false;   // per instantiation: up to 64 KB of staged W
-                if (!set) {
+                auto kern = hi ? kg_tn_partial<MM, true, true> : df ? kg_tn_partial<MM, true> : kg_tn_partial<MM, false>;
+                static const bool set = [] {   // per instantiation: up to 64 KB of staged W
+                    cudaFuncSetAttribute(kg_tn_partial<MM, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8192 * 8);
                     cudaFuncSetAttribute(kg_tn_partial<MM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8192 * 8);
                     cudaFuncSetAttribute(kg_tn_partial<MM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8192 * 8);
-                    set = true;
-                }
+                    return true;
+                }();
+                (void)set;
                 kern<<<grid_for(total), TS_THREADS, smem, s>>>(T, P, nt);
             });
-        }, df ? "g_tn_df" : "g_tn64", bytes, flops, rtotal == 0});
+        }, hi ? "g_tn_hi" : df ? "g_tn_df" : "g_tn64", bytes, flops, rtotal == 0});
     if (rtotal > 0)
         pend_.push_back({[=](const char* d) {
             const TnTask* T = (const TnTask*)(d + roff);

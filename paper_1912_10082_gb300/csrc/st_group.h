@@ -30,7 +30,8 @@ struct FoldTask {
     Batch2 bt;
     FdEpi ep;
     int gx, gy, gz;   // tiles: gx * gy * gz (gz = 2 * batch: both parities)
-    int tc;           // FP32 only: 1 = tensor-core tiles (128 x 128), 0 = SIMT tiles (32 x 32)
+    int tc;           // FP32 only: 1 = tensor-core tiles (128 x 128), 0 = SIMT tiles
+    int tm;           // SIMT tiles: 16 tm x 16 tm outputs (tm 2, or 4 for the FP32 vector-read tile)
 };
 
 // Box-stencil product O1 = S1 X (+ beta O1), O2 = S2 X (k_stencil_box's tile body, FP64).
@@ -131,8 +132,10 @@ class GroupPhase {
     // Each add_* queues one grouped launch (skipped when it has no task).
     void fold(int tsize, int side, const std::vector<FoldTask>& t);   // tsize 4 (float) or 8 (double)
     void fold_tc(int side, const std::vector<FoldTask>& t);           // FP32 tasks on the tensor cores
+    void fold_simt(int tsize, int side, int tm, const std::vector<FoldTask>& t);
     void stencil(int dim, const std::vector<StencilTask>& t);
-    void tn(bool df, const std::vector<TnTask>& t);                  // partials and their sums: two launches
+    // partials and their sums: two launches; hi: the FP32 product of the double-float leading parts
+    void tn(bool df, const std::vector<TnTask>& t, bool hi = false);
     void nn(bool df, const std::vector<NnTask>& t);
     void trsm(const std::vector<TrsmTask>& t);
     void chol(const std::vector<CholTask>& t);

@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(256) k_gemm_fold(int n, int other, const T* __
                                                    const T* __restrict__ H0, const T* __restrict__ H1,
                                                    const T* __restrict__ G0, const T* __restrict__ G1,
                                                    T* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep) {
-    gemm_fold_body<T, TM, SIDE>(n, other, X, ldx, H0, H1, G0, G1, C, ldc, bt, ep, blockIdx.x, blockIdx.y, blockIdx.z);
+    fold_tile<T, TM, SIDE>(n, other, X, ldx, H0, H1, G0, G1, C, ldc, bt, ep, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // The FP32 mode product on the tensor cores (one tile a CTA; see fold_tc_body).
@@ -887,13 +887,13 @@ __global__ void k_to_df(int n, int m, const double* __restrict__ X, long long ld
     to_df_body(n, m, X, ldx, Y, ldy, blockIdx.x);
 }
 
-template <int MAXM>
+template <int MAXM, bool HI>
 __global__ void __launch_bounds__(TS_THREADS) k_ts_tn_df_partial(int n, int k, int m, int rows,
                                                                  const float2* __restrict__ V, long long ldv,
                                                                  const float2* __restrict__ W, long long ldw,
                                                                  float2* __restrict__ part) {
     extern __shared__ double sm[];
-    ts_tn_df_partial_body<MAXM>(n, k, m, rows, V, ldv, W, ldw, part, sm, blockIdx.x, blockIdx.y);
+    ts_tn_df_partial_body<MAXM, HI>(n, k, m, rows, V, ldv, W, ldw, part, sm, blockIdx.x, blockIdx.y);
 }
 
 // H = sum over chunks of the (hi, lo) partials, each folded to FP64 first:
@@ -1977,13 +1977,17 @@ template <int MAXM> struct LaunchTn {
 };
 template <int MAXM> struct LaunchTnDf {
     static void go(dim3 grid, size_t smem, cudaStream_t s, int n, int k, int m, int rows, const float2* V, int ldv,
-                   const float2* W, int ldw, float2* part) {
+                   const float2* W, int ldw, float2* part, bool hi) {
         static const bool set = [] {
-            cudaFuncSetAttribute(k_ts_tn_df_partial<MAXM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
+            cudaFuncSetAttribute(k_ts_tn_df_partial<MAXM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
+            cudaFuncSetAttribute(k_ts_tn_df_partial<MAXM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 8);
             return true;
         }();
         (void)set;
-        k_ts_tn_df_partial<MAXM><<<grid, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, part);
+        if (hi)
+            k_ts_tn_df_partial<MAXM, true><<<grid, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, part);
+        else
+            k_ts_tn_df_partial<MAXM, false><<<grid, TS_THREADS, smem, s>>>(n, k, m, rows, V, ldv, W, ldw, part);
     }
 };
 template <int MAXM> struct LaunchNn {
@@ -2059,12 +2063,13 @@ int st_to_df(int n, int m, const double* X, int ldx, float2* Y, int ldy, cudaStr
 }
 
 int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2* W, int ldw, double* H, int ldh,
-                    double* partial, cudaStream_t s) {
+                    double* partial, cudaStream_t s, bool hi_only) {
     if (k <= 0 || m <= 0) return ST_OK;
     if (m > kMaxCols) {   // wider blocks in chunks of kMaxCols columns
         for (int j0 = 0; j0 < m; j0 += kMaxCols) {
             int mm = m - j0 < kMaxCols ? m - j0 : kMaxCols;
-            ST_TRY(st_tsgemm_tn_df(n, k, mm, V, ldv, W + (size_t)j0 * ldw, ldw, H + (size_t)j0 * ldh, ldh, partial, s));
+            ST_TRY(st_tsgemm_tn_df(n, k, mm, V, ldv, W + (size_t)j0 * ldw, ldw, H + (size_t)j0 * ldh, ldh, partial, s,
+                                   hi_only));
         }
         return ST_OK;
     }
@@ -2078,8 +2083,9 @@ int st_tsgemm_tn_df(int n, int k, int m, const float2* V, int ldv, const float2*
     dim3 grid(nch, (k + TS_CG_DF - 1) / TS_CG_DF);
     if (grid.y > 65535) return ST_EINVAL;
     float2* part2 = reinterpret_cast<float2*>(partial);   // (hi, lo) pairs in the doubles' room
-    st_prof_begin(s, "ts_tn_df", 8.0 * (double)n * (k + m) + 16.0 * (double)nch * k * m, 2.0 * (double)n * k * m);
-    dispatch_m<LaunchTnDf>(m, grid, smem, s, n, k, m, rows, V, ldv, W, ldw, part2);
+    st_prof_begin(s, hi_only ? "ts_tn_hi" : "ts_tn_df", 8.0 * (double)n * (k + m) + 16.0 * (double)nch * k * m,
+                  2.0 * (double)n * k * m);
+    dispatch_m<LaunchTnDf>(m, grid, smem, s, n, k, m, rows, V, ldv, W, ldw, part2, hi_only);
     ST_LAUNCH_CHECK();
     k_ts_reduce_df<<<(k * m + 7) / 8, 256, 0, s>>>(nch, k, m, part2, H, ldh);
     st_prof_end(s);

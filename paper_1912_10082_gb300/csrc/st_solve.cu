@@ -1130,7 +1130,10 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
         double* W = p->V + (size_t)k * n;
         ST_TRY(resolvent(s, p->V + (size_t)lo * n, n, MV + (size_t)lo * n, n, pl, W, n));
         // each pass is one product [V, W]^T W: its first k rows are the Gram-Schmidt
-        // coefficients, its last pl rows the Gram matrix of W before the update
+        // coefficients, its last pl rows the Gram matrix of W before the update.  Mixed
+        // precision: the first pass in FP32 on the leading parts, the second in double-float
+        // (the update W - V h of both passes in double-float, so W = V (h0 + h1) + W' holds
+        // to double-float accuracy whatever the accuracy of h0)
         const int kk = k + pl;
         double* dh[2];
         for (int pass = 0; pass < 2; ++pass) {
@@ -1139,7 +1142,8 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
                 ST_TRY(st_to_df(n, pl, W, n, p->Vdf + (size_t)k * n, n, c.s));
                 double* part;
                 ST_TRY(st_slot(p, S_PART, sizeof(double) * st_tsgemm_partial_elems(n, kk, pl), (void**)&part));
-                ST_TRY(st_tsgemm_tn_df(n, kk, pl, p->Vdf, n, p->Vdf + (size_t)k * n, n, dh[pass], kk, part, c.s));
+                ST_TRY(st_tsgemm_tn_df(n, kk, pl, p->Vdf, n, p->Vdf + (size_t)k * n, n, dh[pass], kk, part, c.s,
+                                       pass == 0));
             } else {
                 ST_TRY(ts_tn_dev(c, kk, pl, p->V, n, W, n, dh[pass], kk));
             }

@@ -72,16 +72,39 @@ int main() {
                     hostpar::threads_for((double)n * n * n / 3.0), (int)same, e1 / na, e2);
         bad += !(same && acc);
     }
-    // LU with partial pivoting (the convection-diffusion projected recurrence): A X = B and A^T X = B
-    for (int n : {7, 64, 301}) {
+    // LU with partial pivoting (the convection-diffusion projected recurrence, and the block upper
+    // Hessenberg matrix of the residual formula: lower bandwidth 4): A X = B and A^T X = B; the banded
+    // matrices also against an LU whose row loops run over every row (the same factors, value for value)
+    for (int band : {-1, 4}) for (int n : {7, 64, 301}) {
         std::mt19937 g(100 + n);
         std::normal_distribution<double> nd;
         std::vector<double> A((size_t)n * n), B((size_t)n * 3);
         for (auto& x : A) x = nd(g);
         for (auto& x : B) x = nd(g);
+        if (band >= 0)
+            for (int j = 0; j < n; ++j)
+                for (int i = j + band + 1; i < n; ++i) A[(size_t)j * n + i] = 0.0;
         std::vector<double> F = A, X = B, Xt = B;
         std::vector<int> piv(n);
         const bool ok = dense::lu(n, F.data(), n, piv.data());
+        if (band >= 0) {
+            std::vector<double> G = A;
+            std::vector<int> pg(n);
+            for (int j = 0; j < n; ++j) {
+                int pr = j;
+                for (int i = j + 1; i < n; ++i)
+                    if (std::fabs(G[(size_t)j * n + i]) > std::fabs(G[(size_t)j * n + pr])) pr = i;
+                pg[j] = pr;
+                for (int c = 0; c < n; ++c) std::swap(G[(size_t)c * n + j], G[(size_t)c * n + pr]);
+                for (int i = j + 1; i < n; ++i) G[(size_t)j * n + i] /= G[(size_t)j * n + j];
+                for (int c = j + 1; c < n; ++c)
+                    for (int i = j + 1; i < n; ++i) G[(size_t)c * n + i] -= G[(size_t)j * n + i] * G[(size_t)c * n + j];
+            }
+            bool same = pg == piv;
+            for (size_t q = 0; q < G.size(); ++q) same = same && G[q] == F[q];
+            std::printf("lu band=%d n=%d same_as_full=%d\n", band, n, (int)same);
+            bad += !same;
+        }
         dense::lu_solve(n, F.data(), n, piv.data(), X.data(), n, 3);
         const bool okt = dense::lu_solve_transpose(n, F.data(), n, piv.data(), Xt.data(), n, 3);
         double r = 0, rt = 0, na = 0, nx = 0, nxt = 0;
@@ -99,7 +122,8 @@ int main() {
             }
         for (double x : A) na = std::max(na, std::fabs(x));
         const bool acc = ok && okt && r <= 1e-13 * n * na * nx && rt <= 1e-13 * n * na * nxt;
-        std::printf("lu n=%d resid=%.2e resid_T=%.2e %s\n", n, r / (na * nx), rt / (na * nxt), acc ? "ok" : "BAD");
+        std::printf("lu band=%d n=%d resid=%.2e resid_T=%.2e %s\n", band, n, r / (na * nx), rt / (na * nxt),
+                    acc ? "ok" : "BAD");
         bad += !acc;
     }
     {
@@ -178,6 +202,42 @@ int main() {
         const bool ok = orth <= 1e-14 && rec <= 1e-13 && low == 0.0 && er <= 1e-13 * ns * ne && eo <= 1e-13;
         std::printf("thin_qr orth=%.2e rec=%.2e lower=%.1e sym_eig resid=%.2e orth=%.2e %s\n", orth, rec, low,
                     er / ns, eo, ok ? "ok" : "BAD");
+        bad += !ok;
+    }
+    // thin QR of a wide matrix (a time factor F2 with fewer rows than columns): A = Q R, the first m
+    // columns of Q orthonormal, the others zero, R zero from row m on; the arrays are sized exactly and
+    // surrounded by guard values that must stay untouched
+    {
+        const int m = 3, n = 16, guard = 64;
+        std::mt19937 g(21);
+        std::normal_distribution<double> nd;
+        std::vector<double> A((size_t)m * n), Qb((size_t)m * n + 2 * guard, 7.0), Rb((size_t)n * n + 2 * guard, 7.0);
+        for (auto& x : A) x = nd(g);
+        double* Q = Qb.data() + guard;
+        double* R = Rb.data() + guard;
+        std::memcpy(Q, A.data(), sizeof(double) * m * n);
+        dense::thin_qr(m, n, Q, m, R, n);
+        bool guards = true;
+        for (int i = 0; i < guard; ++i)
+            guards = guards && Qb[i] == 7.0 && Qb[guard + (size_t)m * n + i] == 7.0 && Rb[i] == 7.0 &&
+                     Rb[guard + (size_t)n * n + i] == 7.0;
+        double orth = 0, rec = 0, zero = 0;
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) {
+                double qq = 0;
+                for (int r = 0; r < m; ++r) qq += Q[(size_t)a * m + r] * Q[(size_t)b * m + r];
+                orth = std::max(orth, std::fabs(qq - (a == b && a < m ? 1.0 : 0.0)));
+                if (a >= m || a > b) zero = std::max(zero, std::fabs(R[(size_t)b * n + a]));
+            }
+        for (int c = 0; c < n; ++c)
+            for (int r = 0; r < m; ++r) {
+                double acc = 0;
+                for (int k = 0; k < n; ++k) acc += Q[(size_t)k * m + r] * R[(size_t)c * n + k];
+                rec = std::max(rec, std::fabs(acc - A[(size_t)c * m + r]));
+            }
+        const bool ok = guards && orth <= 1e-14 && rec <= 1e-13 && zero == 0.0;
+        std::printf("thin_qr wide guards=%d orth=%.2e rec=%.2e zero=%.1e %s\n", (int)guards, orth, rec, zero,
+                    ok ? "ok" : "BAD");
         bad += !ok;
     }
     // one-sided Jacobi SVD (rank compression of F): graded singular values 1 .. 1e-14 between random

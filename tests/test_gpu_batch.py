@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import paper_1912_10082_gb300 as st
-from oracle import fem, kron, timefe
+from oracle import fem, kron, residual, timefe
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -172,16 +172,18 @@ def test_batch_fills_dense_outputs():
             p.close()
 
 
+
 def test_batch_tensor_core_mode_products_match_oracle():
-    """Mixed precision batch whose grids take the tensor-core (3xTF32) tiles for the mode products along their
-    long directions (folded length 64 and more) and the SIMT tiles along the short ones; ragged 2D and 3D."""
+    """Mixed precision batch of 16-column problems whose long directions (folded length 128 and more, 64+ tiles
+    a launch) take the tensor-core (3xTF32) tiles for the mode products, beside a problem that stays on the SIMT
+    tiles; the same numbers as st_solve on each problem, and the oracle's direct solve."""
     rng = np.random.default_rng(41)
-    shapes = [(2, [127, 127]), (2, [129, 64]), (3, [131, 9, 8]), (2, [255, 17])]
+    shapes = [(2, [255, 255]), (2, [257, 131]), (3, [255, 20, 8]), (2, [63, 63])]
     cases = []
     for i, (dim, ns) in enumerate(shapes):
-        nt = 5
+        nt = 16   # rank 16 loads keep 16-column blocks
         nh = int(np.prod(ns))
-        F1, F2 = workloads.gaussian_factors(nh, nt, 2, seed=700 + i)
+        F1, F2 = workloads.gaussian_factors(nh, nt, 16, seed=700 + i)
         cases.append(dict(dim=dim, n=ns, n_t=nt, kappa=float(10.0 ** rng.uniform(-1, 1)),
                           F1=np.asfortranarray(F1), F2=np.asfortranarray(F2)))
     probs = [st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=st.ST_MIXED, tol=1e-10, maxit=300)
@@ -193,11 +195,54 @@ def test_batch_tensor_core_mode_products_match_oracle():
         for i, c in enumerate(cases):
             V, Y, stats, status = res[i]
             assert status == st.ST_OK and stats["relres"] <= 1e-10, (i, status, stats)
+            with st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=st.ST_MIXED, tol=1e-10,
+                            maxit=300) as twin:
+                V1, Y1, s1, _ = twin.solve(c["F1"], c["F2"])
+                torch.cuda.synchronize()
+                assert s1["iterations"] == stats["iterations"] and torch.equal(V1, V) and torch.equal(Y1, Y), i
             U = dense(V, Y)
-            ref = oracle_solution(c)
+            M, A = fem.tensor_operators(c["dim"], c["n"], kappa=c["kappa"])
+            D, C = timefe.time_matrices(c["n_t"], 1.0)
+            ref = kron.forward_substitution(M, A, D, C, c["F1"] @ c["F2"].T)
             err = np.linalg.norm(U - ref) / np.linalg.norm(ref)
             assert err <= 1e-6, (i, err)
             assert np.max(column_errors(U, ref)) <= 1e-5, i
+    finally:
+        for p in probs:
+            p.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(st.ST_MIXED, 1e-9), (st.ST_FP64, 1e-10)])
+def test_batch_larger_grids_match_single_solves(prec, tol):
+    """Grids whose mode products fill the 64 x 64 vector-read FP32 tiles of the grouped launches (the single
+    solve picks its own tile shapes): the same basis and coefficients bit for bit, and the oracle's FP64 residual
+    of the batched solution within the tolerance."""
+    shapes = [(2, [127, 127]), (2, [200, 70]), (3, [70, 66, 9]), (2, [255, 64])]
+    cases = []
+    for i, (dim, ns) in enumerate(shapes):
+        nt = [24, 13, 6, 9][i]
+        F1, F2 = workloads.gaussian_factors(int(np.prod(ns)), nt, 2, seed=800 + i)
+        cases.append(dict(dim=dim, n=ns, n_t=nt, kappa=[0.3, 1.0, 3.0, 0.7][i],
+                          F1=np.asfortranarray(F1), F2=np.asfortranarray(F2)))
+    probs = [st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=prec, tol=tol, maxit=300)
+             for c in cases]
+    try:
+        res, bs = st.solve_batch(probs, [c["F1"] for c in cases], [c["F2"] for c in cases])
+        torch.cuda.synchronize()
+        assert bs["grouped"] == len(cases)
+        for i, c in enumerate(cases):
+            V, Y, stats, status = res[i]
+            assert status == st.ST_OK, (i, status)
+            with st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=prec, tol=tol,
+                            maxit=300) as twin:
+                V1, Y1, s1, _ = twin.solve(c["F1"], c["F2"])
+                torch.cuda.synchronize()
+                assert s1["iterations"] == stats["iterations"], i
+                assert torch.equal(V1, V) and torch.equal(Y1, Y), i
+            M, A = fem.tensor_operators(c["dim"], c["n"], kappa=c["kappa"])
+            D, C = timefe.time_matrices(c["n_t"], 1.0)
+            true_res = residual.relres_lowrank(M, A, D, C, V.cpu().numpy(), Y.cpu().numpy(), c["F1"], c["F2"])
+            assert true_res <= 1.01 * tol, (i, true_res)
     finally:
         for p in probs:
             p.close()

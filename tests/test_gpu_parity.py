@@ -7,6 +7,7 @@ mixed solves to 1e-6 (the stated targets), run at tighter residual tolerances.
 """
 
 import numpy as np
+import scipy.sparse.linalg as spla
 import pytest
 import torch
 
@@ -141,6 +142,19 @@ def test_shift_solve_matches_sparse_lu(dim, n, prec, tol):
         with st.Problem(dim, n, 4, 1.0, kappa=0.8) as prob:
             out = host(prob.shift_solve(s, dev(X), precision=prec))
         assert relerr(out, ref) <= tol, (s, relerr(out, ref))
+
+
+@pytest.mark.parametrize("dim,n", [(2, (255, 255)), (2, (257, 131)), (3, (255, 7, 6))])
+def test_shift_solve_many_columns_tensor_core_tiles(dim, n):
+    """64 columns: the FP32 mode products along the 255+ point directions take the tensor-core (3xTF32) tiles,
+    the others the SIMT tiles; mixed precision (FP32 transform, FP64 refinement) against a sparse LU solve."""
+    M, A = ops(dim, n, kappa=0.8)
+    X = np.random.default_rng(5).standard_normal((M.shape[0], 64))
+    for s in (3.0, 1e4):
+        ref = spla.splu((A + s * M).tocsc()).solve(M @ X)
+        with st.Problem(dim, n, 4, 1.0, kappa=0.8) as prob:
+            out = host(prob.shift_solve(s, dev(X), precision=st.ST_MIXED))
+        assert relerr(out, ref) <= 1e-10, (s, relerr(out, ref))
 
 
 @pytest.mark.parametrize("dim,n,eps", [(1, 31, 0.05), (2, (40, 21), 0.01), (2, 15, 0.5), (3, (33, 9, 5), 0.05)])
@@ -297,6 +311,25 @@ def test_solve_rank1_memory_accounting():
     assert status == st.ST_OK
     assert stats["mu_mem"] == stats["iterations"] + 1
     assert stats["basis_cols"] == stats["iterations"]
+
+
+@pytest.mark.parametrize("prec,tol,err_tol", [(st.ST_FP64, 1e-12, 1e-8), (st.ST_MIXED, 1e-10, 1e-6)])
+def test_solve_load_with_more_columns_than_time_steps(prec, tol, err_tol):
+    """F1 F2^T with 12 columns on a 4-step time grid (rank at most 4): the rank compression keeps the time
+    factor's 4 directions; single and batched solves against the oracle's direct solve."""
+    for dim, n in ((2, (15, 11)), (3, (6, 5, 4))):
+        M, A = ops(dim, n, kappa=0.9)
+        D, C = timefe.time_matrices(4, 1.0)
+        F1, F2 = workloads.gaussian_factors(M.shape[0], 4, 12, seed=6)
+        F1, F2 = np.asfortranarray(F1), np.asfortranarray(F2)
+        ref = kron.solve_sparse(M, A, D, C, F1 @ F2.T)
+        with st.Problem(dim, n, 4, 1.0, kappa=0.9, precision=prec, tol=tol) as prob:
+            V, Y, stats, status = prob.solve(dev(F1), dev(F2))
+            assert status == st.ST_OK and stats["p"] <= 4, stats
+            assert relerr(host(V @ Y), ref) <= err_tol
+            res, _ = st.solve_batch([prob], [F1], [F2])
+            assert res[0][3] == st.ST_OK
+            assert relerr(host(res[0][0] @ res[0][1]), ref) <= err_tol
 
 
 def test_solve_zero_load_and_bad_arguments():
