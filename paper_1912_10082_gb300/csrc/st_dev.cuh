@@ -259,8 +259,13 @@ __device__ __forceinline__ void fold32_v4_body(int n, int other, const float* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    constexpr int PER = BM * BK / 256;   // staged entries of each operand a thread
     for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int idx = tid; idx < BM * BK; idx += 256) {
+        // all loads of the chunk first (independent, in flight together), then the shared-memory stores
+        float va[PER], vb[PER];
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int idx = tid + 256 * e;
             const int mm = idx / BK, kk = idx % BK;
             const int gm = m0 + mm, gk = k0 + kk;
             float v = 0.0f;
@@ -272,9 +277,11 @@ __device__ __forceinline__ void fold32_v4_body(int n, int other, const float* __
                     v = Gp[(size_t)gm * K + gk];
                 }
             }
-            As[kk][pos(mm)] = v;
+            va[e] = v;
         }
-        for (int idx = tid; idx < BK * BN; idx += 256) {
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int idx = tid + 256 * e;
             const int kk = idx / BN, nn = idx % BN;
             const int gk = k0 + kk, gn = n0 + nn;
             float v = 0.0f;
@@ -286,7 +293,13 @@ __device__ __forceinline__ void fold32_v4_body(int n, int other, const float* __
                                   : X[(size_t)gk * ldx + gn] + sgn * X[(size_t)(n - 1 - gk) * ldx + gn];
                 }
             }
-            Bs[kk][pos(nn)] = v;
+            vb[e] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+            const int idx = tid + 256 * e;
+            As[idx % BK][pos(idx / BK)] = va[e];
+            Bs[idx / BN][pos(idx % BN)] = vb[e];
         }
         __syncthreads();
         const int kt = min(BK, K - k0);   // beyond it both operands are zero: the chain stops where K does
@@ -542,19 +555,31 @@ __device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int r
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     float2* out = part + (size_t)chunk * k * m;
-    for (int cc = warp; cc < TS_CG_DF; cc += TS_THREADS / 32) {
-        const int a = by * TS_CG_DF + cc;
-        if (a >= k) break;
-        const float2* v = V + (size_t)a * ldv + r0;
-        float2 SH[MP], SL[MP];
+    // the FP32 product (HI) takes two basis columns a warp at a time (a0 and a0 + 8): twice the loads in
+    // flight and one shared read of W for both, where its short FMA chains leave the loads exposed; the
+    // double-float product keeps one (its longer chains already hide them, and a second set of
+    // accumulators cost more in occupancy than it gave).  Each column's sum runs in the same order either way.
+    constexpr int NW = TS_THREADS / 32, CPW = HI ? 2 : 1;
+    for (int cc = warp; cc < TS_CG_DF; cc += CPW * NW) {
+        const int a0 = by * TS_CG_DF + cc;
+        if (a0 >= k) break;
+        int na = 1;   // columns of this pass: a0, a0 + NW, ...
+        while (na < CPW && cc + na * NW < TS_CG_DF && a0 + na * NW < k) ++na;
+        const float2* v[CPW];
 #pragma unroll
-        for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
+        for (int c = 0; c < CPW; ++c) v[c] = V + (size_t)(a0 + (c < na ? c : 0) * NW) * ldv + r0;
+        float2 SH[CPW][MP], SL[CPW][MP];
+#pragma unroll
+        for (int c = 0; c < CPW; ++c)
+#pragma unroll
+            for (int q = 0; q < MP; ++q) SH[c][q] = SL[c][q] = make_float2(0.f, 0.f);
         for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
-            float2 x[TS_UNROLL];
+            float2 xv[CPW][TS_UNROLL];
 #pragma unroll
             for (int u = 0; u < TS_UNROLL; ++u) {
-                int rr = base + 32 * u;
-                x[u] = rr < nr ? v[rr] : make_float2(0.f, 0.f);
+                const int rr = base + 32 * u;
+#pragma unroll
+                for (int c = 0; c < CPW; ++c) xv[c][u] = rr < nr && c < na ? v[c][rr] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < TS_UNROLL; ++u) {
@@ -563,28 +588,36 @@ __device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int r
                 for (int q = 0; q < MP; ++q) {
                     if (q >= np) continue;
                     const float4 b = Ws[q * rows + rr];
-                    if constexpr (HI)
-                        SH[q] = __ffma2_rn(make_float2(x[u].x, x[u].x), make_float2(b.x, b.y), SH[q]);
-                    else
-                        df_madd2(SH[q], SL[q], x[u], b);
+#pragma unroll
+                    for (int c = 0; c < CPW; ++c) {
+                        if constexpr (HI)
+                            SH[c][q] = __ffma2_rn(make_float2(xv[c][u].x, xv[c][u].x), make_float2(b.x, b.y), SH[c][q]);
+                        else
+                            df_madd2(SH[c][q], SL[c][q], xv[c][u], b);
+                    }
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < MP; ++q) {
-            if (q >= np) break;
+        for (int c = 0; c < CPW; ++c) {
+            if (c >= na) break;
+            const int a = a0 + c * NW;
 #pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int b = 2 * q + h2;
-                if (b >= m) break;
-                float h = h2 ? SH[q].y : SH[q].x, l = h2 ? SL[q].y : SL[q].x;
+            for (int q = 0; q < MP; ++q) {
+                if (q >= np) break;
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    float oh = __shfl_xor_sync(0xffffffffu, h, off);
-                    float ol = __shfl_xor_sync(0xffffffffu, l, off);
-                    df_add(h, l, oh, ol);
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int b = 2 * q + h2;
+                    if (b >= m) break;
+                    float h = h2 ? SH[c][q].y : SH[c][q].x, l = h2 ? SL[c][q].y : SL[c][q].x;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        float oh = __shfl_xor_sync(0xffffffffu, h, off);
+                        float ol = __shfl_xor_sync(0xffffffffu, l, off);
+                        df_add(h, l, oh, ol);
+                    }
+                    if (lane == 0) out[(size_t)a * m + b] = make_float2(h, l);
                 }
-                if (lane == 0) out[(size_t)a * m + b] = make_float2(h, l);
             }
         }
     }

@@ -12,6 +12,7 @@
 namespace {
 
 constexpr int kMaxGrid = 152 * 24;   // persistent grid: at most 24 CTAs per SM in flight or queued
+constexpr int kSub = 8;              // row blocks of 256 per tile of the elementwise and triangular kernels
 
 // Task index of tile t: the largest i with prefix[i] <= t.
 __device__ __forceinline__ int g_task(const int* __restrict__ prefix, int ntasks, int t) {
@@ -36,7 +37,8 @@ __device__ __forceinline__ void g_load(Task& dst, const Task* src, int tid, int 
 }
 
 template <typename T, int TM, int SIDE>
-__global__ void __launch_bounds__(256, 3) kg_fold(const stg::FoldTask* tasks, const int* prefix, int ntasks) {
+__global__ void __launch_bounds__(256, TM == 4 ? 2 : 3) kg_fold(const stg::FoldTask* tasks, const int* prefix,
+                                                               int ntasks) {
     __shared__ stg::FoldTask tk;
     const int total = prefix[ntasks];
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -172,7 +174,11 @@ __global__ void __launch_bounds__(256) kg_trsm(const stg::TrsmTask* tasks, const
         __syncthreads();
         g_load(tk, tasks + i, threadIdx.x, 256);
         __syncthreads();
-        trsm_right_upper_body(tk.n, tk.m, tk.R, tk.ldr, tk.W, tk.ldw, t - prefix[i]);
+        // kSub row blocks of 256 a tile (fewer task look-ups and barriers per row)
+        for (int sb = 0; sb < kSub; ++sb) {
+            if (sb) __syncthreads();   // the previous block is done reading R from shared memory
+            trsm_right_upper_body(tk.n, tk.m, tk.R, tk.ldr, tk.W, tk.ldw, (t - prefix[i]) * kSub + sb);
+        }
     }
 }
 
@@ -196,26 +202,28 @@ __global__ void __launch_bounds__(256) kg_elem(const stg::ElemTask* tasks, const
         __syncthreads();
         g_load(tk, tasks + i, threadIdx.x, 256);
         __syncthreads();
-        const int local = t - prefix[i];
-        switch (tk.op) {
-            case stg::E_COPY64:
-                copy_cols_body<double, double>(tk.n, tk.m, (const double*)tk.X, tk.ldx, (double*)tk.Y, tk.ldy, 0.0,
-                                               local);
-                break;
-            case stg::E_TO32:
-                copy_cols_body<double, float>(tk.n, tk.m, (const double*)tk.X, tk.ldx, (float*)tk.Y, tk.ldy, 0.0,
-                                              local);
-                break;
-            case stg::E_ADD32:
-                copy_cols_body<float, double>(tk.n, tk.m, (const float*)tk.X, tk.ldx, (double*)tk.Y, tk.ldy, tk.b,
-                                              local);
-                break;
-            case stg::E_AXPBY:
-                axpby_body(tk.n, tk.m, tk.a, (const double*)tk.X, tk.ldx, tk.b, (double*)tk.Y, tk.ldy, local);
-                break;
-            default:
-                to_df_body(tk.n, tk.m, (const double*)tk.X, tk.ldx, (float2*)tk.Y, tk.ldy, local);
-                break;
+        for (int sb = 0; sb < kSub; ++sb) {   // kSub blocks of 256 entries a tile
+            const int local = (t - prefix[i]) * kSub + sb;
+            switch (tk.op) {
+                case stg::E_COPY64:
+                    copy_cols_body<double, double>(tk.n, tk.m, (const double*)tk.X, tk.ldx, (double*)tk.Y, tk.ldy, 0.0,
+                                                   local);
+                    break;
+                case stg::E_TO32:
+                    copy_cols_body<double, float>(tk.n, tk.m, (const double*)tk.X, tk.ldx, (float*)tk.Y, tk.ldy, 0.0,
+                                                  local);
+                    break;
+                case stg::E_ADD32:
+                    copy_cols_body<float, double>(tk.n, tk.m, (const float*)tk.X, tk.ldx, (double*)tk.Y, tk.ldy, tk.b,
+                                                  local);
+                    break;
+                case stg::E_AXPBY:
+                    axpby_body(tk.n, tk.m, tk.a, (const double*)tk.X, tk.ldx, tk.b, (double*)tk.Y, tk.ldy, local);
+                    break;
+                default:
+                    to_df_body(tk.n, tk.m, (const double*)tk.X, tk.ldx, (float2*)tk.Y, tk.ldy, local);
+                    break;
+            }
         }
     }
 }
@@ -491,7 +499,7 @@ void GroupPhase::nn(bool df, const std::vector<NnTask>& t) {
 void GroupPhase::trsm(const std::vector<TrsmTask>& t) {
     if (t.empty()) return;
     std::vector<int> tiles(t.size());
-    for (size_t i = 0; i < t.size(); ++i) tiles[i] = (t[i].n + 255) / 256;
+    for (size_t i = 0; i < t.size(); ++i) tiles[i] = (t[i].n + 256 * kSub - 1) / (256 * kSub);
     int total = 0;
     const size_t off = put_tasks(t, tiles, &total);
     const size_t poff = ST_PREFIX_OF(off, TrsmTask, t.size());
@@ -524,7 +532,7 @@ void GroupPhase::chol(const std::vector<CholTask>& t) {
 void GroupPhase::elem(const std::vector<ElemTask>& t) {
     if (t.empty()) return;
     std::vector<int> tiles(t.size());
-    for (size_t i = 0; i < t.size(); ++i) tiles[i] = (int)(((long long)t[i].n * t[i].m + 255) / 256);
+    for (size_t i = 0; i < t.size(); ++i) tiles[i] = (int)(((long long)t[i].n * t[i].m + 256 * kSub - 1) / (256 * kSub));
     int total = 0;
     const size_t off = put_tasks(t, tiles, &total);
     const size_t poff = ST_PREFIX_OF(off, ElemTask, t.size());

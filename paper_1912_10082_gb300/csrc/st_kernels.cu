@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(256, 2) k_apply_sf3(int nx, int ny, int nz, in
 #pragma unroll
                 for (int r = 0; r < YB + 2; ++r) vv[(j + 1) % 2][r] = okz && oky[r] ? __ldg(up + r * nx) : 0.f;
             }
-            // keep the loads of later planes from being hoisted above this one (registers)
+            // keep the loads of later planes from being hoisted above this one (registers; a third plane in
+            // flight was measured no faster)
             asm volatile("" ::: "memory");
             const int zz = z0 - 1 + j;
             float xm[YB + 2], xa[YB + 2];

@@ -36,6 +36,8 @@ WORKLOADS = {
     "heat3d_small": dict(dim=3, n=63, n_t=128, T=1.0, kappa=1.0, rhs="gaussian", p=4, seed=3),
     # many instances: drawn by batched_instances / served_requests
     "batched": dict(kind="batched", count=256, seed=4, p=2),
+    # a smaller batch of the same kind (profiling captures that must fit a few GB)
+    "batched_small": dict(kind="batched", count=24, seed=4, p=2),
     "served": dict(kind="served", count=2200, warmup=200, seed=5, mean_gap_s=2e-3, p=2),
 }
 
