@@ -14,6 +14,8 @@
 //     the device (classical Gram-Schmidt, each column re-projected until it
 //     settles), then the host half (QR of Q, SVD of the small core,
 //     st_lrgmres.h truncate_core) and P' = Q_P C_p by one tall-skinny product;
+//     a sum with more columns than N_t is first multiplied out to the dense
+//     N_h x N_t matrix (one GEMM), whose QR has N_t columns;
 //   - the preconditioner is st_solve's RKSM driver stopped after
 //     `precond_iters` shifted solves on (P, Q) as the load's factors (blocks of
 //     at most 16 columns, their results summed), Z = V Y truncated.
@@ -75,11 +77,19 @@ class DeviceBackend : public lrgmres::Backend {
         double s = 0.0;
         for (int j = 0; j < y.r; ++j)
             for (int i = 0; i < x.r; ++i) {
-                double q = 0.0;
+                // four partial sums in a fixed order (vectorisable without reassociation)
+                double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
                 const double* qi = &x.Q[(size_t)i * nt_];
                 const double* qj = &y.Q[(size_t)j * nt_];
-                for (int l = 0; l < nt_; ++l) q += qi[l] * qj[l];
-                s += G[(size_t)j * x.r + i] * q;
+                int l = 0;
+                for (; l + 4 <= nt_; l += 4) {
+                    q0 += qi[l] * qj[l];
+                    q1 += qi[l + 1] * qj[l + 1];
+                    q2 += qi[l + 2] * qj[l + 2];
+                    q3 += qi[l + 3] * qj[l + 3];
+                }
+                for (; l < nt_; ++l) q0 += qi[l] * qj[l];
+                s += G[(size_t)j * x.r + i] * ((q0 + q1) + (q2 + q3));
             }
         *out = s;
         return ST_OK;
@@ -230,6 +240,22 @@ class DeviceBackend : public lrgmres::Backend {
             x.Q.clear();
             return ST_OK;
         }
+        if (m > nt_) {
+            // more columns than time steps (sums of several full-rank-in-time vectors): the rank is at most
+            // N_t, so form Z = W Q^T (N_h x N_t) by one dense product and truncate Z I^T instead; the column
+            // QR then runs over N_t columns rather than m
+            std::vector<double> QT((size_t)m * nt_);
+            for (int j = 0; j < m; ++j)
+                for (int l = 0; l < nt_; ++l) QT[(size_t)l * m + j] = Q[(size_t)j * nt_ + l];
+            double *Z, *QTd;
+            if (int st = scratch(kScratchZ, nt_, &Z)) return fail(st);
+            if (int st = scratch(kScratchQT, (int)(((size_t)m * nt_ + n_ - 1) / n_), &QTd)) return fail(st);
+            if (int st = write_dev(c_, QT.data(), m, m, nt_, QTd, m)) return fail(st);
+            if (int st = st_lowrank_dense(n_, m, nt_, W, n_, QTd, m, Z, n_, c_.s)) return fail(st);
+            std::vector<double> I((size_t)nt_ * nt_, 0.0);
+            for (int l = 0; l < nt_; ++l) I[(size_t)l * nt_ + l] = 1.0;
+            return truncate_into(dst, Z, nt_, I);
+        }
         // column-wise QR of W: W = Q_W R (R m x m upper over the kept columns, zero rows elsewhere);
         // kept columns packed to the front, the rest zeroed
         std::vector<double> R((size_t)m * m, 0.0);
@@ -279,6 +305,7 @@ class DeviceBackend : public lrgmres::Backend {
         return ST_OK;
     }
 
+    static constexpr int kScratchZ = 90, kScratchQT = 91;   // ids of the dense-product scratch buffers
     st_problem* p_;
     Ctx c_;
     int n_, nt_;
