@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) kg_stencil(const stg::StencilTask* tasks,
 }
 
 template <int MAXM, bool DF, bool HI = false>
-__global__ void __launch_bounds__(TS_THREADS) kg_tn_partial(const stg::TnTask* tasks, const int* prefix, int ntasks) {
+__global__ void __launch_bounds__(TS_THREADS, 4) kg_tn_partial(const stg::TnTask* tasks, const int* prefix, int ntasks) {
     extern __shared__ double smem[];
     __shared__ stg::TnTask tk;
     const int total = prefix[ntasks];
