@@ -246,3 +246,43 @@ def test_batch_larger_grids_match_single_solves(prec, tol):
     finally:
         for p in probs:
             p.close()
+
+
+def test_batch_mixes_precisions_and_stops_at_maxit_like_st_solve():
+    """One batch holding FP64 and mixed-precision problems, some stopped by a small iteration limit: every problem
+    gets st_solve's status, iterations and numbers (the not-converged best iterate included)."""
+    cases = make_cases(seed=34)[:8]
+    specs = [(st.ST_FP64 if i % 2 else st.ST_MIXED, 3 if i % 3 == 0 else 300) for i in range(len(cases))]
+    probs = [st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=prec, tol=1e-11, maxit=mx)
+             for c, (prec, mx) in zip(cases, specs)]
+    try:
+        res, bs = st.solve_batch(probs, [c["F1"] for c in cases], [c["F2"] for c in cases])
+        torch.cuda.synchronize()
+        assert bs["grouped"] == len(cases)
+        for i, (c, (prec, mx)) in enumerate(zip(cases, specs)):
+            V, Y, stats, status = res[i]
+            with st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], precision=prec, tol=1e-11, maxit=mx) as twin:
+                V1, Y1, s1, st1 = twin.solve(c["F1"], c["F2"], ok=(st.ST_OK, st.ST_ENOTCONV))
+                torch.cuda.synchronize()
+                assert st1 == status, (i, st1, status)
+                assert s1["iterations"] == stats["iterations"] and s1["converged"] == stats["converged"], i
+                assert torch.equal(V1, V) and torch.equal(Y1, Y), i
+            if mx == 3:
+                assert status == st.ST_ENOTCONV and stats["iterations"] == 3, (i, status, stats["iterations"])
+            else:
+                assert status == st.ST_OK
+                ref = oracle_solution(c)
+                assert np.linalg.norm(dense(V, Y) - ref) <= (1e-8 if prec == st.ST_FP64 else 1e-6) * np.linalg.norm(ref)
+    finally:
+        for p in probs:
+            p.close()
+
+
+def test_batch_of_one_and_empty_batch():
+    c = make_cases(seed=35)[1]
+    with st.Problem(c["dim"], c["n"], c["n_t"], 1.0, c["kappa"], tol=1e-12) as p:
+        res, bs = st.solve_batch([p], [c["F1"]], [c["F2"]])
+        assert bs["grouped"] == 1 and res[0][3] == st.ST_OK
+        assert np.linalg.norm(dense(res[0][0], res[0][1]) - oracle_solution(c)) <= 1e-8 * np.linalg.norm(oracle_solution(c))
+    res, bs = st.solve_batch([], [], [])
+    assert res == [] and bs["instances"] == 0
