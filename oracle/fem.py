@@ -93,3 +93,45 @@ def tensor_operators(dim: int, n, kappa: float = 1.0, length=1.0, op: str = "hea
 def node_coordinates_1d(n: int, length: float = 1.0) -> np.ndarray:
     h = length / (n + 1)
     return h * np.arange(1, n + 1)
+
+
+def p1_simplex_operators(nodes: np.ndarray, elems: np.ndarray, interior: np.ndarray, kappa: float = 1.0,
+                         full: bool = False):
+    """P1 mass matrix M and heat operator A = kappa (grad u, grad v) on a simplex mesh (Section 3: X_h the
+    piecewise linear functions vanishing on the boundary).
+
+    Element T with vertices x_0..x_d, B = [x_1 - x_0, ..., x_d - x_0]: |T| = |det B| / d!, the gradients of the
+    barycentric coordinates lambda_1..lambda_d are the rows of B^{-1} and grad lambda_0 = -sum of the others;
+    local stiffness |T| grad lambda_i . grad lambda_j, local mass |T| (1 + delta_ij) / ((d + 1)(d + 2)) (the
+    exact integral of a product of two barycentric coordinates).  Returns the matrices on the interior nodes
+    (rows and columns in node order), or on all nodes with ``full``.
+    """
+    nodes = np.asarray(nodes, dtype=float)
+    elems = np.asarray(elems)
+    d = nodes.shape[1]
+    X = nodes[elems]                                   # E x (d+1) x d
+    B = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))   # E x d x d, columns x_i - x_0
+    det = np.linalg.det(B)
+    fact = 1.0
+    for q in range(2, d + 1):
+        fact *= q
+    vol = np.abs(det) / fact
+    Binv = np.linalg.inv(B)                            # rows: grad lambda_1..d
+    G = np.concatenate([-Binv.sum(axis=1, keepdims=True), Binv], axis=1)   # E x (d+1) x d
+    Kloc = kappa * vol[:, None, None] * np.einsum("eik,ejk->eij", G, G)
+    Mloc = vol[:, None, None] * (np.ones((d + 1, d + 1)) + np.eye(d + 1))[None] / ((d + 1) * (d + 2))
+    rows = np.repeat(elems, d + 1, axis=1).reshape(-1)
+    cols = np.tile(elems, (1, d + 1)).reshape(-1)
+    N = nodes.shape[0]
+    A = sp.csr_matrix((Kloc.reshape(-1), (rows, cols)), shape=(N, N))
+    M = sp.csr_matrix((Mloc.reshape(-1), (rows, cols)), shape=(N, N))
+    A.sum_duplicates()
+    M.sum_duplicates()
+    if full:
+        return M, A
+    keep = np.flatnonzero(np.asarray(interior))
+    M = M[keep][:, keep].tocsr()
+    A = A[keep][:, keep].tocsr()
+    M.sort_indices()
+    A.sort_indices()
+    return M, A

@@ -482,3 +482,43 @@ def test_normal_equations_forward_substitution_matches_direct_elimination():
     U = kron.forward_substitution(M, A, D, C, F1 @ F2.T)
     Un = kron.forward_substitution_normal_cg(M, A, D, C, F1, F2, 3)
     assert np.linalg.norm(Un - U[:, :3]) <= 1e-11 * np.linalg.norm(U[:, :3])
+
+
+# ---------------------------------------------------------------- P1 simplex meshes (general meshes)
+
+@pytest.mark.parametrize("dim,n", [(2, 6), (3, 3)])
+@pytest.mark.parametrize("jitter,flip", [(0.0, False), (0.25, True)])
+def test_p1_simplex_operators_pins(dim, n, jitter, flip):
+    """P1 assembly on a jittered simplex mesh: the full mass matrix integrates 1 to the domain's measure, the
+    full stiffness matrix annihilates constants, and linear functions are harmonic at interior nodes (no
+    interior load for a linear solution); M and A share one sparsity pattern."""
+    import workloads
+    msh = workloads.simplex_mesh(dim, n, seed=1, jitter=jitter, flip=flip)
+    Mf, Af = fem.p1_simplex_operators(msh["nodes"], msh["elems"], msh["interior"], full=True)
+    one = np.ones(Mf.shape[0])
+    assert abs(one @ Mf @ one - 1.0) <= 1e-13
+    assert np.abs(Af @ one).max() <= 1e-13
+    lin = msh["nodes"] @ np.arange(1.0, dim + 1.0) + 0.3
+    assert np.abs((Af @ lin)[msh["interior"]]).max() <= 1e-12
+    M, A = fem.p1_simplex_operators(msh["nodes"], msh["elems"], msh["interior"], kappa=0.7)
+    assert M.shape == (n ** dim, n ** dim)
+    assert np.array_equal(M.indptr, A.indptr) and np.array_equal(M.indices, A.indices)
+    assert abs((A - A.T)).max() <= 1e-15 and np.linalg.eigvalsh(A.toarray()).min() > 0
+    assert np.linalg.eigvalsh(M.toarray()).min() > 0
+
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (3, 4)])
+def test_p1_on_the_regular_simplex_mesh_is_the_finite_difference_stencil(dim, n):
+    """Textbook closed form: on the right-triangle (Kuhn-tetrahedron) mesh of a uniform grid, the P1 stiffness
+    matrix is h^(d-2) times the (2d+1)-point difference Laplacian (2d on the diagonal, -1 to the axis
+    neighbours, 0 across the cell diagonals), and the mass matrix's diagonal is h^d/2 (2D) or 2h^3/5 (3D)."""
+    import workloads
+    msh = workloads.simplex_mesh(dim, n, seed=1, jitter=0.0, flip=False)
+    M, A = fem.p1_simplex_operators(msh["nodes"], msh["elems"], msh["interior"])
+    h = 1.0 / (n + 1)
+    K1 = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1])
+    I = sp.identity(n)
+    lap = sp.kron(I, K1) + sp.kron(K1, I) if dim == 2 else \
+        sp.kron(sp.kron(I, I), K1) + sp.kron(sp.kron(I, K1), I) + sp.kron(sp.kron(K1, I), I)
+    assert abs(A - h ** (dim - 2) * lap).max() <= 1e-13
+    assert np.allclose(M.diagonal(), (0.5 if dim == 2 else 0.4) * h ** dim, rtol=1e-13, atol=0)

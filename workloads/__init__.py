@@ -120,3 +120,55 @@ def request_factors(req):
     f1 = rng.standard_normal((n_h, req["p"]))
     f2 = rng.standard_normal((req["n_t"], req["p"]))
     return f1, f2
+
+
+def simplex_mesh(dim: int, n: int, seed: int = 6, jitter: float = 0.25, flip: bool = True):
+    """A seeded unstructured simplex mesh of the unit square (triangles) or cube (tetrahedra).
+
+    Geometry only: a lattice of (n + 2)^dim nodes with spacing h = 1/(n + 1) (x fastest), every interior node
+    moved by U(-jitter h, jitter h) in each coordinate; 2D cells split into two triangles along a diagonal
+    drawn at random (``flip``; else always the diagonal from the lower-left corner), 3D cells into the six
+    tetrahedra of the Kuhn subdivision along the main diagonal.  Returns dict(nodes (N x dim), elems (E x
+    (dim + 1) node indices), interior (N bool: the nodes off the boundary)).
+    """
+    rng = np.random.default_rng(seed)
+    m = n + 2
+    h = 1.0 / (n + 1)
+    axes = [np.arange(m) * h] * dim
+    grid = np.meshgrid(*axes[::-1], indexing="ij")[::-1]   # x fastest in the flattened order
+    nodes = np.stack([g.reshape(-1) for g in grid], axis=1)
+    idx = np.stack(np.meshgrid(*[np.arange(m)] * dim, indexing="ij")[::-1], axis=-1).reshape(-1, dim)
+    interior = np.all((idx >= 1) & (idx <= n), axis=1)
+    nodes[interior] += rng.uniform(-jitter * h, jitter * h, size=(int(interior.sum()), dim))
+
+    def nid(c):
+        out = 0
+        for d in range(dim - 1, -1, -1):
+            out = out * m + c[d]
+        return out
+
+    elems = []
+    if dim == 2:
+        diag = rng.integers(0, 2, size=(n + 1, n + 1)) if flip else np.zeros((n + 1, n + 1), dtype=int)
+        for j in range(n + 1):
+            for i in range(n + 1):
+                a, b, c, d = nid((i, j)), nid((i + 1, j)), nid((i, j + 1)), nid((i + 1, j + 1))
+                if diag[j, i] == 0:
+                    elems += [(a, b, d), (a, d, c)]
+                else:
+                    elems += [(a, b, c), (b, d, c)]
+    elif dim == 3:
+        perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+        for k in range(n + 1):
+            for j in range(n + 1):
+                for i in range(n + 1):
+                    for p in perms:
+                        c = [i, j, k]
+                        path = [nid(tuple(c))]
+                        for ax in p:
+                            c[ax] += 1
+                            path.append(nid(tuple(c)))
+                        elems.append(tuple(path))
+    else:
+        raise ValueError("dim must be 2 or 3")
+    return dict(nodes=nodes, elems=np.asarray(elems, dtype=np.int64), interior=interior)
