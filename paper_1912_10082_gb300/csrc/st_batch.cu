@@ -1521,8 +1521,9 @@ extern "C" int st_solve_batch(int count, st_problem* const* problems, const doub
         cudaStream_t own = p->stream;
         p->stream = s;
         st_stats st{};
-        status[i] = p->dim < 1 ? ST_ENOTSUP
-                               : solve_impl(p, F1[i], ldf1[i], F2[i], ldf2[i], ncols[i], sols ? &sols[i] : nullptr, &st);
+        status[i] = p->dim < 0 || (p->dim == 0 && p->d.op != ST_HEAT)
+                        ? ST_ENOTSUP
+                        : solve_impl(p, F1[i], ldf1[i], F2[i], ldf2[i], ncols[i], sols ? &sols[i] : nullptr, &st);
         p->stream = own;
         if (stats) stats[i] = st;
     }

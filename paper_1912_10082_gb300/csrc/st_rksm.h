@@ -19,7 +19,8 @@ inline double ms_since(Clock::time_point t0) {
 
 enum SlotId {
     S_F1D = 0, S_F1C, S_MAQ, S_WH, S_WH2, S_TMP, S_X32, S_W32, S_T32, S_SMALL, S_PART, S_COPY, S_MV,
-    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT, S_WDF, S_GH, S_GHD, S_GPART
+    S_RES, S_RESP, S_LRQ, S_LRZ, S_CNF1, S_CNF2, S_CNBUF, S_CNTMP, S_GZ, S_GT, S_WDF, S_GH, S_GHD, S_GPART,
+    S_CG, S_CGS
 };
 
 struct Ctx {
@@ -80,6 +81,11 @@ std::vector<double> upper_product(int m, const double* R2, const double* R1);
 int check_gap(const std::vector<int>& hist_it, const std::vector<double>& hist_res, int it, double res, double tol,
               double cost);
 // The single-problem driver (st_solve).
+// Problems given as CSR matrices (st_pcg.cu): (cm M + ca A) X = B by Jacobi-preconditioned block CG, and the
+// pencil interval of (A, M) estimated once per problem.
+int pcg_solve(Ctx& c, double cm, double ca, const double* B, int ldb, int ncols, double* X, int ldx, double rtol,
+              int maxit, int* iters_out);
+int csr_spectrum(Ctx& c);
 int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int p0, st_solution* sol,
                st_stats* st);
 

@@ -166,6 +166,18 @@ int shifted_solve(Ctx& c, int prec, double shift, const double* X, int ldx, cons
                   double* W, int ldw) {
     st_problem* p = c.p;
     size_t nm = (size_t)c.n * ncols;
+    if (p->dim == 0) {
+        // CSR problem: (A + s M) W = M X by the algebraic inner solver, to 1e-12 relative per column
+        if (!MX) {
+            double* mx;
+            ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&mx));
+            ST_TRY(st_spmm_comb64(p, 1.0, 0.0, X, ldx, ncols, 0.0, mx, c.n, c.s));
+            MX = mx;
+            ldmx = c.n;
+        }
+        int its = 0;
+        return pcg_solve(c, shift, 1.0, MX, ldmx, ncols, W, ldw, 1e-12, 50000, &its);
+    }
     if (prec == ST_FP64) {
         double* tmp;
         ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&tmp));
@@ -198,6 +210,10 @@ int shifted_solve(Ctx& c, int prec, double shift, const double* X, int ldx, cons
 int mass_inverse(Ctx& c, int prec, const double* X, int ldx, int ncols, double* W, int ldw) {
     st_problem* p = c.p;
     size_t nm = (size_t)c.n * ncols;
+    if (p->dim == 0) {
+        int its = 0;
+        return pcg_solve(c, 1.0, 0.0, X, ldx, ncols, W, ldw, 1e-13, 20000, &its);
+    }
     if (prec == ST_FP64) {
         double* tmp;
         ST_TRY(st_slot(p, S_TMP, sizeof(double) * nm, (void**)&tmp));
@@ -873,14 +889,16 @@ int solve_impl(st_problem* p, const double* F1, int ldf1, const double* F2, int 
     Ctx c{p, p->stream, p->n_h};
     const int n = p->n_h, nt = p->n_t;
     const double dt = p->dt;
-    const int prec = p->d.precision;
+    // problems given as CSR matrices run in FP64 (the inner solver is FP64 CG)
+    const int prec = p->dim == 0 ? ST_FP64 : p->d.precision;
     const double tol = p->d.tol;
     st_stats S{};
     auto tp = Clock::now();
     Stage sg(c);
     // heat: A symmetric, exact fast-diagonalisation shifted solves; convection-diffusion:
     // A nonsymmetric, preconditioned FGMRES shifted solves and unsymmetrised projections
-    const bool sym = p->tensor_heat;
+    const bool sym = p->tensor_heat || p->dim == 0;
+    if (p->dim == 0) ST_TRY(csr_spectrum(c));
     const double inner_tol = std::max(1e-13, 1e-3 * tol);
     auto resolvent = [&](double s, const double* X, int ldx, const double* MX, int ldmx, int m, double* W,
                          int ldw) -> int {
@@ -1474,7 +1492,8 @@ extern "C" int st_solve(st_problem* p, const double* F1, int ldf1, const double*
                         st_solution* sol, st_stats* stats) {
     if (!p || !F1 || !F2) return ST_EINVAL;
     if (ncols < 1 || ncols > 16 || ldf1 < p->n_h || ldf2 < p->n_t) return ST_EINVAL;
-    if (p->dim < 1) return ST_ENOTSUP;
+    // box grids (heat or convection-diffusion); CSR matrices for heat (M and A symmetric positive definite)
+    if (p->dim < 0 || (p->dim == 0 && p->d.op != ST_HEAT)) return ST_ENOTSUP;
     return solve_impl(p, F1, ldf1, F2, ldf2, ncols, sol, stats);
 }
 
@@ -1489,7 +1508,8 @@ extern "C" int st_shift_solve(st_problem* p, double s, const double* X, int ldx,
                               int precision) {
     if (!p || !X || !W || ncols < 1 || ldx < p->n_h || ldw < p->n_h) return ST_EINVAL;
     if (precision != ST_FP64 && precision != ST_MIXED) return ST_EINVAL;
-    if (!p->tensor_heat && !(p->dim >= 1 && p->d.op == ST_CONVDIFF)) return ST_ENOTSUP;
+    if (!p->tensor_heat && !(p->dim >= 1 && p->d.op == ST_CONVDIFF) && !(p->dim == 0 && p->d.op == ST_HEAT))
+        return ST_ENOTSUP;
     if (!(s > -p->lam_min)) return ST_EINVAL;
     Ctx c{p, p->stream, p->n_h};
     // process in column groups of at most 16 through a private buffer (X and W may alias)
@@ -1497,7 +1517,7 @@ extern "C" int st_shift_solve(st_problem* p, double s, const double* X, int ldx,
         int m = std::min(16, ncols - j0);
         double* buf;
         ST_TRY(st_slot(p, S_COPY, sizeof(double) * (size_t)p->n_h * m, (void**)&buf));
-        if (p->tensor_heat)
+        if (p->tensor_heat || p->dim == 0)
             ST_TRY(shifted_solve(c, precision, s, X + (size_t)j0 * ldx, ldx, nullptr, 0, m, buf, p->n_h));
         else
             ST_TRY(shifted_solve_fgmres(c, precision, s, X + (size_t)j0 * ldx, ldx, nullptr, 0, m, buf, p->n_h, 1e-12,
