@@ -416,6 +416,68 @@ def apply_measure(st, torch, prob, stream, flush_l2, pk, launches=20):
     return out
 
 
+def mesh_comparator(st, torch, stream, n=34, n_t=500, T=10.0, seed=6):
+    """A general-mesh problem shaped like the paper's Example 1 (Section 5): 3D heat on (-1,1)^3, I = (0, 10),
+    P1 elements on a seeded jittered Kuhn-tetrahedron mesh (n^3 interior nodes: 39,304 for n = 34, against the
+    paper's 41,300) with N_t = 500, the rank-1 load 10 t sin t cos(pi x/2) cos(pi y/2) cos(pi z/2) (space factor
+    M g with g the nodal values, time factor the exact interval integrals of 10 t sin t), FP64 RKSM to 1e-8
+    through the CSR path (Jacobi-preconditioned CG inner solves).  The mesh and matrices come from
+    workloads.simplex_mesh and st_p1_mesh_csr; one warm-up solve (which also estimates the pencil interval)
+    and one timed solve."""
+    import numpy as np
+    import scipy.sparse as sp
+    import workloads
+    msh = workloads.simplex_mesh(3, n, seed=seed)
+    nodes = 2.0 * msh["nodes"] - 1.0
+    rp, col, mv, av = st.p1_mesh_csr(nodes, msh["elems"], msh["interior"])
+    nh = len(rp) - 1
+    M = sp.csr_matrix((mv, col, rp), shape=(nh, nh))
+    xi = nodes[msh["interior"]]
+    g = np.prod(np.cos(0.5 * np.pi * xi), axis=1)
+    F1 = np.asfortranarray((M @ g)[:, None])
+    t = np.linspace(0.0, T, n_t + 1)
+    a, b_ = t[:-1], t[1:]
+    F2 = np.asfortranarray((10.0 * (np.sin(b_) - b_ * np.cos(b_) - np.sin(a) + a * np.cos(a)))[:, None])
+    out = {}
+    with st.Problem(0, 1, n_t, T, tol=1e-8, maxit=400, stream=stream, csr=(rp, col, mv, av)) as prob:
+        f1 = st.colmajor(torch.from_numpy(F1).cuda())
+        f2 = st.colmajor(torch.from_numpy(F2).cuda())
+        ms = []
+        for it in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V, Y, stats, status = prob.solve(f1, f2)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        relres_cert = prob.residual_lowrank(V, Y, f1, f2)
+        # Table 1's comparison solver on the same problem (one timed solve)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Vl, Yl, ls, lst = prob.solve_lrfgmres(f1, f2, maxit=50, precond_iters=5, trunc=1e-12,
+                                              ok=(st.ST_OK, st.ST_ENOTCONV))
+        e1.record(stream)
+        e1.synchronize()
+        ml = e0.elapsed_time(e1)
+        lr = {"value": nh * n_t / (ml * 1e-3), "ms": ml, "outer_iterations": ls["iterations"],
+              "rksm_iterations": ls["inner_iterations"], "mu_mem": ls["mu_mem"], "relres_estimate": ls["relres"],
+              "relres_certified": prob.residual_lowrank(Vl, Yl, f1, f2), "converged": ls["converged"],
+              "paper_same_shape": {"dof_per_s": 1.53e5, "outer_iterations": 4, "mu_mem": 75}}
+        out = {"value": nh * n_t / (ms[-1] * 1e-3), "ms": ms[-1], "first_solve_ms": ms[0], "n_h": nh, "n_t": n_t,
+               "lrfgmres_rksm_fp64": lr,
+               "iterations": stats["iterations"], "mu_mem": stats["mu_mem"], "rank": stats["rank"],
+               "relres": stats["relres"], "relres_certified": relres_cert, "status": int(status),
+               "how": "P1 on a jittered Kuhn mesh of (-1,1)^3, Example 1's rank-1 load, FP64, CSR path",
+               "paper_rksm_same_shape": {"n_h": 41300, "n_t": 500, "dof_per_s": 3.13e5,
+                                         "note": "Matlab on 2.1 GHz CPUs, Table 1; context, not a target"}}
+    print(f"[bench] general mesh P1 3D {nh} x {n_t}: {out['ms']:.1f} ms, its {out['iterations']}, "
+          f"LR-FGMRES {out['lrfgmres_rksm_fp64']['ms']:.1f} ms, relres {out['relres']:.2e}", file=sys.stderr,
+          flush=True)
+    return out
+
+
 def bench_batched(args, wl, rank, world, local):
     """Batched workload: 256 2D heat instances of mixed sizes solved at once by st_solve_batch (lock-step RKSM,
     every device step one grouped launch over the instances still iterating)."""
@@ -532,6 +594,7 @@ def bench_batched(args, wl, rank, world, local):
           f"executor mixed {comps['mixed_rksm_executor']['ms_per_step']:.1f} ms", file=sys.stderr, flush=True)
     if not args.no_singles:
         comps["single_problems"] = single_comparators(st, torch, ("heat2d_gauss", "heat3d"), stream)
+        comps["general_mesh_p1_3d"] = mesh_comparator(st, torch, stream)
     apply = {}
     flush = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     flush_out = torch.empty(1, dtype=torch.float32, device="cuda")

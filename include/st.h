@@ -137,6 +137,26 @@ int st_destroy(st_problem* p);
 /* st_problem_info -- sizes of a problem (host outputs, any may be NULL). */
 int st_problem_info(const st_problem* p, int* n_h, int* n_t, int* nnz, double* dt);
 
+/* st_p1_mesh_csr -- P1 mass matrix M and heat operator A = kappa (grad u, grad v) of a simplex mesh on its
+ * interior nodes (paper Section 3: X_h the continuous piecewise linear functions vanishing on the boundary;
+ * Example 1 uses such meshes), assembled on the host in CSR form with one shared, sorted pattern -- the input of
+ * st_setup's dim == 0 path (st_desc.row_ptr, col_idx, m_vals, a_vals).
+ *   dim            2 (triangles) or 3 (tetrahedra)
+ *   n_nodes, xyz   node coordinates, n_nodes x dim, row-major (node i at xyz[i*dim .. i*dim+dim-1])
+ *   n_elems, elems vertex indices, n_elems x (dim+1), row-major
+ *   interior       n_nodes flags: nonzero for the nodes that carry unknowns (Dirichlet nodes are 0); the
+ *                  unknowns are numbered in node order
+ *   row_ptr (n_h+1), col_idx, m_vals, a_vals (nnz): caller-owned outputs; pass NULL for all four to get
+ *                  the sizes only, then call again with arrays of those sizes
+ *   n_h, nnz       outputs: interior node count and nonzeros of the shared pattern
+ * Element T, vertices x_0..x_d, B = [x_1 - x_0, ..., x_d - x_0]: |T| = |det B| / d!, barycentric gradients the
+ * rows of B^-1 and minus their sum; local stiffness kappa |T| grad l_i . grad l_j, local mass
+ * |T| (1 + delta_ij) / ((d+1)(d+2)).  Host only (no GPU call).  ST_EINVAL on bad sizes, an index out of
+ * range or a degenerate element. */
+int st_p1_mesh_csr(int dim, int n_nodes, const double* xyz, int n_elems, const int* elems,
+                   const unsigned char* interior, double kappa, int* row_ptr, int* col_idx, double* m_vals,
+                   double* a_vals, int* n_h, int* nnz);
+
 /* st_get_csr -- copy the assembled matrices to host arrays (sizes from
  * st_problem_info): row_ptr (n_h+1), col_idx (nnz), m_vals, a_vals (nnz).
  * Any pointer may be NULL.  Synchronises the stream. */

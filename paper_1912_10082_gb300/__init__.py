@@ -36,7 +36,7 @@ ABI_SYMBOLS = (
     "st_shift_solve_noalloc", "st_shift_solve_noalloc_max", "st_set_coefficients", "st_request_bytes",
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
     "st_executor_destroy", "st_executor_set_policy", "st_autotune", "st_autotune_reset", "st_autotune_count",
-    "st_autotune_save", "st_autotune_load", "st_solve_batch", "st_solve_lrfgmres",
+    "st_autotune_save", "st_autotune_load", "st_solve_batch", "st_solve_lrfgmres", "st_p1_mesh_csr",
 )
 
 
@@ -122,6 +122,7 @@ def lib() -> C.CDLL:
         "st_destroy": ([vp], i),
         "st_problem_info": ([vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)], i),
         "st_get_csr": ([vp, vp, vp, vp, vp], i),
+        "st_p1_mesh_csr": ([i, i, vp, i, vp, vp, d, vp, vp, vp, vp, C.POINTER(i), C.POINTER(i)], i),
         "st_apply": ([vp, i, vp, i, vp, i], i),
         "st_rhs_manufactured": ([vp, vp, i, vp, i], i),
         "st_shift_solve": ([vp, d, vp, i, i, vp, i, i], i),
@@ -237,6 +238,26 @@ def make_desc(dim: int, n, n_t: int, T: float = 1.0, kappa: float = 1.0, *, leng
     d.n_t, d.T = int(n_t), float(T)
     d.precision, d.tol, d.maxit, d.max_basis = int(precision), float(tol), int(maxit), int(max_basis)
     return d
+
+
+def p1_mesh_csr(nodes, elems, interior, kappa: float = 1.0):
+    """st_p1_mesh_csr: P1 mass matrix and heat operator of a simplex mesh on its interior nodes, as the
+    (row_ptr, col_idx, m_vals, a_vals) tuple that Problem(0, ..., csr=...) takes.  Host only."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    elems = np.ascontiguousarray(elems, dtype=np.int32)
+    inter = np.ascontiguousarray(interior, dtype=np.uint8)
+    dim = nodes.shape[1]
+    nh, nnz = C.c_int(), C.c_int()
+    args = (dim, nodes.shape[0], nodes.ctypes.data, elems.shape[0], elems.ctypes.data, inter.ctypes.data,
+            float(kappa))
+    _check(lib().st_p1_mesh_csr(*args, None, None, None, None, C.byref(nh), C.byref(nnz)), "st_p1_mesh_csr")
+    rp = np.empty(nh.value + 1, dtype=np.int32)
+    col = np.empty(nnz.value, dtype=np.int32)
+    mv = np.empty(nnz.value)
+    av = np.empty(nnz.value)
+    _check(lib().st_p1_mesh_csr(*args, rp.ctypes.data, col.ctypes.data, mv.ctypes.data, av.ctypes.data,
+                                C.byref(nh), C.byref(nnz)), "st_p1_mesh_csr")
+    return rp, col, mv, av
 
 
 class Problem:

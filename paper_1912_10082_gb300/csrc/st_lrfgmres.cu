@@ -325,8 +325,8 @@ extern "C" int st_solve_lrfgmres(st_problem* p, const double* F1, int ldf1, cons
     if (!p || !F1 || !F2 || ncols < 1 || ldf1 < p->n_h || ldf2 < p->n_t || maxit < 1 || precond_iters < 0 ||
         !(trunc >= 0.0))
         return ST_EINVAL;
-    if (!p->tensor_heat) {
-        st_note_msg("st_solve_lrfgmres: the RKSM preconditioner needs the tensor-grid heat solver");
+    if (!p->tensor_heat && !(p->dim == 0 && p->d.op == ST_HEAT)) {
+        st_note_msg("st_solve_lrfgmres: the RKSM preconditioner needs a heat problem (box grid or CSR matrices)");
         return ST_ENOTSUP;
     }
     const auto t0 = Clock::now();

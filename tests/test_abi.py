@@ -5,6 +5,7 @@ import re
 import subprocess
 from pathlib import Path
 
+import numpy as np
 import pytest
 
 ROOT = Path(__file__).resolve().parent.parent
@@ -75,3 +76,28 @@ def test_struct_layouts_match_c(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert int(out[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
+
+
+@pytest.mark.parametrize("dim,n,jitter", [(2, 9, 0.25), (3, 4, 0.25), (2, 6, 0.0)])
+def test_p1_mesh_assembly_matches_the_oracle(dim, n, jitter):
+    """st_p1_mesh_csr (host code of the library, no GPU) against the oracle's P1 assembly on the same mesh: the
+    same pattern, values within rounding."""
+    import paper_1912_10082_gb300 as st
+    import workloads
+    from oracle import fem
+    msh = workloads.simplex_mesh(dim, n, seed=2, jitter=jitter)
+    rp, col, mv, av = st.p1_mesh_csr(msh["nodes"], msh["elems"], msh["interior"], kappa=0.9)
+    M, A = fem.p1_simplex_operators(msh["nodes"], msh["elems"], msh["interior"], kappa=0.9)
+    assert np.array_equal(rp, M.indptr) and np.array_equal(col, M.indices)
+    assert np.abs(mv - M.data).max() <= 1e-15 * np.abs(M.data).max() * 10
+    assert np.abs(av - A.data).max() <= 1e-14 * np.abs(A.data).max()
+
+
+def test_p1_mesh_assembly_refuses_bad_input():
+    import paper_1912_10082_gb300 as st
+    nodes = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [2.0, 0.0]])
+    inter = np.ones(4, dtype=np.uint8)
+    with pytest.raises(st.StError):
+        st.p1_mesh_csr(nodes, np.array([[0, 1, 3]]), inter)   # degenerate (collinear) triangle
+    with pytest.raises(st.StError):
+        st.p1_mesh_csr(nodes, np.array([[0, 1, 7]]), inter)   # index out of range

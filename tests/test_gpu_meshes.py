@@ -84,3 +84,24 @@ def test_csr_problem_requested_in_mixed_precision_runs_in_fp64_and_in_a_batch_as
         res, bs = st.solve_batch([p64, box], [F1, np.asfortranarray(G1)], [F2, np.asfortranarray(G2)])
         assert bs["grouped"] == 1 and res[0][3] == st.ST_OK and res[1][3] == st.ST_OK
         assert torch.equal(res[0][0], V) and torch.equal(res[0][1], Y)
+
+
+def test_csr_lrfgmres_matches_direct_solution_and_oracle():
+    """LR-FGMRES+RKSM (Table 1's comparison solver) on a general mesh: the direct solve, the oracle's
+    LR-FGMRES+RKSM solution, and the exact residual of the returned factors."""
+    from oracle import lrfgmres
+    M, A = mesh_ops(3, 6, seed=12, kappa=0.7)
+    nt = 12
+    D, C = timefe.time_matrices(nt, 1.0)
+    F1, F2 = workloads.gaussian_factors(M.shape[0], nt, 2, seed=44)
+    ref = kron.solve_sparse(M, A, D, C, F1 @ F2.T)
+    tol = 1e-10
+    with csr_problem(M, A, nt, tol=tol) as prob:
+        V, Y, stats, status = prob.solve_lrfgmres(np.asfortranarray(F1), np.asfortranarray(F2), maxit=40,
+                                                  precond_iters=5, trunc=1e-12)
+        Vh, Yh = V.cpu().numpy(), Y.cpu().numpy()
+    assert status == st.ST_OK and stats["converged"] == 1
+    assert relerr(Vh @ Yh, ref) <= 1e-8
+    assert residual.relres_lowrank(M, A, D, C, Vh, Yh, F1, F2) <= 20 * tol
+    orc = lrfgmres.lr_fgmres(M, A, D, C, F1, F2, tol=tol, maxit=40, precond_iters=5, trunc=1e-12)
+    assert relerr(Vh @ Yh, orc["P"] @ orc["Q"].T) <= 1e-8
