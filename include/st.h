@@ -124,8 +124,9 @@ typedef struct st_stats {
  * and operator matrices on the device (Kronecker products of 1D
  * M = h/6 tridiag(1,4,1), K = 1/h tridiag(-1,2,-1), G = 1/2 tridiag(-1,0,1))
  * and tables for the fast-diagonalisation shifted solve.  For dim == 0 the
- * CSR arrays are copied from host memory (st_solve and st_timestep_cn then
- * return ST_ENOTSUP: they need the tensor-grid solver).
+ * CSR arrays are copied from host memory (st_solve, st_shift_solve and
+ * st_solve_lrfgmres then use the algebraic inner solver for heat problems;
+ * st_timestep_cn returns ST_ENOTSUP: it needs the tensor-grid solver).
  * Ownership: the handle owns every device buffer it allocates until
  * st_destroy.  Errors: ST_EINVAL (bad sizes or fields, nnz > INT_MAX),
  * ST_ENOMEM, ST_ECUDA.  *out is NULL on error. */
@@ -186,8 +187,12 @@ int st_rhs_manufactured(st_problem* p, double* F1, int ldf1, double* F2, int ldf
  * transforms in FP64, or FP32 under ST_MIXED), all columns advanced together,
  * stopped at a relative residual of 1e-12 per column; synchronises with the
  * host every few steps.  X, W: device double, n_h x p, ld >= n_h; may alias.
- * s > -lambda_min (of eps K for convection-diffusion).  ST_ENOTSUP for
- * problems given by user matrices. */
+ * s > -lambda_min (of eps K for convection-diffusion).  Heat problems given
+ * as user CSR matrices (dim == 0; M and A symmetric positive definite):
+ * Jacobi-preconditioned conjugate gradients, all columns advanced together,
+ * to a relative residual of 1e-12 per column, FP64 whatever the precision;
+ * synchronises every few iterations.  ST_ENOTSUP for convection-diffusion
+ * given by user matrices. */
 int st_shift_solve(st_problem* p, double s, const double* X, int ldx, int ncols,
                    double* W, int ldw, int precision);
 
@@ -277,7 +282,8 @@ int st_autotune_load(const char* path, const char* device_tag, int* loaded);
  * F1: n_h x p (ld ldf1), F2: n_t x p (ld ldf2), double, host OR device.
  * 1 <= p <= 16.  Output in *sol (V, Y owned by the handle; U_dense filled if
  * given).  stats may be NULL.  Synchronises.  Returns ST_OK, ST_ENOTCONV
- * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (dim == 0), ST_EINVAL
+ * (best iterate returned), ST_EBREAKDOWN, ST_ENOTSUP (convection-diffusion
+ * given as user matrices), ST_EINVAL
  * (also for a NaN or Inf in F1 or F2, or an F1 whose Gram matrix overflows).
  * Heat (ST_HEAT): the shifted solves are exact fast-diagonalisation
  * transforms.  Convection-diffusion (ST_CONVDIFF, A nonsymmetric): each
@@ -290,7 +296,13 @@ int st_autotune_load(const char* path, const char* device_tag, int* loaded);
  * or inside FGMRES as the preconditioner), basis products in double-float
  * arithmetic on the FP32 pipes (about 48 significant bits), and on
  * convection-diffusion grids of at least 2^15 points FGMRES cycles in FP32
- * refined on the FP64 residual. */
+ * refined on the FP64 residual.  Heat given as user CSR matrices (dim == 0,
+ * e.g. P1 on a simplex mesh from st_p1_mesh_csr; M and A symmetric positive
+ * definite): the shifted solves and the start block's M^{-1} F1 are
+ * Jacobi-preconditioned conjugate gradients (to 1e-12 / 1e-13 relative per
+ * column), the pencil interval of the adaptive shifts is estimated at the
+ * first solve (power and inverse iteration), and the solve runs in FP64
+ * whatever the requested precision. */
 int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ldf2, int ncols,
              st_solution* sol, st_stats* stats);
 
@@ -303,7 +315,7 @@ int st_solve(st_problem* p, const double* F1, int ldf1, const double* F2, int ld
  * stopped after precond_iters shifted solves on the vector's factors (blocks
  * of at most 16 columns, their results summed).  Stops when the least-squares
  * residual estimate is <= the problem's tol, or after maxit steps.  Heat
- * problems on box grids (ST_ENOTSUP otherwise).  F1, F2 as st_solve (host or
+ * problems, on box grids or as user CSR matrices (ST_ENOTSUP otherwise).  F1, F2 as st_solve (host or
  * device, 1 <= ncols).  Output in *sol: V = P (n_h x k), Y = Q^T (k x n_t),
  * owned by the handle (valid until its next solve or st_destroy), U_dense
  * filled if given.  stats (may be NULL): iterations = GMRES steps, basis_cols
