@@ -158,6 +158,30 @@ int st_p1_mesh_csr(int dim, int n_nodes, const double* xyz, int n_elems, const i
                    const unsigned char* interior, double kappa, int* row_ptr, int* col_idx, double* m_vals,
                    double* a_vals, int* n_h, int* nnz);
 
+/* st_wave_matrices -- the one-dimensional matrices of the wave equation's space-time system (paper Section 3
+ * "The Wave Equation", Section 4 eq. 3terms; Section 5 Example 2's cubic B-splines), assembled on the host:
+ * test space R (x) Z with Z the cubic B-splines of an open uniform knot vector on n_x intervals of (0, 1) without
+ * the two that are nonzero at an end point (N_h = n_x + 1, Dirichlet), R the cubic B-splines on n_t intervals of
+ * (0, T) without the two that are nonzero in value or slope at T (N_t = n_t + 1).  Outputs (any may be NULL),
+ * dense column-major: Mh = (psi_i, psi_j), Ah = (psi_i', psi_j'), Qh = (psi_i'', psi_j'') (N_h x N_h);
+ * Mt = (rho^k, rho^l), Dt[k][l] = ((rho^k)'', rho^l), Qt = ((rho^k)'', (rho^l)'') (N_t x N_t).  4-point
+ * Gauss-Legendre on every knot interval (exact).  Host only.  ST_EINVAL for n_x < 4, n_t < 4 or T <= 0. */
+int st_wave_matrices(int n_x, int n_t, double T, double* Mh, double* Ah, double* Qh, double* Mt, double* Dt,
+                     double* Qt);
+
+/* st_wave_solve -- the wave equation's space-time system, M_h U Q_t^T + A_h U (D_t + D_t^T) + Q_h U M_t = F1 F2^T
+ * (Section 4 eq. 3terms; matrices of st_wave_matrices, unknown U N_h x N_t, U[i][k] the coefficient of the trial
+ * function (rho^k)'' psi_i + rho^k A psi_i), by GMRES on vec(U) (X_0 = 0, no restart, classical Gram-Schmidt
+ * twice) right-preconditioned by M_h W Q_t^T + Q_h W M_t = V, solved by diagonalising the pencils (Q_h, M_h)
+ * and (Q_t, M_t) on the host ("GMRES+LYAP").  Stops when the residual estimate |g_{j+1}| / ||F||_F <= tol, or
+ * after maxit steps (ST_ENOTCONV, the last iterate returned).  F1 (N_h x p, ld ldf1), F2 (N_t x p, ld ldf2) host
+ * or device; U (N_h x N_t, ld ldu) host or device, written.  stats (may be NULL): iterations, relres (the
+ * estimate), converged, ms_total, ms_phase[0] = host set-up (matrices and eigendecompositions).  stream: the
+ * caller's stream (NULL: the legacy stream); device memory (about (maxit + 8) N_h N_t doubles) is taken and
+ * released on it.  Synchronises.  Errors: ST_EINVAL, ST_ENOMEM, ST_EBREAKDOWN, ST_ECUDA. */
+int st_wave_solve(int n_x, int n_t, double T, const double* F1, int ldf1, const double* F2, int ldf2, int p,
+                  double tol, int maxit, double* U, int ldu, st_stats* stats, void* stream);
+
 /* st_get_csr -- copy the assembled matrices to host arrays (sizes from
  * st_problem_info): row_ptr (n_h+1), col_idx (nnz), m_vals, a_vals (nnz).
  * Any pointer may be NULL.  Synchronises the stream. */

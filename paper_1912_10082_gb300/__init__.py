@@ -37,6 +37,7 @@ ABI_SYMBOLS = (
     "st_executor_create", "st_executor_submit", "st_executor_wait", "st_executor_pending", "st_executor_now",
     "st_executor_destroy", "st_executor_set_policy", "st_autotune", "st_autotune_reset", "st_autotune_count",
     "st_autotune_save", "st_autotune_load", "st_solve_batch", "st_solve_lrfgmres", "st_p1_mesh_csr",
+    "st_wave_matrices", "st_wave_solve",
 )
 
 
@@ -123,6 +124,8 @@ def lib() -> C.CDLL:
         "st_problem_info": ([vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(d)], i),
         "st_get_csr": ([vp, vp, vp, vp, vp], i),
         "st_p1_mesh_csr": ([i, i, vp, i, vp, vp, d, vp, vp, vp, vp, C.POINTER(i), C.POINTER(i)], i),
+        "st_wave_matrices": ([i, i, d, vp, vp, vp, vp, vp, vp], i),
+        "st_wave_solve": ([i, i, d, vp, i, vp, i, i, d, i, vp, i, C.POINTER(StStats), vp], i),
         "st_apply": ([vp, i, vp, i, vp, i], i),
         "st_rhs_manufactured": ([vp, vp, i, vp, i], i),
         "st_shift_solve": ([vp, d, vp, i, i, vp, i, i], i),
@@ -258,6 +261,33 @@ def p1_mesh_csr(nodes, elems, interior, kappa: float = 1.0):
     _check(lib().st_p1_mesh_csr(*args, rp.ctypes.data, col.ctypes.data, mv.ctypes.data, av.ctypes.data,
                                 C.byref(nh), C.byref(nnz)), "st_p1_mesh_csr")
     return rp, col, mv, av
+
+
+def wave_matrices(n_x: int, n_t: int, T: float = 1.0):
+    """st_wave_matrices: (Mh, Ah, Qh, Mt, Dt, Qt) of the wave equation's space-time system as numpy arrays."""
+    nh, nt = n_x + 1, n_t + 1
+    out = [np.zeros((nh, nh), order="F") for _ in range(3)] + [np.zeros((nt, nt), order="F") for _ in range(3)]
+    _check(lib().st_wave_matrices(int(n_x), int(n_t), float(T), *[a.ctypes.data for a in out]), "st_wave_matrices")
+    return tuple(out)
+
+
+def wave_solve(n_x: int, n_t: int, T, F1, F2, tol: float = 1e-8, maxit: int = 300, U=None, stream=None,
+               ok=(ST_OK,)):
+    """st_wave_solve (GMRES+LYAP on the wave equation's three-term system): returns (U, stats, status); U is a
+    device tensor (N_h x N_t, column-major) unless one is given (host numpy or device torch)."""
+    import torch
+    nh, nt = n_x + 1, n_t + 1
+    p1, l1, _, m = _ptr_ld(F1)
+    p2, l2, _, _ = _ptr_ld(F2)
+    if U is None:
+        U = empty_colmajor(nh, nt)
+    pu, lu, _, _ = _ptr_ld(U)
+    stats = StStats()
+    sv = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    st = lib().st_wave_solve(int(n_x), int(n_t), float(T), p1, l1, p2, l2, m, float(tol), int(maxit), pu, lu,
+                             C.byref(stats), sv)
+    _check(st, "st_wave_solve", ok)
+    return U, stats.as_dict(), st
 
 
 class Problem:

@@ -271,6 +271,9 @@ int st_copy_cols64(int n, int m, const double* X, int ldx, double* Y, int ldy, c
 int st_convert_64_32(int n, int m, const double* X, int ldx, float* Y, int ldy, cudaStream_t s);
 int st_convert_32_64_add(int n, int m, const float* X, int ldx, double* Y, int ldy, double beta, cudaStream_t s);
 int st_axpby64(int n, int m, double a, const double* X, int ldx, double b, double* Y, int ldy, cudaStream_t s);
+// C = X Y, all column-major (r x c = r x s times s x c), FP64.
+int st_gemm_cm(int r, int c, int s, const double* X, int ldx, const double* Y, int ldy, double* C, int ldc,
+               cudaStream_t st);
 int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const double* Y, int ldy,
                      double* U, int ldu, cudaStream_t s);
 

@@ -2163,6 +2163,15 @@ int st_axpby64(int n, int m, double a, const double* X, int ldx, double b, doubl
     return ST_OK;
 }
 
+// C (r x c, column-major) = X (r x s) Y (s x c): as the row-major product C^T = Y^T X^T.
+int st_gemm_cm(int r, int c, int s, const double* X, int ldx, const double* Y, int ldy, double* C, int ldc,
+               cudaStream_t st) {
+    FdEpi plain{};
+    plain.coef = 1.0;
+    Batch2 bt{1, 0, 0, 0, 0, 0, 0};
+    return launch_gemm_rr<double>(c, r, s, Y, ldy, X, ldx, C, ldc, 1, bt, plain, st, "dense_gemm");
+}
+
 // U (n x n_t, col-major) = V (n x k) Y (k x n_t): as row-major U^T = Y^T V^T.
 int st_lowrank_dense(int n, int k, int n_t, const double* V, int ldv, const double* Y, int ldy, double* U, int ldu,
                      cudaStream_t s) {

@@ -101,3 +101,15 @@ def test_p1_mesh_assembly_refuses_bad_input():
         st.p1_mesh_csr(nodes, np.array([[0, 1, 3]]), inter)   # degenerate (collinear) triangle
     with pytest.raises(st.StError):
         st.p1_mesh_csr(nodes, np.array([[0, 1, 7]]), inter)   # index out of range
+
+
+@pytest.mark.parametrize("nx,nt,T", [(6, 9, 1.0), (13, 5, 2.5)])
+def test_wave_matrices_match_the_oracle(nx, nt, T):
+    """st_wave_matrices (host code, no GPU) against the oracle's B-spline Gram matrices."""
+    import paper_1912_10082_gb300 as st
+    from oracle import wave
+    mine = st.wave_matrices(nx, nt, T)
+    ref = wave.wave_matrices(nx, nt, T)
+    for a, b in zip(mine, ref):
+        assert a.shape == b.shape
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
