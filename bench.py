@@ -478,6 +478,47 @@ def mesh_comparator(st, torch, stream, n=34, n_t=500, T=10.0, seed=6):
     return out
 
 
+def wave_comparator(st, torch, sizes=(255, 511), tol=1e-7):
+    """The paper's second workload (Section 5, Example 2): the wave equation u_tt - u_xx = f on (0,1) x (0,1) with
+    cubic B-splines in space and time, f = (2 + 4 pi^2 t^2) sin(2 pi x) (exact solution t^2 sin(2 pi x)), solved
+    by GMRES+LYAP (st_wave_solve) to the residual tol (the paper does not state Example 2's tolerance; 1e-7 gives
+    its iteration count at N_h = N_t = 256).  The load is the B-spline moments of the two separable terms, by
+    scipy's B-splines and 4-point Gauss-Legendre (input preparation).  One warm-up and one timed solve a size."""
+    import numpy as np
+    from scipy.interpolate import BSpline
+
+    def moments(nint, f, kept):
+        t = np.concatenate([np.zeros(3), np.linspace(0.0, 1.0, nint + 1), np.ones(3)])
+        g, w = np.polynomial.legendre.leggauss(4)
+        e = np.linspace(0.0, 1.0, nint + 1)
+        a, b_ = e[:-1], e[1:]
+        x = (0.5 * (b_ - a)[:, None] * g + 0.5 * (a + b_)[:, None]).ravel()
+        wx = (0.5 * (b_ - a)[:, None] * w).ravel()
+        return (BSpline.design_matrix(x, t, 3).T @ (wx * f(x)))[kept]
+
+    out = {}
+    for n in sizes:
+        fx = moments(n, lambda x: np.sin(2 * np.pi * x), np.arange(1, n + 2))
+        F1 = np.asfortranarray(np.stack([fx, fx], axis=1))
+        F2 = np.asfortranarray(np.stack([moments(n, lambda t: 2.0 + 0.0 * t, np.arange(0, n + 1)),
+                                         moments(n, lambda t: 4.0 * np.pi ** 2 * t ** 2, np.arange(0, n + 1))],
+                                        axis=1))
+        ms = []
+        for it in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            U, stats, status = st.wave_solve(n, n, 1.0, F1, F2, tol=tol, maxit=400, ok=(st.ST_OK, st.ST_ENOTCONV))
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t0))
+        nh = n + 1
+        out[f"{nh}x{nh}"] = {"value": nh * nh / (ms[-1] * 1e-3), "unit": "DoF/s", "ms": ms[-1],
+                             "host_setup_ms": stats["ms_phase"][0], "iterations": stats["iterations"],
+                             "relres": stats["relres"], "status": int(status), "tol": tol}
+        print(f"[bench] wave GMRES+LYAP {nh}x{nh}: {ms[-1]:.1f} ms, its {stats['iterations']}", file=sys.stderr,
+              flush=True)
+    return out
+
+
 def bench_batched(args, wl, rank, world, local):
     """Batched workload: 256 2D heat instances of mixed sizes solved at once by st_solve_batch (lock-step RKSM,
     every device step one grouped launch over the instances still iterating)."""
@@ -595,6 +636,7 @@ def bench_batched(args, wl, rank, world, local):
     if not args.no_singles:
         comps["single_problems"] = single_comparators(st, torch, ("heat2d_gauss", "heat3d"), stream)
         comps["general_mesh_p1_3d"] = mesh_comparator(st, torch, stream)
+        comps["wave_gmres_lyap"] = wave_comparator(st, torch)
     apply = {}
     flush = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     flush_out = torch.empty(1, dtype=torch.float32, device="cuda")
