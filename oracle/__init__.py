@@ -10,7 +10,8 @@ arXiv:1912.10082) that it restates.
 
 Modules
 -------
-fem       spatial P1 / Q1 mass, stiffness and convection matrices (Section 3, "X_h")
+fem       spatial P1 / Q1 mass, stiffness and convection matrices (Section 3, "X_h"), and P1 on
+          simplex meshes (general meshes, Section 5 Example 1's kind)
 timefe    time matrices D_t, C_t of hat trial / indicator test functions (Section 3)
 kron      Kronecker assembly B = D_t (x) M + C_t (x) A, its vec identity and exact
           direct solves (Section 3 eqs. par1/par2; Section 4 eq. Kroneckersum)
@@ -20,6 +21,9 @@ residual  relative residual norms of dense and low-rank iterates (Section 4)
 rksm      rational Krylov Galerkin projection (RKSM) reference (Section 4)
 lrfgmres  low-rank flexible GMRES preconditioned by RKSM, the comparison solver
           of Section 5, Example 1 (Table 1)
+wave      the wave equation's space-time system with cubic B-splines, its direct
+          solve and GMRES+LYAP (Section 3 "The Wave Equation", Section 4
+          eq. 3terms, Section 5 Example 2)
 
 Pins (tests marked ``not gpu``): closed-form 1D generalised eigenpairs, Gauss
 quadrature of every matrix entry from the basis functions, an exact rational
@@ -27,7 +31,10 @@ solve of a tiny system, Crank-Nicolson equivalence, the manufactured closed form
 second-order convergence, and the Galerkin invariants of the RKSM reference;
 for LR-FGMRES+RKSM the Eckart-Young truncation error, GMRES's minimal residual
 over the explicit Krylov space, one step with an exact preconditioner and the
-direct solution.
+direct solution; for the simplex P1 matrices the domain measure, constants, linear
+exactness and the difference-stencil closed form; for the wave equation the textbook
+cubic B-spline stencils, SPD, the preconditioner inverse and second-order convergence
+to Example 2's solution.
 Parity unpinned: the RKSM iteration counts and shift sequence (the paper only
 says the shifts are chosen adaptively); the converged solution is pinned.
 """
