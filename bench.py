@@ -7,7 +7,9 @@ rational Krylov Galerkin method (paper Section 4) for every problem, in lock ste
 every device step one grouped launch over the problems still iterating.  One step
 = one solve of the whole batch with the load factors resident in HBM.  Compared on
 the same GPU with the FP64 batch, batched Crank-Nicolson, the thread-per-slot
-executor, and single heat2d_gauss / heat3d solves.  Prints one JSON line (rank 0).
+executor, single heat2d_gauss / heat3d solves (with LR-FGMRES+RKSM on heat2d_gauss),
+an Example-1-shaped problem on a general P1 mesh (RKSM and LR-FGMRES+RKSM through the
+CSR path) and the wave equation of Example 2 (GMRES+LYAP).  Prints one JSON line (rank 0).
 
 Other workloads: ``--workload heat2d|heat2d_gauss|heat3d|heat3d_small`` (one
 st_solve per step), ``served`` (a Poisson request stream through the executor).
