@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "st_common.cuh"
@@ -159,7 +160,12 @@ extern "C" int st_wave_solve(int n_x, int n_t, double T, const double* F1, int l
     for (int j = 0; j < nt; ++j)
         for (int i = 0; i < nt; ++i) St[(size_t)j * nt + i] = Dt[(size_t)j * nt + i] + Dt[(size_t)i * nt + j];
     std::vector<double> Sh, lh, Se, lt;
-    if (!pencil_eig(nh, Qh, Mh, Sh, lh) || !pencil_eig(nt, Qt, Mt, Se, lt)) {
+    // the two pencils on two host threads (each a dense symmetric eigenproblem)
+    bool ok_t = false;
+    std::thread tt([&] { ok_t = pencil_eig(nt, Qt, Mt, Se, lt); });
+    const bool ok_h = pencil_eig(nh, Qh, Mh, Sh, lh);
+    tt.join();
+    if (!ok_h || !ok_t) {
         st_note_msg("st_wave_solve: a mass matrix is not positive definite");
         return ST_EBREAKDOWN;
     }
