@@ -229,8 +229,9 @@ void fd_steps(const st_problem* p, FdKind kind, double shift, double coef, const
             t.ep = ep;
             // the single-problem launch's tile choice (so a problem's result does not depend on the path)
             t.tc = sizeof(T) == 4 && fold_tc_default(t.n, t.other, batch) ? 1 : 0;
-            // FP32 SIMT: the 64 x 64 vector-read tile where both output extents fill it
-            t.tm = sizeof(T) == 4 && std::min(M, N) >= 64 ? 4 : 2;
+            // FP32 SIMT: the 64 x 64 vector-read tile for every problem (small problems leave part of a tile
+            // idle, but one launch serves the whole step: the tile shape does not change a result)
+            t.tm = sizeof(T) == 4 ? 4 : 2;
             const int ex = t.tc ? FTC_N : 16 * t.tm, ey = t.tc ? FTC_M : 16 * t.tm;
             t.gx = (N + ex - 1) / ex;
             t.gy = (M + ey - 1) / ey;
