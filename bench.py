@@ -389,7 +389,9 @@ def single_comparators(st, torch, names, stream):
 def apply_measure(st, torch, prob, stream, flush_l2, pk, launches=20):
     """The fused space-time apply Y = (D (x) M + C (x) A) U (st_apply) on a dense N_h x N_t U, FP32 and FP64, L2
     flushed before each launch.  Algorithmic bytes: U read once and Y written once (the box stencil reads no
-    matrix)."""
+    matrix).  A short device sleep after the flush keeps the stream busy while the host enqueues the start event
+    and the apply, so the events bracket the kernel and not the host's call into the library (tens of
+    microseconds through the binding, the size of the 2D launch itself)."""
     import statistics
     out = {}
     for dtype_, tag in ((torch.float32, "apply32"), (torch.float64, "apply64")):
@@ -402,6 +404,7 @@ def apply_measure(st, torch, prob, stream, flush_l2, pk, launches=20):
             evs = []
             for _ in range(launches):
                 flush_l2()
+                torch.cuda._sleep(200000)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)

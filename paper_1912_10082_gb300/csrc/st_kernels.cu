@@ -192,101 +192,113 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && DIM == 2) ? 3 : 1) k_a
     }
 }
 
-// FP32 variant: a lane loads only its own x of the (YB+2)(ZB+2) rows and takes
-// the x - 1 and x + 1 values from its neighbours by warp shuffles, so a warp
-// of 32 lanes yields 30 outputs per row from one coalesced load per row (the
-// two edge lanes only supply halo values).  The STEPS + 1 columns a thread
-// walks are unrolled, the next column's loads issued PD columns ahead.  The
-// sums run in the same order as k_apply_box (dz, dy, dx lexicographic).
-template <typename T, int DIM, int YB, int ZB, int STEPS, int PD>
-__global__ void __launch_bounds__(256, DIM == 2 ? 3 : 1) k_apply_box_sh(int nx, int ny, int nz, int n_t,
-                                                                          BoxStencil<T> S, const T* __restrict__ U,
-                                                                          long long ldu, T* __restrict__ Y,
-                                                                          long long ldy) {
-    constexpr int RY = YB + 2, RZ = DIM == 3 ? ZB + 2 : 1;
-    constexpr int NV = RY * RZ;
-    const int nxs = (nx + 29) / 30, nyb = (ny + 8 * YB - 1) / (8 * YB);
-    int b = blockIdx.x;
-    const int xs = b % nxs;
-    b /= nxs;
-    const int yb = b % nyb;
-    const int zb = b / nyb;
+// FP32 apply on a 2D box grid, two time columns a pass.  A lane holds U[x, c]
+// and U[x, c + 1] of each of its YB + 2 rows as one f32x2 pair, so every term
+// of the P and N stencils is one packed FMA for both columns; the sums run term
+// for term in the order of k_apply_box (dy, dx lexicographic), so the results
+// equal a column-at-a-time FP32 kernel's bit for bit.  x - 1 and x + 1 come
+// from the neighbouring lanes by warp shuffles: a warp of 32 lanes yields 30
+// outputs a row from one coalesced load a row and column (the two edge lanes
+// only supply halo values).  A thread owns YB rows and walks NP pairs
+// (c, c + 1), starting at c = l0 - 1 whose P u is not needed: Y_c = P u_c -
+// N u_{c-1} with N u_{c-1} carried from the previous pair, and Y_{c+1} = P
+// u_{c+1} - N u_c from the same pass.  Threads whose rows and columns are all in
+// range load without predicates (only the CTAs at the grid's edges and the
+// first and last time chunks take the checked loads).  Y is written with
+// evict-first stores: nothing here reads it again.
+template <int YB, int NP>
+__global__ void __launch_bounds__(256, 2) k_apply_box_tp(int nx, int ny, int n_t, BoxStencil<float> S,
+                                                         const float* __restrict__ U, long long ldu,
+                                                         float* __restrict__ Y, long long ldy) {
+    constexpr int RY = YB + 2;
+    constexpr int STEPS = 2 * NP - 1;   // output columns a CTA
+    const int nxs = (nx + 29) / 30;
+    const int xs = blockIdx.x % nxs;
+    const int yb = blockIdx.x / nxs;
     const int lane = threadIdx.x;
     const int x = xs * 30 + lane - 1;
     const int y0 = (yb * 8 + threadIdx.y) * YB;
-    const int z0 = zb * ZB;
-    if (y0 >= ny || (DIM == 3 && z0 >= nz)) return;   // uniform over the warp: the shuffles see all lanes
+    if (y0 >= ny) return;   // uniform over the warp: the shuffles see all lanes
     const bool okx = x >= 0 && x < nx;
     const bool emit = lane >= 1 && lane <= 30 && x < nx;
-    const long long nxy = (long long)nx * ny;
-    bool ok[NV];
+    bool ok[RY];
 #pragma unroll
-    for (int iz = 0; iz < RZ; ++iz)
-#pragma unroll
-        for (int iy = 0; iy < RY; ++iy)
-            ok[iz * RY + iy] = okx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny &&
-                               (DIM < 3 || (z0 + iz - 1 >= 0 && z0 + iz - 1 < nz));
-    const long long base = ((long long)(DIM == 3 ? z0 : 0) * ny + y0) * nx + x;
+    for (int iy = 0; iy < RY; ++iy) ok[iy] = okx && y0 + iy - 1 >= 0 && y0 + iy - 1 < ny;
+    const long long base = (long long)y0 * nx + x;
     const int l0 = blockIdx.y * STEPS;
-    auto load = [&](int c, T* v) {
+    const bool inner = l0 >= 1 && l0 + STEPS <= n_t && okx && y0 >= 1 && y0 + YB < ny;
+    float2 P2[9], N2[9];   // the 2D stencil: entries 9..17 of the 27-point tables (dz = 0)
 #pragma unroll
-        for (int iz = 0; iz < RZ; ++iz)
+    for (int e = 0; e < 9; ++e) {
+        P2[e] = make_float2(S.p[9 + e], S.p[9 + e]);
+        N2[e] = make_float2(S.q[9 + e], S.q[9 + e]);
+    }
+    const float* ub = U + base - nx;   // row y0 - 1
+    // rows y0 - 1 .. y0 + YB of columns c0 and c0 + 1
+    auto load = [&](int c0, float2* v) {
+        const float* u0 = ub + (long long)c0 * ldu;
+        const float* u1 = u0 + ldu;
+        if (inner) {
 #pragma unroll
             for (int iy = 0; iy < RY; ++iy) {
-                const long long off = (long long)(DIM == 3 ? iz - 1 : 0) * nxy + (long long)(iy - 1) * nx;
-                v[iz * RY + iy] =
-                    (c >= 0 && c < n_t && ok[iz * RY + iy]) ? __ldg(U + (long long)c * ldu + base + off) : T(0);
+                v[iy].x = __ldg(u0 + iy * nx);
+                v[iy].y = __ldg(u1 + iy * nx);
             }
+        } else {
+            const bool k0 = c0 >= 0 && c0 < n_t, k1 = c0 + 1 >= 0 && c0 + 1 < n_t;
+#pragma unroll
+            for (int iy = 0; iy < RY; ++iy) {
+                v[iy].x = (k0 && ok[iy]) ? __ldg(u0 + iy * nx) : 0.f;
+                v[iy].y = (k1 && ok[iy]) ? __ldg(u1 + iy * nx) : 0.f;
+            }
+        }
     };
-    T buf[PD + 1][NV];
-    T pn[YB * ZB];
+    float2 buf[2][RY];
+    float pn[YB];   // N u_{c0 - 1}
 #pragma unroll
-    for (int j = 0; j < PD; ++j) load(l0 - 1 + j, buf[j]);
+    for (int o = 0; o < YB; ++o) pn[o] = 0.f;
+    load(l0 - 1, buf[0]);
 #pragma unroll
-    for (int j = 0; j <= STEPS; ++j) {
-        const int c = l0 - 1 + j;   // column c; j = 0 is the previous chunk's last (N u_{l0-1} only)
-        if (j + PD <= STEPS) load(l0 - 1 + j + PD, buf[(j + PD) % (PD + 1)]);
-        if (c >= n_t) break;
-        const T* v = buf[j % (PD + 1)];
-        T tP[YB * ZB], tN[YB * ZB];
+    for (int j = 0; j < NP; ++j) {
+        const int c0 = l0 - 1 + 2 * j, c1 = c0 + 1;
+        if (j + 1 < NP) load(c0 + 2, buf[(j + 1) % 2]);   // the next pair's loads in flight
+        if (c0 >= n_t) break;
+        const float2* v = buf[j % 2];
+        float2 tP[YB], tN[YB];
 #pragma unroll
-        for (int o = 0; o < YB * ZB; ++o) tP[o] = tN[o] = T(0);
+        for (int o = 0; o < YB; ++o) tP[o] = tN[o] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int iz = 0; iz < RZ; ++iz)
+        for (int iy = 0; iy < RY; ++iy) {
+            const float2 w0 = v[iy];
+            float2 wm, wp;
+            wm.x = __shfl_up_sync(0xffffffffu, w0.x, 1);
+            wm.y = __shfl_up_sync(0xffffffffu, w0.y, 1);
+            wp.x = __shfl_down_sync(0xffffffffu, w0.x, 1);
+            wp.y = __shfl_down_sync(0xffffffffu, w0.y, 1);
 #pragma unroll
-            for (int iy = 0; iy < RY; ++iy) {
-                const T w0 = v[iz * RY + iy];
-                const T wm = __shfl_up_sync(0xffffffffu, w0, 1);
-                const T wp = __shfl_down_sync(0xffffffffu, w0, 1);
-#pragma unroll
-                for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
-#pragma unroll
-                    for (int oy = 0; oy < YB; ++oy) {
-                        const int dz = DIM == 3 ? iz - 1 - oz : 0, dy = iy - 1 - oy;
-                        if (dz < -1 || dz > 1 || dy < -1 || dy > 1) continue;
-                        const int e = (dz + 1) * 9 + (dy + 1) * 3;
-                        const int o = oz * YB + oy;
-                        tP[o] += S.p[e] * wm;
-                        tN[o] += S.q[e] * wm;
-                        tP[o] += S.p[e + 1] * w0;
-                        tN[o] += S.q[e + 1] * w0;
-                        tP[o] += S.p[e + 2] * wp;
-                        tN[o] += S.q[e + 2] * wp;
-                    }
+            for (int oy = 0; oy < YB; ++oy) {
+                const int dy = iy - 1 - oy;
+                if (dy < -1 || dy > 1) continue;
+                const int e = (dy + 1) * 3;
+                tP[oy] = __ffma2_rn(P2[e], wm, tP[oy]);
+                tN[oy] = __ffma2_rn(N2[e], wm, tN[oy]);
+                tP[oy] = __ffma2_rn(P2[e + 1], w0, tP[oy]);
+                tN[oy] = __ffma2_rn(N2[e + 1], w0, tN[oy]);
+                tP[oy] = __ffma2_rn(P2[e + 2], wp, tP[oy]);
+                tN[oy] = __ffma2_rn(N2[e + 2], wp, tN[oy]);
             }
-        if (j >= 1 && c >= 0 && emit) {
+        }
+        if (emit) {
+            float* yc = Y + (long long)c0 * ldy + base;
 #pragma unroll
-            for (int oz = 0; oz < (DIM == 3 ? ZB : 1); ++oz)
-#pragma unroll
-                for (int oy = 0; oy < YB; ++oy) {
-                    if (y0 + oy >= ny || (DIM == 3 && z0 + oz >= nz)) continue;
-                    const int o = oz * YB + oy;
-                    Y[(size_t)c * ldy + base + (long long)(DIM == 3 ? oz : 0) * nxy + (long long)oy * nx] =
-                        tP[o] - pn[o];
-                }
+            for (int oy = 0; oy < YB; ++oy) {
+                if (y0 + oy >= ny) continue;
+                if (c0 >= l0) __stcs(yc + oy * nx, tP[oy].x - pn[oy]);
+                if (c1 >= l0 && c1 < n_t) __stcs(yc + ldy + oy * nx, tP[oy].y - tN[oy].x);
+            }
         }
 #pragma unroll
-        for (int o = 0; o < YB * ZB; ++o) pn[o] = c >= 0 ? tN[o] : T(0);
+        for (int o = 0; o < YB; ++o) pn[o] = tN[o].y;
     }
 }
 
@@ -1490,23 +1502,28 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
             S.p[e] = (T)(sizeof(T) == 8 ? p->box_p64[e] : p->box_p32[e]);
             S.q[e] = (T)(sizeof(T) == 8 ? p->box_q64[e] : p->box_q32[e]);
         }
-        // blocks of 32 x-points (30 outputs for the shuffle kernel) by 8 thread rows; each thread
-        // YB (x ZB) points and `steps` columns.  FP32: shuffle kernel, 2D 4 rows x 8 columns,
-        // 3D 4 x 2 points x 8 columns.  FP64 (FP64-ALU-bound): 2D 4 rows x 8, 3D 2 x 2 x 16.
-        const bool sh = sizeof(T) == 4;
-        const int YB = p->dim == 2 ? 4 : (sh ? 4 : 2), ZB = p->dim == 2 ? 1 : 2;
-        const int xw = sh ? 30 : 32;
-        long long blocks = (long long)((nx + xw - 1) / xw) * ((ny + 8 * YB - 1) / (8 * YB)) *
+        // blocks of 32 x-points by 8 thread rows; each thread YB (x ZB) points and `steps`
+        // columns.  FP32: the time-pair kernel in 2D and the sum-factorised kernel in 3D (their
+        // own blockings below).  FP64 (FP64-ALU-bound): 2D 4 rows x 8, 3D 2 x 2 x 16.
+        const int YB = p->dim == 2 ? 4 : 2, ZB = p->dim == 2 ? 1 : 2;   // FP64 blockings
+        long long blocks = (long long)((nx + 31) / 32) * ((ny + 8 * YB - 1) / (8 * YB)) *
                            (p->dim == 3 ? (nz + ZB - 1) / ZB : 1);
-        const int steps = (p->dim == 2 || sh) ? 8 : 16;
+        const int steps = p->dim == 2 ? 8 : 16;
         dim3 grid((unsigned)blocks, (unsigned)((n_t + steps - 1) / steps));
-        if (blocks > 0x7fffffffLL || grid.y > 65535) return ST_EINVAL;
+        if (sizeof(T) == 8 && (blocks > 0x7fffffffLL || grid.y > 65535)) return ST_EINVAL;
         double ts = (double)sizeof(T);
         st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32", ts * 2.0 * (double)p->n_h * n_t,
                       4.0 * (double)p->max_row_nnz * p->n_h * n_t);
         if constexpr (sizeof(T) == 4) {
             if (p->dim == 2) {
-                k_apply_box_sh<T, 2, 4, 1, 8, 1><<<grid, dim3(32, 8), 0, s>>>(nx, ny, nz, n_t, S, U, ldu, Y, ldy);
+                // 30 x-points by 8 x 4 rows a CTA; 15 time columns (8 pairs, the first starting one
+                // column early for N u_{l0-1})
+                constexpr int YB2 = 4, NP2 = 8, ST2 = 2 * NP2 - 1;
+                const long long b2 = (long long)((nx + 29) / 30) * ((ny + 8 * YB2 - 1) / (8 * YB2));
+                const dim3 g2((unsigned)b2, (unsigned)((n_t + ST2 - 1) / ST2));
+                if (b2 > 0x7fffffffLL || g2.y > 65535) return ST_EINVAL;
+                k_apply_box_tp<YB2, NP2><<<g2, dim3(32, 8), 0, s>>>(nx, ny, n_t, S, (const float*)U, ldu,
+                                                                   (float*)Y, ldy);
             } else {
                 // sum-factorised: 30 x-points, 8 x 4 rows in y, 6 planes in z a CTA; 16 time columns
                 // (the fastest of the blockings measured on 63^3 x 128 and 127^3 x 512)

@@ -82,7 +82,11 @@ def test_setup_csr_matches_oracle(dim, n, kw):
 
 @pytest.mark.parametrize("dim,n,nt,pad", [(1, 13, 5, 0), (2, 7, 33, 3), (2, 33, 100, 0), (3, 6, 17, 1), (1, 1, 1, 0),
                                          # several CTA tiles a direction, ragged edges, n_t not a multiple of 8
-                                         (3, (65, 37, 19), 45, 5), (2, (300, 70), 77, 0), (3, (97, 9, 8), 9, 0)])
+                                         (3, (65, 37, 19), 45, 5), (2, (300, 70), 77, 0), (3, (97, 9, 8), 9, 0),
+                                         # 2D FP32 time pairs: interior CTAs in y and time (unchecked loads),
+                                         # full and ragged 15-column chunks, a single column
+                                         (2, (200, 130), 46, 2), (2, 64, 15, 0), (2, (61, 97), 31, 1),
+                                         (2, 40, 1, 0)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_apply_matches_kronecker_form(dim, n, nt, pad, dtype):
     M, A = ops(dim, n, kappa=1.3)
@@ -94,6 +98,32 @@ def test_apply_matches_kronecker_form(dim, n, nt, pad, dtype):
         Ud.copy_(torch.from_numpy(U).to(dtype))
         Yd = prob.apply(Ud)
         out = host(Yd)
+    tol = 1e-14 if dtype == torch.float64 else 2e-6
+    assert relerr(out, ref) <= tol
+
+
+@pytest.mark.parametrize("dim,n,nt,kw", [
+    (2, (70, 45), 33, {"op": "convdiff", "eps": 0.05, "beta": (1.0, 0.5)}),
+    (3, (40, 21, 13), 20, {"op": "convdiff", "eps": 0.2, "beta": (1.0, 0.5, 0.25)}),
+    (2, (66, 80), 17, {"length": (1.0, 2.5)}),
+    (3, (35, 12, 9), 16, {"length": (1.0, 0.5, 2.0)}),
+])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_apply_convdiff_and_box_lengths_match_kronecker_form(dim, n, nt, kw, dtype):
+    """The box kernels on non-symmetric (convection) and anisotropic (unequal box sides) 1D factors: the 2D
+    stencil from the assembled rows, the 3D FP32 sum factorisation from the 1D factors."""
+    if kw.get("op") == "convdiff":
+        M, A = fem.tensor_operators(dim, n, op="convdiff", eps=kw["eps"], beta=kw["beta"])
+        prob = st.Problem(dim, n, nt, 0.9, op=st.ST_CONVDIFF, eps=kw["eps"], beta=kw["beta"])
+    else:
+        M, A = fem.tensor_operators(dim, n, kappa=0.8, length=kw["length"])
+        prob = st.Problem(dim, n, nt, 0.9, kappa=0.8, length=kw["length"])
+    D, C = timefe.time_matrices(nt, 0.9)
+    U = np.random.default_rng(3).standard_normal((M.shape[0], nt))
+    ref = kron.apply(M, A, D, C, U)
+    with prob:
+        Ud = torch.from_numpy(U).to(dtype).cuda().t().contiguous().t()
+        out = host(prob.apply(Ud))
     tol = 1e-14 if dtype == torch.float64 else 2e-6
     assert relerr(out, ref) <= tol
 
