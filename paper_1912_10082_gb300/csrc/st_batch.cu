@@ -38,27 +38,35 @@ using namespace rksm;
 namespace {
 
 // ---- batch staging: one download region and one upload region for all instances ----
+// The device buffer is stream-ordered and the pinned mirror comes from the library's pool, so growing or
+// releasing them never waits for the other solves on the device.
 struct BStage {
     double* d = nullptr;   // device: [down cap | up cap]
     double* h = nullptr;   // pinned mirror
-    size_t cap = 0, down = 0, up = 0;
+    size_t cap = 0, down = 0, up = 0, hbytes = 0;
+    cudaStream_t s_ = nullptr;
     ~BStage() {
-        if (d) cudaFree(d);
-        if (h) cudaFreeHost(h);
+        if (s_) cudaStreamSynchronize(s_);   // the last copies have landed
+        if (d) cudaFreeAsync(d, s_);
+        st_pinned_put(h, hbytes);
     }
     // room for need doubles in each region; the stream is idle between phases
     int reserve(size_t need, cudaStream_t s) {
         down = up = 0;
         if (need <= cap) return ST_OK;
         ST_CUDA_TRY(cudaStreamSynchronize(s));
-        if (d) cudaFree(d);
-        if (h) cudaFreeHost(h);
+        if (d) cudaFreeAsync(d, s);
+        st_pinned_put(h, hbytes);
         d = nullptr;
         h = nullptr;
-        cap = 0;
+        cap = hbytes = 0;
+        s_ = s;
         const size_t c = std::max<size_t>(need + need / 2, 1 << 14);
-        cudaError_t e = cudaMalloc((void**)&d, sizeof(double) * 2 * c);
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&h, sizeof(double) * 2 * c);
+        cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * 2 * c, s);
+        if (e == cudaSuccess) {
+            h = (double*)st_pinned_get(sizeof(double) * 2 * c, &hbytes);
+            if (!h) e = cudaErrorMemoryAllocation;
+        }
         if (e != cudaSuccess) {
             cudaGetLastError();
             st_note_cuda(e, "batch staging", __FILE__, __LINE__);

@@ -32,6 +32,14 @@
 void st_note_cuda(cudaError_t e, const char* what, const char* file, int line);
 void st_note_msg(const char* msg);   // sets the text returned by st_last_error
 
+// Pinned host buffers taken from and returned to a process-wide pool (st_setup.cu).  Allocating or freeing
+// pinned memory, like a synchronous device allocation or free, waits for the whole device, so a solve that
+// grew or released its staging this way would stall every other solve running on the GPU.  st_pinned_get
+// returns at least `bytes` (the size in *got) or nullptr; st_pinned_put takes a buffer back once no copy
+// in flight uses it.  Pooled buffers stay allocated for the life of the process.
+void* st_pinned_get(size_t bytes, size_t* got);
+void st_pinned_put(void* ptr, size_t bytes);
+
 // launch accounting and optional event timing (st_profile.cu)
 void st_count_launch();
 void st_count_launches(unsigned long long n);
@@ -141,6 +149,7 @@ struct st_problem {
     double* sm_dev = nullptr;
     double* sm_host = nullptr;
     size_t sm_cap = 0;
+    size_t sm_host_bytes = 0;   // size of the pooled pinned buffer behind sm_host
 };
 
 // Returns a device buffer of at least `bytes` for slot `id` (contents not kept on growth).

@@ -65,6 +65,7 @@ constexpr int TS_THREADS = 256;
 constexpr int TS_CG = 16;      // basis columns per CTA of H = V^T W
 constexpr int TS_CG_DF = 32;   // the same for the double-float product (half the restaging of W per basis column)
 constexpr int TS_UNROLL = 8;   // independent loads in flight per lane
+constexpr int TS_PIPE = 4;     // rows a lane per block of the software-pipelined double-float products
 
 // Rows of one chunk of H = V^T W: enough chunks that chunks x column groups
 // fill the GPU about four CTAs deep (a few basis columns need many short
@@ -573,16 +574,29 @@ __device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int r
         for (int c = 0; c < CPW; ++c)
 #pragma unroll
             for (int q = 0; q < MP; ++q) SH[c][q] = SL[c][q] = make_float2(0.f, 0.f);
-        for (int base = lane; base < nr; base += 32 * TS_UNROLL) {
-            float2 xv[CPW][TS_UNROLL];
+        // double-float: software-pipelined, the next block's V loads issued before this block's
+        // multiply-adds, so they stay in flight through the dependent double-float chains; FP32 (short
+        // chains): eight rows a lane loaded, then used.  The rows are taken in the same order either way.
+        constexpr bool PIPE = !HI;
+        constexpr int U = PIPE ? TS_PIPE : TS_UNROLL;
+        float2 xv[CPW][U];
+        auto load_block = [&](float2 (&x)[CPW][U], int b0) {
 #pragma unroll
-            for (int u = 0; u < TS_UNROLL; ++u) {
-                const int rr = base + 32 * u;
+            for (int u = 0; u < U; ++u) {
+                const int rr = b0 + 32 * u;
 #pragma unroll
-                for (int c = 0; c < CPW; ++c) xv[c][u] = rr < nr && c < na ? v[c][rr] : make_float2(0.f, 0.f);
+                for (int c = 0; c < CPW; ++c) x[c][u] = rr < nr && c < na ? v[c][rr] : make_float2(0.f, 0.f);
             }
+        };
+        if constexpr (PIPE) load_block(xv, lane);
+        for (int base = lane; base < nr; base += 32 * U) {
+            float2 xn[CPW][U];
+            if constexpr (PIPE)
+                load_block(xn, base + 32 * U);
+            else
+                load_block(xv, base);
 #pragma unroll
-            for (int u = 0; u < TS_UNROLL; ++u) {
+            for (int u = 0; u < U; ++u) {
                 int rr = min(base + 32 * u, rows - 1);
 #pragma unroll
                 for (int q = 0; q < MP; ++q) {
@@ -596,6 +610,12 @@ __device__ __forceinline__ void ts_tn_df_partial_body(int n, int k, int m, int r
                             df_madd2(SH[c][q], SL[c][q], xv[c][u], b);
                     }
                 }
+            }
+            if constexpr (PIPE) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int c = 0; c < CPW; ++c) xv[c][u] = xn[c][u];
             }
         }
 #pragma unroll
@@ -666,18 +686,27 @@ __device__ __forceinline__ void ts_nn_df_body(int n, int k, int m, double alpha,
             float2 SH[MP], SL[MP];
 #pragma unroll
             for (int q = 0; q < MP; ++q) SH[q] = SL[q] = make_float2(0.f, 0.f);
-            for (int a = 0; a < kt; a += TS_UNROLL) {
-                float2 x[TS_UNROLL];
+            // software-pipelined like the product above: the next block's loads before this block's FMAs
+            constexpr int U = TS_PIPE;
+            float2 x[U];
+            auto load_block = [&](float2 (&xb)[U], int b0) {
 #pragma unroll
-                for (int u = 0; u < TS_UNROLL; ++u)
-                    x[u] = a + u < kt ? V[(size_t)(a0 + a + u) * ldv + r] : make_float2(0.f, 0.f);
+                for (int u = 0; u < U; ++u)
+                    xb[u] = b0 + u < kt ? V[(size_t)(a0 + b0 + u) * ldv + r] : make_float2(0.f, 0.f);
+            };
+            load_block(x, 0);
+            for (int a = 0; a < kt; a += U) {
+                float2 xn[U];
+                load_block(xn, a + U);
 #pragma unroll
-                for (int u = 0; u < TS_UNROLL; ++u) {
+                for (int u = 0; u < U; ++u) {
                     if (a + u >= kt) break;
 #pragma unroll
                     for (int q = 0; q < MP; ++q)
                         if (q < np) df_madd2(SH[q], SL[q], x[u], Hs[(a + u) * MP + q]);
                 }
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[u] = xn[u];
             }
 #pragma unroll
             for (int q = 0; q < MP; ++q) {

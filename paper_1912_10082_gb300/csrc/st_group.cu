@@ -247,29 +247,34 @@ void with_maxm(int m, F&& f) {
 namespace stg {
 
 GroupArena::~GroupArena() {
-    if (h) cudaFreeHost(h);
-    if (d) cudaFree(d);
+    if (s_) cudaStreamSynchronize(s_);   // the last task-table copies have landed
+    if (d) cudaFreeAsync(d, s_);
+    st_pinned_put(h, hbytes);
 }
 
+// Growth takes a stream-ordered device buffer and a pinned buffer from the library's pool, so it never waits
+// for the work of other streams (a synchronous allocation or free would).
 int GroupArena::reserve(size_t bytes, cudaStream_t s) {
     if (used + bytes <= cap) return ST_OK;
     ST_CUDA_TRY(cudaStreamSynchronize(s));   // earlier copies and launches may still read h and d
     used = 0;
     if (bytes <= cap) return ST_OK;
-    if (h) cudaFreeHost(h);
-    if (d) cudaFree(d);
+    if (d) cudaFreeAsync(d, s);
+    st_pinned_put(h, hbytes);
     h = nullptr;
     d = nullptr;
-    cap = 0;
+    cap = hbytes = 0;
+    s_ = s;
     const size_t want = std::max<size_t>(4 * bytes, 1 << 20);
-    cudaError_t e = cudaMallocHost((void**)&h, want);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d, want);
+    h = (char*)st_pinned_get(want, &hbytes);
+    cudaError_t e = h ? cudaMallocAsync((void**)&d, want, s) : cudaErrorMemoryAllocation;
     if (e != cudaSuccess) {
         cudaGetLastError();
         st_note_cuda(e, "grouped task tables", __FILE__, __LINE__);
-        if (h) cudaFreeHost(h);
+        st_pinned_put(h, hbytes);
         h = nullptr;
         d = nullptr;
+        hbytes = 0;
         return ST_ENOMEM;
     }
     cap = want;

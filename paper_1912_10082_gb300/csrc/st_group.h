@@ -116,9 +116,10 @@ struct ElemTask {
 // (right after a synchronisation), so a table is never overwritten while a
 // copy or a launch may still read it.
 struct GroupArena {
-    char* h = nullptr;
-    char* d = nullptr;
-    size_t cap = 0, used = 0;
+    char* h = nullptr;   // pinned, from the library's pool
+    char* d = nullptr;   // stream-ordered
+    size_t cap = 0, used = 0, hbytes = 0;
+    cudaStream_t s_ = nullptr;
     ~GroupArena();
     // Room for `bytes` more; when the buffers must grow, synchronises s first
     // (everything earlier has then run, so the new buffers start empty).

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <climits>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -55,6 +56,39 @@ static void keep_pool_memory() {
     }
     cudaGetLastError();
     done[dev] = true;
+}
+
+namespace {
+std::mutex g_pin_mu;
+std::multimap<size_t, void*> g_pin_free;   // pooled pinned buffers by size (powers of two from 64 KiB)
+}  // namespace
+
+void* st_pinned_get(size_t bytes, size_t* got) {
+    size_t c = (size_t)64 << 10;
+    while (c < bytes) c <<= 1;
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        auto it = g_pin_free.lower_bound(c);
+        if (it != g_pin_free.end() && it->first <= 4 * c) {   // a pooled buffer at most 4x the class
+            void* ptr = it->second;
+            *got = it->first;
+            g_pin_free.erase(it);
+            return ptr;
+        }
+    }
+    void* ptr = nullptr;
+    if (cudaMallocHost(&ptr, c) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *got = c;
+    return ptr;
+}
+
+void st_pinned_put(void* ptr, size_t bytes) {
+    if (!ptr) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.emplace(bytes, ptr);
 }
 
 int st_alloc(st_problem* p, void** ptr, size_t bytes) {
@@ -438,9 +472,9 @@ static int setup_user_csr(st_problem* p, const st_desc& d) {
 extern "C" int st_destroy(st_problem* p) {
     if (!p) return ST_OK;
     if (p->cn_graph) cudaGraphExecDestroy((cudaGraphExec_t)p->cn_graph);
-    if (p->sm_host) cudaFreeHost(p->sm_host);
     for (void* ptr : p->owned) cudaFreeAsync(ptr, p->stream);
     cudaStreamSynchronize(p->stream);
+    st_pinned_put(p->sm_host, p->sm_host_bytes);   // no copy in flight uses it now
     cudaGetLastError();
     p->owned.clear();
     delete p;

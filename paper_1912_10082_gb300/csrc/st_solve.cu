@@ -420,17 +420,17 @@ int stage_reserve(st_problem* p, size_t need) {
     if (p->sm_cap >= need) return ST_OK;
     size_t cap = std::max<size_t>({need, 2 * p->sm_cap, (size_t)8192});
     if (p->sm_dev || p->sm_host) ST_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    if (p->sm_dev) st_free_one(p, p->sm_dev);
-    if (p->sm_host) cudaFreeHost(p->sm_host);
+    if (p->sm_dev) st_free_one(p, p->sm_dev);   // stream-ordered
+    st_pinned_put(p->sm_host, p->sm_host_bytes);   // the stream is idle: no copy uses it
     p->sm_dev = nullptr;
     p->sm_host = nullptr;
     p->sm_cap = 0;
+    p->sm_host_bytes = 0;
     ST_TRY(st_alloc(p, (void**)&p->sm_dev, sizeof(double) * 2 * cap));
-    cudaError_t e = cudaMallocHost((void**)&p->sm_host, sizeof(double) * 2 * cap);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        st_note_cuda(e, "cudaMallocHost", __FILE__, __LINE__);
-        p->sm_host = nullptr;
+    p->sm_host = (double*)st_pinned_get(sizeof(double) * 2 * cap, &p->sm_host_bytes);
+    if (!p->sm_host) {
+        st_note_msg("pinned host staging: allocation failed");
+        p->sm_host_bytes = 0;
         return ST_ENOMEM;
     }
     p->sm_cap = cap;

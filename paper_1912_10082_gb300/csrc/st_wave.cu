@@ -324,7 +324,7 @@ extern "C" int st_wave_solve(int n_x, int n_t, double T, const double* F1, int l
     for (void* ptr : host.owned) cudaFreeAsync(ptr, s);   // the workspace slots of the tall-skinny products
     host.owned.clear();
     cudaStreamSynchronize(s);
-    if (host.sm_host) cudaFreeHost(host.sm_host);
+    st_pinned_put(host.sm_host, host.sm_host_bytes);   // after the stream synchronisation above
     host.sm_host = nullptr;
     cudaGetLastError();
     if (stats) stats->ms_total = ms_since(t0);
