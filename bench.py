@@ -593,6 +593,15 @@ def bench_batched(args, wl, rank, world, local):
     wall1 = 1e3 * (time.perf_counter() - t0)
     torch.cuda.nvtx.range_pop()
     prof = st.profile_end()
+    if args.stop_after_profile:
+        # profiler captures of the pass's launches end here: no comparator runs under the profiler
+        if rank == 0:
+            print(json.dumps({"profile_pass_only": True, "wall_ms": wall1,
+                              "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items()}}),
+                  flush=True)
+        for p in mixed:
+            p.close()
+        return 0
     roof = roofline_of(prof, pk["hbm_gbs"])
     if roof:
         roof["peak_source"] = pk["src"] if roof["unit"] == "GB/s" else "derived"
@@ -773,6 +782,8 @@ def main():
                     help="time the shifted solves' launch variants before the warm-up and keep the fastest (auto: on "
                          "for the batched and served workloads, off for single problems, which keep the launch "
                          "variants the ncu traffic figures were captured on)")
+    ap.add_argument("--stop-after-profile", action="store_true",
+                    help="batched workload: end after the one-group profile pass (profiler captures of its launches)")
     ap.add_argument("--slots", type=int, default=16, help="executor slots of the batched and served workloads")
     ap.add_argument("--requests", type=int, default=0, help="served workload: number of requests (0: all)")
     ap.add_argument("--gap-scale", type=float, default=1.0, help="served workload: scale of the mean arrival gap")
