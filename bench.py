@@ -386,12 +386,13 @@ def single_comparators(st, torch, names, stream):
     return out
 
 
-def apply_measure(st, torch, prob, stream, flush_l2, pk, launches=20):
+def apply_measure(st, torch, prob, stream, flush_l2, pk, launches=20, csr_nnz=None):
     """The fused space-time apply Y = (D (x) M + C (x) A) U (st_apply) on a dense N_h x N_t U, FP32 and FP64, L2
     flushed before each launch.  Algorithmic bytes: U read once and Y written once (the box stencil reads no
     matrix).  A short device sleep after the flush keeps the stream busy while the host enqueues the start event
     and the apply, so the events bracket the kernel and not the host's call into the library (tens of
-    microseconds through the binding, the size of the 2D launch itself)."""
+    microseconds through the binding, the size of the 2D launch itself).  A CSR problem (csr_nnz given) adds its matrix
+    read once: column indices, P and N values and the row pointers."""
     import statistics
     out = {}
     for dtype_, tag in ((torch.float32, "apply32"), (torch.float64, "apply64")):
@@ -414,6 +415,8 @@ def apply_measure(st, torch, prob, stream, flush_l2, pk, launches=20):
         torch.cuda.synchronize()
         ms_a = statistics.mean(a.elapsed_time(b) for a, b in evs)
         byts = 2.0 * Ua.element_size() * prob.n_h * prob.n_t
+        if csr_nnz is not None:
+            byts += csr_nnz * (4.0 + 2.0 * Ua.element_size()) + 4.0 * (prob.n_h + 1)
         out[tag] = {"ms_per_launch": ms_a, "bytes_per_launch": byts, "achieved_gbs": byts / (ms_a * 1e-3) / 1e9,
                     "frac_of_hbm": byts / (ms_a * 1e-3) / 1e9 / pk["hbm_gbs"],
                     "dof_per_s": prob.n_h * prob.n_t / (ms_a * 1e-3)}
@@ -457,6 +460,12 @@ def mesh_comparator(st, torch, stream, n=34, n_t=500, T=10.0, seed=6):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
         relres_cert = prob.residual_lowrank(V, Y, f1, f2)
+        # the CSR space-time apply (SpMM over the dense N_h x N_t block) on the same mesh
+        flush = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        flush_out = torch.empty(1, dtype=torch.float32, device="cuda")
+        spmm = apply_measure(st, torch, prob, stream, lambda: torch.sum(flush, dim=0, out=flush_out[0]), peaks(),
+                             csr_nnz=len(col))
+        del flush
         # Table 1's comparison solver on the same problem (one timed solve)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -471,7 +480,7 @@ def mesh_comparator(st, torch, stream, n=34, n_t=500, T=10.0, seed=6):
               "relres_certified": prob.residual_lowrank(Vl, Yl, f1, f2), "converged": ls["converged"],
               "paper_same_shape": {"dof_per_s": 1.53e5, "outer_iterations": 4, "mu_mem": 75}}
         out = {"value": nh * n_t / (ms[-1] * 1e-3), "ms": ms[-1], "first_solve_ms": ms[0], "n_h": nh, "n_t": n_t,
-               "lrfgmres_rksm_fp64": lr,
+               "lrfgmres_rksm_fp64": lr, "apply_csr": spmm,
                "iterations": stats["iterations"], "mu_mem": stats["mu_mem"], "rank": stats["rank"],
                "relres": stats["relres"], "relres_certified": relres_cert, "status": int(status),
                "how": "P1 on a jittered Kuhn mesh of (-1,1)^3, Example 1's rank-1 load, FP64, CSR path",

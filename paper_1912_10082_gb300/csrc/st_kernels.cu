@@ -19,8 +19,8 @@ namespace {
 // warp own consecutive rows, so the gathers U[col, l] of a warp are
 // coalesced.  t_N of step l is carried to step l+1.
 // ---------------------------------------------------------------------------
-template <typename T, int MAXNNZ>
-__global__ void __launch_bounds__(128) k_apply_reg(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
+template <typename T, int MAXNNZ, int MINB = 1>
+__global__ void __launch_bounds__(128, MINB) k_apply_reg(int n_h, int n_t, int chunk, const int* __restrict__ row_ptr,
                                                    const int* __restrict__ col, const T* __restrict__ pv,
                                                    const T* __restrict__ nv, const T* __restrict__ U, long long ldu,
                                                    T* __restrict__ Y, long long ldy) {
@@ -1556,10 +1556,16 @@ int st_apply_kernel(st_problem* p, const T* U, int ldu, T* Y, int ldy, int n_t, 
     st_prof_begin(s, sizeof(T) == 8 ? "apply64" : "apply32",
                   ts * 2.0 * (double)p->n_h * n_t + (double)p->nnz * (4.0 + 2.0 * ts) + 4.0 * (p->n_h + 1),
                   4.0 * (double)p->nnz * n_t);
+    // register buckets of the row length: 3 (1D), 9 (2D P1/Q1), 16 (3D P1 on Kuhn-type meshes: 15), 27 (3D Q1);
+    // a padded entry still costs a gather and two FMAs, and the 27-wide FP32 thread held 248 registers
     if (p->max_row_nnz <= 3)
         k_apply_reg<T, 3><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
     else if (p->max_row_nnz <= 9)
-        k_apply_reg<T, 9><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
+        k_apply_reg<T, 9, sizeof(T) == 4 ? 4 : 1><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv,
+                                                                        U, ldu, Y, ldy);
+    else if (p->max_row_nnz <= 16)
+        k_apply_reg<T, 16, sizeof(T) == 4 ? 4 : 1><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv,
+                                                                         nv, U, ldu, Y, ldy);
     else if (p->max_row_nnz <= 27)
         k_apply_reg<T, 27><<<grid, 128, 0, s>>>(p->n_h, n_t, chunk, p->row_ptr, p->col, pv, nv, U, ldu, Y, ldy);
     else
