@@ -132,7 +132,12 @@ typedef struct st_stats {
  * ST_ENOMEM, ST_ECUDA.  *out is NULL on error. */
 int st_setup(const st_desc* d, st_problem** out);
 
-/* st_destroy -- free the handle and everything it owns.  NULL is accepted. */
+/* st_destroy -- free the handle and everything it owns.  NULL is accepted.
+ * The handle's pinned host staging goes back to a library-wide pool for the
+ * next handle or batch instead of being freed: freeing pinned memory (like a
+ * synchronous device free) waits for the whole device, which would stall the
+ * solves of other handles.  The pool keeps its buffers for the life of the
+ * process (at most the largest staging in use at once, per size class). */
 int st_destroy(st_problem* p);
 
 /* st_problem_info -- sizes of a problem (host outputs, any may be NULL). */

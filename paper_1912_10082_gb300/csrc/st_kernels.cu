@@ -1632,6 +1632,8 @@ int st_spmm_ma(st_problem* p, const T* X, int ldx, int ncols, T* OM, int ldm, T*
         k_spmm_ma_reg<T, 3><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
     else if (p->max_row_nnz <= 9)
         k_spmm_ma_reg<T, 9><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
+    else if (p->max_row_nnz <= 16)   // 3D P1 rows (15 entries on Kuhn-type meshes)
+        k_spmm_ma_reg<T, 16><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
     else if (p->max_row_nnz <= 27)
         k_spmm_ma_reg<T, 27><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, mv, av, X, ldx, OM, ldm, OA, lda);
     else
@@ -1666,6 +1668,9 @@ int st_spmm_at64(st_problem* p, const double* X, int ldx, int ncols, double* Out
     else if (p->max_row_nnz <= 9)
         k_spmm_ma_reg<double, 9><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
                                                          Out, ldo, nullptr, 0);
+    else if (p->max_row_nnz <= 16)
+        k_spmm_ma_reg<double, 16><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
+                                                          Out, ldo, nullptr, 0);
     else if (p->max_row_nnz <= 27)
         k_spmm_ma_reg<double, 27><<<blocks, 128, 0, s>>>(p->n_h, ncols, p->row_ptr, p->col, p->at64, p->at64, X, ldx,
                                                           Out, ldo, nullptr, 0);
