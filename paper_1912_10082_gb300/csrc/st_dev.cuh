@@ -224,14 +224,17 @@ __device__ __forceinline__ void gemm_fold_body(int n, int other, const T* __rest
 // in shared memory with the rows (columns) a thread owns -- ty, ty + 16, ty + 32, ty + 48 -- next to each
 // other, so one 16-byte read feeds four outputs (two reads for sixteen FMAs, where the scalar 4 x 4 tile
 // issues eight).  Every output is the same FMA chain over the folded index in the same order as in
-// gemm_fold_body, so the two tiles give the same bits.
+// gemm_fold_body, so the two tiles give the same bits.  The folded index is staged 32 deep: eight entries
+// of each operand a thread in registers between the loads and the shared stores, which leaves room for
+// four CTAs an SM in the grouped kernel (64 deep held 128 registers and two CTAs; the load phases of a
+// tile are then hidden by the other CTAs' FMAs).
 template <int SIDE>
 __device__ __forceinline__ void fold32_v4_body(int n, int other, const float* __restrict__ X, long long ldx,
                                                const float* __restrict__ H0, const float* __restrict__ H1,
                                                const float* __restrict__ G0, const float* __restrict__ G1,
                                                float* __restrict__ C, long long ldc, Batch2 bt, FdEpi ep, int bx,
                                                int by, int bz) {
-    constexpr int BM = 64, BN = 64, BK = 64, LD = 68;   // row stride: 16-byte aligned, staging stores 4-way at most
+    constexpr int BM = 64, BN = 64, BK = 32, LD = 68;   // row stride: 16-byte aligned, staging stores 4-way at most
     __shared__ __align__(16) float As[BK][LD];
     __shared__ __align__(16) float Bs[BK][LD];
     const int par = bz & 1;

@@ -36,8 +36,10 @@ __device__ __forceinline__ void g_load(Task& dst, const Task* src, int tid, int 
     for (int w = tid; w < (int)(sizeof(Task) / 4); w += nthr) d[w] = __ldg(s + w);
 }
 
+// FP32 64 x 64 tiles: four CTAs an SM (64 registers; the x-direction tile spills a few words, still faster
+// than three CTAs without spills)
 template <typename T, int TM, int SIDE>
-__global__ void __launch_bounds__(256, TM == 4 ? 2 : 3) kg_fold(const stg::FoldTask* tasks, const int* prefix,
+__global__ void __launch_bounds__(256, TM == 4 && sizeof(T) == 4 ? 4 : 3) kg_fold(const stg::FoldTask* tasks, const int* prefix,
                                                                int ntasks) {
     __shared__ stg::FoldTask tk;
     const int total = prefix[ntasks];
